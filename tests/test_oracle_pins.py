@@ -1,0 +1,463 @@
+"""Pins of the CPU oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: an
+independent Philox implementation (Triton's, run in its CPU interpreter),
+scipy's Poisson distribution, exact rational arithmetic, a brute-force scan
+of every cell, exact 3-D geometry, and brute-force recounts of its own per-hit
+dumps.  The paper prints no worked example (its validation compares CPU and
+GPU runs on the same random numbers, Sec. 6), so these are the pins.
+"""
+import math
+import os
+import subprocess
+import sys
+from fractions import Fraction
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import oracle as O
+from paper_2103_14737_gb300 import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# ---------------------------------------------------------------------------
+# Philox4x32-10 (random draws, Sec. 4: three per hit)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", [0, 1, 20210326, 0xDEADBEEFCAFEBABE])
+def test_philox_matches_triton_interpreter(tmp_path, seed):
+    pytest.importorskip("triton")
+    pytest.importorskip("torch")
+    rng = np.random.default_rng(seed & 0xFFFF)
+    ctr = rng.integers(0, 2**32, size=(256, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    cf, of = tmp_path / "c.npy", tmp_path / "o.npy"
+    np.save(cf, ctr)
+    subprocess.run([sys.executable, os.path.join(HERE, "triton_philox_ref.py"), str(cf), str(seed), str(of)],
+                   check=True, timeout=600)
+    ref = np.load(of)
+    assert np.array_equal(O.philox(ctr, seed), ref)
+
+
+def test_philox_statistics():
+    n = 1 << 15
+    ctr = np.zeros((n, 4), dtype=np.uint32)
+    ctr[:, 0] = np.arange(n)
+    ctr[:, 1] = 5
+    ctr[:, 2] = 17
+    ctr[:, 3] = 3
+    x = O.philox(ctr, 1)
+    for w in range(4):
+        hist = np.bincount((x[:, w] >> 24).astype(np.int64), minlength=256)
+        assert stats.chisquare(hist).pvalue > 1e-4
+        bits = ((x[:, w][:, None] >> np.arange(32, dtype=np.uint32)) & 1).mean(0)
+        assert np.all(np.abs(bits - 0.5) < 5 * 0.5 / math.sqrt(n))
+    # consecutive counters uncorrelated
+    u = (x[:, 0] >> 8).astype(np.float64) / 2**24
+    assert abs(np.corrcoef(u[:-1], u[1:])[0, 1]) < 5 / math.sqrt(n)
+    # avalanche: flipping one counter bit flips about half the output bits
+    ctr2 = ctr.copy()
+    ctr2[:, 2] ^= 1 << 7
+    y = O.philox(ctr2, 1)
+    flips = np.unpackbits((x ^ y).view(np.uint8)).mean()
+    assert abs(flips - 0.5) < 0.01
+
+
+# ---------------------------------------------------------------------------
+# Poisson hit count (Listing 1: get_number_of_hits)
+# ---------------------------------------------------------------------------
+def _pmf_chi2(draws, mu):
+    kmax = int(draws.max())
+    obs = np.bincount(draws, minlength=kmax + 1).astype(np.float64)
+    exp = stats.poisson.pmf(np.arange(kmax + 1), mu) * len(draws)
+    exp[-1] += stats.poisson.sf(kmax, mu) * len(draws)
+    # pool bins with small expectations
+    o, e, acc_o, acc_e = [], [], 0.0, 0.0
+    for oi, ei in zip(obs, exp):
+        acc_o += oi
+        acc_e += ei
+        if acc_e >= 20:
+            o.append(acc_o)
+            e.append(acc_e)
+            acc_o = acc_e = 0.0
+    o[-1] += acc_o
+    e[-1] += acc_e
+    e = np.array(e) * (sum(o) / sum(e))
+    return stats.chisquare(o, e).pvalue
+
+
+@pytest.mark.parametrize("mu,n", [(0.5, 60000), (3.0, 60000), (9.9, 60000), (10.0, 1000000),
+                                  (12.5, 1000000), (40.0, 1000000), (250.0, 200000)])
+def test_poisson_pmf(mu, n):
+    d = O.poisson(np.full(n, mu), 11, layer=3, particle=np.arange(n), event=7)
+    assert _pmf_chi2(d, mu) > 1e-4
+
+
+@pytest.mark.parametrize("mu,n", [(10.0, 1000000), (100.0, 200000), (5000.0, 40000), (14000.0, 40000)])
+def test_poisson_moments(mu, n):
+    d = O.poisson(np.full(n, mu), 5, layer=np.arange(n) % 24, particle=np.arange(n) // 24, event=1).astype(np.float64)
+    assert abs(d.mean() - mu) < 5 * math.sqrt(mu / n)
+    assert abs(d.var() - mu) < 5 * mu * math.sqrt(2.0 / n) + 5 * math.sqrt(mu / n)
+
+
+def test_poisson_inversion_matches_scipy_ppf():
+    """For mu < 10 the count is the inverse CDF of the first 53-bit uniform."""
+    n = 20000
+    rng = np.random.default_rng(3)
+    mu = rng.uniform(0.01, 9.99, size=n)
+    part = np.arange(n, dtype=np.uint32)
+    d = O.poisson(mu, 99, layer=2, particle=part, event=4)
+    ctr = np.stack([np.zeros(n, np.uint32), np.full(n, 2 | (1 << 16), np.uint32), part, np.full(n, 4, np.uint32)], 1)
+    x = O.philox(ctr, 99).astype(np.uint64)
+    u = ((x[:, 0] >> 5) * 2**26 + (x[:, 1] >> 6)).astype(np.float64) / 2.0**53
+    ref = stats.poisson.ppf(u, mu).astype(np.int64)
+    # ppf: smallest k with CDF(k) >= u; the sampler: smallest k with u < F_k.
+    # They differ only when u sits on a CDF step to rounding precision.
+    mism = np.nonzero(ref != d)[0]
+    for i in mism:
+        assert abs(stats.poisson.cdf(d[i], mu[i]) - u[i]) < 1e-12 or abs(stats.poisson.cdf(ref[i], mu[i]) - u[i]) < 1e-12
+    assert len(mism) <= 2
+
+
+def test_poisson_zero_mu():
+    assert O.poisson(np.array([0.0, -1.0]), 1, 0, 0, 0).tolist() == [0, 0]
+
+
+# ---------------------------------------------------------------------------
+# Parametrisation selection (Sec. 1: by type, energy and location)
+# ---------------------------------------------------------------------------
+def _expected_entry(prm, t, E, eta):
+    NT, NE, NH, NL = prm.frac.shape
+    m, ex = math.frexp(float(np.float32(E)))
+    eb = min(max((ex - 1) - prm.ebin_log2_min, 0), NE - 1)
+    hb = min(math.floor(Fraction(float(abs(np.float32(eta)))) * Fraction(prm.eta_bin_scale)), NH - 1)
+    return (t * NE + eb) * NH + hb
+
+
+def test_param_entry_bins(prm, oprm):
+    cases = []
+    for k in range(0, 30):
+        for E in (2.0**k, np.nextafter(np.float32(2.0**k), np.float32(0)), 1.5 * 2.0**k):
+            cases.append((k % 3, float(E), 0.3))
+    for hb in range(0, 101):
+        for eta in (hb / 20.0, -hb / 20.0, np.nextafter(np.float32(hb / 20.0), np.float32(10)),
+                    np.nextafter(np.float32(hb / 20.0), np.float32(-10))):
+            cases.append((1, 5000.0, float(eta)))
+    cases += [(2, 1e6, 7.5), (0, 1e30, -50.0), (1, 1e-3, 0.0)]
+    for t, E, eta in cases:
+        assert O.param_entry(oprm, t, E, eta) == _expected_entry(prm, t, E, eta), (t, E, eta)
+    # the paper's benchmark electron: 65.536 GeV = 2^16 MeV, eta 0.22
+    assert O.param_entry(oprm, 0, 65536.0, 0.22) == (0 * 17 + 10) * 100 + 4
+
+
+# ---------------------------------------------------------------------------
+# Shape histogram inverse CDF (three random numbers per hit, Sec. 4)
+# ---------------------------------------------------------------------------
+def _exact_thresholds(w):
+    w = [Fraction(float(v)) for v in np.asarray(w, np.float32)]
+    C = sum(w)
+    K = max(i for i, v in enumerate(w) if v > 0)
+    T, c = [], Fraction(0)
+    for k, v in enumerate(w):
+        c += v
+        T.append(min(2**32 - 1, math.floor(2**32 * c / C)) if k < K else 2**32 - 1)
+    return np.array(T, dtype=np.uint64), K
+
+
+def _sample_bins(T, K, x0):
+    # independent formulation: first k < K with x0 < T[k], else K
+    k = np.searchsorted(T[:K].astype(np.uint64), x0.astype(np.uint64), side="right")
+    return np.minimum(k, K)
+
+
+def test_thresholds_exact_and_chi2(prm):
+    rng = np.random.default_rng(5)
+    w_all = prm.shape_w.reshape(-1, 128)
+    n = 1 << 17
+    ctr = np.zeros((n, 4), np.uint32)
+    ctr[:, 0] = np.arange(n)
+    x0 = O.philox(ctr, 77)[:, 0]
+    for e in rng.integers(0, len(w_all), size=6):
+        w = w_all[e]
+        T, K = O.thresholds(w)
+        Tx, Kx = _exact_thresholds(w)
+        assert K == Kx
+        diff = T.astype(np.int64) - Tx.astype(np.int64)
+        assert np.all(np.abs(diff) <= 1) and np.count_nonzero(diff) <= 2
+        bins = _sample_bins(T, K, x0)
+        for i in range(0, n, 4099):
+            assert O.sample_bin(T, K, int(x0[i])) == bins[i]
+        obs = np.bincount(bins, minlength=128)
+        p = w.astype(np.float64) / w.astype(np.float64).sum()
+        exp = p * n
+        keep = exp >= 5
+        o = np.append(obs[keep], obs[~keep].sum())
+        ex = np.append(exp[keep], exp[~keep].sum())
+        if ex[-1] == 0:
+            o, ex = o[:-1], ex[:-1]
+        assert stats.chisquare(o, ex * o.sum() / ex.sum()).pvalue > 1e-4
+
+
+def test_thresholds_edges_zero_bins_single_bin():
+    w = np.zeros(128, np.float32)
+    w[[3, 4, 50, 90]] = [1.0, 0.0, 2.5, 0.25]
+    T, K = O.thresholds(w)
+    assert K == 90
+    for k in range(K):
+        if T[k] > 0:
+            assert O.sample_bin(T, K, int(T[k]) - 1) <= k
+        assert O.sample_bin(T, K, int(T[k])) > k or T[k] == 0xFFFFFFFF
+    chosen = set()
+    for x in list(range(0, 2**32, 2**20)) + [0, 2**32 - 1] + [int(t) for t in T] + [max(int(t) - 1, 0) for t in T]:
+        chosen.add(O.sample_bin(T, K, x))
+    assert chosen == {3, 50, 90}
+    one = np.zeros(128, np.float32)
+    one[77] = 3.0
+    T1, K1 = O.thresholds(one)
+    assert K1 == 77
+    for x in (0, 1, 2**31, 2**32 - 1):
+        assert O.sample_bin(T1, K1, x) == 77
+    assert O.thresholds(np.zeros(128, np.float32))[1] == -1
+
+
+# ---------------------------------------------------------------------------
+# Cell lookup (Listing 2: getDDE) against a brute-force scan of every cell
+# ---------------------------------------------------------------------------
+def _cell_boxes(geo, layer):
+    rb, re = geo.layer_region_begin[layer], geo.layer_region_begin[layer + 1]
+    out = []
+    for r in range(rb, re):
+        R = geo.regions[r]
+        ie, ip = np.meshgrid(np.arange(R["n_eta"]), np.arange(R["n_phi"]), indexing="ij")
+        cid = R["cell_offset"] + ie * R["n_phi"] + ip
+        out.append(dict(region=r, cid=cid.ravel(), ie=ie.ravel(), ip=ip.ravel(),
+                        elo=R["eta_lo"] + ie.ravel() * R["deta"], ehi=R["eta_lo"] + (ie.ravel() + 1) * R["deta"],
+                        plo=R["phi_lo"] + ip.ravel() * R["dphi"], phi_hi=R["phi_lo"] + (ip.ravel() + 1) * R["dphi"],
+                        n_eta=R["n_eta"], rlo=R["eta_lo"], rhi=R["eta_lo"] + R["n_eta"] * R["deta"]))
+    return out
+
+
+def _brute_candidates(boxes, eta, phi, tol=1e-9):
+    """Cells that may own (eta, phi): nearest region(s) by eta distance, then
+    every cell of it whose [eta) x [phi) box (eta clamped into the region,
+    phi taken mod 2 pi) contains the point within tol."""
+    d = np.array([max(b["rlo"] - eta, eta - b["rhi"], 0.0) for b in boxes])
+    dmin = d.min()
+    cand = set()
+    for i, b in enumerate(boxes):
+        if d[i] > dmin + tol:
+            continue
+        e = min(max(eta, b["rlo"]), b["rhi"])
+        p = b["plo"][0] + ((phi - b["plo"][0]) % (2 * math.pi))
+        m_e = (b["elo"] - tol <= e) & (e <= b["ehi"] + tol)
+        m_p = ((b["plo"] - tol <= p) & (p <= b["phi_hi"] + tol)) | (p >= b["plo"][0] + 2 * math.pi - tol) & (b["ip"] == 0) \
+            | (p <= b["plo"][0] + tol) & (b["ip"] == b["ip"].max())
+        cand.update(b["cid"][m_e & m_p].tolist())
+    return cand
+
+
+def test_cell_lookup_bruteforce(geo, ogeo):
+    rng = np.random.default_rng(11)
+    n_unique = n_total = 0
+    for layer in range(geo.n_layers):
+        boxes = _cell_boxes(geo, layer)
+        pts = list(zip(rng.uniform(-5.5, 5.5, 60), rng.uniform(-3 * math.pi, 3 * math.pi, 60)))
+        # edges of random cells, +-1 ulp, and region boundaries / gaps
+        for b in boxes:
+            for j in rng.integers(0, len(b["cid"]), 3):
+                for ev in (b["elo"][j], b["ehi"][j]):
+                    for pv in (b["plo"][j], b["phi_hi"][j]):
+                        for de in (-1, 0, 1):
+                            for dp in (-1, 1):
+                                e = ev if de == 0 else np.nextafter(ev, ev + de)
+                                pts.append((e, np.nextafter(pv, pv + dp)))
+            pts.append((b["rlo"] - 0.01, 0.3))
+            pts.append((b["rhi"] + 0.01, -0.3))
+        eta = np.array([p[0] for p in pts])
+        phi = np.array([p[1] for p in pts])
+        got = O.cells(ogeo, layer, eta, phi)
+        for i in range(len(pts)):
+            c = _brute_candidates(boxes, eta[i], phi[i])
+            assert int(got[i]) in c, (layer, eta[i], phi[i], got[i], c)
+            n_total += 1
+            n_unique += len(c) == 1
+    assert n_unique > 0.2 * n_total
+
+
+def test_cell_centres_round_trip(geo, ogeo):
+    """Every cell centre maps back to that cell: the numbering is a bijection."""
+    seen = np.zeros(geo.n_cells, np.int32)
+    for layer in range(geo.n_layers):
+        for b in _cell_boxes(geo, layer):
+            eta = 0.5 * (b["elo"] + b["ehi"])
+            phi = 0.5 * (b["plo"] + b["phi_hi"])
+            got = O.cells(ogeo, layer, eta, phi)
+            assert np.array_equal(got, b["cid"])
+            seen[got] += 1
+    assert np.all(seen == 1)
+
+
+# ---------------------------------------------------------------------------
+# (r, alpha) -> (eta, phi) against exact 3-D geometry (Listing 1: extrapol)
+# ---------------------------------------------------------------------------
+def _exact_3d(layer_rec, eta_c, phi_c, r, a):
+    rz, barrel = float(layer_rec["rz"]), bool(layer_rec["barrel"])
+    if barrel:
+        R = rz
+        z = R * math.sinh(eta_c) + r * math.cos(a)
+        rho = math.hypot(R, r * math.sin(a))
+        return math.asinh(z / rho), phi_c + math.atan2(r * math.sin(a), R)
+    s = 1.0 if eta_c >= 0 else -1.0
+    rho0 = rz / math.sinh(abs(eta_c))
+    x = rho0 + r * math.cos(a)
+    y = r * math.sin(a)
+    return s * math.asinh(rz / math.hypot(x, y)), phi_c + math.atan2(y, x)
+
+
+@pytest.mark.parametrize("eta_c,E", [(0.22, 2.0**20), (-1.1, 2.0**19), (2.0, 2.0**20), (-2.9, 2.0**20), (4.1, 2.0**20)])
+def test_linear_map_matches_3d_geometry(geo, ogeo, oprm, eta_c, E):
+    parts = synth.single_particle(1, ptype=1, E=E, eta=eta_c, phi=0.7)
+    res = O.simulate(ogeo, oprm, parts, seed=3, hit_cap=400000, hit_positions=True)
+    assert res.status == 0 and res.n_hits > 0
+    starts = np.concatenate([[0], np.cumsum(res.task_n)])
+    checked = 0
+    for t in range(res.n_tasks):
+        layer = int(res.task_layer[t])
+        se, sp = O.scales(ogeo, layer, float(np.float32(eta_c)))
+        sl = slice(starts[t], starts[t + 1])
+        r, a = res.hit_r[sl], res.hit_alpha[sl]
+        small = r * max(abs(se), abs(sp)) < 0.02
+        for i in np.nonzero(small)[0][:200]:
+            e3, p3 = _exact_3d(geo.layers[layer], float(np.float32(eta_c)), float(np.float32(0.7)), r[i], a[i])
+            sc = r[i] * max(abs(se), abs(sp))
+            assert abs(res.hit_eta[sl][i] - e3) <= 4 * sc * sc + 1e-12
+            assert abs(res.hit_phi[sl][i] - p3) <= 4 * sc * sc + 1e-12
+            checked += 1
+    assert checked > 50
+
+
+# ---------------------------------------------------------------------------
+# Shape sampling statistics from the hit loop
+# ---------------------------------------------------------------------------
+def test_hit_bins_and_in_bin_uniformity(prm, ogeo, oprm):
+    parts = synth.single_particle(1, ptype=0, E=2.0**21, eta=0.22)
+    res = O.simulate(ogeo, oprm, parts, seed=9, hit_cap=500000, hit_positions=True)
+    assert res.status == 0
+    t = int(np.argmax(res.task_n))
+    starts = np.concatenate([[0], np.cumsum(res.task_n)])
+    sl = slice(starts[t], starts[t + 1])
+    bins = res.hit_bin[sl].astype(np.int64)
+    entry = O.param_entry(oprm, 0, 2.0**21, 0.22) * prm.frac.shape[-1] + int(res.task_layer[t])
+    w = prm.shape_w.reshape(-1, 128)[entry].astype(np.float64)
+    exp = w / w.sum() * len(bins)
+    obs = np.bincount(bins, minlength=128)
+    keep = exp >= 5
+    o = np.append(obs[keep], obs[~keep].sum())
+    e = np.append(exp[keep], exp[~keep].sum())
+    assert stats.chisquare(o, e * o.sum() / e.sum()).pvalue > 1e-4
+    re_, ae_ = prm.r_edges.astype(np.float64), prm.a_edges.astype(np.float64)
+    ir, ia = bins // 8, bins % 8
+    ur = (res.hit_r[sl] - re_[ir]) / (re_[ir + 1] - re_[ir])
+    ua = (res.hit_alpha[sl] - ae_[ia]) / (ae_[ia + 1] - ae_[ia])
+    assert np.all((ur >= 0) & (ur < 1) & (ua >= 0) & (ua < 1))
+    assert stats.kstest(ur, "uniform").pvalue > 1e-4
+    assert stats.kstest(ua, "uniform").pvalue > 1e-4
+    # r and alpha use separate random numbers: jointly uniform in the bin
+    joint = np.histogram2d(ur, ua, bins=4, range=[[0, 1], [0, 1]])[0].ravel()
+    assert stats.chisquare(joint).pvalue > 1e-4
+    assert abs(np.corrcoef(ur, ua)[0, 1]) < 5 / math.sqrt(len(ur))
+
+
+def test_hit_stream_counter_layout(prm, ogeo, oprm):
+    """Hit h of the task (event ev, particle p, layer l) uses Philox block
+    (h, l | 0 << 16, p, ev): word 0 -> shape bin, word 1 -> r, word 2 -> alpha.
+    The Poisson draws use purpose 1 in the second word, a separate stream."""
+    parts = synth.single_particle(2, ptype=2, E=2.0**17, eta=-0.61, phi=2.0)
+    seed, fe = 0x1234567890AB, 40
+    res = O.simulate(ogeo, oprm, parts, seed=seed, first_event=fe, hit_cap=100000, hit_positions=True)
+    NL = prm.frac.shape[-1]
+    base = O.param_entry(oprm, 2, 2.0**17, -0.61)
+    starts = np.concatenate([[0], np.cumsum(res.task_n)])
+    re_, ae_ = prm.r_edges.astype(np.float64), prm.a_edges.astype(np.float64)
+    for t in range(res.n_tasks):
+        l, e, n = int(res.task_layer[t]), int(res.task_event[t]), int(res.task_n[t])
+        T, K = O.thresholds(prm.shape_w.reshape(-1, 128)[base * NL + l])
+        ctr = np.stack([np.arange(n, dtype=np.uint32), np.full(n, l, np.uint32), np.zeros(n, np.uint32),
+                        np.full(n, fe + e, np.uint32)], 1)
+        x = O.philox(ctr, seed)
+        bins = _sample_bins(T, K, x[:, 0])
+        sl = slice(starts[t], starts[t + 1])
+        assert np.array_equal(res.hit_bin[sl], bins)
+        ir, ia = bins // 8, bins % 8
+        r = re_[ir] + (x[:, 1] >> 8).astype(np.float64) / 2**24 * (re_[ir + 1] - re_[ir])
+        a = ae_[ia] + (x[:, 2] >> 8).astype(np.float64) / 2**24 * (ae_[ia + 1] - ae_[ia])
+        assert np.array_equal(res.hit_r[sl], r) and np.array_equal(res.hit_alpha[sl], a)
+
+
+# ---------------------------------------------------------------------------
+# Task assembly (Listing 1: nhit, float Ehit = E(layer) / nhit)
+# ---------------------------------------------------------------------------
+def test_task_assembly(prm, ogeo, oprm):
+    parts = synth.ttbar_like(seed=4)
+    res = O.simulate(ogeo, oprm, parts, seed=21, first_event=5)
+    NL = prm.frac.shape[-1]
+    ev, pa, la, nn, eh = [], [], [], [], []
+    mus = []
+    for p in range(parts.n):
+        base = O.param_entry(oprm, int(parts.type[p]), float(parts.E[p]), float(parts.eta[p]))
+        for l in range(NL):
+            El = np.float32(parts.E[p]) * prm.frac.reshape(-1, NL)[base, l]
+            if not El > 0:
+                continue
+            mu = np.float32(El / prm.mean_hit_E.reshape(-1, NL)[base, l])
+            ev.append(0), pa.append(p), la.append(l), mus.append(float(mu))
+            eh.append(El)
+    n = np.maximum(1, O.poisson(np.array(mus), 21, layer=np.array(la), particle=np.array(pa), event=5))
+    Ehit = (np.array(eh, np.float32) / n.astype(np.float32)).astype(np.float32)
+    assert res.n_tasks == len(la)
+    assert np.array_equal(res.task_layer, la) and np.array_equal(res.task_particle, pa)
+    assert np.array_equal(res.task_n, n)
+    assert np.array_equal(res.task_Ehit.view(np.uint32), Ehit.view(np.uint32))
+    assert res.n_hits == int(n.sum())
+
+
+# ---------------------------------------------------------------------------
+# Conservation, canonical fold, sharding
+# ---------------------------------------------------------------------------
+def test_energy_conservation(ogeo, oprm):
+    parts = synth.pileup(seed=2, n_events=1, mu_pu=10)
+    res = O.simulate(ogeo, oprm, parts, seed=1)
+    hit_sum = float(np.sum(res.task_n.astype(np.float64) * res.task_Ehit.astype(np.float64)))
+    assert abs(res.cells64.sum() - hit_sum) <= 1e-12 * hit_sum
+    assert abs(hit_sum - res.E_layers) <= 1e-6 * res.E_layers
+
+
+def test_canonical_fold_bruteforce(ogeo, oprm):
+    parts = synth.pileup(seed=3, n_events=2, mu_pu=3, hs_particles=40)
+    res = O.simulate(ogeo, oprm, parts, seed=8, hit_cap=10**7)
+    assert res.status == 0
+    task_of_hit = np.repeat(np.arange(res.n_tasks), res.task_n)
+    ev_of_hit = res.task_event[task_of_hit]
+    canon = np.zeros_like(res.cells_canon)
+    c64 = np.zeros_like(res.cells64)
+    key = (ev_of_hit.astype(np.int64) * ogeo.n_cells + res.hit_cell) * res.n_tasks + task_of_hit
+    uk, cnt = np.unique(key, return_counts=True)  # sorted by (event, cell, task)
+    for k, c in zip(uk.tolist(), cnt.tolist()):
+        t = k % res.n_tasks
+        ec = k // res.n_tasks
+        e, cell = divmod(ec, ogeo.n_cells)
+        canon[e, cell] = np.float32(canon[e, cell] + np.float32(np.float32(c) * res.task_Ehit[t]))
+        c64[e, cell] += c * float(res.task_Ehit[t])
+    assert np.array_equal(canon.view(np.uint32), res.cells_canon.view(np.uint32))
+    assert np.allclose(c64, res.cells64, rtol=1e-12, atol=0)
+
+
+def test_event_sharding_invariance(ogeo, oprm):
+    parts = synth.pileup(seed=5, n_events=4, mu_pu=5)
+    full = O.simulate(ogeo, oprm, parts, seed=13, first_event=100)
+    part = O.simulate(ogeo, oprm, parts.events(2, 4), seed=13, first_event=102)
+    assert np.array_equal(full.cells64[2:4], part.cells64)
+    assert np.array_equal(full.cells_canon[2:4].view(np.uint32), part.cells_canon.view(np.uint32))
