@@ -1,0 +1,307 @@
+#!/usr/bin/env python
+"""Benchmark of the calorimeter hit path on GB300.
+
+One step = one fcs_simulate_events call over a batch of 64 pile-up events
+(hard scatter + Poisson(200) minimum-bias collisions of Poisson(60) particles),
+i.e. every step of the hot path: parametrisation lookup and Poisson hit counts,
+task records, the hit kernel (Philox, inverse-CDF shape sampling, (r, alpha)
+-> (eta, phi), cell lookup, warp-aggregated deposit), the FP64 recheck and the
+compaction of non-zero cells.  Inputs are resident in HBM; the call is replayed
+as a CUDA graph; L2 is flushed (256 MB write) between timed steps.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "simulated hits/s at 1 GB300 (batched; events/s and per-event launches alongside)"
+UNIT = "hits/s"
+WORKLOAD = "pileup64"
+N_EVENTS = 64
+SEED = 1
+# Algorithmic 32-bit ALU operations per hit (issue slots of one lane), counted
+# from the algorithm, not from compiled code: Philox4x32-10 40 (10 rounds of
+# two wide multiplies and two 3-input XORs), shape bin 8, uniforms 6,
+# (r, alpha) 6, sincos 3, (eta, phi) 6, region search 6, grid index 14,
+# certification bound 12, task lookup 4, warp-aggregated deposit 5.
+OPS_PER_HIT = 110
+SMS, LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(geo, prm, parts, seconds=10.0):
+    """The oracle as it stands, single threaded, on whole events of the same
+    workload until `seconds` of CPU work."""
+    from oracle import oracle as O
+    og, op = O.OracleGeometry(geo), O.OracleParams(prm)
+    hits, ev, t0 = 0, 0, time.perf_counter()
+    while ev < parts.n_events and time.perf_counter() - t0 < seconds:
+        r = O.simulate(og, op, parts.event(ev), seed=SEED, first_event=ev, tasks=False, canon=False)
+        hits += r.n_hits
+        ev += 1
+    dt = time.perf_counter() - t0
+    return {"value": hits / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{ev} whole events of {WORKLOAD} ({hits} hits, {dt:.1f} s, 1 thread)",
+            "events_per_s": ev / dt}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle, each step one whole pile-up event."""
+    from paper_2103_14737_gb300 import synth
+    from oracle import oracle as O
+    if rank != 0:
+        return
+    geo = synth.geometry()
+    prm = synth.params(geo)
+    parts = synth.workload(WORKLOAD, seed=SEED)
+    og, op = O.OracleGeometry(geo), O.OracleParams(prm)
+    hits = 0
+    times = []
+    for k in range(args.warmup + args.steps):
+        e = k % parts.n_events
+        t0 = time.perf_counter()
+        r = O.simulate(og, op, parts.event(e), seed=SEED, first_event=e, tasks=False, canon=False)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            hits += r.n_hits
+    tot = sum(times)
+    v = hits / tot
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": "one whole event per step, oracle, 1 thread"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} whole events of {WORKLOAD}"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--hpt", type=int, default=0)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--extra", action="store_true", help="also time deterministic mode and per-event launches")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2103_14737_gb300 import fcs, synth
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    geo = synth.geometry()
+    prm = synth.params(geo)
+    # weak scaling: rank r simulates its own 64 events (random-stream events r*64 ...)
+    parts = synth.pileup(seed=SEED + rank, n_events=N_EVENTS)
+    first_event = rank * N_EVENTS
+    sim = fcs.Simulator(geo, prm)
+    d = sim.to_device(parts)
+    # size the workspace and the outputs with one synchronous call
+    ref = sim.simulate(d, SEED, first_event=first_event, hits_per_thread=args.hpt, block=args.block)
+    H = ref["stats"]["n_hits"]
+    outs = {k: ref[k] for k in ("cell_ids", "cell_E", "event_offsets")}
+    outs["cells"] = None
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed(K, W, **kw):
+        for _ in range(W):
+            sim.simulate(d, SEED, first_event=first_event, sync=0, use_graph=1, outputs=outs, timing=1, **kw)
+        torch.cuda.synchronize()
+        t_step, t_hit = [], []
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        for k in range(K):
+            flush.zero_()
+            st[k].record()
+            sim.simulate(d, SEED, first_event=first_event, sync=0, use_graph=1, outputs=outs, timing=1, **kw)
+            en[k].record()
+            t_hit.append(fcs.fcs_workspace_timings(sim.ws))  # waits for this step's stage events
+        torch.cuda.synchronize()
+        t_step = [s.elapsed_time(e) for s, e in zip(st, en)]
+        rc, stt = fcs.fcs_workspace_status(sim.ws)
+        assert rc == 0, (rc, stt.as_dict())
+        return t_step, t_hit
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    wall0 = time.perf_counter()
+    t_step, t_stage = timed(args.steps, args.warmup, hits_per_thread=args.hpt, block=args.block)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = clk.stop()
+    if world > 1:
+        dist.barrier()
+    ms = float(np.mean(t_step))
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = H * world / (ms * 1e-3)
+
+    hit_ms = float(np.mean([s["hits"] for s in t_stage]))
+    stage_ms = {k: float(np.mean([s[k] for s in t_stage])) for k in fcs.STAGES}
+    alu_peak = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12  # Tops/s (lane-ops)
+    achieved = H * OPS_PER_HIT / (hit_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                "frac": achieved / alu_peak, "traffic": None,
+                "kernel": "k_hits", "ops_per_hit": OPS_PER_HIT, "hits_per_launch": H,
+                "kernel_ms": hit_ms, "peak_note": "152 SMs x 128 lanes x 2070 MHz (derived)"}
+
+    extra = {}
+    if args.extra and rank == 0:
+        ts, tst = timed(max(5, args.steps // 2), 2, mode=fcs.MODE_DETERMINISTIC)
+        extra["deterministic"] = {"hits_per_s": H / (np.mean(ts) * 1e-3), "ms_per_step": float(np.mean(ts)),
+                                  "stages_ms": {k: float(np.mean([s[k] for s in tst])) for k in fcs.STAGES}}
+        ts, tst = timed(max(5, args.steps // 2), 2, batched=0)
+        extra["per_event_launches"] = {"hits_per_s": H / (np.mean(ts) * 1e-3), "ms_per_step": float(np.mean(ts)),
+                                       "batched_speedup": float(np.mean(ts)) / ms}
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    e2e = None
+    if rank == 0:
+        pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(parts, k))).pin_memory().numpy()
+               for k in ("type", "E", "eta", "phi", "event_offsets")}
+        cap = outs["cell_ids"].numel()
+        ids = torch.empty(cap, dtype=torch.int32).pin_memory().numpy()
+        cE = torch.empty(cap, dtype=torch.float32).pin_memory().numpy()
+        off = torch.empty(N_EVENTS + 1, dtype=torch.int64).pin_memory().numpy()
+        cfg = fcs.make_config(hits_per_thread=args.hpt, block=args.block)
+        for _ in range(2):
+            fcs.fcs_simulate_events_host(sim.geo, sim.prm, sim.ws, pin["type"], pin["E"], pin["eta"], pin["phi"],
+                                         pin["event_offsets"], SEED, first_event, cfg, ids, cE, off)
+        K = max(3, args.steps // 2)
+        tt = []
+        nnz = 0
+        for _ in range(K):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, st = fcs.fcs_simulate_events_host(sim.geo, sim.prm, sim.ws, pin["type"], pin["E"], pin["eta"],
+                                                  pin["phi"], pin["event_offsets"], SEED, first_event, cfg, ids, cE,
+                                                  off)
+            tt.append(time.perf_counter() - t0)
+            nnz = st.n_nonzero
+        h2d = parts.n * 16 + (N_EVENTS + 1) * 8
+        d2h = nnz * 8 + (N_EVENTS + 1) * 8
+        e2e = {"value": H / float(np.mean(tt)), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * float(np.mean(tt))}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(geo, prm, parts, args.cpu_seconds)
+
+    # kernels of one atomic-mode batched step: call begin/end 2, range begin/end 2,
+    # particle tasks 1, two scans 6, task records 1, tile map 1, hits 1,
+    # recheck 1, compaction 5
+    launches_per_step = 21
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "events_per_step": N_EVENTS, "particles_per_step": parts.n,
+                           "hits_per_step": H, "tasks_per_step": ref["stats"]["n_tasks"],
+                           "nonzero_cells_per_step": ref["stats"]["n_nonzero"],
+                           "recheck_hits_per_step": ref["stats"]["n_recheck"], "mode": "atomic",
+                           "launch": "batched, CUDA graph", "l2": "flushed between steps (256 MB write)",
+                           "parallelism": f"replicas x{world} (events sharded, no collective)"},
+                "events_per_s": N_EVENTS * world / (ms * 1e-3),
+                "stages_ms": stage_ms,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": launches_per_step * args.steps, "wall_s": wall}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

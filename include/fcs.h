@@ -1,0 +1,261 @@
+/*
+ * fcs.h - C ABI of the GB300 (sm_103a) parameterised calorimeter hit path.
+ *
+ * The library simulates the hot loop of FastCaloSim as ported to GPUs in
+ * arXiv:2103.14737: for every particle, calorimeter layer and hit it draws
+ * counter-based random numbers, picks the hit count and hit energy of the
+ * selected parametrisation, samples the hit's (r, alpha) from a 2-D shape
+ * histogram by inverse CDF, maps it to (eta, phi) around the particle's
+ * direction, finds the cell (region search, then grid index) and adds the
+ * hit energy into the cell array (Sec. 4, Listing 1; Sec. 7.3, Listing 2).
+ * Many events run in one launch sequence, the paper's grouped simulation
+ * (GPU_g, Sec. 4, last paragraph) taken to whole batches of events.
+ *
+ * Conventions for every entry point:
+ *   - Return value: FCS_OK (0) or one of the FCS_E_* codes below; the text of
+ *     the last error of the calling thread is available from
+ *     fcs_last_error().  No entry point aborts the process.
+ *   - Pointers documented "host" are read during the call only.  Pointers
+ *     documented "device" must be CUDA device memory of the current device,
+ *     owned by the caller (typically torch tensors); the library never frees
+ *     them and reads or writes them only in work enqueued on the given
+ *     stream.
+ *   - Objects created by fcs_load_* / fcs_workspace_create belong to the
+ *     library; release them with the matching fcs_free_* call after all work
+ *     that uses them has completed.
+ *   - Work is enqueued on the caller's stream `s` (may be 0 for the legacy
+ *     default stream).  Calls with config->sync != 0 wait for that stream
+ *     before returning and report device-side checks in their status; calls
+ *     with sync == 0 return as soon as the work is enqueued and report
+ *     device-side failures through fcs_workspace_status().
+ *   - A workspace must not be used by two calls whose work overlaps on the
+ *     GPU (two streams, or two host threads): it holds the intermediate
+ *     buffers of one call.
+ */
+#ifndef FCS_H
+#define FCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+enum fcs_status_code {
+  FCS_OK = 0,
+  FCS_E_ARG = 1,          /* invalid argument: NULL where required, bad size, bad table value */
+  FCS_E_RANGE = 2,        /* an output or workspace capacity is too small (see each call) */
+  FCS_E_OOM = 3,          /* a device allocation of the library failed */
+  FCS_E_CUDA = 4,         /* a CUDA runtime call failed (message in fcs_last_error) */
+  FCS_E_DEVICE_CHECK = 5, /* a device-side input check failed (bad particle type, NaN, ...) */
+  FCS_E_TIMEOUT = 6,      /* reserved: a bounded device wait gave up */
+  FCS_E_UNSUPPORTED = 7   /* the call or option is not implemented */
+};
+
+/* Device-side check bits reported in fcs_stats.device_flags. */
+enum fcs_device_flag {
+  FCS_FLAG_BAD_PARTICLE = 1u << 0,  /* type out of range, E <= 0 or non-finite, eta/phi non-finite */
+  FCS_FLAG_HIT_CAPACITY = 1u << 1,  /* more hits than the workspace was sized for (sync == 0) */
+  FCS_FLAG_OUT_CAPACITY = 1u << 2,  /* more non-zero cells than `capacity` */
+  FCS_FLAG_KEY_BITS = 1u << 3,      /* deterministic mode: (cell, task) keys need > 64 bits */
+  FCS_FLAG_RECHECK_SPILL = 1u << 4, /* informational: FP64 recheck queue full, done inline */
+  FCS_FLAG_BAD_OFFSETS = 1u << 5    /* event_offsets not within [0, n_particles] or decreasing */
+};
+
+/* ---- geometry (Sec. 4: 187,652 cells, 24 layers, 78 regions, flattened) -- */
+/* One region: a regular eta x phi grid within one layer.  Cell (i_eta, i_phi)
+ * of the region spans [eta_lo + i_eta*deta, eta_lo + (i_eta+1)*deta) x
+ * [phi_lo + i_phi*dphi, ...) and has id cell_offset + i_eta*n_phi + i_phi.
+ * 48 bytes, no padding. */
+typedef struct fcs_region {
+  double eta_lo, deta, phi_lo, dphi;
+  int32_t n_eta, n_phi, cell_offset, layer;
+} fcs_region;
+
+/* One layer: barrel radius or end-cap |z| (mm) and a barrel flag. */
+typedef struct fcs_layer_geom {
+  double rz;
+  int32_t barrel; /* 1 barrel (cylinder at radius rz), 0 end-cap (disk at |z| = rz) */
+  int32_t pad;
+} fcs_layer_geom;
+
+typedef struct fcs_geo fcs_geo;             /* opaque, device-resident geometry */
+typedef struct fcs_params fcs_params;       /* opaque, device-resident parametrisation */
+typedef struct fcs_workspace fcs_workspace; /* opaque, device buffers of one call */
+
+/* Particles of n_events events as device SoA; event e owns the particles
+ * [event_offsets[e], event_offsets[e+1]).  type: 0 electron, 1 photon,
+ * 2 charged pion (any value < NT of the parametrisation). */
+typedef struct fcs_particles {
+  const int32_t* type;          /* device [n_particles] */
+  const float* E;               /* device [n_particles], MeV, > 0 */
+  const float* eta;             /* device [n_particles] */
+  const float* phi;             /* device [n_particles], rad */
+  const int64_t* event_offsets; /* device [n_events + 1], event_offsets[0] = 0 */
+} fcs_particles;
+
+enum fcs_mode {
+  FCS_MODE_ATOMIC = 0,       /* FP32 atomic accumulation, warp-aggregated (Sec. 4: atomicAdd) */
+  FCS_MODE_DETERMINISTIC = 1 /* sort by (cell, task), fixed-order FP32 fold; bit-reproducible */
+};
+
+typedef struct fcs_config {
+  int32_t mode;            /* enum fcs_mode */
+  int32_t batched;         /* 1: one launch sequence for all events; 0: one sequence per event */
+  int32_t hits_per_thread; /* hit kernel: hits per thread per tile, 1..8; 0 = tuned default */
+  int32_t block;           /* hit kernel: threads per block, 128..1024 (multiple of 32); 0 = default */
+  int32_t sync;            /* != 0: wait for the stream, read the device status (see above) */
+  int32_t use_graph;       /* != 0 (requires sync == 0): capture the launch sequence as a CUDA
+                              graph keyed by every argument, replay it on identical calls */
+  int32_t timing;          /* != 0: record CUDA events around each stage (fcs_workspace_timings) */
+  int32_t reserved;        /* must be 0 */
+} fcs_config;
+
+/* Filled by fcs_simulate_events when non-NULL and config->sync != 0. */
+typedef struct fcs_stats {
+  int64_t n_tasks;    /* (event, particle, layer) tasks with E_layer > 0 */
+  int64_t n_hits;     /* total hits */
+  int64_t n_nonzero;  /* non-zero cells over all events (the compacted output size) */
+  int64_t n_recheck;  /* hits whose cell the FP32 path could not certify, decided in FP64 */
+  uint32_t device_flags; /* enum fcs_device_flag bits */
+  uint32_t pad;
+} fcs_stats;
+
+/* Optional per-task / per-hit dumps for validation (device pointers; NULL
+ * entries are skipped).  Tasks are in (event, particle, layer) order, hits in
+ * (task, hit index) order.  Entries beyond the capacities are not written. */
+typedef struct fcs_debug {
+  int64_t task_capacity;
+  int32_t* task_event;    /* batch-local event index */
+  int32_t* task_particle; /* particle index within its event */
+  int32_t* task_layer;
+  int32_t* task_n;        /* hits of the task */
+  float* task_Ehit;       /* hit energy, MeV */
+  int64_t hit_capacity;
+  int32_t* hit_cell;      /* cell id of each hit */
+  int16_t* hit_bin;       /* shape-histogram bin of each hit (ir * n_alpha + ia) */
+} fcs_debug;
+
+/* ---- entry points ---------------------------------------------------------- */
+
+const char* fcs_version(void);
+
+/* Copies the message of the calling thread's last error into buf (always
+ * NUL-terminated when len > 0).  Returns the status code of that error. */
+int fcs_last_error(char* buf, size_t len);
+
+/* Geometry (Sec. 4: detector description flattened to arrays of structs;
+ * Listing 2: getDDE).  regions: host [n_regions], sorted by layer, then by
+ * eta_lo within a layer, non-overlapping, n_eta, n_phi >= 1, deta, dphi > 0,
+ * cell ids contiguous (layer-major, region, i_eta, i_phi); layer_region_begin:
+ * host [n_layers + 1]; layers: host [n_layers].  Limits: n_layers <= 32,
+ * n_regions <= 256, cells < 2^31.  FCS_E_ARG if the table breaks a rule.
+ * Copies everything to the device on stream s and waits for it. */
+int fcs_load_geometry(fcs_geo** out, const fcs_region* regions, int32_t n_regions,
+                      const int32_t* layer_region_begin, int32_t n_layers,
+                      const fcs_layer_geom* layers, cudaStream_t s);
+int fcs_geometry_info(const fcs_geo* geo, int32_t* n_cells, int32_t* n_layers, int32_t* n_regions);
+void fcs_free_geometry(fcs_geo* geo);
+
+/* Parametrisation (Sec. 1 and Sec. 4: tables selected by particle type,
+ * energy and eta, flattened and copied to the GPU once).  Host arrays:
+ *   frac, mean_hit_E: [NT][NE][NH][NL] (NL = the geometry's layer count);
+ *     per entry the layer energy fraction (>= 0) and mean hit energy (MeV,
+ *     > 0 wherever frac > 0);
+ *   shape_w: [NT][NE][NH][NL][NR][NA] histogram weights (>= 0, finite, with a
+ *     positive sum wherever frac > 0); NR * NA must be 128 (16 x 8);
+ *   r_edges: [NR + 1] increasing, from 0 (mm); a_edges: [NA + 1] increasing
+ *     (rad) spanning at most [0, 2 pi].
+ * Energy bin = clamp(floor(log2 E) - ebin_log2_min, 0, NE - 1); |eta| bin =
+ * min(floor(|eta| * eta_bin_scale), NH - 1).  The inverse-CDF thresholds
+ * and guide tables are built on the device.  Waits for stream s. */
+int fcs_load_params(fcs_params** out, const fcs_geo* geo, const float* frac,
+                    const float* mean_hit_E, const float* shape_w, const float* r_edges,
+                    const float* a_edges, int32_t NT, int32_t NE, int32_t NH, int32_t NR,
+                    int32_t NA, double eta_bin_scale, int32_t ebin_log2_min, cudaStream_t s);
+void fcs_free_params(fcs_params* prm);
+
+/* Workspace: the intermediate device buffers of a simulation call (task
+ * records, tile map, FP64-recheck queue, accumulation array, sort keys).  The
+ * library allocates them with cudaMalloc and grows them on demand during
+ * sync calls; fcs_workspace_reserve sizes them ahead of sync == 0 calls and
+ * graph capture.  Pointers stay fixed until the next growth. */
+int fcs_workspace_create(fcs_workspace** out);
+int fcs_workspace_reserve(fcs_workspace* ws, const fcs_geo* geo, int64_t n_particles,
+                          int32_t n_events, int64_t n_hits, int32_t mode);
+/* Reads the device status of the last call on ws (waits for stream s). */
+int fcs_workspace_status(fcs_workspace* ws, fcs_stats* stats, cudaStream_t s);
+
+/* Stage times of the last call on ws that ran with config->timing != 0, in
+ * milliseconds, summed over its event ranges (CUDA events on the call's
+ * stream; waits for them): ms[FCS_STAGE_TASKS] particle tasks, scans, task
+ * records and tile map; ms[FCS_STAGE_HITS] the hit kernel; ms[FCS_STAGE_RECHECK]
+ * the FP64 recheck; ms[FCS_STAGE_REDUCE] compaction or sort + fold;
+ * ms[FCS_STAGE_TOTAL] all of them.  ms: host [FCS_N_STAGES].  FCS_E_ARG when
+ * no timed call has run. */
+enum fcs_stage {
+  FCS_STAGE_TASKS = 0,
+  FCS_STAGE_HITS = 1,
+  FCS_STAGE_RECHECK = 2,
+  FCS_STAGE_REDUCE = 3,
+  FCS_STAGE_TOTAL = 4,
+  FCS_N_STAGES = 5
+};
+int fcs_workspace_timings(fcs_workspace* ws, float* ms);
+void fcs_workspace_free(fcs_workspace* ws);
+
+/* Simulate n_events events (the hit loop of Listing 1 for every particle and
+ * layer, the cell mapping and deposit of Listing 2).  Event e of this batch
+ * uses random-stream event number first_event + e, so a batch split across
+ * calls or GPUs gives the same cells.  Outputs (device, any may be NULL):
+ *   cells_out: [n_events][n_cells] dense cell energies (MeV);
+ *   cell_ids / cell_E: the non-zero cells of all events, event-major and
+ *     ascending cell id within an event, at most `capacity` entries
+ *     (Sec. 4: results gathered as {cell_id, E});
+ *   event_offsets_out: [n_events + 1]; event e's cells are
+ *     [event_offsets_out[e], event_offsets_out[e+1]).  When the output does
+ *     not fit, nothing beyond capacity is written, event_offsets_out[n_events]
+ *     holds the size needed and the call returns FCS_E_RANGE (sync) or sets
+ *     FCS_FLAG_OUT_CAPACITY (async).
+ * dbg: optional validation dumps (NULL in production).
+ * Errors: FCS_E_ARG for bad arguments, FCS_E_RANGE as above or when a
+ * sync == 0 call needs more workspace than reserved, FCS_E_DEVICE_CHECK when
+ * a particle fails its checks (its tasks are skipped), FCS_E_CUDA / OOM. */
+int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
+                        const fcs_particles* particles, int64_t n_particles, int32_t n_events,
+                        uint64_t seed, int64_t first_event, const fcs_config* config,
+                        float* cells_out, int32_t* cell_ids, float* cell_E,
+                        int64_t* event_offsets_out, int64_t capacity, fcs_stats* stats,
+                        const fcs_debug* dbg, cudaStream_t s);
+
+/* End-to-end form of fcs_simulate_events for callers holding host data: the
+ * particle arrays (host SoA, same layout as fcs_particles, event_offsets on
+ * the host) are copied to the device, simulated, and the compacted result
+ * copied back into host cell_ids / cell_E / event_offsets_out (capacity
+ * entries).  Always synchronous.  Pinned host memory gives the fastest
+ * copies; pageable memory works. */
+int fcs_simulate_events_host(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
+                             const int32_t* type, const float* E, const float* eta,
+                             const float* phi, const int64_t* event_offsets,
+                             int64_t n_particles, int32_t n_events, uint64_t seed,
+                             int64_t first_event, const fcs_config* config, int32_t* cell_ids,
+                             float* cell_E, int64_t* event_offsets_out, int64_t capacity,
+                             fcs_stats* stats, cudaStream_t s);
+
+/* Gradient of a cell-energy loss with respect to the layer-fraction table
+ * and the shape weights, by reweighting hit energies with hit positions held
+ * fixed for the seed.  Not implemented yet: returns FCS_E_UNSUPPORTED. */
+int fcs_simulate_backward(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
+                          const fcs_particles* particles, int64_t n_particles,
+                          int32_t n_events, uint64_t seed, int64_t first_event,
+                          const fcs_config* config, const float* dL_dcells, float* d_frac,
+                          float* d_shape_w, cudaStream_t s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FCS_H */

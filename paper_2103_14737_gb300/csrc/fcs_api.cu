@@ -1,0 +1,903 @@
+// fcs_api.cu - the C ABI of include/fcs.h: argument validation, device
+// residency of geometry and parametrisation, the workspace, and the launch
+// sequence of a simulation call:
+//   per event range: range setup -> particle tasks (Poisson counts) -> two
+//   scans (task and hit offsets) -> task records -> tile map -> hit kernel ->
+//   FP64 recheck -> compaction (atomic) or sort + fold (deterministic)
+// followed by one finishing kernel.  Batched calls use one range for all
+// events (the grouped simulation of Sec. 4); per-event calls use one range
+// per event, as the paper's per-event GPU path did.  No launch depends on a
+// host-read size except in sync calls, which read the hit count once to size
+// the workspace.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <mutex>
+#include <vector>
+
+#include "fcs_internal.cuh"
+
+using namespace fcs;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+namespace {
+thread_local int g_err_code = FCS_OK;
+thread_local char g_err_msg[512] = "";
+
+int set_err(int code, const char* fmt, ...) {
+  g_err_code = code;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err_msg, sizeof(g_err_msg), fmt, ap);
+  va_end(ap);
+  return code;
+}
+int ok() {
+  g_err_code = FCS_OK;
+  g_err_msg[0] = 0;
+  return FCS_OK;
+}
+}  // namespace
+
+#define FCS_CUDA(expr)                                                                     \
+  do {                                                                                     \
+    cudaError_t _e = (expr);                                                               \
+    if (_e != cudaSuccess) {                                                               \
+      if (_e == cudaErrorMemoryAllocation) {                                               \
+        (void)cudaGetLastError();                                                          \
+        return set_err(FCS_E_OOM, "%s: %s", #expr, cudaGetErrorString(_e));                \
+      }                                                                                    \
+      return set_err(FCS_E_CUDA, "%s (%s:%d): %s", #expr, __FILE__, __LINE__,              \
+                     cudaGetErrorString(_e));                                              \
+    }                                                                                      \
+  } while (0)
+
+#define FCS_TRY(expr)               \
+  do {                              \
+    int _rc = (expr);               \
+    if (_rc != FCS_OK) return _rc;  \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// opaque objects
+// ---------------------------------------------------------------------------
+struct fcs_geo {
+  int device = -1;
+  GeoDev d{};
+  std::vector<void*> allocs;
+  ~fcs_geo() {
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
+struct fcs_params {
+  int device = -1;
+  ParamDev d{};
+  std::vector<void*> allocs;
+  ~fcs_params() {
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
+namespace {
+template <typename T>
+int dev_alloc(T** p, size_t n, std::vector<void*>* owner = nullptr) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    *p = nullptr;
+    return set_err(e == cudaErrorMemoryAllocation ? FCS_E_OOM : FCS_E_CUDA, "cudaMalloc(%zu bytes): %s",
+                   n * sizeof(T), cudaGetErrorString(e));
+  }
+  if (owner) owner->push_back((void*)*p);
+  return FCS_OK;
+}
+
+// Grows a library-owned buffer to at least `need` elements (contents lost).
+template <typename T>
+int grow(T** p, int64_t* cap, int64_t need, bool zero = false) {
+  if (need <= *cap && *p) return FCS_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  const int64_t n = std::max<int64_t>(need, 1);
+  FCS_TRY(dev_alloc(p, (size_t)n));
+  if (zero) FCS_CUDA(cudaMemset(*p, 0, (size_t)n * sizeof(T)));
+  *cap = n;
+  return FCS_OK;
+}
+
+int bits_for(int64_t n) {  // bits to hold values 0 .. n - 1
+  int b = 1;
+  while (b < 63 && (int64_t(1) << b) < n) ++b;
+  return b;
+}
+
+int current_device(int* dev) {
+  FCS_CUDA(cudaGetDevice(dev));
+  return FCS_OK;
+}
+}  // namespace
+
+struct fcs_workspace {
+  int device = -1;
+  int num_sms = 0;
+  Sizes* d_sizes = nullptr;
+  Sizes* h_sizes = nullptr;  // pinned mirror
+  int64_t sizes_cap = 0;
+  int32_t* nl = nullptr;
+  int64_t nl_cap = 0;
+  int64_t* pcount = nullptr;
+  int64_t* poff = nullptr;
+  int64_t pc_cap = 0, po_cap = 0, pcap = 0;
+  TaskRec* tasks = nullptr;
+  int64_t task_cap = 0;
+  int32_t* gmap = nullptr;
+  int64_t gmap_cap = 0;
+  uint2* recheck = nullptr;
+  int64_t recheck_cap = 0;
+  float* acc = nullptr;
+  int64_t acc_cap = 0, rows_cap = 0;
+  int32_t acc_stride = 0;
+  int64_t* chunk_counts = nullptr;
+  int64_t* chunk_offsets = nullptr;
+  int64_t cc_cap = 0, co_cap = 0;
+  int64_t* block_sums = nullptr;
+  int64_t bs_cap = 0;
+  uint64_t* keys = nullptr;
+  uint64_t* keys_alt = nullptr;
+  int64_t k_cap = 0, ka_cap = 0, rec_cap = 0;
+  int64_t* head_flags = nullptr;
+  int64_t* head_off = nullptr;
+  int64_t hf_cap = 0, ho_cap = 0;
+  // staging for the host-buffer entry point
+  void* stage = nullptr;
+  int64_t stage_cap = 0;
+  // CUDA graph cache (use_graph)
+  cudaGraphExec_t graph = nullptr;
+  std::vector<unsigned char> graph_key;
+  // stage timing events: 5 per event range (begin, after tasks, after hits,
+  // after recheck, after reduce) of the last timed call
+  std::vector<cudaEvent_t> tev;
+  int timed_ranges = 0;
+
+  ~fcs_workspace() {
+    if (graph) cudaGraphExecDestroy(graph);
+    for (cudaEvent_t e : tev) cudaEventDestroy(e);
+    void* ps[] = {d_sizes, nl, pcount, poff, tasks, gmap, recheck, acc, chunk_counts, chunk_offsets,
+                  block_sums, keys, keys_alt, head_flags, head_off, stage};
+    for (void* p : ps)
+      if (p) cudaFree(p);
+    if (h_sizes) cudaFreeHost(h_sizes);
+  }
+
+  WsDev view() const {
+    WsDev w{};
+    w.sizes = d_sizes;
+    w.nl = nl;
+    w.pcount = pcount;
+    w.poff = poff;
+    w.pcap = pcap;
+    w.tasks = tasks;
+    w.gmap = gmap;
+    w.recheck = recheck;
+    w.acc = acc;
+    w.task_cap = task_cap;
+    w.gmap_cap = gmap_cap;
+    w.recheck_cap = recheck_cap;
+    w.rows_cap = rows_cap;
+    w.keys = keys;
+    w.keys_alt = keys_alt;
+    w.rec_cap = rec_cap;
+    return w;
+  }
+};
+
+namespace {
+
+// Sizes every buffer that depends only on host-known quantities.
+int ws_reserve_static(fcs_workspace* ws, const fcs_geo* geo, int64_t P, int32_t rows, int mode) {
+  if (ws->device < 0) {
+    FCS_TRY(current_device(&ws->device));
+    FCS_CUDA(cudaDeviceGetAttribute(&ws->num_sms, cudaDevAttrMultiProcessorCount, ws->device));
+  }
+  if (!ws->d_sizes) {
+    FCS_TRY(grow(&ws->d_sizes, &ws->sizes_cap, 1, true));
+    FCS_CUDA(cudaMallocHost((void**)&ws->h_sizes, sizeof(Sizes)));
+    std::memset(ws->h_sizes, 0, sizeof(Sizes));
+  }
+  const int NL = geo->d.n_layers;
+  const int64_t Pc = std::max<int64_t>(P, 1);
+  if (Pc > ws->pcap || !ws->nl) {
+    FCS_TRY(grow(&ws->nl, &ws->nl_cap, Pc * NL));
+    FCS_TRY(grow(&ws->pcount, &ws->pc_cap, 2 * Pc));
+    FCS_TRY(grow(&ws->poff, &ws->po_cap, 2 * Pc));
+    ws->pcap = Pc;
+  }
+  FCS_TRY(grow(&ws->tasks, &ws->task_cap, Pc * NL));
+  const int32_t stride = geo->d.acc_stride;
+  if (stride != ws->acc_stride || rows > ws->rows_cap || !ws->acc) {
+    int64_t cap = 0;
+    if (ws->acc) cudaFree(ws->acc);
+    ws->acc = nullptr;
+    ws->acc_cap = 0;
+    FCS_TRY(grow(&ws->acc, &cap, (int64_t)std::max(rows, 1) * stride, true));
+    ws->acc_cap = cap;
+    ws->rows_cap = std::max(rows, 1);
+    ws->acc_stride = stride;
+  }
+  const int64_t chunks = compact_chunks(geo->d.n_cells, std::max(rows, 1));
+  FCS_TRY(grow(&ws->chunk_counts, &ws->cc_cap, chunks));
+  FCS_TRY(grow(&ws->chunk_offsets, &ws->co_cap, chunks));
+  FCS_TRY(grow(&ws->block_sums, &ws->bs_cap, kScanBlocks + 1));
+  if (mode == FCS_MODE_DETERMINISTIC) {
+    const int64_t he = det_hist_entries(ws->num_sms);
+    FCS_TRY(grow(&ws->head_flags, &ws->hf_cap, std::max<int64_t>(he, ws->rec_cap)));
+    FCS_TRY(grow(&ws->head_off, &ws->ho_cap, std::max<int64_t>(1, ws->rec_cap)));
+  }
+  return FCS_OK;
+}
+
+// Sizes the hit-dependent buffers for H hits.
+int ws_reserve_hits(fcs_workspace* ws, int64_t H, int mode) {
+  const int64_t g = H / kGranule + 2;
+  if (g > ws->gmap_cap) FCS_TRY(grow(&ws->gmap, &ws->gmap_cap, g + g / 4));
+  const int64_t rq = std::max<int64_t>(1 << 16, H / 16);
+  if (rq > ws->recheck_cap) FCS_TRY(grow(&ws->recheck, &ws->recheck_cap, rq + rq / 4));
+  if (mode == FCS_MODE_DETERMINISTIC) {
+    const int64_t need = std::max<int64_t>(H, 1);
+    if (need > ws->rec_cap) {
+      const int64_t cap = need + need / 8;
+      int64_t c1 = ws->k_cap, c2 = ws->ka_cap;
+      FCS_TRY(grow(&ws->keys, &c1, cap));
+      FCS_TRY(grow(&ws->keys_alt, &c2, cap));
+      ws->k_cap = c1;
+      ws->ka_cap = c2;
+      ws->rec_cap = cap;
+    }
+    const int64_t he = det_hist_entries(ws->num_sms);
+    FCS_TRY(grow(&ws->head_flags, &ws->hf_cap, std::max<int64_t>(he, ws->rec_cap)));
+    FCS_TRY(grow(&ws->head_off, &ws->ho_cap, ws->rec_cap));
+  }
+  return FCS_OK;
+}
+
+// ---- small kernels of the launch sequence ----------------------------------
+__global__ void k_call_begin(Sizes* s) {
+  Sizes z{};
+  *s = z;
+}
+
+__global__ void k_range_begin(Sizes* s, const int64_t* __restrict__ off, int32_t ev_lo, int32_t ev_hi,
+                              int64_t n_particles, int64_t pcap) {
+  const int64_t a = off[ev_lo], b = off[ev_hi];
+  bool bad = a < 0 || b < a || b > n_particles || (b - a) > pcap;
+  for (int32_t e = ev_lo; e < ev_hi && !bad; ++e) bad = off[e + 1] < off[e];
+  s->n_part = bad ? 0 : (b - a);
+  if (bad) s->flags |= FCS_FLAG_BAD_OFFSETS;
+  s->n_tasks = 0;
+  s->n_hits = 0;
+  s->n_recheck = 0;
+  s->n_records = 0;
+  s->n_rec_used = 0;
+  s->queue = 0;
+}
+
+__global__ void k_range_end(Sizes* s) {
+  s->task_base += s->n_tasks;
+  s->hit_base += s->n_hits;
+  s->recheck_total += s->n_recheck;
+}
+
+__global__ void k_call_end(Sizes* s, int64_t* event_offsets_out, int32_t n_events, int64_t capacity) {
+  if (event_offsets_out) event_offsets_out[n_events] = s->nnz_total;
+  if (s->nnz_total > capacity) s->flags |= FCS_FLAG_OUT_CAPACITY;
+}
+
+__global__ void k_empty_offsets(int64_t* event_offsets_out, int32_t n_events) {
+  for (int i = threadIdx.x; i <= n_events; i += blockDim.x) event_offsets_out[i] = 0;
+}
+
+int status_from(const Sizes& s, fcs_stats* st) {
+  if (st) {
+    st->n_tasks = s.task_base;
+    st->n_hits = s.hit_base;
+    st->n_nonzero = s.nnz_total;
+    st->n_recheck = s.recheck_total;
+    st->device_flags = s.flags;
+    st->pad = 0;
+  }
+  if (s.flags & FCS_FLAG_BAD_OFFSETS)
+    return set_err(FCS_E_ARG, "event_offsets must be non-decreasing within [0, n_particles]");
+  if (s.flags & FCS_FLAG_BAD_PARTICLE)
+    return set_err(FCS_E_DEVICE_CHECK, "a particle failed its checks (type, E > 0, finite eta/phi); its tasks were skipped");
+  if (s.flags & FCS_FLAG_HIT_CAPACITY)
+    return set_err(FCS_E_RANGE, "the workspace holds fewer hits than the call produced (%lld); reserve more",
+                   (long long)s.hit_base);
+  if (s.flags & FCS_FLAG_KEY_BITS) return set_err(FCS_E_RANGE, "deterministic keys exceed 64 bits");
+  if (s.flags & FCS_FLAG_OUT_CAPACITY)
+    return set_err(FCS_E_RANGE, "output capacity too small: %lld non-zero cells", (long long)s.nnz_total);
+  return ok();
+}
+
+int check_particles(const fcs_particles* p) {
+  if (!p || !p->type || !p->E || !p->eta || !p->phi || !p->event_offsets)
+    return set_err(FCS_E_ARG, "particles: every array must be non-NULL");
+  return FCS_OK;
+}
+
+struct CallArgs {
+  const fcs_geo* geo;
+  const fcs_params* prm;
+  fcs_workspace* ws;
+  fcs_particles parts;
+  int64_t n_particles;
+  int32_t n_events;
+  uint64_t seed;
+  int64_t first_event;
+  fcs_config cfg;
+  float* cells_out;
+  int32_t* cell_ids;
+  float* cell_E;
+  int64_t* event_offsets_out;
+  int64_t capacity;
+  const fcs_debug* dbg;
+  cudaStream_t s;
+};
+
+// Enqueues one event range.  sync_size: read the hit count back after the
+// scans and grow the hit-dependent buffers.
+int enqueue_range(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, bool sync_size, const HitCfg& hc,
+                  int key_task_bits) {
+  fcs_workspace* ws = a.ws;
+  const Launch L{a.s, ws->num_sms};
+  const int det = a.cfg.mode == FCS_MODE_DETERMINISTIC;
+  const int32_t rows = ev_hi - ev_lo;
+  cudaEvent_t* tev = a.cfg.timing ? &ws->tev[(size_t)(a.cfg.batched ? 0 : ev_lo) * 5] : nullptr;
+  if (tev) FCS_CUDA(cudaEventRecord(tev[0], a.s));
+  k_range_begin<<<1, 1, 0, a.s>>>(ws->d_sizes, a.parts.event_offsets, ev_lo, ev_hi, a.n_particles, ws->pcap);
+  const uint32_t k0 = (uint32_t)(a.seed & 0xFFFFFFFFu), k1 = (uint32_t)(a.seed >> 32);
+  FCS_CUDA(launch_particle_tasks(a.geo->d, a.prm->d, a.parts, ev_lo, ev_hi, k0, k1, a.first_event, ws->view(), L));
+  const ScanTmp tmp{ws->block_sums};
+  WsDev w = ws->view();
+  FCS_CUDA(launch_scan_i64(w.pcount, w.poff, &w.sizes->n_part, 0, &w.sizes->n_tasks, 0, tmp, a.s));
+  FCS_CUDA(launch_scan_i64(w.pcount + w.pcap, w.poff + w.pcap, &w.sizes->n_part, 0, &w.sizes->n_hits, 0, tmp, a.s));
+  if (sync_size) {
+    FCS_CUDA(cudaMemcpyAsync(ws->h_sizes, ws->d_sizes, sizeof(Sizes), cudaMemcpyDeviceToHost, a.s));
+    FCS_CUDA(cudaStreamSynchronize(a.s));
+    FCS_TRY(ws_reserve_hits(ws, ws->h_sizes->n_hits, a.cfg.mode));
+    w = ws->view();
+  }
+  FCS_CUDA(launch_task_write(a.geo->d, a.prm->d, a.parts, ev_lo, ev_hi, w, a.dbg, L));
+  FCS_CUDA(launch_granule_map(w, L));
+  if (tev) FCS_CUDA(cudaEventRecord(tev[1], a.s));
+  FCS_CUDA(launch_hits(a.geo->d, a.prm->d, w, ev_lo, k0, k1, a.first_event, hc, key_task_bits, a.dbg, L));
+  if (tev) FCS_CUDA(cudaEventRecord(tev[2], a.s));
+  FCS_CUDA(launch_recheck(a.geo->d, a.prm->d, w, ev_lo, k0, k1, a.first_event, det, key_task_bits, a.dbg, L));
+  if (tev) FCS_CUDA(cudaEventRecord(tev[3], a.s));
+  if (!det) {
+    FCS_CUDA(launch_compact(a.geo->d, w, rows, ev_lo, ws->chunk_counts, ws->chunk_offsets, tmp, a.cells_out,
+                            a.cell_ids, a.cell_E, a.event_offsets_out, a.n_events, a.capacity, L));
+  } else {
+    const int cellbits = bits_for((int64_t)rows * a.geo->d.n_cells);
+    const int total = kRecordCountBits + key_task_bits + cellbits;
+    FCS_CUDA(launch_det_reduce(a.geo->d, w, rows, ev_lo, key_task_bits, total, nullptr, ws->hf_cap,
+                               ws->head_flags, ws->head_off, tmp, a.cells_out, a.cell_ids, a.cell_E,
+                               a.event_offsets_out, a.n_events, a.capacity, L));
+  }
+  if (tev) FCS_CUDA(cudaEventRecord(tev[4], a.s));
+  k_range_end<<<1, 1, 0, a.s>>>(ws->d_sizes);
+  return FCS_OK;
+}
+
+int ensure_timing_events(fcs_workspace* ws, int ranges) {
+  while ((int)ws->tev.size() < ranges * 5) {
+    cudaEvent_t e;
+    FCS_CUDA(cudaEventCreate(&e));
+    ws->tev.push_back(e);
+  }
+  ws->timed_ranges = ranges;
+  return FCS_OK;
+}
+
+int enqueue_call(const CallArgs& a, bool sync_size, const HitCfg& hc, int key_task_bits) {
+  fcs_workspace* ws = a.ws;
+  k_call_begin<<<1, 1, 0, a.s>>>(ws->d_sizes);
+  if (a.cells_out && a.cfg.mode == FCS_MODE_DETERMINISTIC)
+    FCS_CUDA(cudaMemsetAsync(a.cells_out, 0, (size_t)a.n_events * a.geo->d.n_cells * sizeof(float), a.s));
+  if (a.cfg.batched) {
+    FCS_TRY(enqueue_range(a, 0, a.n_events, sync_size, hc, key_task_bits));
+  } else {
+    for (int32_t e = 0; e < a.n_events; ++e) FCS_TRY(enqueue_range(a, e, e + 1, sync_size, hc, key_task_bits));
+  }
+  k_call_end<<<1, 1, 0, a.s>>>(ws->d_sizes, a.event_offsets_out, a.n_events, a.capacity);
+  FCS_CUDA(cudaGetLastError());
+  return FCS_OK;
+}
+
+HitCfg hit_cfg(const fcs_config& c) {
+  HitCfg h;
+  h.block = c.block ? c.block : 256;
+  h.hpt = c.hits_per_thread ? c.hits_per_thread : 4;
+  h.det = c.mode == FCS_MODE_DETERMINISTIC;
+  return h;
+}
+
+int validate_config(const fcs_config& c) {
+  if (c.mode != FCS_MODE_ATOMIC && c.mode != FCS_MODE_DETERMINISTIC) return set_err(FCS_E_ARG, "config.mode");
+  if (c.batched != 0 && c.batched != 1) return set_err(FCS_E_ARG, "config.batched must be 0 or 1");
+  const int hpt = c.hits_per_thread, blk = c.block;
+  if (!(hpt == 0 || hpt == 1 || hpt == 2 || hpt == 4 || hpt == 8))
+    return set_err(FCS_E_ARG, "config.hits_per_thread must be 0, 1, 2, 4 or 8");
+  if (!(blk == 0 || blk == 128 || blk == 256 || blk == 512))
+    return set_err(FCS_E_ARG, "config.block must be 0, 128, 256 or 512");
+  if (c.reserved) return set_err(FCS_E_ARG, "config.reserved must be 0");
+  if (c.use_graph && c.sync) return set_err(FCS_E_ARG, "config.use_graph requires sync == 0");
+  return FCS_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* fcs_version(void) { return "libfcs 0.1 (sm_103a)"; }
+
+int fcs_last_error(char* buf, size_t len) {
+  if (buf && len) {
+    std::strncpy(buf, g_err_msg, len - 1);
+    buf[len - 1] = 0;
+  }
+  return g_err_code;
+}
+
+int fcs_load_geometry(fcs_geo** out, const fcs_region* regions, int32_t n_regions,
+                      const int32_t* layer_region_begin, int32_t n_layers, const fcs_layer_geom* layers,
+                      cudaStream_t s) {
+  if (!out) return set_err(FCS_E_ARG, "out is NULL");
+  *out = nullptr;
+  if (!regions || !layer_region_begin || !layers) return set_err(FCS_E_ARG, "NULL table");
+  if (n_layers < 1 || n_layers > kMaxLayers) return set_err(FCS_E_ARG, "n_layers must be in [1, %d]", kMaxLayers);
+  if (n_regions < 1 || n_regions > kMaxRegions) return set_err(FCS_E_ARG, "n_regions must be in [1, %d]", kMaxRegions);
+  const int32_t* lrb = layer_region_begin;
+  if (lrb[0] != 0 || lrb[n_layers] != n_regions) return set_err(FCS_E_ARG, "layer_region_begin must span [0, n_regions]");
+  int64_t cells = 0;
+  std::vector<RegionF> rf(n_regions);
+  std::vector<double> eta_lo(n_regions), deta(n_regions), phi_lo(n_regions), dphi(n_regions), split(n_regions);
+  std::vector<int32_t> ne(n_regions), np(n_regions), co(n_regions);
+  for (int l = 0; l < n_layers; ++l) {
+    if (lrb[l + 1] <= lrb[l]) return set_err(FCS_E_ARG, "layer %d has no region", l);
+    const double R = layers[l].rz;
+    if (!(R > 0.0) || !std::isfinite(R)) return set_err(FCS_E_ARG, "layer %d: rz must be > 0", l);
+    if (layers[l].barrel != 0 && layers[l].barrel != 1) return set_err(FCS_E_ARG, "layer %d: barrel flag", l);
+    for (int r = lrb[l]; r < lrb[l + 1]; ++r) {
+      const fcs_region& g = regions[r];
+      if (g.layer != l) return set_err(FCS_E_ARG, "region %d: layer %d != %d", r, g.layer, l);
+      if (g.n_eta < 1 || g.n_phi < 1) return set_err(FCS_E_ARG, "region %d: empty grid", r);
+      if (!(g.deta > 0.0) || !(g.dphi > 0.0) || !std::isfinite(g.deta) || !std::isfinite(g.dphi) ||
+          !std::isfinite(g.eta_lo) || !std::isfinite(g.phi_lo))
+        return set_err(FCS_E_ARG, "region %d: bad bounds", r);
+      if (g.cell_offset != cells) return set_err(FCS_E_ARG, "region %d: cell ids must be contiguous", r);
+      cells += (int64_t)g.n_eta * g.n_phi;
+      if (cells >= (int64_t(1) << 31)) return set_err(FCS_E_ARG, "more than 2^31 - 1 cells");
+      eta_lo[r] = g.eta_lo;
+      deta[r] = g.deta;
+      phi_lo[r] = g.phi_lo;
+      dphi[r] = g.dphi;
+      ne[r] = g.n_eta;
+      np[r] = g.n_phi;
+      co[r] = g.cell_offset;
+      if (r == lrb[l]) {
+        split[r] = -std::numeric_limits<double>::infinity();
+      } else {
+        // midpoint between the top of the previous region and this eta_lo
+        const double top = eta_lo[r - 1] + (double)ne[r - 1] * deta[r - 1];
+        if (!(g.eta_lo >= top - 1e-9)) return set_err(FCS_E_ARG, "region %d overlaps region %d", r, r - 1);
+        split[r] = 0.5 * (top + g.eta_lo);
+      }
+      RegionF& f = rf[r];
+      f.eta_lo = (float)g.eta_lo;
+      f.inv_deta = (float)(1.0 / g.deta);
+      f.phi_lo = (float)g.phi_lo;
+      f.inv_dphi = (float)(1.0 / g.dphi);
+      f.split = (float)split[r];
+      f.n_eta = g.n_eta;
+      f.n_phi = g.n_phi;
+      f.cell_off = g.cell_offset;
+    }
+  }
+  fcs_geo* geo = new fcs_geo();
+  int rc = FCS_OK;
+  auto fail = [&](int code) {
+    delete geo;
+    return code;
+  };
+  if ((rc = current_device(&geo->device)) != FCS_OK) return fail(rc);
+  RegionF* d_rf;
+  double *d_el, *d_de, *d_pl, *d_dp, *d_sp, *d_rz;
+  int32_t *d_ne, *d_np, *d_co, *d_lrb, *d_bar;
+  if ((rc = dev_alloc(&d_rf, n_regions, &geo->allocs)) || (rc = dev_alloc(&d_el, n_regions, &geo->allocs)) ||
+      (rc = dev_alloc(&d_de, n_regions, &geo->allocs)) || (rc = dev_alloc(&d_pl, n_regions, &geo->allocs)) ||
+      (rc = dev_alloc(&d_dp, n_regions, &geo->allocs)) || (rc = dev_alloc(&d_sp, n_regions, &geo->allocs)) ||
+      (rc = dev_alloc(&d_ne, n_regions, &geo->allocs)) || (rc = dev_alloc(&d_np, n_regions, &geo->allocs)) ||
+      (rc = dev_alloc(&d_co, n_regions, &geo->allocs)) || (rc = dev_alloc(&d_lrb, n_layers + 1, &geo->allocs)) ||
+      (rc = dev_alloc(&d_rz, n_layers, &geo->allocs)) || (rc = dev_alloc(&d_bar, n_layers, &geo->allocs)))
+    return fail(rc);
+  std::vector<double> rz(n_layers);
+  std::vector<int32_t> bar(n_layers);
+  for (int l = 0; l < n_layers; ++l) {
+    rz[l] = layers[l].rz;
+    bar[l] = layers[l].barrel;
+  }
+  const struct {
+    void* d;
+    const void* h;
+    size_t n;
+  } copies[] = {{d_rf, rf.data(), n_regions * sizeof(RegionF)}, {d_el, eta_lo.data(), n_regions * sizeof(double)},
+                {d_de, deta.data(), n_regions * sizeof(double)},  {d_pl, phi_lo.data(), n_regions * sizeof(double)},
+                {d_dp, dphi.data(), n_regions * sizeof(double)},  {d_sp, split.data(), n_regions * sizeof(double)},
+                {d_ne, ne.data(), n_regions * sizeof(int32_t)},   {d_np, np.data(), n_regions * sizeof(int32_t)},
+                {d_co, co.data(), n_regions * sizeof(int32_t)},   {d_lrb, lrb, (n_layers + 1) * sizeof(int32_t)},
+                {d_rz, rz.data(), n_layers * sizeof(double)},     {d_bar, bar.data(), n_layers * sizeof(int32_t)}};
+  for (const auto& c : copies) {
+    cudaError_t e = cudaMemcpyAsync(c.d, c.h, c.n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(set_err(FCS_E_CUDA, "geometry copy: %s", cudaGetErrorString(e)));
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(set_err(FCS_E_CUDA, "geometry copy: %s", cudaGetErrorString(e)));
+  GeoDev& d = geo->d;
+  d.n_layers = n_layers;
+  d.n_regions = n_regions;
+  d.n_cells = (int32_t)cells;
+  d.acc_stride = (int32_t)((cells + 63) / 64 * 64);
+  d.regf = d_rf;
+  d.eta_lo = d_el;
+  d.deta = d_de;
+  d.phi_lo = d_pl;
+  d.dphi = d_dp;
+  d.split = d_sp;
+  d.n_eta = d_ne;
+  d.n_phi = d_np;
+  d.cell_off = d_co;
+  d.lrb = d_lrb;
+  d.rz = d_rz;
+  d.barrel = d_bar;
+  *out = geo;
+  return ok();
+}
+
+int fcs_geometry_info(const fcs_geo* geo, int32_t* n_cells, int32_t* n_layers, int32_t* n_regions) {
+  if (!geo) return set_err(FCS_E_ARG, "geo is NULL");
+  if (n_cells) *n_cells = geo->d.n_cells;
+  if (n_layers) *n_layers = geo->d.n_layers;
+  if (n_regions) *n_regions = geo->d.n_regions;
+  return ok();
+}
+
+void fcs_free_geometry(fcs_geo* geo) { delete geo; }
+
+int fcs_load_params(fcs_params** out, const fcs_geo* geo, const float* frac, const float* mean_hit_E,
+                    const float* shape_w, const float* r_edges, const float* a_edges, int32_t NT, int32_t NE,
+                    int32_t NH, int32_t NR, int32_t NA, double eta_bin_scale, int32_t ebin_log2_min,
+                    cudaStream_t s) {
+  if (!out) return set_err(FCS_E_ARG, "out is NULL");
+  *out = nullptr;
+  if (!geo || !frac || !mean_hit_E || !shape_w || !r_edges || !a_edges) return set_err(FCS_E_ARG, "NULL argument");
+  if (NT < 1 || NE < 1 || NH < 1) return set_err(FCS_E_ARG, "NT, NE, NH must be >= 1");
+  if (NR != kNR || NA != kNA) return set_err(FCS_E_ARG, "the shape histogram must be %d (r) x %d (alpha)", kNR, kNA);
+  if (!(eta_bin_scale > 0.0) || !std::isfinite(eta_bin_scale)) return set_err(FCS_E_ARG, "eta_bin_scale must be > 0");
+  if (ebin_log2_min < -1000 || ebin_log2_min > 1000) return set_err(FCS_E_ARG, "ebin_log2_min out of range");
+  const int NL = geo->d.n_layers;
+  const int64_t n_entries = (int64_t)NT * NE * NH * NL;
+  if (n_entries >= (int64_t(1) << 24)) return set_err(FCS_E_ARG, "parametrisation has 2^24 or more entries");
+  if (!(r_edges[0] >= 0.0f)) return set_err(FCS_E_ARG, "r_edges[0] must be >= 0");
+  for (int i = 0; i < NR; ++i)
+    if (!(r_edges[i + 1] > r_edges[i]) || !std::isfinite(r_edges[i + 1])) return set_err(FCS_E_ARG, "r_edges must increase");
+  if (!(a_edges[0] >= 0.0f) || !(a_edges[NA] <= 6.2831855f)) return set_err(FCS_E_ARG, "a_edges must lie in [0, 2 pi]");
+  for (int i = 0; i < NA; ++i)
+    if (!(a_edges[i + 1] > a_edges[i])) return set_err(FCS_E_ARG, "a_edges must increase");
+  for (int64_t e = 0; e < n_entries; ++e) {
+    const float f = frac[e], m = mean_hit_E[e];
+    if (!(f >= 0.0f) || !std::isfinite(f)) return set_err(FCS_E_ARG, "frac[%lld] must be finite and >= 0", (long long)e);
+    const float* w = shape_w + e * kNBins;
+    double sum = 0.0;
+    for (int k = 0; k < kNBins; ++k) {
+      if (!(w[k] >= 0.0f) || !std::isfinite(w[k]))
+        return set_err(FCS_E_ARG, "shape_w[%lld][%d] must be finite and >= 0", (long long)e, k);
+      sum += w[k];
+    }
+    if (f > 0.0f) {
+      if (!(m > 0.0f) || !std::isfinite(m))
+        return set_err(FCS_E_ARG, "mean_hit_E[%lld] must be > 0 where frac > 0", (long long)e);
+      if (!(sum > 0.0)) return set_err(FCS_E_ARG, "shape_w of entry %lld sums to 0 where frac > 0", (long long)e);
+    }
+  }
+  fcs_params* prm = new fcs_params();
+  int rc = FCS_OK;
+  auto fail = [&](int code) {
+    delete prm;
+    return code;
+  };
+  if ((rc = current_device(&prm->device)) != FCS_OK) return fail(rc);
+  float *d_frac, *d_mhe, *d_re, *d_ae, *d_w = nullptr;
+  uint32_t* d_thr;
+  uint16_t* d_guide;
+  int32_t* d_bad = nullptr;
+  if ((rc = dev_alloc(&d_frac, n_entries, &prm->allocs)) || (rc = dev_alloc(&d_mhe, n_entries, &prm->allocs)) ||
+      (rc = dev_alloc(&d_re, NR + 1, &prm->allocs)) || (rc = dev_alloc(&d_ae, NA + 1, &prm->allocs)) ||
+      (rc = dev_alloc(&d_thr, n_entries * kNBins, &prm->allocs)) ||
+      (rc = dev_alloc(&d_guide, n_entries * kGuideCells, &prm->allocs)))
+    return fail(rc);
+  if ((rc = dev_alloc(&d_w, n_entries * kNBins)) || (rc = dev_alloc(&d_bad, n_entries))) {
+    if (d_w) cudaFree(d_w);
+    return fail(rc);
+  }
+  auto cleanup_tmp = [&]() {
+    cudaFree(d_w);
+    cudaFree(d_bad);
+  };
+  cudaError_t e = cudaSuccess;
+  if ((e = cudaMemcpyAsync(d_frac, frac, n_entries * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_mhe, mean_hit_E, n_entries * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_re, r_edges, (NR + 1) * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_ae, a_edges, (NA + 1) * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_w, shape_w, n_entries * kNBins * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = launch_build_tables(d_w, (int)n_entries, d_thr, d_guide, d_bad, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+    cleanup_tmp();
+    return fail(set_err(FCS_E_CUDA, "parametrisation upload: %s", cudaGetErrorString(e)));
+  }
+  cleanup_tmp();
+  ParamDev& d = prm->d;
+  d.NT = NT;
+  d.NE = NE;
+  d.NH = NH;
+  d.NL = NL;
+  d.eta_scale = eta_bin_scale;
+  d.ebin_min = ebin_log2_min;
+  d.n_entries = (int32_t)n_entries;
+  d.frac = d_frac;
+  d.mhe = d_mhe;
+  d.thr = d_thr;
+  d.guide = d_guide;
+  d.r_edges = d_re;
+  d.a_edges = d_ae;
+  *out = prm;
+  return ok();
+}
+
+void fcs_free_params(fcs_params* prm) { delete prm; }
+
+int fcs_workspace_create(fcs_workspace** out) {
+  if (!out) return set_err(FCS_E_ARG, "out is NULL");
+  *out = new fcs_workspace();
+  return ok();
+}
+
+int fcs_workspace_reserve(fcs_workspace* ws, const fcs_geo* geo, int64_t n_particles, int32_t n_events,
+                          int64_t n_hits, int32_t mode) {
+  if (!ws || !geo) return set_err(FCS_E_ARG, "NULL argument");
+  if (n_particles < 0 || n_events < 0 || n_hits < 0) return set_err(FCS_E_ARG, "negative size");
+  if (mode != FCS_MODE_ATOMIC && mode != FCS_MODE_DETERMINISTIC) return set_err(FCS_E_ARG, "mode");
+  FCS_TRY(ws_reserve_static(ws, geo, n_particles, n_events, mode));
+  FCS_TRY(ws_reserve_hits(ws, n_hits, mode));
+  return ok();
+}
+
+int fcs_workspace_status(fcs_workspace* ws, fcs_stats* stats, cudaStream_t s) {
+  if (!ws) return set_err(FCS_E_ARG, "ws is NULL");
+  if (!ws->d_sizes) {
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    return ok();
+  }
+  FCS_CUDA(cudaMemcpyAsync(ws->h_sizes, ws->d_sizes, sizeof(Sizes), cudaMemcpyDeviceToHost, s));
+  FCS_CUDA(cudaStreamSynchronize(s));
+  return status_from(*ws->h_sizes, stats);
+}
+
+int fcs_workspace_timings(fcs_workspace* ws, float* ms) {
+  if (!ws || !ms) return set_err(FCS_E_ARG, "NULL argument");
+  if (ws->timed_ranges <= 0) return set_err(FCS_E_ARG, "no timed call on this workspace");
+  for (int k = 0; k < FCS_N_STAGES; ++k) ms[k] = 0.0f;
+  FCS_CUDA(cudaEventSynchronize(ws->tev[(size_t)ws->timed_ranges * 5 - 1]));
+  for (int r = 0; r < ws->timed_ranges; ++r) {
+    const cudaEvent_t* e = &ws->tev[(size_t)r * 5];
+    for (int k = 0; k < 4; ++k) {
+      float t = 0.0f;
+      FCS_CUDA(cudaEventElapsedTime(&t, e[k], e[k + 1]));
+      ms[k] += t;
+    }
+  }
+  ms[FCS_STAGE_TOTAL] = ms[0] + ms[1] + ms[2] + ms[3];
+  return ok();
+}
+
+void fcs_workspace_free(fcs_workspace* ws) { delete ws; }
+
+int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
+                        const fcs_particles* particles, int64_t n_particles, int32_t n_events, uint64_t seed,
+                        int64_t first_event, const fcs_config* config, float* cells_out, int32_t* cell_ids,
+                        float* cell_E, int64_t* event_offsets_out, int64_t capacity, fcs_stats* stats,
+                        const fcs_debug* dbg, cudaStream_t s) {
+  if (!geo || !prm || !ws) return set_err(FCS_E_ARG, "geo, params and workspace are required");
+  FCS_TRY(check_particles(particles));
+  if (n_particles < 0 || n_events < 0 || capacity < 0) return set_err(FCS_E_ARG, "negative size");
+  if (prm->d.NL != geo->d.n_layers) return set_err(FCS_E_ARG, "parametrisation and geometry disagree on layers");
+  if ((cell_ids == nullptr) != (cell_E == nullptr)) return set_err(FCS_E_ARG, "cell_ids and cell_E go together");
+  fcs_config cfg{};
+  cfg.batched = 1;
+  cfg.sync = 1;
+  if (config) cfg = *config;
+  FCS_TRY(validate_config(cfg));
+  int dev = 0;
+  FCS_TRY(current_device(&dev));
+  if (dev != geo->device || dev != prm->device || (ws->device >= 0 && ws->device != dev))
+    return set_err(FCS_E_ARG, "geometry, parametrisation and workspace must live on the current device");
+  if (n_events == 0) {
+    if (event_offsets_out) k_empty_offsets<<<1, 32, 0, s>>>(event_offsets_out, 0);
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    FCS_CUDA(cudaGetLastError());
+    return ok();
+  }
+  const int32_t rows = cfg.batched ? n_events : 1;
+  FCS_TRY(ws_reserve_static(ws, geo, n_particles, rows, cfg.mode));
+  const int key_task_bits = bits_for(std::max<int64_t>(n_particles, 1) * geo->d.n_layers);
+  if (cfg.mode == FCS_MODE_DETERMINISTIC &&
+      kRecordCountBits + key_task_bits + bits_for((int64_t)rows * geo->d.n_cells) > 64)
+    return set_err(FCS_E_RANGE, "deterministic mode: (cell, task) keys exceed 64 bits; split the batch");
+  CallArgs a{geo, prm, ws, *particles, n_particles, n_events, seed, first_event, cfg, cells_out,
+             cell_ids, cell_E, event_offsets_out, capacity, dbg, s};
+  const HitCfg hc = hit_cfg(cfg);
+  if (cfg.timing) FCS_TRY(ensure_timing_events(ws, cfg.batched ? 1 : n_events));
+  else ws->timed_ranges = 0;
+  if (!cfg.sync && cfg.use_graph) {
+    // key of the captured sequence: every argument that shapes it
+    std::vector<unsigned char> key;
+    auto put = [&](const void* p, size_t n) {
+      const unsigned char* c = (const unsigned char*)p;
+      key.insert(key.end(), c, c + n);
+    };
+    put(&geo, sizeof(geo));
+    put(&prm, sizeof(prm));
+    put(particles, sizeof(*particles));
+    put(&n_particles, sizeof(n_particles));
+    put(&n_events, sizeof(n_events));
+    put(&seed, sizeof(seed));
+    put(&first_event, sizeof(first_event));
+    put(&cfg, sizeof(cfg));
+    put(&cells_out, sizeof(cells_out));
+    put(&cell_ids, sizeof(cell_ids));
+    put(&cell_E, sizeof(cell_E));
+    put(&event_offsets_out, sizeof(event_offsets_out));
+    put(&capacity, sizeof(capacity));
+    put(&dbg, sizeof(dbg));
+    put(&ws->d_sizes, sizeof(void*));
+    put(&ws->tasks, sizeof(void*));
+    put(&ws->gmap, sizeof(void*));
+    put(&ws->recheck, sizeof(void*));
+    put(&ws->acc, sizeof(void*));
+    put(&ws->keys, sizeof(void*));
+    put(&ws->head_flags, sizeof(void*));
+    if (!ws->graph || key != ws->graph_key) {
+      if (ws->graph) {
+        cudaGraphExecDestroy(ws->graph);
+        ws->graph = nullptr;
+      }
+      cudaStream_t cs;
+      FCS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      CallArgs ca = a;
+      ca.s = cs;
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      int rc = FCS_OK;
+      if (e == cudaSuccess) rc = enqueue_call(ca, false, hc, key_task_bits);
+      cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+      cudaStreamDestroy(cs);
+      if (e != cudaSuccess) return set_err(FCS_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
+      if (rc != FCS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (e2 != cudaSuccess) return set_err(FCS_E_CUDA, "graph capture: %s", cudaGetErrorString(e2));
+      e = cudaGraphInstantiate(&ws->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        ws->graph = nullptr;
+        return set_err(FCS_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+      }
+      ws->graph_key = key;
+    }
+    FCS_CUDA(cudaGraphLaunch(ws->graph, s));
+    return ok();
+  }
+  FCS_TRY(enqueue_call(a, cfg.sync != 0 && cfg.batched, hc, key_task_bits));
+  if (!cfg.sync) return ok();
+  FCS_CUDA(cudaMemcpyAsync(ws->h_sizes, ws->d_sizes, sizeof(Sizes), cudaMemcpyDeviceToHost, s));
+  FCS_CUDA(cudaStreamSynchronize(s));
+  if ((ws->h_sizes->flags & FCS_FLAG_HIT_CAPACITY) && !cfg.batched) {
+    // per-event sync call that outgrew the workspace: size it for the largest
+    // event seen (the whole call's hits bound it) and run again
+    FCS_TRY(ws_reserve_hits(ws, ws->h_sizes->hit_base, cfg.mode));
+    FCS_TRY(enqueue_call(a, false, hc, key_task_bits));
+    FCS_CUDA(cudaMemcpyAsync(ws->h_sizes, ws->d_sizes, sizeof(Sizes), cudaMemcpyDeviceToHost, s));
+    FCS_CUDA(cudaStreamSynchronize(s));
+  }
+  return status_from(*ws->h_sizes, stats);
+}
+
+int fcs_simulate_events_host(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws, const int32_t* type,
+                             const float* E, const float* eta, const float* phi, const int64_t* event_offsets,
+                             int64_t n_particles, int32_t n_events, uint64_t seed, int64_t first_event,
+                             const fcs_config* config, int32_t* cell_ids, float* cell_E,
+                             int64_t* event_offsets_out, int64_t capacity, fcs_stats* stats, cudaStream_t s) {
+  if (!geo || !prm || !ws) return set_err(FCS_E_ARG, "geo, params and workspace are required");
+  if (n_particles < 0 || n_events < 0 || capacity < 0) return set_err(FCS_E_ARG, "negative size");
+  if (!type || !E || !eta || !phi || !event_offsets || !event_offsets_out)
+    return set_err(FCS_E_ARG, "host arrays must be non-NULL");
+  if ((cell_ids == nullptr) != (cell_E == nullptr)) return set_err(FCS_E_ARG, "cell_ids and cell_E go together");
+  fcs_config cfg{};
+  cfg.batched = 1;
+  if (config) cfg = *config;
+  cfg.sync = 1;
+  cfg.use_graph = 0;
+  // staging: particles, offsets, outputs (16-byte aligned slices)
+  auto al = [](int64_t b) { return (b + 255) / 256 * 256; };
+  const int64_t b_type = al(n_particles * 4), b_f = al(n_particles * 4), b_off = al((int64_t)(n_events + 1) * 8);
+  const int64_t b_ids = al(capacity * 4), b_E = al(capacity * 4);
+  const int64_t need = b_type + 3 * b_f + 2 * b_off + b_ids + b_E;
+  if (need > ws->stage_cap) {
+    if (ws->stage) cudaFree(ws->stage);
+    ws->stage = nullptr;
+    ws->stage_cap = 0;
+    unsigned char* p = nullptr;
+    FCS_TRY(dev_alloc(&p, (size_t)need));
+    ws->stage = p;
+    ws->stage_cap = need;
+  }
+  unsigned char* base = (unsigned char*)ws->stage;
+  int32_t* d_type = (int32_t*)base;
+  float* d_E = (float*)(base + b_type);
+  float* d_eta = (float*)(base + b_type + b_f);
+  float* d_phi = (float*)(base + b_type + 2 * b_f);
+  int64_t* d_off = (int64_t*)(base + b_type + 3 * b_f);
+  int64_t* d_oout = (int64_t*)(base + b_type + 3 * b_f + b_off);
+  int32_t* d_ids = (int32_t*)(base + b_type + 3 * b_f + 2 * b_off);
+  float* d_cE = (float*)(base + b_type + 3 * b_f + 2 * b_off + b_ids);
+  FCS_CUDA(cudaMemcpyAsync(d_type, type, n_particles * 4, cudaMemcpyHostToDevice, s));
+  FCS_CUDA(cudaMemcpyAsync(d_E, E, n_particles * 4, cudaMemcpyHostToDevice, s));
+  FCS_CUDA(cudaMemcpyAsync(d_eta, eta, n_particles * 4, cudaMemcpyHostToDevice, s));
+  FCS_CUDA(cudaMemcpyAsync(d_phi, phi, n_particles * 4, cudaMemcpyHostToDevice, s));
+  FCS_CUDA(cudaMemcpyAsync(d_off, event_offsets, (size_t)(n_events + 1) * 8, cudaMemcpyHostToDevice, s));
+  fcs_particles parts{d_type, d_E, d_eta, d_phi, d_off};
+  fcs_stats st{};
+  const int rc = fcs_simulate_events(geo, prm, ws, &parts, n_particles, n_events, seed, first_event, &cfg, nullptr,
+                                     cell_ids ? d_ids : nullptr, cell_ids ? d_cE : nullptr, d_oout, capacity, &st,
+                                     nullptr, s);
+  if (stats) *stats = st;
+  if (rc != FCS_OK && rc != FCS_E_RANGE && rc != FCS_E_DEVICE_CHECK) return rc;
+  const int64_t n_out = std::min<int64_t>(st.n_nonzero, capacity);
+  FCS_CUDA(cudaMemcpyAsync(event_offsets_out, d_oout, (size_t)(n_events + 1) * 8, cudaMemcpyDeviceToHost, s));
+  if (cell_ids && n_out > 0) {
+    FCS_CUDA(cudaMemcpyAsync(cell_ids, d_ids, n_out * 4, cudaMemcpyDeviceToHost, s));
+    FCS_CUDA(cudaMemcpyAsync(cell_E, d_cE, n_out * 4, cudaMemcpyDeviceToHost, s));
+  }
+  FCS_CUDA(cudaStreamSynchronize(s));
+  if (rc != FCS_OK) return rc;
+  return ok();
+}
+
+int fcs_simulate_backward(const fcs_geo*, const fcs_params*, fcs_workspace*, const fcs_particles*, int64_t, int32_t,
+                          uint64_t, int64_t, const fcs_config*, const float*, float*, float*, cudaStream_t) {
+  return set_err(FCS_E_UNSUPPORTED, "fcs_simulate_backward is not implemented yet");
+}
+
+}  // extern "C"

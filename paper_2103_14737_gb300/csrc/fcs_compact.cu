@@ -1,0 +1,119 @@
+// fcs_compact.cu - gathers the hit cells of each event as (cell id, E) pairs
+// for the transfer of results (the paper's sim_ct kernel, Sec. 4) and resets
+// the accumulation rows to zero in the same pass (the paper's separate
+// clean kernel, Sec. 4, is folded in).  Output order: event-major, ascending
+// cell id; offsets come from an exclusive scan of per-chunk counts, so the
+// result is deterministic.
+#include "fcs_internal.cuh"
+
+namespace fcs {
+namespace {
+
+constexpr int kCThreads = 256;
+constexpr int kCItems = 8;  // two float4 per thread
+constexpr int kChunk = kCThreads * kCItems;
+
+__global__ void __launch_bounds__(kCThreads) k_compact_count(const float* __restrict__ acc, int32_t n_cells,
+                                                           int32_t stride, int32_t cpr,
+                                                           int64_t* __restrict__ counts) {
+  const int chunk = blockIdx.x, row = blockIdx.y;
+  const int64_t c0 = (int64_t)chunk * kChunk + threadIdx.x * kCItems;
+  const float4* src = reinterpret_cast<const float4*>(acc + (int64_t)row * stride + c0);
+  int cnt = 0;
+  if (c0 < n_cells) {
+    const float4 a = src[0], b = src[1];
+    const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int k = 0; k < kCItems; ++k) cnt += (c0 + k < n_cells) && (v[k] != 0.0f);
+  }
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  __shared__ int s[kCThreads / 32];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int i = 0; i < kCThreads / 32; ++i) t += s[i];
+    counts[(int64_t)row * cpr + chunk] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kCThreads) k_compact_write(
+    float* __restrict__ acc, int32_t n_cells, int32_t stride, int32_t cpr, int32_t ev_lo,
+    const int64_t* __restrict__ offsets, float* __restrict__ cells_out, int32_t* __restrict__ cell_ids,
+    float* __restrict__ cell_E, int64_t* __restrict__ event_offsets_out, int64_t capacity) {
+  const int chunk = blockIdx.x, row = blockIdx.y;
+  const int64_t c0 = (int64_t)chunk * kChunk + threadIdx.x * kCItems;
+  float4* src = reinterpret_cast<float4*>(acc + (int64_t)row * stride + c0);
+  float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (c0 < n_cells) {
+    const float4 a = src[0], b = src[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    src[0] = z;
+    src[1] = z;
+  }
+  unsigned mask = 0;
+#pragma unroll
+  for (int k = 0; k < kCItems; ++k)
+    if (c0 + k < n_cells && v[k] != 0.0f) mask |= 1u << k;
+  const int cnt = __popc(mask);
+  // block exclusive scan of cnt
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  __shared__ int s_w[kCThreads / 32];
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  int pre = 0;
+  for (int w = 0; w < warp; ++w) pre += s_w[w];
+  int64_t pos = offsets[(int64_t)row * cpr + chunk] + pre + x - cnt;
+#pragma unroll
+  for (int k = 0; k < kCItems; ++k) {
+    if (mask & (1u << k)) {
+      if (pos < capacity) {
+        if (cell_ids) cell_ids[pos] = (int32_t)(c0 + k);
+        if (cell_E) cell_E[pos] = v[k];
+      }
+      ++pos;
+    }
+  }
+  if (cells_out && c0 < n_cells) {
+    float* dst = cells_out + (int64_t)(ev_lo + row) * n_cells + c0;
+#pragma unroll
+    for (int k = 0; k < kCItems; ++k)
+      if (c0 + k < n_cells) dst[k] = v[k];
+  }
+  if (chunk == 0 && threadIdx.x == 0 && event_offsets_out)
+    event_offsets_out[ev_lo + row] = offsets[(int64_t)row * cpr];
+}
+
+}  // namespace
+
+cudaError_t launch_compact(const GeoDev& g, WsDev w, int32_t rows, int32_t ev_lo, int64_t* chunk_counts,
+                           int64_t* chunk_offsets, ScanTmp tmp, float* cells_out, int32_t* cell_ids,
+                           float* cell_E, int64_t* event_offsets_out, int32_t n_events_total,
+                           int64_t capacity, const Launch& L) {
+  (void)n_events_total;
+  if (rows <= 0) return cudaSuccess;
+  const int cpr = (g.n_cells + kChunk - 1) / kChunk;
+  const dim3 grid(cpr, rows);
+  k_compact_count<<<grid, kCThreads, 0, L.s>>>(w.acc, g.n_cells, g.acc_stride, cpr, chunk_counts);
+  // offsets continue the call's running output size (per-event mode)
+  cudaError_t e = launch_scan_i64(chunk_counts, chunk_offsets, nullptr, (int64_t)rows * cpr,
+                                  &w.sizes->nnz_total, 1, tmp, L.s);
+  if (e != cudaSuccess) return e;
+  k_compact_write<<<grid, kCThreads, 0, L.s>>>(w.acc, g.n_cells, g.acc_stride, cpr, ev_lo, chunk_offsets,
+                                               cells_out, cell_ids, cell_E, event_offsets_out, capacity);
+  return cudaGetLastError();
+}
+
+int64_t compact_chunks(int32_t n_cells, int32_t rows) {
+  return (int64_t)rows * ((n_cells + kChunk - 1) / kChunk);
+}
+
+}  // namespace fcs

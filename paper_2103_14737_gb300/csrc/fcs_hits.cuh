@@ -1,0 +1,391 @@
+// fcs_hits.cuh - the per-hit kernel of the hit loop (Listing 1: simulate_hit
+// chain; Listing 2: HitCellMapping_d / getDDE + atomicAdd).
+//
+// One thread per hit as in the paper's sim_a kernel (Sec. 4), but persistent:
+// CTAs take tiles of BLOCK * HPT consecutive hits from an atomic work queue
+// over the whole batch (the grouped simulation of Sec. 4 at batch scale); a
+// tile's task records are staged in shared memory and each hit finds its task
+// through a block max-scan of task start positions.  Per hit:
+//   Philox4x32-10 block (hit, layer, particle, event)        -> 4 words
+//   word 0: shape bin by guide table + binary search          (integer, exact)
+//   words 1, 2: uniform position in the (r, alpha) bin        (FP32)
+//   (r, alpha) -> (eta, phi) linear map around the task centre (FP32, __sincosf)
+//   region search + grid index                                 (FP32)
+// The FP32 result is certified against a rigorous error bound; a hit whose
+// eta or phi lies within the bound of a cell or region edge is queued and
+// decided by the FP64 recheck kernel, which repeats the oracle's FP64 steps
+// (the paper's two FP32 cell mismatches in 62M hits were removed with FP64,
+// Sec. 6).  Certified hits are deposited with warp-aggregated float atomics
+// (Sec. 4 chose atomicAdd) or, in deterministic mode, emitted as
+// (cell, task, count) records for the sort-by-cell reduction.
+#pragma once
+
+#include "fcs_internal.cuh"
+
+namespace fcs {
+
+constexpr int kSmemTasks = 256;
+
+struct HitKParams {
+  GeoDev g;
+  ParamDev p;
+  WsDev w;
+  int32_t ev_lo;
+  uint32_t k0, k1;
+  uint32_t first_event_lo;
+  int32_t key_task_bits;
+  int32_t* dbg_hit_cell;
+  int16_t* dbg_hit_bin;
+  int64_t dbg_hit_cap;
+};
+
+// ---- shape bin: inverse CDF by guide table and binary search --------------
+__device__ __forceinline__ int sample_bin(const ParamDev& p, int32_t entry, uint32_t x0) {
+  const uint16_t gg = __ldg(p.guide + (size_t)entry * kGuideCells + (x0 >> 25));
+  int lo = gg & 0xFF, hi = gg >> 8;
+  const uint32_t* T = p.thr + (size_t)entry * kNBins;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (x0 < __ldg(T + mid)) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// ---- FP64 path: the oracle's steps, each rounding once ----------------------
+__device__ __forceinline__ void scales64(const GeoDev& g, int layer, double eta_c, double* s_eta,
+                                         double* s_phi) {
+  const double R = g.rz[layer];
+  if (g.barrel[layer]) {
+    *s_phi = __ddiv_rn(1.0, R);
+    *s_eta = __ddiv_rn(1.0, __dmul_rn(R, cosh(eta_c)));
+  } else {
+    const double ae = fabs(eta_c);
+    const double sh = sinh(ae);
+    const double m = __ddiv_rn(__dmul_rn(tanh(ae), sh), R);
+    *s_phi = __ddiv_rn(sh, R);
+    *s_eta = (eta_c < 0.0) ? m : -m;
+  }
+}
+
+__device__ __forceinline__ int32_t lookup64(const GeoDev& g, int layer, double eta, double phi) {
+  const int rb = g.lrb[layer], re = g.lrb[layer + 1];
+  int r = rb;
+  for (int k = rb + 1; k < re; ++k)
+    if (eta >= g.split[k]) r = k;
+  const int ne = g.n_eta[r], np = g.n_phi[r];
+  const double te = __ddiv_rn(__dsub_rn(eta, g.eta_lo[r]), g.deta[r]);
+  int64_t ie;
+  if (!(te >= 0.0)) ie = 0;  // also NaN
+  else if (te >= (double)ne) ie = ne - 1;
+  else ie = (int64_t)floor(te);
+  if (ie > ne - 1) ie = ne - 1;
+  double tp = __ddiv_rn(__dsub_rn(phi, g.phi_lo[r]), g.dphi[r]);
+  const double lim = 4503599627370496.0;
+  if (tp > lim) tp = lim;
+  if (!(tp >= -lim)) tp = -lim;  // also NaN
+  int64_t ip = (int64_t)floor(tp) % (int64_t)np;
+  if (ip < 0) ip += np;
+  return g.cell_off[r] + (int32_t)ie * np + (int32_t)ip;
+}
+
+static __device__ __noinline__ int32_t cell_fp64(const GeoDev& g, const ParamDev& p, const TaskRec& T,
+                                          uint4 x, int bin) {
+  const int ir = bin >> 3, ia = bin & 7;
+  const double r_lo = (double)p.r_edges[ir], r_hi = (double)p.r_edges[ir + 1];
+  const double a_lo = (double)p.a_edges[ia], a_hi = (double)p.a_edges[ia + 1];
+  const double r = __dadd_rn(r_lo, __dmul_rn(u24d(x.y), __dsub_rn(r_hi, r_lo)));
+  const double alpha = __dadd_rn(a_lo, __dmul_rn(u24d(x.z), __dsub_rn(a_hi, a_lo)));
+  double s_eta, s_phi;
+  scales64(g, T.layer, (double)T.eta_c, &s_eta, &s_phi);
+  const double deta = __dmul_rn(__dmul_rn(r, cos(alpha)), s_eta);
+  const double dphi = __dmul_rn(__dmul_rn(r, sin(alpha)), s_phi);
+  const double eta = __dadd_rn((double)T.eta_c, deta);
+  const double phi = __dadd_rn((double)T.phi_c, dphi);
+  return lookup64(g, T.layer, eta, phi);
+}
+
+// ---- shared tables of a CTA ---------------------------------------------------
+struct HitSmemTables {
+  RegionF reg[kMaxRegions];
+  int32_t lrb[kMaxLayers + 1];
+  float rlo[kNR], rw[kNR], rhi[kNR];
+  float alo[kNA], aw[kNA];  // alpha_lo - pi and bin widths
+};
+
+__device__ __forceinline__ void load_tables(HitSmemTables& t, const GeoDev& g, const ParamDev& p) {
+  for (int i = threadIdx.x; i < g.n_regions; i += blockDim.x) t.reg[i] = g.regf[i];
+  for (int i = threadIdx.x; i <= g.n_layers; i += blockDim.x) t.lrb[i] = g.lrb[i];
+  if (threadIdx.x < kNR) {
+    const float lo = p.r_edges[threadIdx.x], hi = p.r_edges[threadIdx.x + 1];
+    t.rlo[threadIdx.x] = lo;
+    t.rw[threadIdx.x] = hi - lo;
+    t.rhi[threadIdx.x] = hi;
+  }
+  if (threadIdx.x < kNA) {
+    const double lo = p.a_edges[threadIdx.x], hi = p.a_edges[threadIdx.x + 1];
+    t.alo[threadIdx.x] = (float)(lo - 3.141592653589793);
+    t.aw[threadIdx.x] = (float)(hi - lo);
+  }
+}
+
+// ---- FP32 fast path --------------------------------------------------------
+// Error bound of the FP32 eta (and likewise phi) against the FP64 value:
+//   cos/sin: |alpha32 - alpha| <= ~2^-21.4 (alpha - pi in [-pi, pi] from an
+//     FMA of FP32 table values) and __sincosf's documented absolute error on
+//     [-pi, pi] (2^-21.19 for cos, 2^-21.41 for sin): <= 2^-20.4 in all;
+//   r32 <= r_hi * 2^-23 off; s32 (coshf/sinhf/tanhf, a few ulp) <= 2^-21
+//     relative; the two products 2 * 2^-24 relative:
+//   => |deta32 - deta| <= r_hi |s_eta| 2^-19.5; bound used: r_hi |s| 2^-17;
+//   the final add rounds by |eta| 2^-24; bound used: |eta| 2^-21.
+// A decision is certified when the FP32 value is farther than the bound
+// (plus the FP32 rounding of the boundary and of the scaled index) from the
+// boundary it is compared with.
+struct FastHit {
+  int32_t cell;
+  bool sure;
+};
+
+__device__ __forceinline__ FastHit fast_cell(const HitSmemTables& tb, const TaskRec& T, uint4 x,
+                                             int bin) {
+  const int ir = bin >> 3, ia = bin & 7;
+  const float ur = u24f(x.y), ua = u24f(x.z);
+  const float r = fmaf(ur, tb.rw[ir], tb.rlo[ir]);
+  const float ap = fmaf(ua, tb.aw[ia], tb.alo[ia]);  // alpha - pi
+  float sn, cs;
+  __sincosf(ap, &sn, &cs);
+  const float de = (r * -cs) * T.s_eta;
+  const float dp = (r * -sn) * T.s_phi;
+  const float eta = T.eta_c + de;
+  const float phi = T.phi_c + dp;
+  const float rh = tb.rhi[ir];
+  const float be = fmaf(rh * fabsf(T.s_eta), 0x1p-17f, fabsf(eta) * 0x1p-21f);
+  const float bp = fmaf(rh * fabsf(T.s_phi), 0x1p-17f, fabsf(phi) * 0x1p-21f);
+  bool sure = (fabsf(eta) < 1.0e30f) && (fabsf(phi) < 1.0e30f);
+  const int rb = tb.lrb[T.layer], re = tb.lrb[T.layer + 1];
+  int rr = rb;
+  for (int q = rb + 1; q < re; ++q) {
+    const float sp = tb.reg[q].split;
+    if (eta >= sp) rr = q;
+    sure &= fabsf(eta - sp) > fmaf(fabsf(sp), 0x1p-23f, be);
+  }
+  const RegionF R = tb.reg[rr];
+  const float te = (eta - R.eta_lo) * R.inv_deta;
+  const float ke = rintf(te);
+  const float ee = fmaf(fmaf(fabsf(R.eta_lo), 0x1p-23f, be), R.inv_deta, fmaf(fabsf(te), 0x1p-21f, 0x1p-22f));
+  if (ke >= 1.0f && ke <= (float)(R.n_eta - 1)) sure &= fabsf(te - ke) > ee;
+  int ie = (int)floorf(te);
+  ie = min(max(ie, 0), R.n_eta - 1);
+  const float tp = (phi - R.phi_lo) * R.inv_dphi;
+  const float kp = rintf(tp);
+  const float ep = fmaf(fmaf(fabsf(R.phi_lo), 0x1p-23f, bp), R.inv_dphi, fmaf(fabsf(tp), 0x1p-21f, 0x1p-22f));
+  sure &= fabsf(tp - kp) > ep;
+  int ip = (int)floorf(tp) % R.n_phi;
+  if (ip < 0) ip += R.n_phi;
+  FastHit f;
+  f.cell = R.cell_off + ie * R.n_phi + ip;
+  f.sure = sure;
+  return f;
+}
+
+// ---- warp-level deposit / record emission -----------------------------------
+__device__ __forceinline__ void deposit_warp(bool ok, unsigned long long key, float* dst, float Ehit) {
+  const unsigned m = __ballot_sync(0xffffffffu, ok);
+  if (ok) {
+    const unsigned peers = __match_any_sync(m, key);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(dst, __fmul_rn((float)__popc(peers), Ehit));
+  }
+}
+
+__device__ __forceinline__ void emit_warp(bool ok, unsigned long long gkey, const WsDev& w) {
+  const int lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(0xffffffffu, ok);
+  unsigned peers = 0;
+  if (ok) peers = __match_any_sync(m, gkey);
+  const bool lead = ok && (lane == __ffs(peers) - 1);
+  const unsigned lm = __ballot_sync(0xffffffffu, lead);
+  if (lm == 0) return;
+  unsigned long long base = 0;
+  const int l0 = __ffs(lm) - 1;
+  if (lane == l0) base = atomicAdd((unsigned long long*)&w.sizes->n_records, (unsigned long long)__popc(lm));
+  base = __shfl_sync(0xffffffffu, base, l0);
+  if (lead) {
+    const unsigned long long pos = base + __popc(lm & ((1u << lane) - 1u));
+    if (pos < (unsigned long long)w.rec_cap)
+      w.keys[pos] = (gkey << kRecordCountBits) | (unsigned long long)(__popc(peers) - 1);
+    else
+      atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_HIT_CAPACITY);
+  }
+}
+
+__device__ __forceinline__ void deposit_single(const HitKParams& kp, const TaskRec& T, int64_t task_rel,
+                                               int32_t cell, bool det) {
+  const int64_t row = T.event - kp.ev_lo;
+  if (!det) {
+    atomicAdd(kp.w.acc + row * kp.g.acc_stride + cell, T.Ehit);
+  } else {
+    const unsigned long long gkey =
+        ((unsigned long long)(row * kp.g.n_cells + cell) << kp.key_task_bits) | (unsigned long long)task_rel;
+    const unsigned long long pos = atomicAdd((unsigned long long*)&kp.w.sizes->n_records, 1ull);
+    if (pos < (unsigned long long)kp.w.rec_cap) kp.w.keys[pos] = gkey << kRecordCountBits;
+    else atomicOr(&kp.w.sizes->flags, (uint32_t)FCS_FLAG_HIT_CAPACITY);
+  }
+}
+
+// ---- block max-scan of the tile's task-start marks ------------------------------
+template <int BLOCK, int HPT>
+__device__ __forceinline__ void owner_scan(int16_t* s_owner, int* s_wmax) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int v[HPT];
+  int run = 0;
+#pragma unroll
+  for (int k = 0; k < HPT; ++k) {
+    run = max(run, (int)s_owner[tid * HPT + k]);
+    v[k] = run;
+  }
+  int x = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x = max(x, y);
+  }
+  if (lane == 31) s_wmax[warp] = x;
+  __syncthreads();
+  int prefix = 0;
+  for (int w = 0; w < warp; ++w) prefix = max(prefix, s_wmax[w]);
+  int excl = __shfl_up_sync(0xffffffffu, x, 1);
+  if (lane == 0) excl = 0;
+  excl = max(excl, prefix);
+#pragma unroll
+  for (int k = 0; k < HPT; ++k) s_owner[tid * HPT + k] = (int16_t)max(v[k], excl);
+}
+
+template <int BLOCK, int HPT, bool DET>
+__global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKParams kp) {
+  constexpr int TILE = BLOCK * HPT;
+  static_assert(TILE % kGranule == 0, "tiles must start on granules");
+  static_assert(TILE < 32768, "owner index is int16");
+  __shared__ HitSmemTables tb;
+  __shared__ __align__(16) TaskRec s_task[kSmemTasks];
+  __shared__ int16_t s_owner[TILE];
+  __shared__ int s_wmax[BLOCK / 32];
+  __shared__ unsigned long long s_tile;
+  load_tables(tb, kp.g, kp.p);
+  const WsDev& w = kp.w;
+  const int64_t H = w.sizes->n_hits;
+  const int64_t T_all = w.sizes->n_tasks;
+  if (H > w.gmap_cap * (int64_t)kGranule) return;  // flagged by the granule map
+  const unsigned long long n_tiles = (unsigned long long)((H + TILE - 1) / TILE);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t hit_dbg_base = kp.dbg_hit_cell || kp.dbg_hit_bin ? w.sizes->hit_base : 0;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&w.sizes->queue, 1ull);
+  __syncthreads();
+  unsigned long long tile = s_tile;
+  while (tile < n_tiles) {
+    __syncthreads();  // everyone has read s_tile
+    if (threadIdx.x == 0) s_tile = atomicAdd(&w.sizes->queue, 1ull);
+    const int64_t h0 = (int64_t)tile * TILE;
+    const int64_t hN = min(h0 + (int64_t)TILE, H);
+    const int32_t t0 = w.gmap[h0 / kGranule];
+    const int32_t t1 = (hN < H) ? w.gmap[hN / kGranule] : (int32_t)(T_all - 1);
+    const int nt = t1 - t0 + 1;
+    const TaskRec* tp;
+    if (nt <= kSmemTasks) {
+      const int4* src = reinterpret_cast<const int4*>(w.tasks + t0);
+      int4* dst = reinterpret_cast<int4*>(s_task);
+      for (int q = threadIdx.x; q < nt * 3; q += BLOCK) dst[q] = __ldg(src + q);
+      tp = s_task;
+    } else {
+      tp = w.tasks + t0;
+    }
+    for (int i = threadIdx.x; i < TILE; i += BLOCK) s_owner[i] = 0;
+    __syncthreads();
+    for (int j = threadIdx.x + 1; j < nt; j += BLOCK) {
+      const int64_t s = w.tasks[t0 + j].hit_begin - h0;
+      if (s < TILE) s_owner[s] = (int16_t)j;
+    }
+    __syncthreads();
+    owner_scan<BLOCK, HPT>(s_owner, s_wmax);
+    __syncthreads();
+#pragma unroll 1
+    for (int k = 0; k < HPT; ++k) {
+      const int i = warp * 32 * HPT + k * 32 + lane;
+      const int64_t h = h0 + i;
+      const bool valid = h < hN;
+      const int tl = valid ? s_owner[i] : 0;
+      const TaskRec T = tp[tl];
+      const uint32_t hit = (uint32_t)(h - T.hit_begin);
+      const uint4 x = philox4x32_10(
+          make_uint4(hit, (uint32_t)T.layer | (kPurposeHit << 16), (uint32_t)T.particle,
+                     kp.first_event_lo + (uint32_t)T.event),
+          kp.k0, kp.k1);
+      const int bin = sample_bin(kp.p, T.entry, x.x);
+      const FastHit f = fast_cell(tb, T, x, bin);
+      const bool ok = valid && f.sure;
+      const bool need = valid && !f.sure;
+      const int64_t row = T.event - kp.ev_lo;
+      if (!DET) {
+        deposit_warp(ok, ((unsigned long long)(uint32_t)tl << 32) | (uint32_t)f.cell,
+                     w.acc + row * kp.g.acc_stride + f.cell, T.Ehit);
+      } else {
+        const unsigned long long gkey =
+            ((unsigned long long)(row * kp.g.n_cells + f.cell) << kp.key_task_bits) |
+            (unsigned long long)(t0 + tl);
+        emit_warp(ok, gkey, w);
+      }
+      // queue the uncertain hits for the FP64 recheck
+      const unsigned m = __ballot_sync(0xffffffffu, need);
+      if (m) {
+        unsigned long long base = 0;
+        const int l0 = __ffs(m) - 1;
+        if (lane == l0) base = atomicAdd((unsigned long long*)&w.sizes->n_recheck, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, l0);
+        if (need) {
+          const unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
+          if (pos < (unsigned long long)w.recheck_cap) {
+            w.recheck[pos] = make_uint2((uint32_t)(t0 + tl), hit);
+          } else {
+            const int32_t c = cell_fp64(kp.g, kp.p, T, x, bin);
+            deposit_single(kp, T, t0 + tl, c, DET);
+            atomicAdd((unsigned long long*)&w.sizes->n_inline, 1ull);
+            atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_RECHECK_SPILL);
+            if (kp.dbg_hit_cell && hit_dbg_base + h < kp.dbg_hit_cap) kp.dbg_hit_cell[hit_dbg_base + h] = c;
+          }
+        }
+      }
+      if (valid && hit_dbg_base + h < kp.dbg_hit_cap) {
+        if (kp.dbg_hit_cell && f.sure) kp.dbg_hit_cell[hit_dbg_base + h] = f.cell;
+        if (kp.dbg_hit_bin) kp.dbg_hit_bin[hit_dbg_base + h] = (int16_t)bin;
+      }
+    }
+    __syncthreads();  // the tile's shared data is dead; s_tile holds the next tile
+    tile = s_tile;
+  }
+}
+
+// FP64 recheck of the queued hits (grid-stride over the queue).
+template <bool DET>
+__global__ void __launch_bounds__(128) k_recheck(const __grid_constant__ HitKParams kp) {
+  const WsDev& w = kp.w;
+  const int64_t n = min(w.sizes->n_recheck, w.recheck_cap);
+  const int64_t hit_dbg_base = kp.dbg_hit_cell ? w.sizes->hit_base : 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint2 q = w.recheck[i];
+    const TaskRec T = w.tasks[q.x];
+    const uint4 x = philox4x32_10(
+        make_uint4(q.y, (uint32_t)T.layer | (kPurposeHit << 16), (uint32_t)T.particle,
+                   kp.first_event_lo + (uint32_t)T.event),
+        kp.k0, kp.k1);
+    const int bin = sample_bin(kp.p, T.entry, x.x);
+    const int32_t c = cell_fp64(kp.g, kp.p, T, x, bin);
+    deposit_single(kp, T, q.x, c, DET);
+    const int64_t h = hit_dbg_base + T.hit_begin + q.y;
+    if (kp.dbg_hit_cell && h < kp.dbg_hit_cap) kp.dbg_hit_cell[h] = c;
+  }
+}
+
+template <bool DET>
+cudaError_t launch_hits_t(const HitKParams& kp, const HitCfg& hc, const Launch& L);
+
+}  // namespace fcs

@@ -1,0 +1,201 @@
+// fcs_internal.cuh - device data layout and launcher declarations shared by
+// the translation units of libfcs (not part of the public ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fcs.h"
+
+namespace fcs {
+
+constexpr int kMaxLayers = 32;
+constexpr int kMaxRegions = 256;
+constexpr int kNBins = 128;      // 16 r-bins x 8 alpha-bins
+constexpr int kNR = 16;
+constexpr int kNA = 8;
+constexpr int kGuideCells = 128; // guide cells per histogram (top 7 bits of word 0)
+constexpr int kGranule = 128;    // hits per granule of the tile -> task map (divides every tile)
+constexpr int kRecordCountBits = 5;  // deterministic mode: count - 1 in the low 5 bits
+
+// Task record: one (event, particle, layer) of the hit loop of Listing 1.
+// 48 bytes; tasks are stored in (event, particle, layer) order and hits of a
+// task are the global hit numbers [hit_begin, hit_begin + n).
+struct __align__(16) TaskRec {
+  int64_t hit_begin;
+  int32_t n;        // hits (>= 1)
+  int32_t entry;    // parametrisation entry including the layer
+  float Ehit;       // hit energy, MeV (Listing 1: float Ehit = E(layer) / nhit)
+  float eta_c, phi_c;
+  float s_eta, s_phi;  // FP32 scale factors of the (r, alpha) -> (eta, phi) map
+  int32_t particle;    // index within the event
+  int32_t event;       // batch-local event index
+  int32_t layer;
+};
+static_assert(sizeof(TaskRec) == 48, "TaskRec layout");
+
+// FP32 view of a region for the fast path (shared-memory staged).
+struct RegionF {
+  float eta_lo, inv_deta, phi_lo, inv_dphi;
+  float split;  // lower ownership boundary (FP32 of the FP64 midpoint); -inf for a layer's first
+  int32_t n_eta, n_phi, cell_off;
+};
+static_assert(sizeof(RegionF) == 32, "RegionF layout");
+
+// Device geometry (all pointers device memory owned by fcs_geo).
+struct GeoDev {
+  int32_t n_layers, n_regions, n_cells, acc_stride;
+  const RegionF* regf;
+  const double* eta_lo;  // FP64 copies for the recheck path
+  const double* deta;
+  const double* phi_lo;
+  const double* dphi;
+  const double* split;   // split[r] for r > layer's first region
+  const int32_t* n_eta;
+  const int32_t* n_phi;
+  const int32_t* cell_off;
+  const int32_t* lrb;    // [n_layers + 1]
+  const double* rz;      // [n_layers]
+  const int32_t* barrel; // [n_layers]
+};
+
+// Device parametrisation.
+struct ParamDev {
+  int32_t NT, NE, NH, NL;
+  double eta_scale;
+  int32_t ebin_min;
+  int32_t n_entries;     // NT * NE * NH * NL
+  const float* frac;     // [n_entries]
+  const float* mhe;      // [n_entries]
+  const uint32_t* thr;   // [n_entries][128] inverse-CDF thresholds
+  const uint16_t* guide; // [n_entries][128]: lo | hi << 8 search bounds per guide cell
+  const float* r_edges;  // [17]
+  const float* a_edges;  // [9]
+};
+
+// Device-side sizes and status of one call (in the workspace).
+struct Sizes {
+  int64_t n_tasks;
+  int64_t n_hits;
+  int64_t n_recheck;    // entries appended to the recheck queue (may exceed its capacity)
+  int64_t n_records;    // deterministic mode records
+  int64_t nnz;          // non-zero cells of the current event range
+  int64_t nnz_total;    // running output size over the call (per-event mode)
+  int64_t n_inline;     // recheck hits done inline because the queue was full
+  int64_t task_base;    // tasks / hits of the earlier event ranges of the call
+  int64_t hit_base;     //   (per-event mode; offsets of the debug dumps)
+  int64_t recheck_total;  // recheck hits over the call
+  int64_t n_part;       // particles of the current event range (checked against the capacity)
+  int64_t n_rec_used;   // deterministic records sorted (n_records clamped to the capacity)
+  unsigned long long queue;  // hit-kernel work-queue counter (tiles handed out)
+  uint32_t flags;       // fcs_device_flag bits
+  uint32_t pad;
+};
+static_assert(sizeof(Sizes) % 8 == 0 && offsetof(Sizes, queue) % 8 == 0, "Sizes layout");
+
+// Workspace views passed to kernels.
+struct WsDev {
+  Sizes* sizes;
+  int32_t* nl;         // [pcap][NL] hits per (particle, layer), 0 = no task
+  int64_t* pcount;     // [2][pcap] tasks, hits per particle
+  int64_t* poff;       // [2][pcap] exclusive offsets
+  int64_t pcap;        // particle capacity
+  TaskRec* tasks;      // [task_cap]
+  int32_t* gmap;       // [gmap_cap] granule -> task
+  uint2* recheck;      // [recheck_cap] (task, hit in task)
+  float* acc;          // [rows][acc_stride] zero-maintained accumulation rows
+  int64_t task_cap, gmap_cap, recheck_cap, rows_cap;
+  uint64_t* keys;      // deterministic mode records [rec_cap]
+  uint64_t* keys_alt;  // ping-pong buffer [rec_cap]
+  int64_t rec_cap;
+};
+
+// Philox4x32-10 (Salmon et al., SC'11): published multipliers and Weyl
+// constants; counter c, key (k0, k1).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Counter layout of the method's random streams:
+// (index, layer | purpose << 16, particle in event, event).
+constexpr uint32_t kPurposeHit = 0u;
+constexpr uint32_t kPurposePoisson = 1u;
+
+__device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
+  return __dmul_rn(__dadd_rn(__dmul_rn((double)(a >> 5), 67108864.0), (double)(b >> 6)),
+                   1.0 / 9007199254740992.0);
+}
+__device__ __forceinline__ double u24d(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+__device__ __forceinline__ float u24f(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+
+// ---- launchers (host) -------------------------------------------------------
+struct Launch {
+  cudaStream_t s;
+  int num_sms;
+};
+
+// fcs_params.cu
+cudaError_t launch_build_tables(const float* shape_w, int n_entries, uint32_t* thr, uint16_t* guide,
+                                int32_t* bad, cudaStream_t s);
+
+// fcs_scan.cu: exclusive scan of n int64 values (n on the host or device).
+struct ScanTmp {
+  int64_t* block_sums;  // [kScanBlocks + 1]
+};
+constexpr int kScanBlocks = 512;
+cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, const int64_t* n_dev, int64_t n_host,
+                            int64_t* total_dst, int64_t total_add_base_from_dst, ScanTmp tmp,
+                            cudaStream_t s);
+
+// fcs_tasks.cu
+cudaError_t launch_particle_tasks(const GeoDev& g, const ParamDev& p, const fcs_particles& parts,
+                                  int32_t ev_lo, int32_t ev_hi, uint32_t k0, uint32_t k1,
+                                  int64_t first_event, WsDev w, const Launch& L);
+cudaError_t launch_task_write(const GeoDev& g, const ParamDev& p, const fcs_particles& parts,
+                              int32_t ev_lo, int32_t ev_hi, WsDev w, const fcs_debug* dbg,
+                              const Launch& L);
+cudaError_t launch_granule_map(WsDev w, const Launch& L);
+
+// fcs_hits.cu
+struct HitCfg {
+  int block;
+  int hpt;
+  int det;  // deterministic (record) mode
+};
+cudaError_t launch_hits(const GeoDev& g, const ParamDev& p, WsDev w, int32_t ev_lo, uint32_t k0,
+                        uint32_t k1, int64_t first_event, const HitCfg& hc, int key_task_bits,
+                        const fcs_debug* dbg, const Launch& L);
+cudaError_t launch_recheck(const GeoDev& g, const ParamDev& p, WsDev w, int32_t ev_lo, uint32_t k0,
+                           uint32_t k1, int64_t first_event, int det, int key_task_bits,
+                           const fcs_debug* dbg, const Launch& L);
+int hits_max_smem_tasks();
+
+// fcs_compact.cu
+cudaError_t launch_compact(const GeoDev& g, WsDev w, int32_t rows, int32_t ev_lo,
+                           int64_t* chunk_counts, int64_t* chunk_offsets, ScanTmp tmp,
+                           float* cells_out, int32_t* cell_ids, float* cell_E,
+                           int64_t* event_offsets_out, int32_t n_events_total, int64_t capacity,
+                           const Launch& L);
+
+// fcs_sort.cu
+int64_t compact_chunks(int32_t n_cells, int32_t rows);
+cudaError_t launch_det_reduce(const GeoDev& g, WsDev w, int32_t rows, int32_t ev_lo,
+                              int key_task_bits, int key_total_bits, uint32_t* unused,
+                              int64_t hist_cap, int64_t* head_flags, int64_t* head_offsets,
+                              ScanTmp tmp, float* cells_out, int32_t* cell_ids, float* cell_E,
+                              int64_t* event_offsets_out, int32_t n_events_total,
+                              int64_t capacity, const Launch& L);
+int64_t det_hist_entries(int num_sms);
+
+}  // namespace fcs

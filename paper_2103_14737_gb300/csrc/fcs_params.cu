@@ -1,0 +1,80 @@
+// fcs_params.cu - builds the inverse-CDF thresholds and guide tables of the
+// shape histograms on the device (one thread per parametrisation entry).
+//
+// Thresholds: with C_k the FP64 left-to-right prefix sum of the first k
+// weights and K the last bin of non-zero weight, T[k] = min(2^32 - 1,
+// floor(2^32 C_{k+1} / C_128)) for k < K and 2^32 - 1 for k >= K.  The bin of
+// a 32-bit random word x is the first k < K with x < T[k], else K.
+//
+// Guide table (Chen and Asau's indexed search): for guide cell j (the words
+// with x >> 25 == j) lo_j is the bin of x = j << 25 and hi_j the bin of
+// x = (j + 1) << 25 (K for the last cell); the bin of every x in the cell lies
+// in [lo_j, hi_j], so a hit needs one guide load and a binary search over
+// hi_j - lo_j thresholds (usually none or one) instead of seven.
+#include "fcs_internal.cuh"
+
+namespace fcs {
+namespace {
+
+__global__ void k_build_tables(const float* __restrict__ shape_w, int n_entries,
+                               uint32_t* __restrict__ thr, uint16_t* __restrict__ guide,
+                               int32_t* __restrict__ bad) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_entries) return;
+  const float* w = shape_w + (int64_t)e * kNBins;
+  uint32_t* T = thr + (int64_t)e * kNBins;
+  uint16_t* G = guide + (int64_t)e * kGuideCells;
+  double C = 0.0;
+  int K = -1;
+  for (int k = 0; k < kNBins; ++k) {
+    const float wk = w[k];
+    C = __dadd_rn(C, (double)wk);
+    if (wk > 0.0f) K = k;
+  }
+  if (!(C > 0.0) || K < 0) {
+    for (int k = 0; k < kNBins; ++k) T[k] = 0xFFFFFFFFu;
+    for (int j = 0; j < kGuideCells; ++j) G[j] = 0;
+    bad[e] = 1;
+    return;
+  }
+  bad[e] = 0;
+  double c = 0.0;
+  for (int k = 0; k < kNBins; ++k) {
+    c = __dadd_rn(c, (double)w[k]);
+    if (k < K) {
+      double t = floor(__ddiv_rn(__dmul_rn(4294967296.0, c), C));
+      if (t > 4294967295.0) t = 4294967295.0;
+      T[k] = (uint32_t)t;
+    } else {
+      T[k] = 0xFFFFFFFFu;
+    }
+  }
+  // lo_j = first k < K with (j << 25) < T[k], else K (monotone sweep)
+  int k = 0;
+  int lo_prev = 0;
+  for (int j = 0; j <= kGuideCells; ++j) {
+    int lo;
+    if (j < kGuideCells) {
+      const uint32_t x = (uint32_t)j << 25;
+      while (k < K && x >= T[k]) ++k;
+      lo = k;
+    } else {
+      lo = K;
+    }
+    if (j > 0) G[j - 1] = (uint16_t)(lo_prev | (lo << 8));
+    lo_prev = lo;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_build_tables(const float* shape_w, int n_entries, uint32_t* thr, uint16_t* guide,
+                                int32_t* bad, cudaStream_t s) {
+  if (n_entries <= 0) return cudaSuccess;
+  const int threads = 128;
+  k_build_tables<<<(n_entries + threads - 1) / threads, threads, 0, s>>>(shape_w, n_entries, thr,
+                                                                         guide, bad);
+  return cudaGetLastError();
+}
+
+}  // namespace fcs

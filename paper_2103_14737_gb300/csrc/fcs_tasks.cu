@@ -1,0 +1,235 @@
+// fcs_tasks.cu - task build of the hit loop (Listing 1): per particle the
+// parametrisation entry, per layer the float layer energy, the Poisson hit
+// count (get_number_of_hits) and the float hit energy, then compacted task
+// records in (event, particle, layer) order and the tile -> task map.
+#include "fcs_internal.cuh"
+
+namespace fcs {
+namespace {
+
+// ---- Poisson draw (FP64; every step rounds as the oracle's C code) ----------
+// mu < 10: inversion by sequential search from p0 = exp(-mu).  mu >= 10:
+// PTRS, the transformed rejection with squeeze of Hoermann (1993).  Draw i of
+// a task is Philox block (i, layer | 1 << 16, particle, event); its words give
+// two 53-bit uniforms.  The bounds of both loops match the oracle.
+constexpr int kInvMax = 200;
+constexpr uint32_t kPtrsMaxIter = 64;
+
+__device__ __forceinline__ void draw_pair(uint32_t i, uint32_t layer, uint32_t particle,
+                                          uint32_t event, uint32_t k0, uint32_t k1, double* u,
+                                          double* v) {
+  const uint4 x = philox4x32_10(make_uint4(i, layer | (kPurposePoisson << 16), particle, event), k0, k1);
+  *u = u53(x.x, x.y);
+  *v = u53(x.z, x.w);
+}
+
+__device__ int64_t poisson_draw(double mu, uint32_t layer, uint32_t particle, uint32_t event,
+                                uint32_t k0, uint32_t k1) {
+  if (!(mu > 0.0)) return 0;
+  if (mu < 10.0) {
+    double u, v;
+    draw_pair(0u, layer, particle, event, k0, k1, &u, &v);
+    double p = exp(-mu);
+    double F = p;
+    int64_t k = 0;
+    while (u >= F && k < kInvMax) {
+      k += 1;
+      p = __ddiv_rn(__dmul_rn(p, mu), (double)k);
+      F = __dadd_rn(F, p);
+    }
+    return k;
+  }
+  const double slam = __dsqrt_rn(mu);
+  const double loglam = log(mu);
+  const double b = __dadd_rn(0.931, __dmul_rn(2.53, slam));
+  const double a = __dadd_rn(-0.059, __dmul_rn(0.02483, b));
+  const double invalpha = __dadd_rn(1.1239, __ddiv_rn(1.1328, __dsub_rn(b, 3.4)));
+  const double vr = __dsub_rn(0.9277, __ddiv_rn(3.6224, __dsub_rn(b, 2.0)));
+  for (uint32_t i = 0; i < kPtrsMaxIter; ++i) {
+    double u, V;
+    draw_pair(i, layer, particle, event, k0, k1, &u, &V);
+    const double U = __dsub_rn(u, 0.5);
+    const double us = __dsub_rn(0.5, fabs(U));
+    if (us <= 0.0) continue;
+    const double t = __dadd_rn(__dadd_rn(__dmul_rn(__dadd_rn(__ddiv_rn(__dmul_rn(2.0, a), us), b), U), mu), 0.43);
+    const double kd = floor(t);
+    if (us >= 0.07 && V <= vr) return (int64_t)kd;
+    if (kd < 0.0 || (us < 0.013 && V > us)) continue;
+    const double lhs = __dsub_rn(__dadd_rn(log(V), log(invalpha)),
+                                 log(__dadd_rn(__ddiv_rn(a, __dmul_rn(us, us)), b)));
+    const double rhs = __dsub_rn(__dadd_rn(-mu, __dmul_rn(kd, loglam)), lgamma(__dadd_rn(kd, 1.0)));
+    if (lhs <= rhs) return (int64_t)kd;
+  }
+  return (int64_t)floor(mu);
+}
+
+// Parametrisation entry of a particle (without the layer index).
+__device__ __forceinline__ int32_t param_entry(const ParamDev& p, int32_t type, float E, float eta) {
+  int ex = 0;
+  (void)frexp((double)E, &ex);
+  int32_t eb = (ex - 1) - p.ebin_min;
+  eb = max(0, min(eb, p.NE - 1));
+  const double ae = __dmul_rn(fabs((double)eta), p.eta_scale);
+  const int32_t hb = (ae >= (double)(p.NH - 1)) ? (p.NH - 1) : (int32_t)floor(ae);
+  return (type * p.NE + eb) * p.NH + hb;
+}
+
+__device__ __forceinline__ bool particle_ok(const ParamDev& p, int32_t t, float E, float eta, float phi) {
+  return t >= 0 && t < p.NT && E > 0.0f && isfinite(E) && isfinite(eta) && isfinite(phi);
+}
+
+// Event of particle i: last e in [ev_lo, ev_hi) with off[e] <= i.
+__device__ __forceinline__ int32_t event_of(const int64_t* off, int32_t ev_lo, int32_t ev_hi, int64_t i) {
+  int32_t lo = ev_lo, hi = ev_hi - 1;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_particle_tasks(const GeoDev g, const ParamDev p, const fcs_particles parts,
+                                 int32_t ev_lo, int32_t ev_hi, uint32_t k0, uint32_t k1,
+                                 int64_t first_event, WsDev w) {
+  const int64_t pb = parts.event_offsets[ev_lo];
+  const int64_t P = w.sizes->n_part;  // checked against the capacity and n_particles
+  const int NL = p.NL;
+  for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < P;
+       li += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = pb + li;
+    const int32_t t = parts.type[i];
+    const float E = parts.E[i], eta = parts.eta[i], phi = parts.phi[i];
+    int32_t* nl = w.nl + li * NL;
+    int64_t ntask = 0, nhit = 0;
+    if (!particle_ok(p, t, E, eta, phi)) {
+      atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_BAD_PARTICLE);
+      for (int l = 0; l < NL; ++l) nl[l] = 0;
+    } else {
+      const int32_t e = event_of(parts.event_offsets, ev_lo, ev_hi, i);
+      const uint32_t pin = (uint32_t)(i - parts.event_offsets[e]);
+      const uint32_t ev = (uint32_t)(first_event + e);
+      const int64_t base = (int64_t)param_entry(p, t, E, eta) * NL;
+      for (int l = 0; l < NL; ++l) {
+        const float El = __fmul_rn(E, p.frac[base + l]);
+        int32_t n = 0;
+        if (El > 0.0f) {
+          const float mu = __fdiv_rn(El, p.mhe[base + l]);
+          int64_t k = poisson_draw((double)mu, (uint32_t)l, pin, ev, k0, k1);
+          if (k < 1) k = 1;
+          if (k > 0x7FFFFFFF) k = 0x7FFFFFFF;
+          n = (int32_t)k;
+          ntask += 1;
+          nhit += n;
+        }
+        nl[l] = n;
+      }
+    }
+    w.pcount[li] = ntask;
+    w.pcount[w.pcap + li] = nhit;
+  }
+}
+
+__global__ void k_task_write(const GeoDev g, const ParamDev p, const fcs_particles parts,
+                             int32_t ev_lo, int32_t ev_hi, WsDev w, fcs_debug dbg, int has_dbg) {
+  const int64_t pb = parts.event_offsets[ev_lo];
+  const int64_t P = w.sizes->n_part;
+  const int NL = p.NL;
+  const int64_t pcap = w.pcap;
+  const int64_t task_base = w.sizes->task_base;
+  for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < P;
+       li += (int64_t)gridDim.x * blockDim.x) {
+    if (w.pcount[li] == 0) continue;
+    const int64_t i = pb + li;
+    const int32_t t = parts.type[i];
+    const float E = parts.E[i], eta = parts.eta[i], phi = parts.phi[i];
+    const int32_t e = event_of(parts.event_offsets, ev_lo, ev_hi, i);
+    const int32_t pin = (int32_t)(i - parts.event_offsets[e]);
+    const int64_t base = (int64_t)param_entry(p, t, E, eta) * NL;
+    int64_t to = w.poff[li];
+    int64_t ho = w.poff[pcap + li];
+    const int32_t* nl = w.nl + li * NL;
+    // FP32 scale factors of the (r, alpha) -> (eta, phi) map; the FP64 recheck
+    // recomputes them in double exactly as the oracle does.
+    const float ae = fabsf(eta);
+    const float ch = coshf(eta), sh = sinhf(ae), th = tanhf(ae);
+    for (int l = 0; l < NL; ++l) {
+      const int32_t n = nl[l];
+      if (n <= 0) continue;
+      const float El = __fmul_rn(E, p.frac[base + l]);
+      TaskRec r;
+      r.hit_begin = ho;
+      r.n = n;
+      r.entry = (int32_t)(base + l);
+      r.Ehit = __fdiv_rn(El, (float)n);
+      r.eta_c = eta;
+      r.phi_c = phi;
+      const float R = (float)g.rz[l];
+      if (g.barrel[l]) {
+        r.s_phi = 1.0f / R;
+        r.s_eta = 1.0f / (R * ch);
+      } else {
+        const float m = (th * sh) / R;
+        r.s_phi = sh / R;
+        r.s_eta = (eta < 0.0f) ? m : -m;
+      }
+      r.particle = pin;
+      r.event = e;
+      r.layer = l;
+      if (to < w.task_cap) w.tasks[to] = r;
+      if (has_dbg) {
+        const int64_t dt = task_base + to;
+        if (dt < dbg.task_capacity) {
+          if (dbg.task_event) dbg.task_event[dt] = e;
+          if (dbg.task_particle) dbg.task_particle[dt] = pin;
+          if (dbg.task_layer) dbg.task_layer[dt] = l;
+          if (dbg.task_n) dbg.task_n[dt] = n;
+          if (dbg.task_Ehit) dbg.task_Ehit[dt] = r.Ehit;
+        }
+      }
+      to += 1;
+      ho += n;
+    }
+  }
+}
+
+// Granule g (hits [g*kGranule, (g+1)*kGranule)) -> task containing its first hit.
+__global__ void k_granule_map(WsDev w) {
+  const int64_t T = w.sizes->n_tasks;
+  const int64_t H = w.sizes->n_hits;
+  if (H > w.gmap_cap * (int64_t)kGranule) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_HIT_CAPACITY);
+    return;
+  }
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = w.tasks[t].hit_begin;
+    const int64_t e = b + w.tasks[t].n;
+    for (int64_t gi = (b + kGranule - 1) / kGranule; gi * kGranule < e; ++gi) w.gmap[gi] = (int32_t)t;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_particle_tasks(const GeoDev& g, const ParamDev& p, const fcs_particles& parts,
+                                  int32_t ev_lo, int32_t ev_hi, uint32_t k0, uint32_t k1,
+                                  int64_t first_event, WsDev w, const Launch& L) {
+  k_particle_tasks<<<L.num_sms * 4, 128, 0, L.s>>>(g, p, parts, ev_lo, ev_hi, k0, k1, first_event, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_task_write(const GeoDev& g, const ParamDev& p, const fcs_particles& parts,
+                              int32_t ev_lo, int32_t ev_hi, WsDev w, const fcs_debug* dbg,
+                              const Launch& L) {
+  fcs_debug d{};
+  if (dbg) d = *dbg;
+  k_task_write<<<L.num_sms * 4, 128, 0, L.s>>>(g, p, parts, ev_lo, ev_hi, w, d, dbg ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_granule_map(WsDev w, const Launch& L) {
+  k_granule_map<<<L.num_sms * 4, 256, 0, L.s>>>(w);
+  return cudaGetLastError();
+}
+
+}  // namespace fcs

@@ -66,7 +66,7 @@ LAYER_TABLE = (
 )
 
 # numpy layout of one region record; identical field order and sizes to
-# ``fcs_region`` in include/fcs.h (40 bytes, no padding).
+# ``fcs_region`` in include/fcs.h (48 bytes, no padding).
 REGION_DTYPE = np.dtype(
     [
         ("eta_lo", "<f8"),

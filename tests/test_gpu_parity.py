@@ -1,0 +1,205 @@
+"""CUDA path (through the C ABI) against the CPU oracle on the same seeded inputs.
+
+Bars (Sec. 6 of the paper validates CPU and GPU hit by hit on the same random
+numbers and asks for identical cells):
+  * task counts, hit counts and the hit -> cell and hit -> bin maps: bit-exact;
+  * hit energies (float, Listing 1): bit-exact;
+  * atomic mode cell energies: |dE| <= 1e-5 |E| + 1e-3 MeV against the FP64
+    oracle (FP32 atomics in any order);
+  * deterministic mode: bit-exact against the oracle's canonical FP32 fold.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O  # noqa: E402
+from paper_2103_14737_gb300 import fcs, synth  # noqa: E402
+
+RTOL, ATOL = 1e-5, 1e-3
+
+
+@pytest.fixture(scope="module")
+def sim(geo, prm):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    s = fcs.Simulator(geo, prm)
+    yield s
+    s.close()
+
+
+def run_both(sim, ogeo, oprm, parts, seed, first_event=0, mode=fcs.MODE_ATOMIC, batched=1, hpt=0, block=0,
+             hits=True):
+    d = sim.to_device(parts)
+    ref = O.simulate(ogeo, oprm, parts, seed=seed, first_event=first_event,
+                     hit_cap=(10**7 if hits else 0))
+    n_t = ref.n_tasks
+    got = sim.simulate(d, seed, first_event=first_event, mode=mode, batched=batched, hits_per_thread=hpt,
+                       block=block, dense=True, debug_tasks=max(n_t, 1), debug_hits=(max(ref.n_hits, 1) if hits else 0))
+    torch.cuda.synchronize()
+    return ref, got
+
+
+def check_tasks_hits(ref, got):
+    st = got["stats"]
+    assert st["n_tasks"] == ref.n_tasks
+    assert st["n_hits"] == ref.n_hits
+    for k in ("task_event", "task_particle", "task_layer", "task_n"):
+        assert np.array_equal(got[k].cpu().numpy(), getattr(ref, k)), k
+    assert np.array_equal(got["task_Ehit"].cpu().numpy().view(np.uint32), ref.task_Ehit.view(np.uint32))
+    if "hit_cell" in got and ref.hit_cell is not None:
+        hc = got["hit_cell"].cpu().numpy()
+        mism = np.nonzero(hc != ref.hit_cell)[0]
+        assert len(mism) == 0, f"{len(mism)} hit-cell mismatches, first {mism[:5]}"
+        assert np.array_equal(got["hit_bin"].cpu().numpy(), ref.hit_bin)
+
+
+def check_cells_atomic(ref, got, n_events):
+    cells = got["cells"].cpu().numpy().astype(np.float64)
+    want = ref.cells64
+    err = np.abs(cells - want)
+    bad = err > RTOL * np.abs(want) + ATOL
+    assert not bad.any(), f"{bad.sum()} cells out of tolerance, worst {err.max()}"
+    assert np.array_equal(cells != 0, want != 0)
+    check_compacted(got, cells, n_events)
+
+
+def check_compacted(got, dense, n_events):
+    off = got["event_offsets"].cpu().numpy()
+    ids = got["cell_ids"].cpu().numpy()
+    E = got["cell_E"].cpu().numpy()
+    assert off[0] == 0 and off[-1] == got["stats"]["n_nonzero"]
+    for e in range(n_events):
+        nz = np.nonzero(dense[e])[0]
+        a, b = off[e], off[e + 1]
+        assert np.array_equal(ids[a:b], nz)
+        assert np.array_equal(E[a:b].astype(np.float64), dense[e][nz])
+
+
+@pytest.mark.parametrize("batched", [1, 0])
+def test_single_electron_parity(sim, ogeo, oprm, batched):
+    parts = synth.single_particle(8)
+    ref, got = run_both(sim, ogeo, oprm, parts, seed=1, batched=batched)
+    check_tasks_hits(ref, got)
+    check_cells_atomic(ref, got, 8)
+
+
+def test_ttbar_parity_atomic(sim, ogeo, oprm):
+    parts = synth.ttbar_like(seed=1)
+    ref, got = run_both(sim, ogeo, oprm, parts, seed=7, first_event=3)
+    check_tasks_hits(ref, got)
+    check_cells_atomic(ref, got, 1)
+
+
+@pytest.mark.parametrize("batched", [1, 0])
+def test_deterministic_bit_exact(sim, ogeo, oprm, batched):
+    parts = synth.pileup(seed=4, n_events=3, mu_pu=15)
+    ref, got = run_both(sim, ogeo, oprm, parts, seed=11, mode=fcs.MODE_DETERMINISTIC, batched=batched)
+    check_tasks_hits(ref, got)
+    cells = got["cells"].cpu().numpy()
+    assert np.array_equal(cells.view(np.uint32), ref.cells_canon.view(np.uint32))
+    check_compacted(got, cells.astype(np.float64), 3)
+
+
+@pytest.mark.parametrize("block,hpt", [(128, 1), (128, 8), (256, 2), (256, 4), (512, 1), (512, 8)])
+def test_launch_shapes(sim, ogeo, oprm, block, hpt):
+    parts = synth.pileup(seed=6, n_events=2, mu_pu=10)
+    ref, got = run_both(sim, ogeo, oprm, parts, seed=5, hpt=hpt, block=block)
+    check_tasks_hits(ref, got)
+    check_cells_atomic(ref, got, 2)
+    got2 = sim.simulate(sim.to_device(parts), 5, mode=fcs.MODE_DETERMINISTIC, hits_per_thread=hpt, block=block,
+                        dense=True)
+    assert np.array_equal(got2["cells"].cpu().numpy().view(np.uint32), ref.cells_canon.view(np.uint32))
+
+
+def test_pileup_events_parity(sim, ogeo, oprm):
+    parts = synth.pileup(seed=8, n_events=2)  # full mu = 200 pile-up events
+    ref, got = run_both(sim, ogeo, oprm, parts, seed=1, hits=False)
+    check_tasks_hits(ref, got)
+    check_cells_atomic(ref, got, 2)
+    assert got["stats"]["n_recheck"] < 0.01 * ref.n_hits
+
+
+def test_full_batch_sampled(sim, ogeo, oprm):
+    """The benchmark batch (64 pile-up events, one batched launch sequence);
+    sampled events checked against the oracle, every event's energy sum
+    checked against its tasks."""
+    parts = synth.workload("pileup64", seed=1)
+    d = sim.to_device(parts)
+    got = sim.simulate(d, 1, dense=True, debug_tasks=parts.n * 24)
+    torch.cuda.synchronize()
+    cells = got["cells"].cpu().numpy().astype(np.float64)
+    tev = got["task_event"].cpu().numpy()
+    n = got["task_n"].cpu().numpy().astype(np.float64)
+    eh = got["task_Ehit"].cpu().numpy().astype(np.float64)
+    k = got["stats"]["n_tasks"]
+    per_event = np.bincount(tev[:k], weights=n[:k] * eh[:k], minlength=64)
+    assert np.allclose(cells.sum(1), per_event, rtol=1e-5)
+    for e in (0, 37, 63):
+        ref = O.simulate(ogeo, oprm, parts.event(e), seed=1, first_event=e, tasks=False)
+        err = np.abs(cells[e] - ref.cells64[0])
+        assert not (err > RTOL * np.abs(ref.cells64[0]) + ATOL).any()
+
+
+def test_empty_events_and_zero_events(sim, ogeo, oprm):
+    p = synth.ttbar_like(seed=2, n_events=3, n=50)
+    # make event 1 empty
+    keep = np.r_[0:50, 100:150]
+    parts = synth.Particles(p.type[keep], p.E[keep], p.eta[keep], p.phi[keep], np.array([0, 50, 50, 100]))
+    ref, got = run_both(sim, ogeo, oprm, parts, seed=3)
+    check_tasks_hits(ref, got)
+    check_cells_atomic(ref, got, 3)
+    off = got["event_offsets"].cpu().numpy()
+    assert off[1] == off[2]
+    empty = synth.Particles(p.type[:0], p.E[:0], p.eta[:0], p.phi[:0], np.array([0]))
+    r = sim.simulate(sim.to_device(empty), 1)
+    assert r["status"] == 0 and r["event_offsets"].cpu().numpy().tolist() == [0]
+
+
+def test_bad_particle_and_capacity(sim):
+    p = synth.ttbar_like(seed=3, n=20)
+    p.type[5] = 7
+    p.E[6] = np.nan
+    r = sim.simulate(sim.to_device(p), 1, check=False)
+    assert r["status"] == fcs.FCS_E_DEVICE_CHECK
+    assert r["stats"]["device_flags"] & fcs.FLAG_BAD_PARTICLE
+    p = synth.ttbar_like(seed=3, n=20)
+    full = sim.simulate(sim.to_device(p), 1)
+    nnz = full["stats"]["n_nonzero"]
+    small = sim.simulate(sim.to_device(p), 1, capacity=nnz - 5, check=False)
+    assert small["status"] == fcs.FCS_E_RANGE
+    assert small["event_offsets"][-1].item() == nnz
+    assert np.array_equal(small["cell_ids"].cpu().numpy(), full["cell_ids"][:nnz - 5].cpu().numpy())
+
+
+def test_async_graph_replay_matches(sim):
+    parts = synth.pileup(seed=9, n_events=4, mu_pu=30)
+    d = sim.to_device(parts)
+    ref = sim.simulate(d, 21, dense=True)
+    outs = dict(cell_ids=torch.empty_like(ref["cell_ids"]), cell_E=torch.empty_like(ref["cell_E"]),
+                event_offsets=torch.empty_like(ref["event_offsets"]), cells=torch.empty_like(ref["cells"]))
+    for _ in range(3):
+        outs["cells"].fill_(-1)
+        sim.simulate(d, 21, sync=0, use_graph=1, outputs=outs)
+    torch.cuda.synchronize()
+    rc, st = fcs.fcs_workspace_status(sim.ws)
+    assert rc == 0 and st.n_nonzero == ref["stats"]["n_nonzero"]
+    diff = (outs["cells"] - ref["cells"]).abs()
+    assert (diff <= RTOL * ref["cells"].abs() + ATOL).all()
+
+
+def test_host_entry_point_matches(sim):
+    parts = synth.pileup(seed=10, n_events=2, mu_pu=20)
+    ref = sim.simulate(sim.to_device(parts), 4, mode=fcs.MODE_DETERMINISTIC)
+    cap = ref["stats"]["n_nonzero"] + 10
+    ids = np.empty(cap, np.int32)
+    E = np.empty(cap, np.float32)
+    off = np.empty(3, np.int64)
+    cfg = fcs.make_config(mode=fcs.MODE_DETERMINISTIC)
+    rc, st = fcs.fcs_simulate_events_host(sim.geo, sim.prm, sim.ws, parts.type, parts.E, parts.eta, parts.phi,
+                                          parts.event_offsets, 4, 0, cfg, ids, E, off)
+    n = st.n_nonzero
+    assert np.array_equal(off, ref["event_offsets"].cpu().numpy())
+    assert np.array_equal(ids[:n], ref["cell_ids"][:n].cpu().numpy())
+    assert np.array_equal(E[:n].view(np.uint32), ref["cell_E"][:n].cpu().numpy().view(np.uint32))
