@@ -158,6 +158,8 @@ def main():
     ap.add_argument("--hpt", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--extra", action="store_true", help="also time deterministic mode and per-event launches")
+    ap.add_argument("--events", type=int, default=N_EVENTS, help="events per step (smaller cases for profiling)")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
@@ -177,8 +179,9 @@ def main():
     geo = synth.geometry()
     prm = synth.params(geo)
     # weak scaling: rank r simulates its own 64 events (random-stream events r*64 ...)
-    parts = synth.pileup(seed=SEED + rank, n_events=N_EVENTS)
-    first_event = rank * N_EVENTS
+    n_ev = args.events
+    parts = synth.pileup(seed=SEED + rank, n_events=n_ev)
+    first_event = rank * n_ev
     sim = fcs.Simulator(geo, prm)
     d = sim.to_device(parts)
     # size the workspace and the outputs with one synchronous call
@@ -246,13 +249,13 @@ def main():
 
     # end to end through the host-buffer entry point (copies inside the timed region)
     e2e = None
-    if rank == 0:
+    if rank == 0 and not args.no_e2e:
         pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(parts, k))).pin_memory().numpy()
                for k in ("type", "E", "eta", "phi", "event_offsets")}
         cap = outs["cell_ids"].numel()
         ids = torch.empty(cap, dtype=torch.int32).pin_memory().numpy()
         cE = torch.empty(cap, dtype=torch.float32).pin_memory().numpy()
-        off = torch.empty(N_EVENTS + 1, dtype=torch.int64).pin_memory().numpy()
+        off = torch.empty(n_ev + 1, dtype=torch.int64).pin_memory().numpy()
         cfg = fcs.make_config(hits_per_thread=args.hpt, block=args.block)
         for _ in range(2):
             fcs.fcs_simulate_events_host(sim.geo, sim.prm, sim.ws, pin["type"], pin["E"], pin["eta"], pin["phi"],
@@ -269,8 +272,8 @@ def main():
                                                   off)
             tt.append(time.perf_counter() - t0)
             nnz = st.n_nonzero
-        h2d = parts.n * 16 + (N_EVENTS + 1) * 8
-        d2h = nnz * 8 + (N_EVENTS + 1) * 8
+        h2d = parts.n * 16 + (n_ev + 1) * 8
+        d2h = nnz * 8 + (n_ev + 1) * 8
         e2e = {"value": H / float(np.mean(tt)), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * float(np.mean(tt))}
 
@@ -286,13 +289,14 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "events_per_step": N_EVENTS, "particles_per_step": parts.n,
+                "config": {"workload": WORKLOAD if n_ev == N_EVENTS else f"pileup{n_ev}",
+                           "events_per_step": n_ev, "particles_per_step": parts.n,
                            "hits_per_step": H, "tasks_per_step": ref["stats"]["n_tasks"],
                            "nonzero_cells_per_step": ref["stats"]["n_nonzero"],
                            "recheck_hits_per_step": ref["stats"]["n_recheck"], "mode": "atomic",
                            "launch": "batched, CUDA graph", "l2": "flushed between steps (256 MB write)",
                            "parallelism": f"replicas x{world} (events sharded, no collective)"},
-                "events_per_s": N_EVENTS * world / (ms * 1e-3),
+                "events_per_s": n_ev * world / (ms * 1e-3),
                 "stages_ms": stage_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches_per_step * args.steps, "wall_s": wall}

@@ -89,7 +89,8 @@ typedef struct fcs_workspace fcs_workspace; /* opaque, device buffers of one cal
 
 /* Particles of n_events events as device SoA; event e owns the particles
  * [event_offsets[e], event_offsets[e+1]).  type: 0 electron, 1 photon,
- * 2 charged pion (any value < NT of the parametrisation). */
+ * 2 charged pion (any value < NT of the parametrisation).  The four particle
+ * arrays may be NULL when n_particles == 0; event_offsets is always required. */
 typedef struct fcs_particles {
   const int32_t* type;          /* device [n_particles] */
   const float* E;               /* device [n_particles], MeV, > 0 */

@@ -327,9 +327,10 @@ int status_from(const Sizes& s, fcs_stats* st) {
   return ok();
 }
 
-int check_particles(const fcs_particles* p) {
-  if (!p || !p->type || !p->E || !p->eta || !p->phi || !p->event_offsets)
-    return set_err(FCS_E_ARG, "particles: every array must be non-NULL");
+int check_particles(const fcs_particles* p, int64_t n_particles) {
+  if (!p || !p->event_offsets) return set_err(FCS_E_ARG, "particles and event_offsets must be non-NULL");
+  if (n_particles > 0 && (!p->type || !p->E || !p->eta || !p->phi))
+    return set_err(FCS_E_ARG, "particles: every array must be non-NULL when n_particles > 0");
   return FCS_OK;
 }
 
@@ -729,7 +730,7 @@ int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace
                         float* cell_E, int64_t* event_offsets_out, int64_t capacity, fcs_stats* stats,
                         const fcs_debug* dbg, cudaStream_t s) {
   if (!geo || !prm || !ws) return set_err(FCS_E_ARG, "geo, params and workspace are required");
-  FCS_TRY(check_particles(particles));
+  FCS_TRY(check_particles(particles, n_particles));
   if (n_particles < 0 || n_events < 0 || capacity < 0) return set_err(FCS_E_ARG, "negative size");
   if (prm->d.NL != geo->d.n_layers) return set_err(FCS_E_ARG, "parametrisation and geometry disagree on layers");
   if ((cell_ids == nullptr) != (cell_E == nullptr)) return set_err(FCS_E_ARG, "cell_ids and cell_E go together");
@@ -841,7 +842,7 @@ int fcs_simulate_events_host(const fcs_geo* geo, const fcs_params* prm, fcs_work
                              int64_t* event_offsets_out, int64_t capacity, fcs_stats* stats, cudaStream_t s) {
   if (!geo || !prm || !ws) return set_err(FCS_E_ARG, "geo, params and workspace are required");
   if (n_particles < 0 || n_events < 0 || capacity < 0) return set_err(FCS_E_ARG, "negative size");
-  if (!type || !E || !eta || !phi || !event_offsets || !event_offsets_out)
+  if (!event_offsets || !event_offsets_out || (n_particles > 0 && (!type || !E || !eta || !phi)))
     return set_err(FCS_E_ARG, "host arrays must be non-NULL");
   if ((cell_ids == nullptr) != (cell_E == nullptr)) return set_err(FCS_E_ARG, "cell_ids and cell_E go together");
   fcs_config cfg{};
