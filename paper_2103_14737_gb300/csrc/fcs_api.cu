@@ -164,7 +164,8 @@ struct fcs_workspace {
   cudaGraphExec_t graph = nullptr;
   std::vector<unsigned char> graph_key;
   // stage timing events: 5 per event range (begin, after tasks, after hits,
-  // after recheck, after reduce) of the last timed call
+  // after recheck, after reduce) of the last timed call; recorded as external
+  // events so that a captured call gets event-record nodes in its graph
   std::vector<cudaEvent_t> tev;
   int timed_ranges = 0;
 
@@ -362,7 +363,7 @@ int enqueue_range(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, bool sync_siz
   const int det = a.cfg.mode == FCS_MODE_DETERMINISTIC;
   const int32_t rows = ev_hi - ev_lo;
   cudaEvent_t* tev = a.cfg.timing ? &ws->tev[(size_t)(a.cfg.batched ? 0 : ev_lo) * 5] : nullptr;
-  if (tev) FCS_CUDA(cudaEventRecord(tev[0], a.s));
+  if (tev) FCS_CUDA(cudaEventRecordWithFlags(tev[0], a.s, cudaEventRecordExternal));
   k_range_begin<<<1, 1, 0, a.s>>>(ws->d_sizes, a.parts.event_offsets, ev_lo, ev_hi, a.n_particles, ws->pcap);
   const uint32_t k0 = (uint32_t)(a.seed & 0xFFFFFFFFu), k1 = (uint32_t)(a.seed >> 32);
   FCS_CUDA(launch_particle_tasks(a.geo->d, a.prm->d, a.parts, ev_lo, ev_hi, k0, k1, a.first_event, ws->view(), L));
@@ -378,11 +379,11 @@ int enqueue_range(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, bool sync_siz
   }
   FCS_CUDA(launch_task_write(a.geo->d, a.prm->d, a.parts, ev_lo, ev_hi, w, a.dbg, L));
   FCS_CUDA(launch_granule_map(w, L));
-  if (tev) FCS_CUDA(cudaEventRecord(tev[1], a.s));
+  if (tev) FCS_CUDA(cudaEventRecordWithFlags(tev[1], a.s, cudaEventRecordExternal));
   FCS_CUDA(launch_hits(a.geo->d, a.prm->d, w, ev_lo, k0, k1, a.first_event, hc, key_task_bits, a.dbg, L));
-  if (tev) FCS_CUDA(cudaEventRecord(tev[2], a.s));
+  if (tev) FCS_CUDA(cudaEventRecordWithFlags(tev[2], a.s, cudaEventRecordExternal));
   FCS_CUDA(launch_recheck(a.geo->d, a.prm->d, w, ev_lo, k0, k1, a.first_event, det, key_task_bits, a.dbg, L));
-  if (tev) FCS_CUDA(cudaEventRecord(tev[3], a.s));
+  if (tev) FCS_CUDA(cudaEventRecordWithFlags(tev[3], a.s, cudaEventRecordExternal));
   if (!det) {
     FCS_CUDA(launch_compact(a.geo->d, w, rows, ev_lo, ws->chunk_counts, ws->chunk_offsets, tmp, a.cells_out,
                             a.cell_ids, a.cell_E, a.event_offsets_out, a.n_events, a.capacity, L));
@@ -393,7 +394,7 @@ int enqueue_range(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, bool sync_siz
                                ws->head_flags, ws->head_off, tmp, a.cells_out, a.cell_ids, a.cell_E,
                                a.event_offsets_out, a.n_events, a.capacity, L));
   }
-  if (tev) FCS_CUDA(cudaEventRecord(tev[4], a.s));
+  if (tev) FCS_CUDA(cudaEventRecordWithFlags(tev[4], a.s, cudaEventRecordExternal));
   k_range_end<<<1, 1, 0, a.s>>>(ws->d_sizes);
   return FCS_OK;
 }
