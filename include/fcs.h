@@ -247,6 +247,37 @@ int fcs_simulate_events_host(const fcs_geo* geo, const fcs_params* prm, fcs_work
                              float* cell_E, int64_t* event_offsets_out, int64_t capacity,
                              fcs_stats* stats, cudaStream_t s);
 
+/* Size of the library's static device scratch used by
+ * fcs_simulate_events_static (16 MiB, held on every GPU that loads the
+ * library until the process exits). */
+#define FCS_STATIC_SCRATCH_BYTES (16 * 1024 * 1024)
+
+/* Atomic-mode, batched fcs_simulate_events that allocates no device memory,
+ * for callers that must not call cudaMalloc/cudaFree while they run: online
+ * trigger or serving loops that cannot take the device-wide synchronisation
+ * an allocation can cause, processes whose device memory is fully reserved by
+ * another framework's pool, or clients running under a memory quota.  This
+ * entry point has no counterpart in the paper; it only changes where the
+ * intermediate buffers live.
+ * Inputs and outputs are as for fcs_simulate_events (device pointers; the
+ * dense cells_out and the validation dumps are not offered); the task
+ * records, tile map, recheck queue and accumulation rows are carved out of
+ * one static device array of FCS_STATIC_SCRATCH_BYTES.  The call is
+ * synchronous on stream s and returns the device status like a sync call.
+ * Limits: the particle tables (about 56 bytes x layers per particle) plus the
+ * accumulation rows (4 bytes x cells, padded, per event) must fit in the
+ * array, and the hits of the call are bounded by what remains (128 hits per
+ * 4 remaining bytes); otherwise FCS_E_RANGE with the sizes in the message.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Every call uses the same array: calls that overlap on the GPU (two streams
+ * or two threads) race and corrupt each other's results. */
+int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* prm,
+                               const fcs_particles* particles, int64_t n_particles,
+                               int32_t n_events, uint64_t seed, int64_t first_event,
+                               int32_t* cell_ids, float* cell_E, int64_t* event_offsets_out,
+                               int64_t capacity, fcs_stats* stats, cudaStream_t s);
+
 /* Gradient of a cell-energy loss with respect to the layer-fraction table
  * and the shape weights, by reweighting hit energies with hit positions held
  * fixed for the seed.  Not implemented yet: returns FCS_E_UNSUPPORTED. */

@@ -903,3 +903,157 @@ int fcs_simulate_backward(const fcs_geo*, const fcs_params*, fcs_workspace*, con
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Simulation without device allocation: the scratch buffers of the launch
+// sequence live in one file-scope device array of fixed size instead of a
+// cudaMalloc'd workspace.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Holds the intermediate buffers of fcs_simulate_events_static.  Every GPU
+// that loads the library keeps this array until the process exits.
+static __device__ __align__(256) unsigned char g_static_scratch[FCS_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {};  // device address of g_static_scratch, per device
+int g_static_sms[kMaxDevices] = {};
+
+// Device address of the array on the current device (host code must not use
+// the symbol itself, which is only a host-side stand-in).
+int static_scratch(int dev, void** ptr, int* sms) {
+  if (dev < 0 || dev >= kMaxDevices) return set_err(FCS_E_ARG, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      return set_err(FCS_E_CUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return set_err(FCS_E_CUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+    g_static_ptr[dev] = p;
+    g_static_sms[dev] = n;
+  }
+  *ptr = g_static_ptr[dev];
+  *sms = g_static_sms[dev];
+  return FCS_OK;
+}
+
+// Bump allocator over the array (256-byte aligned slices).
+struct Carve {
+  unsigned char* base;
+  size_t off, cap;
+  template <typename T>
+  T* take(int64_t n) {
+    const size_t bytes = ((size_t)std::max<int64_t>(n, 1) * sizeof(T) + 255) / 256 * 256;
+    if (off + bytes > cap) return nullptr;
+    T* p = reinterpret_cast<T*>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+
+}  // namespace
+
+extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* prm,
+                                          const fcs_particles* particles, int64_t n_particles,
+                                          int32_t n_events, uint64_t seed, int64_t first_event,
+                                          int32_t* cell_ids, float* cell_E, int64_t* event_offsets_out,
+                                          int64_t capacity, fcs_stats* stats, cudaStream_t s) {
+  if (!geo || !prm) return set_err(FCS_E_ARG, "geo and params are required");
+  FCS_TRY(check_particles(particles, n_particles));
+  if (n_particles < 0 || n_events < 1 || capacity < 0) return set_err(FCS_E_ARG, "bad size");
+  if (!event_offsets_out) return set_err(FCS_E_ARG, "event_offsets_out is required");
+  if ((cell_ids == nullptr) != (cell_E == nullptr)) return set_err(FCS_E_ARG, "cell_ids and cell_E go together");
+  if (prm->d.NL != geo->d.n_layers) return set_err(FCS_E_ARG, "parametrisation and geometry disagree on layers");
+  int dev = 0;
+  FCS_TRY(current_device(&dev));
+  if (dev != geo->device || dev != prm->device)
+    return set_err(FCS_E_ARG, "geometry and parametrisation must live on the current device");
+  void* base = nullptr;
+  int sms = 0;
+  FCS_TRY(static_scratch(dev, &base, &sms));
+
+  // Carve the workspace buffers for this call out of the array.
+  const int NL = geo->d.n_layers;
+  const int64_t P = std::max<int64_t>(n_particles, 1);
+  const int64_t recheck_cap = 32768;
+  fcs_workspace w;  // views only: pointers into the static array, nulled before return
+  w.device = dev;
+  w.num_sms = sms;
+  Carve c{(unsigned char*)base, 0, (size_t)FCS_STATIC_SCRATCH_BYTES};
+  w.d_sizes = c.take<Sizes>(1);
+  w.nl = c.take<int32_t>(P * NL);
+  w.pcount = c.take<int64_t>(2 * P);
+  w.poff = c.take<int64_t>(2 * P);
+  w.pcap = P;
+  w.tasks = c.take<TaskRec>(P * NL);
+  w.task_cap = P * NL;
+  w.acc = c.take<float>((int64_t)n_events * geo->d.acc_stride);
+  w.rows_cap = n_events;
+  w.acc_stride = geo->d.acc_stride;
+  const int64_t chunks = compact_chunks(geo->d.n_cells, n_events);
+  w.chunk_counts = c.take<int64_t>(chunks);
+  w.chunk_offsets = c.take<int64_t>(chunks);
+  w.block_sums = c.take<int64_t>(kScanBlocks + 1);
+  w.recheck = c.take<uint2>(recheck_cap);
+  w.recheck_cap = recheck_cap;
+  const bool fits = w.d_sizes && w.nl && w.pcount && w.poff && w.tasks && w.acc && w.chunk_counts &&
+                    w.chunk_offsets && w.block_sums && w.recheck && c.cap - c.off >= 4096;
+  if (fits) {
+    // the rest of the array maps tiles to tasks: it bounds the hits per call
+    w.gmap_cap = (int64_t)((c.cap - c.off) / sizeof(int32_t));
+    w.gmap = reinterpret_cast<int32_t*>((unsigned char*)base + c.off);
+  }
+  auto release = [&]() {  // the array is not the workspace's to free
+    w.d_sizes = nullptr;
+    w.nl = nullptr;
+    w.pcount = nullptr;
+    w.poff = nullptr;
+    w.tasks = nullptr;
+    w.acc = nullptr;
+    w.chunk_counts = nullptr;
+    w.chunk_offsets = nullptr;
+    w.block_sums = nullptr;
+    w.recheck = nullptr;
+    w.gmap = nullptr;
+  };
+  if (!fits) {
+    release();
+    return set_err(FCS_E_RANGE,
+                   "static scratch of %d bytes is too small for %lld particles x %d layers and %d events of %d "
+                   "cells; use fcs_simulate_events",
+                   (int)FCS_STATIC_SCRATCH_BYTES, (long long)n_particles, NL, n_events, geo->d.n_cells);
+  }
+  fcs_config cfg{};
+  cfg.mode = FCS_MODE_ATOMIC;
+  cfg.batched = 1;
+  cfg.sync = 1;
+  // the array keeps the previous call's contents: the accumulation rows must start at zero
+  int rc = FCS_OK;
+  cudaError_t e = cudaMemsetAsync(w.acc, 0, (size_t)n_events * geo->d.acc_stride * sizeof(float), s);
+  if (e != cudaSuccess) rc = set_err(FCS_E_CUDA, "clearing the static scratch: %s", cudaGetErrorString(e));
+  if (rc == FCS_OK) {
+    CallArgs a{geo, prm, &w, *particles, n_particles, n_events, seed, first_event, cfg, nullptr,
+               cell_ids, cell_E, event_offsets_out, capacity, nullptr, s};
+    const HitCfg hc = hit_cfg(cfg);
+    const int key_task_bits = bits_for(P * NL);
+    rc = enqueue_call(a, false, hc, key_task_bits);
+  }
+  Sizes h{};
+  if (rc == FCS_OK) {
+    e = cudaMemcpyAsync(&h, w.d_sizes, sizeof(Sizes), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = set_err(FCS_E_CUDA, "reading the call status: %s", cudaGetErrorString(e));
+  }
+  release();
+  if (rc != FCS_OK) return rc;
+  if (h.flags & FCS_FLAG_HIT_CAPACITY) {
+    if (stats) status_from(h, stats);
+    return set_err(FCS_E_RANGE, "the call produced more hits than the static scratch maps (%lld > %lld)",
+                   (long long)h.hit_base, (long long)(w.gmap_cap * kGranule));
+  }
+  return status_from(h, stats);
+}

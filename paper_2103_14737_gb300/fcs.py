@@ -30,7 +30,7 @@ MODE_ATOMIC, MODE_DETERMINISTIC = 0, 1
 EXPORTED = ("fcs_version", "fcs_last_error", "fcs_load_geometry", "fcs_geometry_info", "fcs_free_geometry",
             "fcs_load_params", "fcs_free_params", "fcs_workspace_create", "fcs_workspace_reserve",
             "fcs_workspace_status", "fcs_workspace_timings", "fcs_workspace_free", "fcs_simulate_events", "fcs_simulate_events_host",
-            "fcs_simulate_backward")
+            "fcs_simulate_events_static", "fcs_simulate_backward")
 
 
 class FcsError(RuntimeError):
@@ -100,6 +100,7 @@ def load_library(build_if_missing: bool = True):
         L.fcs_simulate_events.argtypes = [vp, vp, vp, vp, i64, i32, u64, i64, vp, vp, vp, vp, vp, i64, vp, vp, vp]
         L.fcs_simulate_events_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i64, i32, u64, i64, vp, vp, vp, vp,
                                                i64, vp, vp]
+        L.fcs_simulate_events_static.argtypes = [vp, vp, vp, i64, i32, u64, i64, vp, vp, vp, i64, vp, vp]
         L.fcs_simulate_backward.argtypes = [vp, vp, vp, vp, i64, i32, u64, i64, vp, vp, vp, vp, vp]
         # every other entry point returns an int status (the ctypes default restype)
         _lib = L
@@ -246,6 +247,24 @@ def fcs_simulate_events_host(geo, prm, ws, type_, E, eta, phi, event_offsets, se
                                     cell_ids.ctypes.data_as(C.c_void_p), cell_E.ctypes.data_as(C.c_void_p),
                                     event_offsets_out.ctypes.data_as(C.c_void_p), len(cell_ids), C.byref(st),
                                     _stream())
+    if check and rc != FCS_OK:
+        _check(rc)
+    return rc, st
+
+
+STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
+
+
+def fcs_simulate_events_static(geo, prm, particles: fcs_particles, n_particles, n_events, seed, first_event,
+                               cell_ids, cell_E, event_offsets_out, check=True):
+    """The allocation-free entry point (scratch in the library's static device
+    array); device tensors in and out, synchronous.  Returns (status, fcs_stats)."""
+    L = load_library()
+    st = fcs_stats()
+    rc = L.fcs_simulate_events_static(geo, prm, C.byref(particles), int(n_particles), int(n_events),
+                                      int(seed) & 0xFFFFFFFFFFFFFFFF, int(first_event), _ptr(cell_ids), _ptr(cell_E),
+                                      _ptr(event_offsets_out), int(cell_ids.numel()) if cell_ids is not None else 0,
+                                      C.byref(st), _stream())
     if check and rc != FCS_OK:
         _check(rc)
     return rc, st
