@@ -123,7 +123,7 @@ typedef struct fcs_stats {
   int64_t n_nonzero;  /* non-zero cells over all events (the compacted output size) */
   int64_t n_recheck;  /* hits whose cell the FP32 path could not certify, decided in FP64 */
   uint32_t device_flags; /* enum fcs_device_flag bits */
-  uint32_t pad;
+  uint32_t n_poisson_fp64; /* hit-count draws with a decision the FP32 path could not certify */
 } fcs_stats;
 
 /* Optional per-task / per-hit dumps for validation (device pointers; NULL

@@ -313,7 +313,7 @@ int status_from(const Sizes& s, fcs_stats* st) {
     st->n_nonzero = s.nnz_total;
     st->n_recheck = s.recheck_total;
     st->device_flags = s.flags;
-    st->pad = 0;
+    st->n_poisson_fp64 = s.n_poisson_fp64;
   }
   if (s.flags & FCS_FLAG_BAD_OFFSETS)
     return set_err(FCS_E_ARG, "event_offsets must be non-decreasing within [0, n_particles]");

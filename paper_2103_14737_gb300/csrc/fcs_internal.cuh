@@ -90,7 +90,7 @@ struct Sizes {
   int64_t n_rec_used;   // deterministic records sorted (n_records clamped to the capacity)
   unsigned long long queue;  // hit-kernel work-queue counter (tiles handed out)
   uint32_t flags;       // fcs_device_flag bits
-  uint32_t pad;
+  uint32_t n_poisson_fp64;  // Poisson draws that needed an FP64 decision (call total)
 };
 static_assert(sizeof(Sizes) % 8 == 0 && offsetof(Sizes, queue) % 8 == 0, "Sizes layout");
 

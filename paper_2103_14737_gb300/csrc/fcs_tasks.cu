@@ -23,8 +23,40 @@ __device__ __forceinline__ void draw_pair(uint32_t i, uint32_t layer, uint32_t p
   *v = u53(x.z, x.w);
 }
 
-__device__ int64_t poisson_draw(double mu, uint32_t layer, uint32_t particle, uint32_t event,
-                                uint32_t k0, uint32_t k1) {
+struct PtrsConst64 {
+  double loglam, b, a, invalpha, vr;
+};
+
+__device__ __forceinline__ PtrsConst64 ptrs_const64(double mu) {
+  PtrsConst64 c;
+  const double slam = __dsqrt_rn(mu);
+  c.loglam = log(mu);
+  c.b = __dadd_rn(0.931, __dmul_rn(2.53, slam));
+  c.a = __dadd_rn(-0.059, __dmul_rn(0.02483, c.b));
+  c.invalpha = __dadd_rn(1.1239, __ddiv_rn(1.1328, __dsub_rn(c.b, 3.4)));
+  c.vr = __dsub_rn(0.9277, __ddiv_rn(3.6224, __dsub_rn(c.b, 2.0)));
+  return c;
+}
+
+// One PTRS iteration in FP64 from its two 53-bit uniforms: the accepted count,
+// or -1 when the iteration rejects.
+__device__ __noinline__ int64_t ptrs_iter64(double mu, const PtrsConst64& c, double u, double V) {
+  const double U = __dsub_rn(u, 0.5);
+  const double us = __dsub_rn(0.5, fabs(U));
+  if (us <= 0.0) return -1;
+  const double t = __dadd_rn(__dadd_rn(__dmul_rn(__dadd_rn(__ddiv_rn(__dmul_rn(2.0, c.a), us), c.b), U), mu), 0.43);
+  const double kd = floor(t);
+  if (us >= 0.07 && V <= c.vr) return (int64_t)kd;
+  if (kd < 0.0 || (us < 0.013 && V > us)) return -1;
+  const double lhs = __dsub_rn(__dadd_rn(log(V), log(c.invalpha)),
+                               log(__dadd_rn(__ddiv_rn(c.a, __dmul_rn(us, us)), c.b)));
+  const double rhs = __dsub_rn(__dadd_rn(-mu, __dmul_rn(kd, c.loglam)), lgamma(__dadd_rn(kd, 1.0)));
+  return (lhs <= rhs) ? (int64_t)kd : -1;
+}
+
+// The whole draw in FP64 (the definition the fast path must reproduce).
+__device__ __noinline__ int64_t poisson_draw(double mu, uint32_t layer, uint32_t particle, uint32_t event,
+                                             uint32_t k0, uint32_t k1) {
   if (!(mu > 0.0)) return 0;
   if (mu < 10.0) {
     double u, v;
@@ -39,26 +71,135 @@ __device__ int64_t poisson_draw(double mu, uint32_t layer, uint32_t particle, ui
     }
     return k;
   }
-  const double slam = __dsqrt_rn(mu);
-  const double loglam = log(mu);
-  const double b = __dadd_rn(0.931, __dmul_rn(2.53, slam));
-  const double a = __dadd_rn(-0.059, __dmul_rn(0.02483, b));
-  const double invalpha = __dadd_rn(1.1239, __ddiv_rn(1.1328, __dsub_rn(b, 3.4)));
-  const double vr = __dsub_rn(0.9277, __ddiv_rn(3.6224, __dsub_rn(b, 2.0)));
+  const PtrsConst64 c = ptrs_const64(mu);
   for (uint32_t i = 0; i < kPtrsMaxIter; ++i) {
     double u, V;
     draw_pair(i, layer, particle, event, k0, k1, &u, &V);
-    const double U = __dsub_rn(u, 0.5);
-    const double us = __dsub_rn(0.5, fabs(U));
-    if (us <= 0.0) continue;
-    const double t = __dadd_rn(__dadd_rn(__dmul_rn(__dadd_rn(__ddiv_rn(__dmul_rn(2.0, a), us), b), U), mu), 0.43);
-    const double kd = floor(t);
-    if (us >= 0.07 && V <= vr) return (int64_t)kd;
-    if (kd < 0.0 || (us < 0.013 && V > us)) continue;
-    const double lhs = __dsub_rn(__dadd_rn(log(V), log(invalpha)),
-                                 log(__dadd_rn(__ddiv_rn(a, __dmul_rn(us, us)), b)));
-    const double rhs = __dsub_rn(__dadd_rn(-mu, __dmul_rn(kd, loglam)), lgamma(__dadd_rn(kd, 1.0)));
-    if (lhs <= rhs) return (int64_t)kd;
+    const int64_t k = ptrs_iter64(mu, c, u, V);
+    if (k >= 0) return k;
+  }
+  return (int64_t)floor(mu);
+}
+
+// ---- FP32 fast path of the same draw ------------------------------------------
+// Every comparison of the FP64 definition is made in FP32 together with a
+// bound on |FP32 value - exact value| (the FP64 values of the definition are
+// within a few 2^-53 of exact, covered by the slack).  When the two sides are
+// farther apart than the bound the FP32 decision is the FP64 one; otherwise
+// the iteration (PTRS) or the whole inversion is redone in FP64.  Bounds:
+//   inversion: expf <= 2 ulp, each of the k multiply/reciprocal steps adds
+//     <= 3 roundings (2^-24 each) to p_k, each partial sum one more, so
+//     |F32_k - F_k| <= 2^-22 + (4k + 1) 2^-24 (F <= 1); used: 2^-21 (k + 2);
+//     the 53-bit uniform rounded to FP32 is off by <= 2^-24.
+//   PTRS constants: sqrtf / logf / IEEE divisions and the FP32 images of the
+//     decimal constants, a few roundings each: relative error <= 2^-20.
+//   uniforms: exact integers rounded once to FP32 (relative 2^-24).
+constexpr float kPtrsFastMaxMu = 4096.0f;  // larger means go to FP64 (counts of ~1e4 lose FP32 headroom)
+
+struct PtrsConst32 {
+  float loglam, b, a, invalpha, vr, two_a;
+};
+
+__device__ __forceinline__ PtrsConst32 ptrs_const32(float mu) {
+  PtrsConst32 c;
+  const float slam = sqrtf(mu);
+  c.loglam = logf(mu);
+  c.b = fmaf(2.53f, slam, 0.931f);
+  c.a = fmaf(0.02483f, c.b, -0.059f);
+  c.invalpha = 1.1239f + 1.1328f / (c.b - 3.4f);
+  c.vr = 0.9277f - 3.6224f / (c.b - 2.0f);
+  c.two_a = 2.0f * c.a;
+  return c;
+}
+
+// One PTRS iteration in FP32.  Returns the accepted count, -1 for a certain
+// rejection, -2 when a decision is uncertain (redo the iteration in FP64).
+__device__ __forceinline__ int64_t ptrs_iter32(float mu, const PtrsConst32& c, uint64_t N, uint64_t M) {
+  if (N == 0) return -1;  // u == 0: us == 0 rejects
+  const uint64_t half = 1ull << 52;
+  const float Uf = (float)((int64_t)N - (int64_t)half) * 0x1p-53f;
+  const float usf = (float)(N < half ? N : (2 * half - N)) * 0x1p-53f;
+  const float Vf = (float)M * 0x1p-53f;
+  // k = floor((2a/us + b) U + mu + 0.43)
+  const float t1 = c.two_a / usf;
+  const float x = ((t1 + c.b) * Uf + mu) + 0.43f;
+  const float bx = (fabsf(t1 * Uf) + fabsf(c.b * Uf)) * 0x1p-18f + (fabsf(x) + 1.0f) * 0x1p-22f;
+  const float kf = floorf(x);
+  const bool k_sure = (x - kf > bx) && (kf + 1.0f - x > bx);
+  // quick accept: us >= 0.07 && V <= vr
+  const float m_us = 0x1p-23f, m_v = 0x1p-19f;
+  const bool us_ge_007 = usf - 0.07f > m_us, us_lt_007 = 0.07f - usf > m_us;
+  const bool v_le_vr = c.vr - Vf > m_v, v_gt_vr = Vf - c.vr > m_v;
+  if (us_ge_007 && v_le_vr) return k_sure ? (int64_t)kf : -2;
+  if (!(us_lt_007 || v_gt_vr)) return -2;  // quick-accept decision uncertain
+  // reject: k < 0 || (us < 0.013 && V > us)
+  const bool k_neg = x + bx < 0.0f, k_nonneg = x - bx >= 0.0f;
+  if (k_neg) return -1;
+  if (!k_nonneg) return -2;
+  const bool us_lt_0013 = 0.013f - usf > m_us, us_ge_0013 = usf - 0.013f > m_us;
+  const float m_vu = (Vf + usf) * 0x1p-22f;
+  const bool v_gt_us = Vf - usf > m_vu, v_le_us = usf - Vf > m_vu;
+  if (us_lt_0013 && v_gt_us) return -1;
+  if (!(us_ge_0013 || v_le_us)) return -2;
+  // full test: log V + log invalpha - log(a / us^2 + b) <= -mu + k log mu - lgamma(k + 1)
+  if (!k_sure) return -2;
+  const float l1 = logf(Vf), l2 = logf(c.invalpha), l3 = logf(c.a / (usf * usf) + c.b);
+  const float kl = kf * c.loglam, lg = lgammaf(kf + 1.0f);
+  const float d = (l1 + l2 - l3) - ((-mu + kl) - lg);
+  const float bd = (fabsf(l1) + fabsf(l2) + fabsf(l3) + fabsf(kl) + fabsf(lg) + mu + 1.0f) * 0x1p-18f;
+  if (d < -bd) return (int64_t)kf;
+  if (d > bd) return -1;
+  return -2;
+}
+
+__device__ __forceinline__ uint64_t bits53(uint32_t a, uint32_t b) {
+  return ((uint64_t)(a >> 5) << 26) | (uint64_t)(b >> 6);
+}
+
+// Poisson draw: FP32 where every decision is certified, FP64 otherwise; the
+// result equals poisson_draw's.  *fp64 counts draws that needed FP64.
+__device__ int64_t poisson_draw_fast(float mu32, uint32_t layer, uint32_t particle, uint32_t event, uint32_t k0,
+                                     uint32_t k1, uint32_t* fp64) {
+  if (!(mu32 > 0.0f)) return 0;
+  const double mu = (double)mu32;
+  if (mu32 < 10.0f) {
+    const uint4 x = philox4x32_10(make_uint4(0u, layer | (kPurposePoisson << 16), particle, event), k0, k1);
+    const float uf = (float)bits53(x.x, x.y) * 0x1p-53f;
+    float p = expf(-mu32);
+    float F = p;
+    int k = 0;
+    while (true) {
+      const float e = (float)(k + 2) * 0x1p-21f;
+      if (uf < F - e) return k;          // u < F_k: stop at k
+      if (!(uf > F + e)) break;          // uncertain
+      if (k == kInvMax) return k;        // the definition stops here too
+      k += 1;
+      p = (p * mu32) * __frcp_rn((float)k);
+      F = F + p;
+    }
+    *fp64 += 1;
+    return poisson_draw(mu, layer, particle, event, k0, k1);
+  }
+  if (mu32 > kPtrsFastMaxMu) {
+    *fp64 += 1;
+    return poisson_draw(mu, layer, particle, event, k0, k1);
+  }
+  const PtrsConst32 c = ptrs_const32(mu32);
+  bool have64 = false;
+  PtrsConst64 c64;
+  for (uint32_t i = 0; i < kPtrsMaxIter; ++i) {
+    const uint4 x = philox4x32_10(make_uint4(i, layer | (kPurposePoisson << 16), particle, event), k0, k1);
+    const uint64_t N = bits53(x.x, x.y), M = bits53(x.z, x.w);
+    int64_t k = ptrs_iter32(mu32, c, N, M);
+    if (k == -2) {
+      if (!have64) {
+        c64 = ptrs_const64(mu);
+        have64 = true;
+        *fp64 += 1;
+      }
+      k = ptrs_iter64(mu, c64, (double)N * (1.0 / 9007199254740992.0), (double)M * (1.0 / 9007199254740992.0));
+    }
+    if (k >= 0) return k;
   }
   return (int64_t)floor(mu);
 }
@@ -102,6 +243,7 @@ __global__ void k_particle_tasks(const GeoDev g, const ParamDev p, const fcs_par
     const float E = parts.E[i], eta = parts.eta[i], phi = parts.phi[i];
     int32_t* nl = w.nl + li * NL;
     int64_t ntask = 0, nhit = 0;
+    uint32_t n_fp64 = 0;
     if (!particle_ok(p, t, E, eta, phi)) {
       atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_BAD_PARTICLE);
       for (int l = 0; l < NL; ++l) nl[l] = 0;
@@ -115,7 +257,7 @@ __global__ void k_particle_tasks(const GeoDev g, const ParamDev p, const fcs_par
         int32_t n = 0;
         if (El > 0.0f) {
           const float mu = __fdiv_rn(El, p.mhe[base + l]);
-          int64_t k = poisson_draw((double)mu, (uint32_t)l, pin, ev, k0, k1);
+          int64_t k = poisson_draw_fast(mu, (uint32_t)l, pin, ev, k0, k1, &n_fp64);
           if (k < 1) k = 1;
           if (k > 0x7FFFFFFF) k = 0x7FFFFFFF;
           n = (int32_t)k;
@@ -127,6 +269,7 @@ __global__ void k_particle_tasks(const GeoDev g, const ParamDev p, const fcs_par
     }
     w.pcount[li] = ntask;
     w.pcount[w.pcap + li] = nhit;
+    if (n_fp64) atomicAdd(&w.sizes->n_poisson_fp64, n_fp64);
   }
 }
 

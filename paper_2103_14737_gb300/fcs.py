@@ -52,10 +52,10 @@ class fcs_config(C.Structure):
 
 class fcs_stats(C.Structure):
     _fields_ = [("n_tasks", C.c_int64), ("n_hits", C.c_int64), ("n_nonzero", C.c_int64),
-                ("n_recheck", C.c_int64), ("device_flags", C.c_uint32), ("pad", C.c_uint32)]
+                ("n_recheck", C.c_int64), ("device_flags", C.c_uint32), ("n_poisson_fp64", C.c_uint32)]
 
     def as_dict(self):
-        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "pad"}
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 class fcs_debug(C.Structure):

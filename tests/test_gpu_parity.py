@@ -113,12 +113,29 @@ def test_launch_shapes(sim, ogeo, oprm, block, hpt):
     assert np.array_equal(got2["cells"].cpu().numpy().view(np.uint32), ref.cells_canon.view(np.uint32))
 
 
+def test_poisson_counts_wide_mu(sim, ogeo, oprm):
+    """Hit counts over mu from ~1e-2 to ~1e5 (inversion, FP32-certified PTRS,
+    the FP64-only large-mu path) equal the oracle's draw for draw."""
+    rng = np.random.default_rng(12)
+    n = 3000
+    E = (2.0 ** rng.uniform(6.0, 22.0, n)).astype(np.float32)
+    parts = synth.Particles(rng.integers(0, 3, n).astype(np.int32), E,
+                            rng.uniform(-3.2, 3.2, n).astype(np.float32),
+                            rng.uniform(-np.pi, np.pi, n).astype(np.float32),
+                            np.array([0, 1000, 2000, 3000], dtype=np.int64))
+    ref, got = run_both(sim, ogeo, oprm, parts, seed=77, first_event=9, hits=False)
+    check_tasks_hits(ref, got)
+    # tasks above mu = 4096 (about 15 % here) are drawn in FP64 on purpose
+    assert got["stats"]["n_poisson_fp64"] < 0.25 * ref.n_tasks
+
+
 def test_pileup_events_parity(sim, ogeo, oprm):
     parts = synth.pileup(seed=8, n_events=2)  # full mu = 200 pile-up events
     ref, got = run_both(sim, ogeo, oprm, parts, seed=1, hits=False)
     check_tasks_hits(ref, got)
     check_cells_atomic(ref, got, 2)
     assert got["stats"]["n_recheck"] < 0.01 * ref.n_hits
+    assert got["stats"]["n_poisson_fp64"] < 0.01 * ref.n_tasks
 
 
 def test_full_batch_sampled(sim, ogeo, oprm):
