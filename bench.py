@@ -284,9 +284,9 @@ def main():
         cpu = cpu_baseline(geo, prm, parts, args.cpu_seconds)
 
     # kernels of one atomic-mode batched step: call begin/end 2, range begin/end 2,
-    # particle tasks 1, two scans 6, task records 1, tile map 1, hits 1,
-    # recheck 1, compaction 5
-    launches_per_step = 21
+    # particle counts 1, task init 1, Poisson 1, two scans 6, task finish 1,
+    # hits 1, recheck 1, compaction 5 (count, scan 3, write)
+    launches_per_step = 22
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -132,13 +132,14 @@ struct fcs_workspace {
   Sizes* d_sizes = nullptr;
   Sizes* h_sizes = nullptr;  // pinned mirror
   int64_t sizes_cap = 0;
-  int32_t* nl = nullptr;
-  int64_t nl_cap = 0;
   int64_t* pcount = nullptr;
   int64_t* poff = nullptr;
   int64_t pc_cap = 0, po_cap = 0, pcap = 0;
   TaskRec* tasks = nullptr;
-  int64_t task_cap = 0;
+  float* tmu = nullptr;
+  int64_t* tn = nullptr;
+  int64_t* th = nullptr;
+  int64_t task_cap = 0, tmu_cap = 0, tn_cap = 0, th_cap = 0;
   int32_t* gmap = nullptr;
   int64_t gmap_cap = 0;
   uint2* recheck = nullptr;
@@ -172,7 +173,7 @@ struct fcs_workspace {
   ~fcs_workspace() {
     if (graph) cudaGraphExecDestroy(graph);
     for (cudaEvent_t e : tev) cudaEventDestroy(e);
-    void* ps[] = {d_sizes, nl, pcount, poff, tasks, gmap, recheck, acc, chunk_counts, chunk_offsets,
+    void* ps[] = {d_sizes, pcount, poff, tasks, tmu, tn, th, gmap, recheck, acc, chunk_counts, chunk_offsets,
                   block_sums, keys, keys_alt, head_flags, head_off, stage};
     for (void* p : ps)
       if (p) cudaFree(p);
@@ -182,11 +183,13 @@ struct fcs_workspace {
   WsDev view() const {
     WsDev w{};
     w.sizes = d_sizes;
-    w.nl = nl;
     w.pcount = pcount;
     w.poff = poff;
     w.pcap = pcap;
     w.tasks = tasks;
+    w.tmu = tmu;
+    w.tn = tn;
+    w.th = th;
     w.gmap = gmap;
     w.recheck = recheck;
     w.acc = acc;
@@ -216,13 +219,15 @@ int ws_reserve_static(fcs_workspace* ws, const fcs_geo* geo, int64_t P, int32_t 
   }
   const int NL = geo->d.n_layers;
   const int64_t Pc = std::max<int64_t>(P, 1);
-  if (Pc > ws->pcap || !ws->nl) {
-    FCS_TRY(grow(&ws->nl, &ws->nl_cap, Pc * NL));
-    FCS_TRY(grow(&ws->pcount, &ws->pc_cap, 2 * Pc));
-    FCS_TRY(grow(&ws->poff, &ws->po_cap, 2 * Pc));
+  if (Pc > ws->pcap || !ws->pcount) {
+    FCS_TRY(grow(&ws->pcount, &ws->pc_cap, Pc));
+    FCS_TRY(grow(&ws->poff, &ws->po_cap, Pc));
     ws->pcap = Pc;
   }
   FCS_TRY(grow(&ws->tasks, &ws->task_cap, Pc * NL));
+  FCS_TRY(grow(&ws->tmu, &ws->tmu_cap, Pc * NL));
+  FCS_TRY(grow(&ws->tn, &ws->tn_cap, Pc * NL));
+  FCS_TRY(grow(&ws->th, &ws->th_cap, Pc * NL));
   const int32_t stride = geo->d.acc_stride;
   if (stride != ws->acc_stride || rows > ws->rows_cap || !ws->acc) {
     int64_t cap = 0;
@@ -366,19 +371,16 @@ int enqueue_range(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, bool sync_siz
   if (tev) FCS_CUDA(cudaEventRecordWithFlags(tev[0], a.s, cudaEventRecordExternal));
   k_range_begin<<<1, 1, 0, a.s>>>(ws->d_sizes, a.parts.event_offsets, ev_lo, ev_hi, a.n_particles, ws->pcap);
   const uint32_t k0 = (uint32_t)(a.seed & 0xFFFFFFFFu), k1 = (uint32_t)(a.seed >> 32);
-  FCS_CUDA(launch_particle_tasks(a.geo->d, a.prm->d, a.parts, ev_lo, ev_hi, k0, k1, a.first_event, ws->view(), L));
   const ScanTmp tmp{ws->block_sums};
   WsDev w = ws->view();
-  FCS_CUDA(launch_scan_i64(w.pcount, w.poff, &w.sizes->n_part, 0, &w.sizes->n_tasks, 0, tmp, a.s));
-  FCS_CUDA(launch_scan_i64(w.pcount + w.pcap, w.poff + w.pcap, &w.sizes->n_part, 0, &w.sizes->n_hits, 0, tmp, a.s));
+  FCS_CUDA(launch_task_counts(a.geo->d, a.prm->d, a.parts, ev_lo, ev_hi, k0, k1, a.first_event, w, tmp, L));
   if (sync_size) {
     FCS_CUDA(cudaMemcpyAsync(ws->h_sizes, ws->d_sizes, sizeof(Sizes), cudaMemcpyDeviceToHost, a.s));
     FCS_CUDA(cudaStreamSynchronize(a.s));
     FCS_TRY(ws_reserve_hits(ws, ws->h_sizes->n_hits, a.cfg.mode));
     w = ws->view();
   }
-  FCS_CUDA(launch_task_write(a.geo->d, a.prm->d, a.parts, ev_lo, ev_hi, w, a.dbg, L));
-  FCS_CUDA(launch_granule_map(w, L));
+  FCS_CUDA(launch_task_finish(w, a.dbg, L));
   if (tev) FCS_CUDA(cudaEventRecordWithFlags(tev[1], a.s, cudaEventRecordExternal));
   FCS_CUDA(launch_hits(a.geo->d, a.prm->d, w, ev_lo, k0, k1, a.first_event, hc, key_task_bits, a.dbg, L));
   if (tev) FCS_CUDA(cudaEventRecordWithFlags(tev[2], a.s, cudaEventRecordExternal));
@@ -985,11 +987,13 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   w.num_sms = sms;
   Carve c{(unsigned char*)base, 0, (size_t)FCS_STATIC_SCRATCH_BYTES};
   w.d_sizes = c.take<Sizes>(1);
-  w.nl = c.take<int32_t>(P * NL);
-  w.pcount = c.take<int64_t>(2 * P);
-  w.poff = c.take<int64_t>(2 * P);
+  w.pcount = c.take<int64_t>(P);
+  w.poff = c.take<int64_t>(P);
   w.pcap = P;
   w.tasks = c.take<TaskRec>(P * NL);
+  w.tmu = c.take<float>(P * NL);
+  w.tn = c.take<int64_t>(P * NL);
+  w.th = c.take<int64_t>(P * NL);
   w.task_cap = P * NL;
   w.acc = c.take<float>((int64_t)n_events * geo->d.acc_stride);
   w.rows_cap = n_events;
@@ -1000,7 +1004,7 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   w.block_sums = c.take<int64_t>(kScanBlocks + 1);
   w.recheck = c.take<uint2>(recheck_cap);
   w.recheck_cap = recheck_cap;
-  const bool fits = w.d_sizes && w.nl && w.pcount && w.poff && w.tasks && w.acc && w.chunk_counts &&
+  const bool fits = w.d_sizes && w.pcount && w.poff && w.tasks && w.tmu && w.tn && w.th && w.acc && w.chunk_counts &&
                     w.chunk_offsets && w.block_sums && w.recheck && c.cap - c.off >= 4096;
   if (fits) {
     // the rest of the array maps tiles to tasks: it bounds the hits per call
@@ -1009,10 +1013,12 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   }
   auto release = [&]() {  // the array is not the workspace's to free
     w.d_sizes = nullptr;
-    w.nl = nullptr;
     w.pcount = nullptr;
     w.poff = nullptr;
     w.tasks = nullptr;
+    w.tmu = nullptr;
+    w.tn = nullptr;
+    w.th = nullptr;
     w.acc = nullptr;
     w.chunk_counts = nullptr;
     w.chunk_offsets = nullptr;

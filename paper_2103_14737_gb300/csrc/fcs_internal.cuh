@@ -97,11 +97,13 @@ static_assert(sizeof(Sizes) % 8 == 0 && offsetof(Sizes, queue) % 8 == 0, "Sizes 
 // Workspace views passed to kernels.
 struct WsDev {
   Sizes* sizes;
-  int32_t* nl;         // [pcap][NL] hits per (particle, layer), 0 = no task
-  int64_t* pcount;     // [2][pcap] tasks, hits per particle
-  int64_t* poff;       // [2][pcap] exclusive offsets
+  int64_t* pcount;     // [pcap] tasks per particle
+  int64_t* poff;       // [pcap] exclusive offsets
   int64_t pcap;        // particle capacity
   TaskRec* tasks;      // [task_cap]
+  float* tmu;          // [task_cap] Poisson mean of each task
+  int64_t* tn;         // [task_cap] hits of each task
+  int64_t* th;         // [task_cap] first hit of each task (exclusive scan of tn)
   int32_t* gmap;       // [gmap_cap] granule -> task
   uint2* recheck;      // [recheck_cap] (task, hit in task)
   float* acc;          // [rows][acc_stride] zero-maintained accumulation rows
@@ -158,14 +160,12 @@ cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, const int64_t* n_de
                             int64_t* total_dst, int64_t total_add_base_from_dst, ScanTmp tmp,
                             cudaStream_t s);
 
-// fcs_tasks.cu
-cudaError_t launch_particle_tasks(const GeoDev& g, const ParamDev& p, const fcs_particles& parts,
-                                  int32_t ev_lo, int32_t ev_hi, uint32_t k0, uint32_t k1,
-                                  int64_t first_event, WsDev w, const Launch& L);
-cudaError_t launch_task_write(const GeoDev& g, const ParamDev& p, const fcs_particles& parts,
-                              int32_t ev_lo, int32_t ev_hi, WsDev w, const fcs_debug* dbg,
-                              const Launch& L);
-cudaError_t launch_granule_map(WsDev w, const Launch& L);
+// fcs_tasks.cu: tasks, Poisson counts and the two scans (task and hit offsets);
+// then the records' hit offsets, the tile map and the validation dumps.
+cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_particles& parts,
+                               int32_t ev_lo, int32_t ev_hi, uint32_t k0, uint32_t k1,
+                               int64_t first_event, WsDev w, ScanTmp tmp, const Launch& L);
+cudaError_t launch_task_finish(WsDev w, const fcs_debug* dbg, const Launch& L);
 
 // fcs_hits.cu
 struct HitCfg {

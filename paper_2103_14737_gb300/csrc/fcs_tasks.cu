@@ -1,7 +1,8 @@
 // fcs_tasks.cu - task build of the hit loop (Listing 1): per particle the
-// parametrisation entry, per layer the float layer energy, the Poisson hit
-// count (get_number_of_hits) and the float hit energy, then compacted task
-// records in (event, particle, layer) order and the tile -> task map.
+// parametrisation entry and its layers with a non-zero float layer energy;
+// per task the Poisson hit count (get_number_of_hits) and the float hit
+// energy; task records in (event, particle, layer) order and the tile -> task
+// map.  Flat per-task kernels keep the Poisson draws of a warp together.
 #include "fcs_internal.cuh"
 
 namespace fcs {
@@ -112,14 +113,35 @@ __device__ __forceinline__ PtrsConst32 ptrs_const32(float mu) {
   return c;
 }
 
+// FP32 images of the 53-bit uniform u = N 2^-53, N = (a >> 5) 2^26 + (b >> 6),
+// built from 32-bit integer conversions only (64-bit integer conversions run
+// on the FP64 pipe).  Relative error <= 2^-23 each; where two terms of
+// opposite sign could cancel, the difference is formed exactly in 32 bits.
+__device__ __forceinline__ float u53f(uint32_t a, uint32_t b) {
+  return fmaf((float)(b >> 6), 0x1p-53f, (float)(a >> 5) * 0x1p-27f);
+}
+__device__ __forceinline__ float u53f_minus_half(uint32_t a, uint32_t b) {  // u - 0.5
+  const uint32_t hi = a >> 5, lo = b >> 6;
+  if (hi >= (1u << 26)) return fmaf((float)lo, 0x1p-53f, (float)(hi - (1u << 26)) * 0x1p-27f);
+  const uint32_t hd = (1u << 26) - hi;  // u - 0.5 = -(hd 2^26 - lo) 2^-53
+  if (hd < 64u) return -(float)((hd << 26) - lo) * 0x1p-53f;
+  return fmaf((float)lo, 0x1p-53f, -(float)hd * 0x1p-27f);
+}
+__device__ __forceinline__ float u53f_edge(uint32_t a, uint32_t b) {  // min(u, 1 - u)
+  const uint32_t hi = a >> 5, lo = b >> 6;
+  if (hi < (1u << 26)) return fmaf((float)lo, 0x1p-53f, (float)hi * 0x1p-27f);
+  const uint32_t hp = (1u << 27) - hi;  // 1 - u = (hp 2^26 - lo) 2^-53
+  if (hp < 64u) return (float)((hp << 26) - lo) * 0x1p-53f;
+  return fmaf(-(float)lo, 0x1p-53f, (float)hp * 0x1p-27f);
+}
+
 // One PTRS iteration in FP32.  Returns the accepted count, -1 for a certain
 // rejection, -2 when a decision is uncertain (redo the iteration in FP64).
-__device__ __forceinline__ int64_t ptrs_iter32(float mu, const PtrsConst32& c, uint64_t N, uint64_t M) {
-  if (N == 0) return -1;  // u == 0: us == 0 rejects
-  const uint64_t half = 1ull << 52;
-  const float Uf = (float)((int64_t)N - (int64_t)half) * 0x1p-53f;
-  const float usf = (float)(N < half ? N : (2 * half - N)) * 0x1p-53f;
-  const float Vf = (float)M * 0x1p-53f;
+__device__ __forceinline__ int64_t ptrs_iter32(float mu, const PtrsConst32& c, uint4 w) {
+  if ((w.x >> 5) == 0 && (w.y >> 6) == 0) return -1;  // u == 0: us == 0 rejects
+  const float Uf = u53f_minus_half(w.x, w.y);
+  const float usf = u53f_edge(w.x, w.y);
+  const float Vf = u53f(w.z, w.w);
   // k = floor((2a/us + b) U + mu + 0.43)
   const float t1 = c.two_a / usf;
   const float x = ((t1 + c.b) * Uf + mu) + 0.43f;
@@ -137,7 +159,7 @@ __device__ __forceinline__ int64_t ptrs_iter32(float mu, const PtrsConst32& c, u
   if (k_neg) return -1;
   if (!k_nonneg) return -2;
   const bool us_lt_0013 = 0.013f - usf > m_us, us_ge_0013 = usf - 0.013f > m_us;
-  const float m_vu = (Vf + usf) * 0x1p-22f;
+  const float m_vu = (Vf + usf) * 0x1p-20f;
   const bool v_gt_us = Vf - usf > m_vu, v_le_us = usf - Vf > m_vu;
   if (us_lt_0013 && v_gt_us) return -1;
   if (!(us_ge_0013 || v_le_us)) return -2;
@@ -152,19 +174,15 @@ __device__ __forceinline__ int64_t ptrs_iter32(float mu, const PtrsConst32& c, u
   return -2;
 }
 
-__device__ __forceinline__ uint64_t bits53(uint32_t a, uint32_t b) {
-  return ((uint64_t)(a >> 5) << 26) | (uint64_t)(b >> 6);
-}
 
 // Poisson draw: FP32 where every decision is certified, FP64 otherwise; the
 // result equals poisson_draw's.  *fp64 counts draws that needed FP64.
 __device__ int64_t poisson_draw_fast(float mu32, uint32_t layer, uint32_t particle, uint32_t event, uint32_t k0,
                                      uint32_t k1, uint32_t* fp64) {
   if (!(mu32 > 0.0f)) return 0;
-  const double mu = (double)mu32;
   if (mu32 < 10.0f) {
     const uint4 x = philox4x32_10(make_uint4(0u, layer | (kPurposePoisson << 16), particle, event), k0, k1);
-    const float uf = (float)bits53(x.x, x.y) * 0x1p-53f;
+    const float uf = u53f(x.x, x.y);
     float p = expf(-mu32);
     float F = p;
     int k = 0;
@@ -178,30 +196,29 @@ __device__ int64_t poisson_draw_fast(float mu32, uint32_t layer, uint32_t partic
       F = F + p;
     }
     *fp64 += 1;
-    return poisson_draw(mu, layer, particle, event, k0, k1);
+    return poisson_draw((double)mu32, layer, particle, event, k0, k1);
   }
   if (mu32 > kPtrsFastMaxMu) {
     *fp64 += 1;
-    return poisson_draw(mu, layer, particle, event, k0, k1);
+    return poisson_draw((double)mu32, layer, particle, event, k0, k1);
   }
   const PtrsConst32 c = ptrs_const32(mu32);
   bool have64 = false;
   PtrsConst64 c64;
   for (uint32_t i = 0; i < kPtrsMaxIter; ++i) {
     const uint4 x = philox4x32_10(make_uint4(i, layer | (kPurposePoisson << 16), particle, event), k0, k1);
-    const uint64_t N = bits53(x.x, x.y), M = bits53(x.z, x.w);
-    int64_t k = ptrs_iter32(mu32, c, N, M);
+    int64_t k = ptrs_iter32(mu32, c, x);
     if (k == -2) {
       if (!have64) {
-        c64 = ptrs_const64(mu);
+        c64 = ptrs_const64((double)mu32);
         have64 = true;
         *fp64 += 1;
       }
-      k = ptrs_iter64(mu, c64, (double)N * (1.0 / 9007199254740992.0), (double)M * (1.0 / 9007199254740992.0));
+      k = ptrs_iter64((double)mu32, c64, u53(x.x, x.y), u53(x.z, x.w));
     }
     if (k >= 0) return k;
   }
-  return (int64_t)floor(mu);
+  return (int64_t)floorf(mu32);
 }
 
 // Parametrisation entry of a particle (without the layer index).
@@ -230,9 +247,8 @@ __device__ __forceinline__ int32_t event_of(const int64_t* off, int32_t ev_lo, i
   return lo;
 }
 
-__global__ void k_particle_tasks(const GeoDev g, const ParamDev p, const fcs_particles parts,
-                                 int32_t ev_lo, int32_t ev_hi, uint32_t k0, uint32_t k1,
-                                 int64_t first_event, WsDev w) {
+// Tasks of a particle: the layers with a non-zero float layer energy.
+__global__ void k_particle_count(const ParamDev p, const fcs_particles parts, int32_t ev_lo, WsDev w) {
   const int64_t pb = parts.event_offsets[ev_lo];
   const int64_t P = w.sizes->n_part;  // checked against the capacity and n_particles
   const int NL = p.NL;
@@ -241,45 +257,24 @@ __global__ void k_particle_tasks(const GeoDev g, const ParamDev p, const fcs_par
     const int64_t i = pb + li;
     const int32_t t = parts.type[i];
     const float E = parts.E[i], eta = parts.eta[i], phi = parts.phi[i];
-    int32_t* nl = w.nl + li * NL;
-    int64_t ntask = 0, nhit = 0;
-    uint32_t n_fp64 = 0;
+    int64_t cnt = 0;
     if (!particle_ok(p, t, E, eta, phi)) {
       atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_BAD_PARTICLE);
-      for (int l = 0; l < NL; ++l) nl[l] = 0;
     } else {
-      const int32_t e = event_of(parts.event_offsets, ev_lo, ev_hi, i);
-      const uint32_t pin = (uint32_t)(i - parts.event_offsets[e]);
-      const uint32_t ev = (uint32_t)(first_event + e);
       const int64_t base = (int64_t)param_entry(p, t, E, eta) * NL;
-      for (int l = 0; l < NL; ++l) {
-        const float El = __fmul_rn(E, p.frac[base + l]);
-        int32_t n = 0;
-        if (El > 0.0f) {
-          const float mu = __fdiv_rn(El, p.mhe[base + l]);
-          int64_t k = poisson_draw_fast(mu, (uint32_t)l, pin, ev, k0, k1, &n_fp64);
-          if (k < 1) k = 1;
-          if (k > 0x7FFFFFFF) k = 0x7FFFFFFF;
-          n = (int32_t)k;
-          ntask += 1;
-          nhit += n;
-        }
-        nl[l] = n;
-      }
+      for (int l = 0; l < NL; ++l) cnt += __fmul_rn(E, p.frac[base + l]) > 0.0f;
     }
-    w.pcount[li] = ntask;
-    w.pcount[w.pcap + li] = nhit;
-    if (n_fp64) atomicAdd(&w.sizes->n_poisson_fp64, n_fp64);
+    w.pcount[li] = cnt;
   }
 }
 
-__global__ void k_task_write(const GeoDev g, const ParamDev p, const fcs_particles parts,
-                             int32_t ev_lo, int32_t ev_hi, WsDev w, fcs_debug dbg, int has_dbg) {
+// Task records in (event, particle, layer) order, without hit counts; the
+// layer energy waits in Ehit and the Poisson mean in tmu.
+__global__ void k_task_init(const GeoDev g, const ParamDev p, const fcs_particles parts, int32_t ev_lo,
+                            int32_t ev_hi, WsDev w) {
   const int64_t pb = parts.event_offsets[ev_lo];
   const int64_t P = w.sizes->n_part;
   const int NL = p.NL;
-  const int64_t pcap = w.pcap;
-  const int64_t task_base = w.sizes->task_base;
   for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < P;
        li += (int64_t)gridDim.x * blockDim.x) {
     if (w.pcount[li] == 0) continue;
@@ -290,21 +285,18 @@ __global__ void k_task_write(const GeoDev g, const ParamDev p, const fcs_particl
     const int32_t pin = (int32_t)(i - parts.event_offsets[e]);
     const int64_t base = (int64_t)param_entry(p, t, E, eta) * NL;
     int64_t to = w.poff[li];
-    int64_t ho = w.poff[pcap + li];
-    const int32_t* nl = w.nl + li * NL;
     // FP32 scale factors of the (r, alpha) -> (eta, phi) map; the FP64 recheck
     // recomputes them in double exactly as the oracle does.
     const float ae = fabsf(eta);
     const float ch = coshf(eta), sh = sinhf(ae), th = tanhf(ae);
     for (int l = 0; l < NL; ++l) {
-      const int32_t n = nl[l];
-      if (n <= 0) continue;
       const float El = __fmul_rn(E, p.frac[base + l]);
+      if (!(El > 0.0f)) continue;
       TaskRec r;
-      r.hit_begin = ho;
-      r.n = n;
+      r.hit_begin = 0;
+      r.n = 0;
       r.entry = (int32_t)(base + l);
-      r.Ehit = __fdiv_rn(El, (float)n);
+      r.Ehit = El;
       r.eta_c = eta;
       r.phi_c = phi;
       const float R = (float)g.rz[l];
@@ -319,59 +311,80 @@ __global__ void k_task_write(const GeoDev g, const ParamDev p, const fcs_particl
       r.particle = pin;
       r.event = e;
       r.layer = l;
-      if (to < w.task_cap) w.tasks[to] = r;
-      if (has_dbg) {
-        const int64_t dt = task_base + to;
-        if (dt < dbg.task_capacity) {
-          if (dbg.task_event) dbg.task_event[dt] = e;
-          if (dbg.task_particle) dbg.task_particle[dt] = pin;
-          if (dbg.task_layer) dbg.task_layer[dt] = l;
-          if (dbg.task_n) dbg.task_n[dt] = n;
-          if (dbg.task_Ehit) dbg.task_Ehit[dt] = r.Ehit;
-        }
+      if (to < w.task_cap) {
+        w.tasks[to] = r;
+        w.tmu[to] = __fdiv_rn(El, p.mhe[base + l]);
       }
       to += 1;
-      ho += n;
     }
   }
 }
 
-// Granule g (hits [g*kGranule, (g+1)*kGranule)) -> task containing its first hit.
-__global__ void k_granule_map(WsDev w) {
-  const int64_t T = w.sizes->n_tasks;
-  const int64_t H = w.sizes->n_hits;
-  if (H > w.gmap_cap * (int64_t)kGranule) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_HIT_CAPACITY);
-    return;
+// One thread per task: n = max(1, Poisson(mu)).
+__global__ void k_task_poisson(WsDev w, uint32_t k0, uint32_t k1, uint32_t first_event_lo) {
+  const int64_t T = min(w.sizes->n_tasks, w.task_cap);
+  uint32_t fp64 = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x) {
+    const TaskRec& r = w.tasks[t];
+    int64_t k = poisson_draw_fast(w.tmu[t], (uint32_t)r.layer, (uint32_t)r.particle,
+                                  first_event_lo + (uint32_t)r.event, k0, k1, &fp64);
+    if (k < 1) k = 1;
+    if (k > 0x7FFFFFFF) k = 0x7FFFFFFF;
+    w.tn[t] = k;
   }
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = w.tasks[t].hit_begin;
-    const int64_t e = b + w.tasks[t].n;
-    for (int64_t gi = (b + kGranule - 1) / kGranule; gi * kGranule < e; ++gi) w.gmap[gi] = (int32_t)t;
+  fp64 = __reduce_add_sync(0xffffffffu, fp64);
+  if ((threadIdx.x & 31) == 0 && fp64) atomicAdd(&w.sizes->n_poisson_fp64, fp64);
+}
+
+// One thread per task: hit offsets, counts and hit energy; the tile map
+// (granule -> task containing its first hit); validation dumps.
+__global__ void k_task_finish(WsDev w, fcs_debug dbg, int has_dbg) {
+  const int64_t T = min(w.sizes->n_tasks, w.task_cap);
+  const int64_t H = w.sizes->n_hits;
+  const bool map_ok = H <= w.gmap_cap * (int64_t)kGranule;
+  if (!map_ok && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_HIT_CAPACITY);
+  const int64_t task_base = w.sizes->task_base;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x) {
+    TaskRec& r = w.tasks[t];
+    const int32_t n = (int32_t)w.tn[t];
+    const int64_t b = w.th[t];
+    const float Ehit = __fdiv_rn(r.Ehit, (float)n);
+    r.hit_begin = b;
+    r.n = n;
+    r.Ehit = Ehit;
+    if (map_ok)
+      for (int64_t gi = (b + kGranule - 1) / kGranule; gi * kGranule < b + n; ++gi) w.gmap[gi] = (int32_t)t;
+    if (has_dbg) {
+      const int64_t dt = task_base + t;
+      if (dt < dbg.task_capacity) {
+        if (dbg.task_event) dbg.task_event[dt] = r.event;
+        if (dbg.task_particle) dbg.task_particle[dt] = r.particle;
+        if (dbg.task_layer) dbg.task_layer[dt] = r.layer;
+        if (dbg.task_n) dbg.task_n[dt] = n;
+        if (dbg.task_Ehit) dbg.task_Ehit[dt] = Ehit;
+      }
+    }
   }
 }
 
 }  // namespace
 
-cudaError_t launch_particle_tasks(const GeoDev& g, const ParamDev& p, const fcs_particles& parts,
-                                  int32_t ev_lo, int32_t ev_hi, uint32_t k0, uint32_t k1,
-                                  int64_t first_event, WsDev w, const Launch& L) {
-  k_particle_tasks<<<L.num_sms * 4, 128, 0, L.s>>>(g, p, parts, ev_lo, ev_hi, k0, k1, first_event, w);
-  return cudaGetLastError();
+cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_particles& parts, int32_t ev_lo,
+                               int32_t ev_hi, uint32_t k0, uint32_t k1, int64_t first_event, WsDev w, ScanTmp tmp,
+                               const Launch& L) {
+  k_particle_count<<<L.num_sms * 4, 128, 0, L.s>>>(p, parts, ev_lo, w);
+  cudaError_t e = launch_scan_i64(w.pcount, w.poff, &w.sizes->n_part, 0, &w.sizes->n_tasks, 0, tmp, L.s);
+  if (e != cudaSuccess) return e;
+  k_task_init<<<L.num_sms * 4, 128, 0, L.s>>>(g, p, parts, ev_lo, ev_hi, w);
+  k_task_poisson<<<L.num_sms * 8, 128, 0, L.s>>>(w, k0, k1, (uint32_t)first_event);
+  // the scan counts the tasks actually written (n_tasks <= task_cap by construction)
+  return launch_scan_i64(w.tn, w.th, &w.sizes->n_tasks, 0, &w.sizes->n_hits, 0, tmp, L.s);
 }
 
-cudaError_t launch_task_write(const GeoDev& g, const ParamDev& p, const fcs_particles& parts,
-                              int32_t ev_lo, int32_t ev_hi, WsDev w, const fcs_debug* dbg,
-                              const Launch& L) {
+cudaError_t launch_task_finish(WsDev w, const fcs_debug* dbg, const Launch& L) {
   fcs_debug d{};
   if (dbg) d = *dbg;
-  k_task_write<<<L.num_sms * 4, 128, 0, L.s>>>(g, p, parts, ev_lo, ev_hi, w, d, dbg ? 1 : 0);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_granule_map(WsDev w, const Launch& L) {
-  k_granule_map<<<L.num_sms * 4, 256, 0, L.s>>>(w);
+  k_task_finish<<<L.num_sms * 8, 128, 0, L.s>>>(w, d, dbg ? 1 : 0);
   return cudaGetLastError();
 }
 
