@@ -66,7 +66,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -150,7 +150,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -284,9 +284,9 @@ def main():
         cpu = cpu_baseline(geo, prm, parts, args.cpu_seconds)
 
     # kernels of one atomic-mode batched step: call begin/end 2, range begin/end 2,
-    # particle counts 1, task init 1, Poisson 1, two scans 6, task finish 1,
-    # hits 1, recheck 1, compaction 5 (count, scan 3, write)
-    launches_per_step = 22
+    # particle counts 1, task init 1, Poisson FP32 + FP64 2, two scans 6,
+    # task finish 1, hits 1, recheck 1, compaction 5 (count, scan 3, write)
+    launches_per_step = 23
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

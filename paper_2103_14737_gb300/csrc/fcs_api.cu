@@ -139,7 +139,9 @@ struct fcs_workspace {
   float* tmu = nullptr;
   int64_t* tn = nullptr;
   int64_t* th = nullptr;
-  int64_t task_cap = 0, tmu_cap = 0, tn_cap = 0, th_cap = 0;
+  int32_t* tlist = nullptr;
+  int32_t* pdefer = nullptr;
+  int64_t task_cap = 0, tmu_cap = 0, tn_cap = 0, th_cap = 0, tl_cap = 0, pd_cap = 0;
   int32_t* gmap = nullptr;
   int64_t gmap_cap = 0;
   uint2* recheck = nullptr;
@@ -173,7 +175,7 @@ struct fcs_workspace {
   ~fcs_workspace() {
     if (graph) cudaGraphExecDestroy(graph);
     for (cudaEvent_t e : tev) cudaEventDestroy(e);
-    void* ps[] = {d_sizes, pcount, poff, tasks, tmu, tn, th, gmap, recheck, acc, chunk_counts, chunk_offsets,
+    void* ps[] = {d_sizes, pcount, poff, tasks, tmu, tn, th, tlist, pdefer, gmap, recheck, acc, chunk_counts, chunk_offsets,
                   block_sums, keys, keys_alt, head_flags, head_off, stage};
     for (void* p : ps)
       if (p) cudaFree(p);
@@ -190,6 +192,8 @@ struct fcs_workspace {
     w.tmu = tmu;
     w.tn = tn;
     w.th = th;
+    w.tlist = tlist;
+    w.pdefer = pdefer;
     w.gmap = gmap;
     w.recheck = recheck;
     w.acc = acc;
@@ -228,6 +232,8 @@ int ws_reserve_static(fcs_workspace* ws, const fcs_geo* geo, int64_t P, int32_t 
   FCS_TRY(grow(&ws->tmu, &ws->tmu_cap, Pc * NL));
   FCS_TRY(grow(&ws->tn, &ws->tn_cap, Pc * NL));
   FCS_TRY(grow(&ws->th, &ws->th_cap, Pc * NL));
+  FCS_TRY(grow(&ws->tlist, &ws->tl_cap, Pc * NL));
+  FCS_TRY(grow(&ws->pdefer, &ws->pd_cap, Pc * NL));
   const int32_t stride = geo->d.acc_stride;
   if (stride != ws->acc_stride || rows > ws->rows_cap || !ws->acc) {
     int64_t cap = 0;
@@ -293,6 +299,9 @@ __global__ void k_range_begin(Sizes* s, const int64_t* __restrict__ off, int32_t
   s->n_recheck = 0;
   s->n_records = 0;
   s->n_rec_used = 0;
+  s->n_inv = 0;
+  s->n_ptrs = 0;
+  s->n_pdefer = 0;
   s->queue = 0;
 }
 
@@ -528,18 +537,22 @@ int fcs_load_geometry(fcs_geo** out, const fcs_region* regions, int32_t n_region
   if ((rc = current_device(&geo->device)) != FCS_OK) return fail(rc);
   RegionF* d_rf;
   double *d_el, *d_de, *d_pl, *d_dp, *d_sp, *d_rz;
+  float* d_rz32;
   int32_t *d_ne, *d_np, *d_co, *d_lrb, *d_bar;
   if ((rc = dev_alloc(&d_rf, n_regions, &geo->allocs)) || (rc = dev_alloc(&d_el, n_regions, &geo->allocs)) ||
       (rc = dev_alloc(&d_de, n_regions, &geo->allocs)) || (rc = dev_alloc(&d_pl, n_regions, &geo->allocs)) ||
       (rc = dev_alloc(&d_dp, n_regions, &geo->allocs)) || (rc = dev_alloc(&d_sp, n_regions, &geo->allocs)) ||
       (rc = dev_alloc(&d_ne, n_regions, &geo->allocs)) || (rc = dev_alloc(&d_np, n_regions, &geo->allocs)) ||
       (rc = dev_alloc(&d_co, n_regions, &geo->allocs)) || (rc = dev_alloc(&d_lrb, n_layers + 1, &geo->allocs)) ||
-      (rc = dev_alloc(&d_rz, n_layers, &geo->allocs)) || (rc = dev_alloc(&d_bar, n_layers, &geo->allocs)))
+      (rc = dev_alloc(&d_rz, n_layers, &geo->allocs)) || (rc = dev_alloc(&d_bar, n_layers, &geo->allocs)) ||
+      (rc = dev_alloc(&d_rz32, n_layers, &geo->allocs)))
     return fail(rc);
   std::vector<double> rz(n_layers);
+  std::vector<float> rz32(n_layers);
   std::vector<int32_t> bar(n_layers);
   for (int l = 0; l < n_layers; ++l) {
     rz[l] = layers[l].rz;
+    rz32[l] = (float)layers[l].rz;
     bar[l] = layers[l].barrel;
   }
   const struct {
@@ -551,7 +564,8 @@ int fcs_load_geometry(fcs_geo** out, const fcs_region* regions, int32_t n_region
                 {d_dp, dphi.data(), n_regions * sizeof(double)},  {d_sp, split.data(), n_regions * sizeof(double)},
                 {d_ne, ne.data(), n_regions * sizeof(int32_t)},   {d_np, np.data(), n_regions * sizeof(int32_t)},
                 {d_co, co.data(), n_regions * sizeof(int32_t)},   {d_lrb, lrb, (n_layers + 1) * sizeof(int32_t)},
-                {d_rz, rz.data(), n_layers * sizeof(double)},     {d_bar, bar.data(), n_layers * sizeof(int32_t)}};
+                {d_rz, rz.data(), n_layers * sizeof(double)},     {d_bar, bar.data(), n_layers * sizeof(int32_t)},
+                {d_rz32, rz32.data(), n_layers * sizeof(float)}};
   for (const auto& c : copies) {
     cudaError_t e = cudaMemcpyAsync(c.d, c.h, c.n, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail(set_err(FCS_E_CUDA, "geometry copy: %s", cudaGetErrorString(e)));
@@ -574,6 +588,7 @@ int fcs_load_geometry(fcs_geo** out, const fcs_region* regions, int32_t n_region
   d.cell_off = d_co;
   d.lrb = d_lrb;
   d.rz = d_rz;
+  d.rz32 = d_rz32;
   d.barrel = d_bar;
   *out = geo;
   return ok();
@@ -632,15 +647,19 @@ int fcs_load_params(fcs_params** out, const fcs_geo* geo, const float* frac, con
     return code;
   };
   if ((rc = current_device(&prm->device)) != FCS_OK) return fail(rc);
-  float *d_frac, *d_mhe, *d_re, *d_ae, *d_w = nullptr;
+  float *d_frac, *d_mhe, *d_re, *d_ae, *d_lf, *d_w = nullptr;
   uint32_t* d_thr;
   uint16_t* d_guide;
   int32_t* d_bad = nullptr;
   if ((rc = dev_alloc(&d_frac, n_entries, &prm->allocs)) || (rc = dev_alloc(&d_mhe, n_entries, &prm->allocs)) ||
       (rc = dev_alloc(&d_re, NR + 1, &prm->allocs)) || (rc = dev_alloc(&d_ae, NA + 1, &prm->allocs)) ||
       (rc = dev_alloc(&d_thr, n_entries * kNBins, &prm->allocs)) ||
-      (rc = dev_alloc(&d_guide, n_entries * kGuideCells, &prm->allocs)))
+      (rc = dev_alloc(&d_guide, n_entries * kGuideCells, &prm->allocs)) ||
+      (rc = dev_alloc(&d_lf, kLfactEntries, &prm->allocs)))
     return fail(rc);
+  // log k! for the FP32 Poisson acceptance test, from the host's FP64 lgamma
+  std::vector<float> lf(kLfactEntries);
+  for (int k = 0; k < kLfactEntries; ++k) lf[k] = (float)std::lgamma((double)k + 1.0);
   if ((rc = dev_alloc(&d_w, n_entries * kNBins)) || (rc = dev_alloc(&d_bad, n_entries))) {
     if (d_w) cudaFree(d_w);
     return fail(rc);
@@ -654,6 +673,7 @@ int fcs_load_params(fcs_params** out, const fcs_geo* geo, const float* frac, con
       (e = cudaMemcpyAsync(d_mhe, mean_hit_E, n_entries * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_re, r_edges, (NR + 1) * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_ae, a_edges, (NA + 1) * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_lf, lf.data(), kLfactEntries * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_w, shape_w, n_entries * kNBins * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = launch_build_tables(d_w, (int)n_entries, d_thr, d_guide, d_bad, s)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess) {
@@ -668,6 +688,11 @@ int fcs_load_params(fcs_params** out, const fcs_geo* geo, const float* frac, con
   d.NL = NL;
   d.eta_scale = eta_bin_scale;
   d.ebin_min = ebin_log2_min;
+  d.eta_scale_int = (eta_bin_scale == std::floor(eta_bin_scale) && eta_bin_scale >= 1.0 && eta_bin_scale <= 255.0)
+                        ? (int32_t)eta_bin_scale
+                        : 0;
+  d.n_lfact = kLfactEntries;
+  d.lfact = d_lf;
   d.n_entries = (int32_t)n_entries;
   d.frac = d_frac;
   d.mhe = d_mhe;
@@ -994,6 +1019,8 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   w.tmu = c.take<float>(P * NL);
   w.tn = c.take<int64_t>(P * NL);
   w.th = c.take<int64_t>(P * NL);
+  w.tlist = c.take<int32_t>(P * NL);
+  w.pdefer = c.take<int32_t>(P * NL);
   w.task_cap = P * NL;
   w.acc = c.take<float>((int64_t)n_events * geo->d.acc_stride);
   w.rows_cap = n_events;
@@ -1004,7 +1031,9 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   w.block_sums = c.take<int64_t>(kScanBlocks + 1);
   w.recheck = c.take<uint2>(recheck_cap);
   w.recheck_cap = recheck_cap;
-  const bool fits = w.d_sizes && w.pcount && w.poff && w.tasks && w.tmu && w.tn && w.th && w.acc && w.chunk_counts &&
+  const bool fits = w.d_sizes && w.pcount && w.poff && w.tasks && w.tmu && w.tn && w.th && w.tlist && w.pdefer &&
+                    w.acc &&
+                    w.chunk_counts &&
                     w.chunk_offsets && w.block_sums && w.recheck && c.cap - c.off >= 4096;
   if (fits) {
     // the rest of the array maps tiles to tasks: it bounds the hits per call
@@ -1019,6 +1048,8 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
     w.tmu = nullptr;
     w.tn = nullptr;
     w.th = nullptr;
+    w.tlist = nullptr;
+    w.pdefer = nullptr;
     w.acc = nullptr;
     w.chunk_counts = nullptr;
     w.chunk_offsets = nullptr;

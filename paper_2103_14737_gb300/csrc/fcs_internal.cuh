@@ -18,6 +18,7 @@ constexpr int kNA = 8;
 constexpr int kGuideCells = 128; // guide cells per histogram (top 7 bits of word 0)
 constexpr int kGranule = 128;    // hits per granule of the tile -> task map (divides every tile)
 constexpr int kRecordCountBits = 5;  // deterministic mode: count - 1 in the low 5 bits
+constexpr int kLfactEntries = 8192;  // log k! table for the FP32 Poisson test (k < 8192)
 
 // Task record: one (event, particle, layer) of the hit loop of Listing 1.
 // 48 bytes; tasks are stored in (event, particle, layer) order and hits of a
@@ -57,6 +58,7 @@ struct GeoDev {
   const int32_t* cell_off;
   const int32_t* lrb;    // [n_layers + 1]
   const double* rz;      // [n_layers]
+  const float* rz32;     // [n_layers] FP32 copy for the fast path
   const int32_t* barrel; // [n_layers]
 };
 
@@ -65,7 +67,10 @@ struct ParamDev {
   int32_t NT, NE, NH, NL;
   double eta_scale;
   int32_t ebin_min;
+  int32_t eta_scale_int; // eta_scale when it is an integer in [1, 255] (exact integer binning), else 0
   int32_t n_entries;     // NT * NE * NH * NL
+  int32_t n_lfact;       // entries of lfact
+  const float* lfact;    // [n_lfact] FP32 of lgamma(k + 1) (host libm, rounded once)
   const float* frac;     // [n_entries]
   const float* mhe;      // [n_entries]
   const uint32_t* thr;   // [n_entries][128] inverse-CDF thresholds
@@ -88,6 +93,9 @@ struct Sizes {
   int64_t recheck_total;  // recheck hits over the call
   int64_t n_part;       // particles of the current event range (checked against the capacity)
   int64_t n_rec_used;   // deterministic records sorted (n_records clamped to the capacity)
+  int64_t n_inv;        // tasks queued for the inversion draw (front of tlist)
+  int64_t n_ptrs;       // tasks queued for the PTRS draw (back of tlist)
+  int64_t n_pdefer;     // draws deferred to FP64 in the current range
   unsigned long long queue;  // hit-kernel work-queue counter (tiles handed out)
   uint32_t flags;       // fcs_device_flag bits
   uint32_t n_poisson_fp64;  // Poisson draws that needed an FP64 decision (call total)
@@ -104,6 +112,8 @@ struct WsDev {
   float* tmu;          // [task_cap] Poisson mean of each task
   int64_t* tn;         // [task_cap] hits of each task
   int64_t* th;         // [task_cap] first hit of each task (exclusive scan of tn)
+  int32_t* tlist;      // [task_cap] task indices grouped by Poisson method
+  int32_t* pdefer;     // [task_cap] tasks whose draw is redone in FP64
   int32_t* gmap;       // [gmap_cap] granule -> task
   uint2* recheck;      // [recheck_cap] (task, hit in task)
   float* acc;          // [rows][acc_stride] zero-maintained accumulation rows

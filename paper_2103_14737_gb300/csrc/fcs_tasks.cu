@@ -99,10 +99,14 @@ constexpr float kPtrsFastMaxMu = 4096.0f;  // larger means go to FP64 (counts of
 
 struct PtrsConst32 {
   float loglam, b, a, invalpha, vr, two_a;
+  const float* lfact;  // log k! table (|error| <= 0.5 ulp + libm's)
+  int32_t n_lfact;
 };
 
-__device__ __forceinline__ PtrsConst32 ptrs_const32(float mu) {
+__device__ __forceinline__ PtrsConst32 ptrs_const32(float mu, const float* lfact, int32_t n_lfact) {
   PtrsConst32 c;
+  c.lfact = lfact;
+  c.n_lfact = n_lfact;
   const float slam = sqrtf(mu);
   c.loglam = logf(mu);
   c.b = fmaf(2.53f, slam, 0.931f);
@@ -152,7 +156,7 @@ __device__ __forceinline__ int64_t ptrs_iter32(float mu, const PtrsConst32& c, u
   const float m_us = 0x1p-23f, m_v = 0x1p-19f;
   const bool us_ge_007 = usf - 0.07f > m_us, us_lt_007 = 0.07f - usf > m_us;
   const bool v_le_vr = c.vr - Vf > m_v, v_gt_vr = Vf - c.vr > m_v;
-  if (us_ge_007 && v_le_vr) return k_sure ? (int64_t)kf : -2;
+  if (us_ge_007 && v_le_vr) return k_sure ? (int64_t)(int32_t)kf : -2;
   if (!(us_lt_007 || v_gt_vr)) return -2;  // quick-accept decision uncertain
   // reject: k < 0 || (us < 0.013 && V > us)
   const bool k_neg = x + bx < 0.0f, k_nonneg = x - bx >= 0.0f;
@@ -166,19 +170,21 @@ __device__ __forceinline__ int64_t ptrs_iter32(float mu, const PtrsConst32& c, u
   // full test: log V + log invalpha - log(a / us^2 + b) <= -mu + k log mu - lgamma(k + 1)
   if (!k_sure) return -2;
   const float l1 = logf(Vf), l2 = logf(c.invalpha), l3 = logf(c.a / (usf * usf) + c.b);
-  const float kl = kf * c.loglam, lg = lgammaf(kf + 1.0f);
+  const int32_t ki = (int32_t)kf;
+  const float kl = kf * c.loglam, lg = (ki < c.n_lfact) ? __ldg(c.lfact + ki) : lgammaf(kf + 1.0f);
   const float d = (l1 + l2 - l3) - ((-mu + kl) - lg);
   const float bd = (fabsf(l1) + fabsf(l2) + fabsf(l3) + fabsf(kl) + fabsf(lg) + mu + 1.0f) * 0x1p-18f;
-  if (d < -bd) return (int64_t)kf;
+  if (d < -bd) return (int64_t)ki;
   if (d > bd) return -1;
   return -2;
 }
 
 
-// Poisson draw: FP32 where every decision is certified, FP64 otherwise; the
-// result equals poisson_draw's.  *fp64 counts draws that needed FP64.
-__device__ int64_t poisson_draw_fast(float mu32, uint32_t layer, uint32_t particle, uint32_t event, uint32_t k0,
-                                     uint32_t k1, uint32_t* fp64) {
+// Poisson draw in FP32 where every decision is certified: the count, or -1
+// when a decision is uncertain (or mu is too large for FP32 headroom); the
+// caller then takes poisson_draw, the FP64 definition, for this task.
+__device__ __forceinline__ int32_t poisson_draw_fp32(float mu32, uint32_t layer, uint32_t particle, uint32_t event,
+                                                     uint32_t k0, uint32_t k1, const float* lfact, int32_t n_lfact) {
   if (!(mu32 > 0.0f)) return 0;
   if (mu32 < 10.0f) {
     const uint4 x = philox4x32_10(make_uint4(0u, layer | (kPurposePoisson << 16), particle, event), k0, k1);
@@ -189,47 +195,55 @@ __device__ int64_t poisson_draw_fast(float mu32, uint32_t layer, uint32_t partic
     while (true) {
       const float e = (float)(k + 2) * 0x1p-21f;
       if (uf < F - e) return k;          // u < F_k: stop at k
-      if (!(uf > F + e)) break;          // uncertain
+      if (!(uf > F + e)) return -1;      // uncertain
       if (k == kInvMax) return k;        // the definition stops here too
       k += 1;
       p = (p * mu32) * __frcp_rn((float)k);
       F = F + p;
     }
-    *fp64 += 1;
-    return poisson_draw((double)mu32, layer, particle, event, k0, k1);
   }
-  if (mu32 > kPtrsFastMaxMu) {
-    *fp64 += 1;
-    return poisson_draw((double)mu32, layer, particle, event, k0, k1);
-  }
-  const PtrsConst32 c = ptrs_const32(mu32);
-  bool have64 = false;
-  PtrsConst64 c64;
+  if (mu32 > kPtrsFastMaxMu) return -1;
+  const PtrsConst32 c = ptrs_const32(mu32, lfact, n_lfact);
   for (uint32_t i = 0; i < kPtrsMaxIter; ++i) {
     const uint4 x = philox4x32_10(make_uint4(i, layer | (kPurposePoisson << 16), particle, event), k0, k1);
-    int64_t k = ptrs_iter32(mu32, c, x);
-    if (k == -2) {
-      if (!have64) {
-        c64 = ptrs_const64((double)mu32);
-        have64 = true;
-        *fp64 += 1;
-      }
-      k = ptrs_iter64((double)mu32, c64, u53(x.x, x.y), u53(x.z, x.w));
-    }
-    if (k >= 0) return k;
+    const int64_t k = ptrs_iter32(mu32, c, x);
+    if (k == -2) return -1;
+    if (k >= 0) return (int32_t)k;
   }
-  return (int64_t)floorf(mu32);
+  return (int32_t)floorf(mu32);
 }
 
-// Parametrisation entry of a particle (without the layer index).
+// Parametrisation entry of a particle (without the layer index).  Energy bin
+// from the float's exponent field (= floor(log2 E) for normal E; subnormal E
+// clamps to bin 0).  |eta| bin: for an integer scale S < 256, |eta| S =
+// m S 2^(e - 150) with m the 24-bit significand, so its floor is an exact
+// integer shift; other scales take the FP64 product, which is exact too.
+__device__ __forceinline__ int32_t eta_bin(const ParamDev& p, float eta) {
+  const uint32_t bits = __float_as_uint(eta) & 0x7FFFFFFFu;
+  const int32_t ef = (int32_t)(bits >> 23);
+  int32_t hb;
+  if (p.eta_scale_int) {
+    if (ef >= 150 + 8) {
+      hb = p.NH - 1;
+    } else {
+      const uint32_t m = (bits & 0x7FFFFFu) | (ef ? 0x800000u : 0u);
+      const uint64_t prod = (uint64_t)m * (uint32_t)p.eta_scale_int;  // < 2^32
+      const int32_t sh = 150 - (ef ? ef : 1);
+      const uint64_t fl = (sh >= 0) ? (sh >= 64 ? 0 : prod >> sh) : (prod << (-sh));
+      hb = fl >= (uint64_t)(p.NH - 1) ? p.NH - 1 : (int32_t)fl;
+    }
+  } else {
+    const double ae = __dmul_rn(fabs((double)eta), p.eta_scale);
+    hb = (ae >= (double)(p.NH - 1)) ? (p.NH - 1) : (int32_t)floor(ae);
+  }
+  return hb;
+}
+
 __device__ __forceinline__ int32_t param_entry(const ParamDev& p, int32_t type, float E, float eta) {
-  int ex = 0;
-  (void)frexp((double)E, &ex);
-  int32_t eb = (ex - 1) - p.ebin_min;
+  const int32_t ef = (int32_t)((__float_as_uint(E) >> 23) & 0xFFu);  // E > 0
+  int32_t eb = (ef - 127) - p.ebin_min;
   eb = max(0, min(eb, p.NE - 1));
-  const double ae = __dmul_rn(fabs((double)eta), p.eta_scale);
-  const int32_t hb = (ae >= (double)(p.NH - 1)) ? (p.NH - 1) : (int32_t)floor(ae);
-  return (type * p.NE + eb) * p.NH + hb;
+  return (type * p.NE + eb) * p.NH + eta_bin(p, eta);
 }
 
 __device__ __forceinline__ bool particle_ok(const ParamDev& p, int32_t t, float E, float eta, float phi) {
@@ -269,71 +283,138 @@ __global__ void k_particle_count(const ParamDev p, const fcs_particles parts, in
 }
 
 // Task records in (event, particle, layer) order, without hit counts; the
-// layer energy waits in Ehit and the Poisson mean in tmu.
+// layer energy waits in Ehit and the Poisson mean in tmu.  Each task index is
+// also filed in tlist by draw method (inversion from the front, PTRS from the
+// back), with one list reservation per warp.
 __global__ void k_task_init(const GeoDev g, const ParamDev p, const fcs_particles parts, int32_t ev_lo,
                             int32_t ev_hi, WsDev w) {
   const int64_t pb = parts.event_offsets[ev_lo];
   const int64_t P = w.sizes->n_part;
   const int NL = p.NL;
-  for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < P;
-       li += (int64_t)gridDim.x * blockDim.x) {
-    if (w.pcount[li] == 0) continue;
-    const int64_t i = pb + li;
-    const int32_t t = parts.type[i];
-    const float E = parts.E[i], eta = parts.eta[i], phi = parts.phi[i];
-    const int32_t e = event_of(parts.event_offsets, ev_lo, ev_hi, i);
-    const int32_t pin = (int32_t)(i - parts.event_offsets[e]);
-    const int64_t base = (int64_t)param_entry(p, t, E, eta) * NL;
-    int64_t to = w.poff[li];
-    // FP32 scale factors of the (r, alpha) -> (eta, phi) map; the FP64 recheck
-    // recomputes them in double exactly as the oracle does.
-    const float ae = fabsf(eta);
-    const float ch = coshf(eta), sh = sinhf(ae), th = tanhf(ae);
-    for (int l = 0; l < NL; ++l) {
-      const float El = __fmul_rn(E, p.frac[base + l]);
-      if (!(El > 0.0f)) continue;
-      TaskRec r;
-      r.hit_begin = 0;
-      r.n = 0;
-      r.entry = (int32_t)(base + l);
-      r.Ehit = El;
-      r.eta_c = eta;
-      r.phi_c = phi;
-      const float R = (float)g.rz[l];
-      if (g.barrel[l]) {
-        r.s_phi = 1.0f / R;
-        r.s_eta = 1.0f / (R * ch);
-      } else {
-        const float m = (th * sh) / R;
-        r.s_phi = sh / R;
-        r.s_eta = (eta < 0.0f) ? m : -m;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base_i = (int64_t)blockIdx.x * blockDim.x; base_i < P; base_i += stride) {
+    const int64_t li = base_i + threadIdx.x;
+    const bool active = li < P && w.pcount[li] > 0;
+    int32_t n_inv = 0, n_ptrs = 0;
+    int64_t t_first = 0;
+    int32_t n_mine = 0;
+    if (active) {
+      const int64_t i = pb + li;
+      const int32_t t = parts.type[i];
+      const float E = parts.E[i], eta = parts.eta[i], phi = parts.phi[i];
+      const int32_t e = event_of(parts.event_offsets, ev_lo, ev_hi, i);
+      const int32_t pin = (int32_t)(i - parts.event_offsets[e]);
+      const int64_t base = (int64_t)param_entry(p, t, E, eta) * NL;
+      int64_t to = w.poff[li];
+      t_first = to;
+      // FP32 scale factors of the (r, alpha) -> (eta, phi) map; the FP64 recheck
+      // recomputes them in double exactly as the oracle does.
+      const float ae = fabsf(eta);
+      const float ch = coshf(eta), sh = sinhf(ae), th = tanhf(ae);
+      for (int l = 0; l < NL; ++l) {
+        const float El = __fmul_rn(E, p.frac[base + l]);
+        if (!(El > 0.0f)) continue;
+        TaskRec r;
+        r.hit_begin = 0;
+        r.n = 0;
+        r.entry = (int32_t)(base + l);
+        r.Ehit = El;
+        r.eta_c = eta;
+        r.phi_c = phi;
+        const float R = g.rz32[l];
+        if (g.barrel[l]) {
+          r.s_phi = 1.0f / R;
+          r.s_eta = 1.0f / (R * ch);
+        } else {
+          const float m = (th * sh) / R;
+          r.s_phi = sh / R;
+          r.s_eta = (eta < 0.0f) ? m : -m;
+        }
+        r.particle = pin;
+        r.event = e;
+        r.layer = l;
+        if (to < w.task_cap) {
+          w.tasks[to] = r;
+          const float mu = __fdiv_rn(El, p.mhe[base + l]);
+          w.tmu[to] = mu;
+          if (mu < 10.0f) ++n_inv;
+          else ++n_ptrs;
+          ++n_mine;
+        }
+        to += 1;
       }
-      r.particle = pin;
-      r.event = e;
-      r.layer = l;
-      if (to < w.task_cap) {
-        w.tasks[to] = r;
-        w.tmu[to] = __fdiv_rn(El, p.mhe[base + l]);
+    }
+    // warp-level reservation in both lists
+    int32_t xi = n_inv, xp = n_ptrs;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t yi = __shfl_up_sync(0xffffffffu, xi, o), yp = __shfl_up_sync(0xffffffffu, xp, o);
+      if (lane >= o) {
+        xi += yi;
+        xp += yp;
       }
-      to += 1;
+    }
+    unsigned long long bi = 0, bp = 0;
+    if (lane == 31) {
+      if (xi) bi = atomicAdd((unsigned long long*)&w.sizes->n_inv, (unsigned long long)xi);
+      if (xp) bp = atomicAdd((unsigned long long*)&w.sizes->n_ptrs, (unsigned long long)xp);
+    }
+    bi = __shfl_sync(0xffffffffu, bi, 31) + (unsigned long long)(xi - n_inv);
+    bp = __shfl_sync(0xffffffffu, bp, 31) + (unsigned long long)(xp - n_ptrs);
+    for (int32_t j = 0; j < n_mine; ++j) {
+      const int64_t t = t_first + j;
+      if (w.tmu[t] < 10.0f) w.tlist[bi++] = (int32_t)t;
+      else w.tlist[w.task_cap - 1 - (int64_t)(bp++)] = (int32_t)t;
     }
   }
 }
 
-// One thread per task: n = max(1, Poisson(mu)).
-__global__ void k_task_poisson(WsDev w, uint32_t k0, uint32_t k1, uint32_t first_event_lo) {
-  const int64_t T = min(w.sizes->n_tasks, w.task_cap);
-  uint32_t fp64 = 0;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x) {
+// One thread per task: n = max(1, Poisson(mu)) in FP32, inversion tasks
+// first, then PTRS tasks, from the grouped index list.  Draws the FP32 path
+// cannot certify are queued for k_task_poisson64, so that FP64 work runs in
+// full warps instead of stalling a warp for one lane.
+__global__ void k_task_poisson(WsDev w, uint32_t k0, uint32_t k1, uint32_t first_event_lo, const float* lfact,
+                               int32_t n_lfact) {
+  const int64_t n_inv = w.sizes->n_inv, n_all = n_inv + w.sizes->n_ptrs;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < n_all; j0 += stride) {
+    const int64_t j = j0 + threadIdx.x;
+    int32_t k = 0;
+    int64_t t = 0;
+    if (j < n_all) {
+      t = (j < n_inv) ? w.tlist[j] : w.tlist[w.task_cap - 1 - (j - n_inv)];
+      const TaskRec& r = w.tasks[t];
+      k = poisson_draw_fp32(w.tmu[t], (uint32_t)r.layer, (uint32_t)r.particle, first_event_lo + (uint32_t)r.event,
+                            k0, k1, lfact, n_lfact);
+      w.tn[t] = (k < 1) ? 1 : k;  // provisional for deferred draws
+    }
+    const bool defer = j < n_all && k < 0;
+    const unsigned m = __ballot_sync(0xffffffffu, defer);
+    if (m) {
+      unsigned long long b = 0;
+      const int l0 = __ffs(m) - 1;
+      if (lane == l0) b = atomicAdd((unsigned long long*)&w.sizes->n_pdefer, (unsigned long long)__popc(m));
+      b = __shfl_sync(0xffffffffu, b, l0);
+      if (defer) w.pdefer[b + __popc(m & ((1u << lane) - 1u))] = (int32_t)t;
+    }
+  }
+}
+
+// The deferred draws in FP64 (the definition itself).
+__global__ void __launch_bounds__(128) k_task_poisson64(WsDev w, uint32_t k0, uint32_t k1, uint32_t first_event_lo) {
+  const int64_t n = w.sizes->n_pdefer;
+  if (blockIdx.x == 0 && threadIdx.x == 0) w.sizes->n_poisson_fp64 += (uint32_t)n;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t t = w.pdefer[q];
     const TaskRec& r = w.tasks[t];
-    int64_t k = poisson_draw_fast(w.tmu[t], (uint32_t)r.layer, (uint32_t)r.particle,
-                                  first_event_lo + (uint32_t)r.event, k0, k1, &fp64);
+    int64_t k = poisson_draw((double)w.tmu[t], (uint32_t)r.layer, (uint32_t)r.particle,
+                             first_event_lo + (uint32_t)r.event, k0, k1);
     if (k < 1) k = 1;
     if (k > 0x7FFFFFFF) k = 0x7FFFFFFF;
     w.tn[t] = k;
   }
-  fp64 = __reduce_add_sync(0xffffffffu, fp64);
-  if ((threadIdx.x & 31) == 0 && fp64) atomicAdd(&w.sizes->n_poisson_fp64, fp64);
 }
 
 // One thread per task: hit offsets, counts and hit energy; the tile map
@@ -376,7 +457,8 @@ cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_par
   cudaError_t e = launch_scan_i64(w.pcount, w.poff, &w.sizes->n_part, 0, &w.sizes->n_tasks, 0, tmp, L.s);
   if (e != cudaSuccess) return e;
   k_task_init<<<L.num_sms * 4, 128, 0, L.s>>>(g, p, parts, ev_lo, ev_hi, w);
-  k_task_poisson<<<L.num_sms * 8, 128, 0, L.s>>>(w, k0, k1, (uint32_t)first_event);
+  k_task_poisson<<<L.num_sms * 8, 128, 0, L.s>>>(w, k0, k1, (uint32_t)first_event, p.lfact, p.n_lfact);
+  k_task_poisson64<<<L.num_sms * 2, 128, 0, L.s>>>(w, k0, k1, (uint32_t)first_event);
   // the scan counts the tasks actually written (n_tasks <= task_cap by construction)
   return launch_scan_i64(w.tn, w.th, &w.sizes->n_tasks, 0, &w.sizes->n_hits, 0, tmp, L.s);
 }
