@@ -160,6 +160,7 @@ def main():
     ap.add_argument("--extra", action="store_true", help="also time deterministic mode and per-event launches")
     ap.add_argument("--events", type=int, default=N_EVENTS, help="events per step (smaller cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
@@ -184,6 +185,12 @@ def main():
     first_event = rank * n_ev
     sim = fcs.Simulator(geo, prm)
     d = sim.to_device(parts)
+    # autotune the hit kernel's launch shape on this workload (not timed)
+    tune = None
+    if not args.hpt and not args.block and not args.no_tune:
+        b, h, table = sim.autotune(d, SEED, first_event=first_event, reps=3)
+        args.block, args.hpt = b, h
+        tune = {"block": b, "hits_per_thread": h, "hits_ms": {f"{k[0]}x{k[1]}": v for k, v in table.items()}}
     # size the workspace and the outputs with one synchronous call
     ref = sim.simulate(d, SEED, first_event=first_event, hits_per_thread=args.hpt, block=args.block)
     H = ref["stats"]["n_hits"]
@@ -296,9 +303,11 @@ def main():
                            "hits_per_step": H, "tasks_per_step": ref["stats"]["n_tasks"],
                            "nonzero_cells_per_step": ref["stats"]["n_nonzero"],
                            "recheck_hits_per_step": ref["stats"]["n_recheck"], "mode": "atomic",
+                           "hit_kernel_shape": f"{args.block or 256}x{args.hpt or 4}",
                            "launch": "batched, CUDA graph", "l2": "flushed between steps (256 MB write)",
                            "parallelism": f"replicas x{world} (events sharded, no collective)"},
                 "events_per_s": n_ev * world / (ms * 1e-3),
+                "autotune": tune,
                 "stages_ms": stage_ms,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches_per_step * args.steps, "wall_s": wall}

@@ -247,6 +247,22 @@ int fcs_simulate_events_host(const fcs_geo* geo, const fcs_params* prm, fcs_work
                              float* cell_E, int64_t* event_offsets_out, int64_t capacity,
                              fcs_stats* stats, cudaStream_t s);
 
+/* Autotuner of the hit kernel's launch shape (the grouped launch of Sec. 4
+ * with a tunable tile).  Runs the call described by the arguments (device
+ * pointers as for fcs_simulate_events; no outputs are kept) once for every
+ * supported (threads per block, hits per thread) pair in {128, 256, 512} x
+ * {1, 2, 4, 8}, `reps` timed repetitions each after one warm-up, and writes
+ * the pair with the smallest median hit-kernel time into config->block and
+ * config->hits_per_thread (config->mode selects the kernel variant; other
+ * fields are ignored).  ms: optional host [12] array, median milliseconds in
+ * the order block-major, hits-per-thread-minor.  Synchronous.  Errors as for
+ * fcs_simulate_events. */
+#define FCS_AUTOTUNE_SHAPES 12
+int fcs_autotune(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
+                 const fcs_particles* particles, int64_t n_particles, int32_t n_events,
+                 uint64_t seed, int64_t first_event, int32_t reps, fcs_config* config,
+                 float* ms, cudaStream_t s);
+
 /* Size of the library's static device scratch used by
  * fcs_simulate_events_static (16 MiB, held on every GPU that loads the
  * library until the process exits). */

@@ -311,9 +311,10 @@ __global__ void k_range_end(Sizes* s) {
   s->recheck_total += s->n_recheck;
 }
 
-__global__ void k_call_end(Sizes* s, int64_t* event_offsets_out, int32_t n_events, int64_t capacity) {
+__global__ void k_call_end(Sizes* s, int64_t* event_offsets_out, int32_t n_events, int64_t capacity,
+                           int32_t want_cells) {
   if (event_offsets_out) event_offsets_out[n_events] = s->nnz_total;
-  if (s->nnz_total > capacity) s->flags |= FCS_FLAG_OUT_CAPACITY;
+  if (want_cells && s->nnz_total > capacity) s->flags |= FCS_FLAG_OUT_CAPACITY;
 }
 
 __global__ void k_empty_offsets(int64_t* event_offsets_out, int32_t n_events) {
@@ -368,6 +369,16 @@ struct CallArgs {
   cudaStream_t s;
 };
 
+// Stage events: inside a stream capture they must be external events to
+// become event-record nodes of the graph; outside a capture plain records.
+cudaError_t record_stage(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t err = cudaStreamIsCapturing(s, &cs);
+  if (err != cudaSuccess) return err;
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                             : cudaEventRecord(e, s);
+}
+
 // Enqueues one event range.  sync_size: read the hit count back after the
 // scans and grow the hit-dependent buffers.
 int enqueue_range(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, bool sync_size, const HitCfg& hc,
@@ -377,7 +388,7 @@ int enqueue_range(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, bool sync_siz
   const int det = a.cfg.mode == FCS_MODE_DETERMINISTIC;
   const int32_t rows = ev_hi - ev_lo;
   cudaEvent_t* tev = a.cfg.timing ? &ws->tev[(size_t)(a.cfg.batched ? 0 : ev_lo) * 5] : nullptr;
-  if (tev) FCS_CUDA(cudaEventRecordWithFlags(tev[0], a.s, cudaEventRecordExternal));
+  if (tev) FCS_CUDA(record_stage(tev[0], a.s));
   k_range_begin<<<1, 1, 0, a.s>>>(ws->d_sizes, a.parts.event_offsets, ev_lo, ev_hi, a.n_particles, ws->pcap);
   const uint32_t k0 = (uint32_t)(a.seed & 0xFFFFFFFFu), k1 = (uint32_t)(a.seed >> 32);
   const ScanTmp tmp{ws->block_sums};
@@ -390,11 +401,11 @@ int enqueue_range(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, bool sync_siz
     w = ws->view();
   }
   FCS_CUDA(launch_task_finish(w, a.dbg, L));
-  if (tev) FCS_CUDA(cudaEventRecordWithFlags(tev[1], a.s, cudaEventRecordExternal));
+  if (tev) FCS_CUDA(record_stage(tev[1], a.s));
   FCS_CUDA(launch_hits(a.geo->d, a.prm->d, w, ev_lo, k0, k1, a.first_event, hc, key_task_bits, a.dbg, L));
-  if (tev) FCS_CUDA(cudaEventRecordWithFlags(tev[2], a.s, cudaEventRecordExternal));
+  if (tev) FCS_CUDA(record_stage(tev[2], a.s));
   FCS_CUDA(launch_recheck(a.geo->d, a.prm->d, w, ev_lo, k0, k1, a.first_event, det, key_task_bits, a.dbg, L));
-  if (tev) FCS_CUDA(cudaEventRecordWithFlags(tev[3], a.s, cudaEventRecordExternal));
+  if (tev) FCS_CUDA(record_stage(tev[3], a.s));
   if (!det) {
     FCS_CUDA(launch_compact(a.geo->d, w, rows, ev_lo, ws->chunk_counts, ws->chunk_offsets, tmp, a.cells_out,
                             a.cell_ids, a.cell_E, a.event_offsets_out, a.n_events, a.capacity, L));
@@ -405,7 +416,7 @@ int enqueue_range(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, bool sync_siz
                                ws->head_flags, ws->head_off, tmp, a.cells_out, a.cell_ids, a.cell_E,
                                a.event_offsets_out, a.n_events, a.capacity, L));
   }
-  if (tev) FCS_CUDA(cudaEventRecordWithFlags(tev[4], a.s, cudaEventRecordExternal));
+  if (tev) FCS_CUDA(record_stage(tev[4], a.s));
   k_range_end<<<1, 1, 0, a.s>>>(ws->d_sizes);
   return FCS_OK;
 }
@@ -430,7 +441,7 @@ int enqueue_call(const CallArgs& a, bool sync_size, const HitCfg& hc, int key_ta
   } else {
     for (int32_t e = 0; e < a.n_events; ++e) FCS_TRY(enqueue_range(a, e, e + 1, sync_size, hc, key_task_bits));
   }
-  k_call_end<<<1, 1, 0, a.s>>>(ws->d_sizes, a.event_offsets_out, a.n_events, a.capacity);
+  k_call_end<<<1, 1, 0, a.s>>>(ws->d_sizes, a.event_offsets_out, a.n_events, a.capacity, a.cell_ids ? 1 : 0);
   FCS_CUDA(cudaGetLastError());
   return FCS_OK;
 }
@@ -778,6 +789,9 @@ int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace
     return ok();
   }
   const int32_t rows = cfg.batched ? n_events : 1;
+  if ((int64_t)rows * geo->d.acc_stride >= (int64_t(1) << 32))
+    return set_err(FCS_E_RANGE, "%d events x %d cells exceed 2^32 accumulation cells; split the batch", rows,
+                   geo->d.acc_stride);
   FCS_TRY(ws_reserve_static(ws, geo, n_particles, rows, cfg.mode));
   const int key_task_bits = bits_for(std::max<int64_t>(n_particles, 1) * geo->d.n_layers);
   if (cfg.mode == FCS_MODE_DETERMINISTIC &&
@@ -861,6 +875,54 @@ int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace
     FCS_CUDA(cudaStreamSynchronize(s));
   }
   return status_from(*ws->h_sizes, stats);
+}
+
+int fcs_autotune(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws, const fcs_particles* particles,
+                 int64_t n_particles, int32_t n_events, uint64_t seed, int64_t first_event, int32_t reps,
+                 fcs_config* config, float* ms, cudaStream_t s) {
+  if (!config) return set_err(FCS_E_ARG, "config is required");
+  if (reps < 1 || reps > 1000) return set_err(FCS_E_ARG, "reps must be in [1, 1000]");
+  static const int kBlocks[3] = {128, 256, 512};
+  static const int kHpt[4] = {1, 2, 4, 8};
+  fcs_config c{};
+  c.mode = config->mode;
+  c.batched = 1;
+  c.sync = 1;
+  // sizes the workspace and validates the arguments
+  FCS_TRY(fcs_simulate_events(geo, prm, ws, particles, n_particles, n_events, seed, first_event, &c, nullptr, nullptr,
+                              nullptr, nullptr, 0, nullptr, nullptr, s));
+  if (n_events == 0) return ok();
+  float best = 1e30f;
+  int best_b = 256, best_h = 4;
+  std::vector<float> t((size_t)reps);
+  for (int ib = 0; ib < 3; ++ib) {
+    for (int ih = 0; ih < 4; ++ih) {
+      c.block = kBlocks[ib];
+      c.hits_per_thread = kHpt[ih];
+      c.sync = 0;
+      c.timing = 1;
+      for (int r = -1; r < reps; ++r) {
+        FCS_TRY(fcs_simulate_events(geo, prm, ws, particles, n_particles, n_events, seed, first_event, &c, nullptr,
+                                    nullptr, nullptr, nullptr, 0, nullptr, nullptr, s));
+        float st[FCS_N_STAGES];
+        FCS_TRY(fcs_workspace_timings(ws, st));
+        if (r >= 0) t[(size_t)r] = st[FCS_STAGE_HITS];
+      }
+      std::sort(t.begin(), t.end());
+      const float med = t[(size_t)reps / 2];
+      if (ms) ms[ib * 4 + ih] = med;
+      if (med < best) {
+        best = med;
+        best_b = kBlocks[ib];
+        best_h = kHpt[ih];
+      }
+    }
+  }
+  fcs_stats st{};
+  FCS_TRY(fcs_workspace_status(ws, &st, s));
+  config->block = best_b;
+  config->hits_per_thread = best_h;
+  return ok();
 }
 
 int fcs_simulate_events_host(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws, const int32_t* type,

@@ -21,6 +21,7 @@ static HitKParams make_params(const GeoDev& g, const ParamDev& p, WsDev w, int32
   kp.k1 = k1;
   kp.first_event_lo = (uint32_t)first_event;
   kp.key_task_bits = key_task_bits;
+  kp.key32 = g.n_cells < (1 << 19) ? 1 : 0;
   kp.dbg_hit_cell = dbg ? dbg->hit_cell : nullptr;
   kp.dbg_hit_bin = dbg ? dbg->hit_bin : nullptr;
   kp.dbg_hit_cap = dbg ? dbg->hit_capacity : 0;

@@ -34,6 +34,7 @@ struct HitKParams {
   uint32_t k0, k1;
   uint32_t first_event_lo;
   int32_t key_task_bits;
+  int32_t key32;  // 32-bit (cell, task-in-tile) match keys (n_cells < 2^19)
   int32_t* dbg_hit_cell;
   int16_t* dbg_hit_bin;
   int64_t dbg_hit_cap;
@@ -89,20 +90,20 @@ __device__ __forceinline__ int32_t lookup64(const GeoDev& g, int layer, double e
   return g.cell_off[r] + (int32_t)ie * np + (int32_t)ip;
 }
 
-static __device__ __noinline__ int32_t cell_fp64(const GeoDev& g, const ParamDev& p, const TaskRec& T,
-                                          uint4 x, int bin) {
+static __device__ __noinline__ int32_t cell_fp64(const GeoDev& g, const ParamDev& p, int32_t layer,
+                                                 float eta_c, float phi_c, uint4 x, int bin) {
   const int ir = bin >> 3, ia = bin & 7;
   const double r_lo = (double)p.r_edges[ir], r_hi = (double)p.r_edges[ir + 1];
   const double a_lo = (double)p.a_edges[ia], a_hi = (double)p.a_edges[ia + 1];
   const double r = __dadd_rn(r_lo, __dmul_rn(u24d(x.y), __dsub_rn(r_hi, r_lo)));
   const double alpha = __dadd_rn(a_lo, __dmul_rn(u24d(x.z), __dsub_rn(a_hi, a_lo)));
   double s_eta, s_phi;
-  scales64(g, T.layer, (double)T.eta_c, &s_eta, &s_phi);
+  scales64(g, layer, (double)eta_c, &s_eta, &s_phi);
   const double deta = __dmul_rn(__dmul_rn(r, cos(alpha)), s_eta);
   const double dphi = __dmul_rn(__dmul_rn(r, sin(alpha)), s_phi);
-  const double eta = __dadd_rn((double)T.eta_c, deta);
-  const double phi = __dadd_rn((double)T.phi_c, dphi);
-  return lookup64(g, T.layer, eta, phi);
+  const double eta = __dadd_rn((double)eta_c, deta);
+  const double phi = __dadd_rn((double)phi_c, dphi);
+  return lookup64(g, layer, eta, phi);
 }
 
 // ---- shared tables of a CTA ---------------------------------------------------
@@ -146,8 +147,22 @@ struct FastHit {
   bool sure;
 };
 
-__device__ __forceinline__ FastHit fast_cell(const HitSmemTables& tb, const TaskRec& T, uint4 x,
-                                             int bin) {
+// A task as the hit loop uses it, staged in shared memory per tile (48 B):
+// 32-bit offsets and the Philox counter words are formed once per task.
+struct TileTask {
+  int32_t rel;      // hit_begin - first hit of the tile (<= 0 for the tile's first task)
+  int32_t entry;    // parametrisation entry (with layer)
+  float Ehit, eta_c, phi_c, s_eta, s_phi;
+  uint32_t ctr_y;   // layer | purpose << 16
+  uint32_t ctr_z;   // particle in event
+  uint32_t ctr_w;   // event number of the random stream
+  uint32_t row_off; // accumulation row offset (atomic) or row * n_cells (deterministic)
+  int32_t layer;
+};
+static_assert(sizeof(TileTask) == 48, "TileTask layout");
+
+template <typename TT>
+__device__ __forceinline__ FastHit fast_cell(const HitSmemTables& tb, const TT& T, uint4 x, int bin) {
   const int ir = bin >> 3, ia = bin & 7;
   const float ur = u24f(x.y), ua = u24f(x.z);
   const float r = fmaf(ur, tb.rw[ir], tb.rlo[ir]);
@@ -180,8 +195,13 @@ __device__ __forceinline__ FastHit fast_cell(const HitSmemTables& tb, const Task
   const float kp = rintf(tp);
   const float ep = fmaf(fmaf(fabsf(R.phi_lo), 0x1p-23f, bp), R.inv_dphi, fmaf(fabsf(tp), 0x1p-21f, 0x1p-22f));
   sure &= fabsf(tp - kp) > ep;
-  int ip = (int)floorf(tp) % R.n_phi;
+  int ip = (int)floorf(tp);
   if (ip < 0) ip += R.n_phi;
+  else if (ip >= R.n_phi) ip -= R.n_phi;
+  if ((unsigned)ip >= (unsigned)R.n_phi) {  // more than one turn in phi: rare
+    ip %= R.n_phi;
+    if (ip < 0) ip += R.n_phi;
+  }
   FastHit f;
   f.cell = R.cell_off + ie * R.n_phi + ip;
   f.sure = sure;
@@ -189,14 +209,6 @@ __device__ __forceinline__ FastHit fast_cell(const HitSmemTables& tb, const Task
 }
 
 // ---- warp-level deposit / record emission -----------------------------------
-__device__ __forceinline__ void deposit_warp(bool ok, unsigned long long key, float* dst, float Ehit) {
-  const unsigned m = __ballot_sync(0xffffffffu, ok);
-  if (ok) {
-    const unsigned peers = __match_any_sync(m, key);
-    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(dst, __fmul_rn((float)__popc(peers), Ehit));
-  }
-}
-
 __device__ __forceinline__ void emit_warp(bool ok, unsigned long long gkey, const WsDev& w) {
   const int lane = threadIdx.x & 31;
   const unsigned m = __ballot_sync(0xffffffffu, ok);
@@ -218,11 +230,11 @@ __device__ __forceinline__ void emit_warp(bool ok, unsigned long long gkey, cons
   }
 }
 
-__device__ __forceinline__ void deposit_single(const HitKParams& kp, const TaskRec& T, int64_t task_rel,
+__device__ __forceinline__ void deposit_single(const HitKParams& kp, int32_t event, float Ehit, int64_t task_rel,
                                                int32_t cell, bool det) {
-  const int64_t row = T.event - kp.ev_lo;
+  const int64_t row = event - kp.ev_lo;
   if (!det) {
-    atomicAdd(kp.w.acc + row * kp.g.acc_stride + cell, T.Ehit);
+    atomicAdd(kp.w.acc + row * kp.g.acc_stride + cell, Ehit);
   } else {
     const unsigned long long gkey =
         ((unsigned long long)(row * kp.g.n_cells + cell) << kp.key_task_bits) | (unsigned long long)task_rel;
@@ -264,45 +276,59 @@ template <int BLOCK, int HPT, bool DET>
 __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKParams kp) {
   constexpr int TILE = BLOCK * HPT;
   static_assert(TILE % kGranule == 0, "tiles must start on granules");
-  static_assert(TILE < 32768, "owner index is int16");
+  static_assert(TILE <= 4096, "owner index and 32-bit match keys need TILE + 1 < 2^13");
   __shared__ HitSmemTables tb;
-  __shared__ __align__(16) TaskRec s_task[kSmemTasks];
+  __shared__ __align__(16) TileTask s_task[kSmemTasks];
   __shared__ int16_t s_owner[TILE];
   __shared__ int s_wmax[BLOCK / 32];
   __shared__ unsigned long long s_tile;
   load_tables(tb, kp.g, kp.p);
+  for (int i = threadIdx.x; i < TILE; i += BLOCK) s_owner[i] = 0;
   const WsDev& w = kp.w;
   const int64_t H = w.sizes->n_hits;
   const int64_t T_all = w.sizes->n_tasks;
-  if (H > w.gmap_cap * (int64_t)kGranule) return;  // flagged by the granule map
+  if (H > w.gmap_cap * (int64_t)kGranule) return;  // flagged by the task finish kernel
   const unsigned long long n_tiles = (unsigned long long)((H + TILE - 1) / TILE);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t hit_dbg_base = kp.dbg_hit_cell || kp.dbg_hit_bin ? w.sizes->hit_base : 0;
+  const uint32_t row_stride = DET ? (uint32_t)kp.g.n_cells : (uint32_t)kp.g.acc_stride;
   if (threadIdx.x == 0) s_tile = atomicAdd(&w.sizes->queue, 1ull);
   __syncthreads();
   unsigned long long tile = s_tile;
   while (tile < n_tiles) {
-    __syncthreads();  // everyone has read s_tile
+    __syncthreads();  // everyone has read s_tile; s_owner is zero again
     if (threadIdx.x == 0) s_tile = atomicAdd(&w.sizes->queue, 1ull);
     const int64_t h0 = (int64_t)tile * TILE;
-    const int64_t hN = min(h0 + (int64_t)TILE, H);
+    const int hn = (int)min((int64_t)TILE, H - h0);  // hits in this tile
     const int32_t t0 = w.gmap[h0 / kGranule];
-    const int32_t t1 = (hN < H) ? w.gmap[hN / kGranule] : (int32_t)(T_all - 1);
+    const int32_t t1 = (h0 + TILE < H) ? w.gmap[(h0 + TILE) / kGranule] : (int32_t)(T_all - 1);
     const int nt = t1 - t0 + 1;
-    const TaskRec* tp;
     if (nt <= kSmemTasks) {
-      const int4* src = reinterpret_cast<const int4*>(w.tasks + t0);
-      int4* dst = reinterpret_cast<int4*>(s_task);
-      for (int q = threadIdx.x; q < nt * 3; q += BLOCK) dst[q] = __ldg(src + q);
-      tp = s_task;
+      // stage the tile's tasks and mark where each starts
+      for (int j = threadIdx.x; j < nt; j += BLOCK) {
+        const TaskRec r = w.tasks[t0 + j];
+        const int64_t s = r.hit_begin - h0;
+        TileTask q;
+        q.rel = (int32_t)s;
+        q.entry = r.entry;
+        q.Ehit = r.Ehit;
+        q.eta_c = r.eta_c;
+        q.phi_c = r.phi_c;
+        q.s_eta = r.s_eta;
+        q.s_phi = r.s_phi;
+        q.ctr_y = (uint32_t)r.layer | (kPurposeHit << 16);
+        q.ctr_z = (uint32_t)r.particle;
+        q.ctr_w = kp.first_event_lo + (uint32_t)r.event;
+        q.row_off = (uint32_t)(r.event - kp.ev_lo) * row_stride;
+        q.layer = r.layer;
+        s_task[j] = q;
+        if (j > 0 && s < TILE) s_owner[s] = (int16_t)j;
+      }
     } else {
-      tp = w.tasks + t0;
-    }
-    for (int i = threadIdx.x; i < TILE; i += BLOCK) s_owner[i] = 0;
-    __syncthreads();
-    for (int j = threadIdx.x + 1; j < nt; j += BLOCK) {
-      const int64_t s = w.tasks[t0 + j].hit_begin - h0;
-      if (s < TILE) s_owner[s] = (int16_t)j;
+      for (int j = threadIdx.x + 1; j < nt; j += BLOCK) {
+        const int64_t s = w.tasks[t0 + j].hit_begin - h0;
+        if (s < TILE) s_owner[s] = (int16_t)j;
+      }
     }
     __syncthreads();
     owner_scan<BLOCK, HPT>(s_owner, s_wmax);
@@ -310,27 +336,45 @@ __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKPara
 #pragma unroll 1
     for (int k = 0; k < HPT; ++k) {
       const int i = warp * 32 * HPT + k * 32 + lane;
-      const int64_t h = h0 + i;
-      const bool valid = h < hN;
+      const bool valid = i < hn;
       const int tl = valid ? s_owner[i] : 0;
-      const TaskRec T = tp[tl];
-      const uint32_t hit = (uint32_t)(h - T.hit_begin);
-      const uint4 x = philox4x32_10(
-          make_uint4(hit, (uint32_t)T.layer | (kPurposeHit << 16), (uint32_t)T.particle,
-                     kp.first_event_lo + (uint32_t)T.event),
-          kp.k0, kp.k1);
+      TileTask T;
+      if (nt <= kSmemTasks) {
+        T = s_task[tl];
+      } else {  // more tasks than the shared copy holds: read the record itself
+        const TaskRec r = w.tasks[t0 + tl];
+        T.rel = (int32_t)(r.hit_begin - h0);
+        T.entry = r.entry;
+        T.Ehit = r.Ehit;
+        T.eta_c = r.eta_c;
+        T.phi_c = r.phi_c;
+        T.s_eta = r.s_eta;
+        T.s_phi = r.s_phi;
+        T.ctr_y = (uint32_t)r.layer | (kPurposeHit << 16);
+        T.ctr_z = (uint32_t)r.particle;
+        T.ctr_w = kp.first_event_lo + (uint32_t)r.event;
+        T.row_off = (uint32_t)(r.event - kp.ev_lo) * row_stride;
+        T.layer = r.layer;
+      }
+      const uint32_t hit = (uint32_t)(i - T.rel);
+      const uint4 x = philox4x32_10(make_uint4(hit, T.ctr_y, T.ctr_z, T.ctr_w), kp.k0, kp.k1);
       const int bin = sample_bin(kp.p, T.entry, x.x);
       const FastHit f = fast_cell(tb, T, x, bin);
       const bool ok = valid && f.sure;
       const bool need = valid && !f.sure;
-      const int64_t row = T.event - kp.ev_lo;
       if (!DET) {
-        deposit_warp(ok, ((unsigned long long)(uint32_t)tl << 32) | (uint32_t)f.cell,
-                     w.acc + row * kp.g.acc_stride + f.cell, T.Ehit);
+        // (cell, task-in-tile) identifies (address, hit energy): 19 + 13 bits
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+          const unsigned peers = kp.key32 ? __match_any_sync(m, ((uint32_t)f.cell << 13) | (uint32_t)tl)
+                                          : __match_any_sync(m, ((unsigned long long)(uint32_t)tl << 32) |
+                                                                    (uint32_t)f.cell);
+          if (lane == __ffs(peers) - 1)
+            atomicAdd(w.acc + T.row_off + f.cell, __fmul_rn((float)__popc(peers), T.Ehit));
+        }
       } else {
         const unsigned long long gkey =
-            ((unsigned long long)(row * kp.g.n_cells + f.cell) << kp.key_task_bits) |
-            (unsigned long long)(t0 + tl);
+            ((unsigned long long)(T.row_off + (uint32_t)f.cell) << kp.key_task_bits) | (unsigned long long)(t0 + tl);
         emit_warp(ok, gkey, w);
       }
       // queue the uncertain hits for the FP64 recheck
@@ -345,18 +389,23 @@ __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKPara
           if (pos < (unsigned long long)w.recheck_cap) {
             w.recheck[pos] = make_uint2((uint32_t)(t0 + tl), hit);
           } else {
-            const int32_t c = cell_fp64(kp.g, kp.p, T, x, bin);
-            deposit_single(kp, T, t0 + tl, c, DET);
+            const int32_t ev = (int32_t)(T.ctr_w - kp.first_event_lo);
+            const int32_t c = cell_fp64(kp.g, kp.p, T.layer, T.eta_c, T.phi_c, x, bin);
+            deposit_single(kp, ev, T.Ehit, t0 + tl, c, DET);
             atomicAdd((unsigned long long*)&w.sizes->n_inline, 1ull);
             atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_RECHECK_SPILL);
-            if (kp.dbg_hit_cell && hit_dbg_base + h < kp.dbg_hit_cap) kp.dbg_hit_cell[hit_dbg_base + h] = c;
+            if (kp.dbg_hit_cell && hit_dbg_base + h0 + i < kp.dbg_hit_cap) kp.dbg_hit_cell[hit_dbg_base + h0 + i] = c;
           }
         }
       }
-      if (valid && hit_dbg_base + h < kp.dbg_hit_cap) {
-        if (kp.dbg_hit_cell && f.sure) kp.dbg_hit_cell[hit_dbg_base + h] = f.cell;
-        if (kp.dbg_hit_bin) kp.dbg_hit_bin[hit_dbg_base + h] = (int16_t)bin;
+      if (kp.dbg_hit_cell || kp.dbg_hit_bin) {
+        const int64_t h = hit_dbg_base + h0 + i;
+        if (valid && h < kp.dbg_hit_cap) {
+          if (kp.dbg_hit_cell && f.sure) kp.dbg_hit_cell[h] = f.cell;
+          if (kp.dbg_hit_bin) kp.dbg_hit_bin[h] = (int16_t)bin;
+        }
       }
+      s_owner[i] = 0;  // ready for the next tile (each slot is read and reset by one thread)
     }
     __syncthreads();  // the tile's shared data is dead; s_tile holds the next tile
     tile = s_tile;
@@ -378,8 +427,8 @@ __global__ void __launch_bounds__(128) k_recheck(const __grid_constant__ HitKPar
                    kp.first_event_lo + (uint32_t)T.event),
         kp.k0, kp.k1);
     const int bin = sample_bin(kp.p, T.entry, x.x);
-    const int32_t c = cell_fp64(kp.g, kp.p, T, x, bin);
-    deposit_single(kp, T, q.x, c, DET);
+    const int32_t c = cell_fp64(kp.g, kp.p, T.layer, T.eta_c, T.phi_c, x, bin);
+    deposit_single(kp, T.event, T.Ehit, q.x, c, DET);
     const int64_t h = hit_dbg_base + T.hit_begin + q.y;
     if (kp.dbg_hit_cell && h < kp.dbg_hit_cap) kp.dbg_hit_cell[h] = c;
   }

@@ -30,7 +30,7 @@ MODE_ATOMIC, MODE_DETERMINISTIC = 0, 1
 EXPORTED = ("fcs_version", "fcs_last_error", "fcs_load_geometry", "fcs_geometry_info", "fcs_free_geometry",
             "fcs_load_params", "fcs_free_params", "fcs_workspace_create", "fcs_workspace_reserve",
             "fcs_workspace_status", "fcs_workspace_timings", "fcs_workspace_free", "fcs_simulate_events", "fcs_simulate_events_host",
-            "fcs_simulate_events_static", "fcs_simulate_backward")
+            "fcs_simulate_events_static", "fcs_autotune", "fcs_simulate_backward")
 
 
 class FcsError(RuntimeError):
@@ -101,6 +101,7 @@ def load_library(build_if_missing: bool = True):
         L.fcs_simulate_events_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i64, i32, u64, i64, vp, vp, vp, vp,
                                                i64, vp, vp]
         L.fcs_simulate_events_static.argtypes = [vp, vp, vp, i64, i32, u64, i64, vp, vp, vp, i64, vp, vp]
+        L.fcs_autotune.argtypes = [vp, vp, vp, vp, i64, i32, u64, i64, i32, vp, vp, vp]
         L.fcs_simulate_backward.argtypes = [vp, vp, vp, vp, i64, i32, u64, i64, vp, vp, vp, vp, vp]
         # every other entry point returns an int status (the ctypes default restype)
         _lib = L
@@ -252,6 +253,23 @@ def fcs_simulate_events_host(geo, prm, ws, type_, E, eta, phi, event_offsets, se
     return rc, st
 
 
+AUTOTUNE_BLOCKS = (128, 256, 512)
+AUTOTUNE_HPT = (1, 2, 4, 8)
+
+
+def fcs_autotune(geo, prm, ws, particles: fcs_particles, n_particles, n_events, seed, first_event, reps=3,
+                 mode=MODE_ATOMIC):
+    """Times every (block, hits_per_thread) shape of the hit kernel on this
+    workload; returns (block, hits_per_thread, {(block, hpt): median ms})."""
+    L = load_library()
+    cfg = make_config(mode=mode)
+    ms = (C.c_float * 12)()
+    _check(L.fcs_autotune(geo, prm, ws, C.byref(particles), int(n_particles), int(n_events),
+                          int(seed) & 0xFFFFFFFFFFFFFFFF, int(first_event), int(reps), C.byref(cfg), ms, _stream()))
+    table = {(b, h): float(ms[i * 4 + j]) for i, b in enumerate(AUTOTUNE_BLOCKS) for j, h in enumerate(AUTOTUNE_HPT)}
+    return cfg.block, cfg.hits_per_thread, table
+
+
 STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 
@@ -314,6 +332,12 @@ class Simulator:
             self.close()
         except Exception:
             pass
+
+    def autotune(self, dparts, seed, first_event=0, reps=3, mode=MODE_ATOMIC):
+        parts = fcs_particles(dparts["type"].data_ptr(), dparts["E"].data_ptr(), dparts["eta"].data_ptr(),
+                              dparts["phi"].data_ptr(), dparts["event_offsets"].data_ptr())
+        return fcs_autotune(self.geo, self.prm, self.ws, parts, dparts["E"].numel(),
+                            dparts["event_offsets"].numel() - 1, seed, first_event, reps, mode)
 
     @staticmethod
     def to_device(parts, device="cuda"):

@@ -220,3 +220,14 @@ def test_host_entry_point_matches(sim):
     assert np.array_equal(off, ref["event_offsets"].cpu().numpy())
     assert np.array_equal(ids[:n], ref["cell_ids"][:n].cpu().numpy())
     assert np.array_equal(E[:n].view(np.uint32), ref["cell_E"][:n].cpu().numpy().view(np.uint32))
+
+
+def test_autotune_picks_a_valid_shape(sim, ogeo, oprm):
+    parts = synth.pileup(seed=13, n_events=2, mu_pu=20)
+    d = sim.to_device(parts)
+    b, h, table = sim.autotune(d, 3, reps=1)
+    assert (b, h) in table and len(table) == 12
+    assert all(v > 0 for v in table.values()) and table[(b, h)] == min(table.values())
+    ref = O.simulate(ogeo, oprm, parts, seed=3)
+    got = sim.simulate(d, 3, block=b, hits_per_thread=h, mode=fcs.MODE_DETERMINISTIC, dense=True)
+    assert np.array_equal(got["cells"].cpu().numpy().view(np.uint32), ref.cells_canon.view(np.uint32))
