@@ -33,13 +33,37 @@ UNIT = "hits/s"
 WORKLOAD = "pileup64"
 N_EVENTS = 64
 SEED = 1
-# Algorithmic 32-bit ALU operations per hit (issue slots of one lane), counted
-# from the algorithm, not from compiled code: Philox4x32-10 40 (10 rounds of
-# two wide multiplies and two 3-input XORs), shape bin 8, uniforms 6,
-# (r, alpha) 6, sincos 3, (eta, phi) 6, region search 6, grid index 14,
-# certification bound 12, task lookup 4, warp-aggregated deposit 5.
-OPS_PER_HIT = 110
-SMS, LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+# ALU roofline of the hit kernel (the hit path's bound, per pipe):
+#   time per hit = sum over pipes of (algorithmic ops per hit / pipe peak),
+# with the algorithmic operation counts of one hit taken from the algorithm
+# (not from compiled code) and each pipe's peak derived from its lanes per SM
+# per clock x 152 SMs x 2070 MHz.  The lane counts of the integer, wide-multiply
+# and MUFU pipes are those the unit microbenchmarks show (fcs_microbench).
+OPS_PER_HIT = {
+    # Philox4x32-10: 10 rounds x 2 (32 x 32 -> 64-bit) multiplies
+    "mulwide": 20,
+    # Philox 20 3-input XORs; bin 6; uniforms 4; region search 6; grid index 10;
+    # deposit 4; task lookup 4
+    "int": 54,
+    # uniforms 2; (r, alpha) 2; sincos range 1; (eta, phi) 4; bounds 8;
+    # scaled indices 4; certification compares 8
+    "fp32": 29,
+    # sin, cos
+    "mufu": 2,
+}
+SMS, SM_MAX_MHZ = 152, 2070.0
+# DRAM bytes per hit of the hit kernel, from the committed ncu summary of its
+# 16-event capture (traffic grows with the hits): valid for the kernel version
+# captured there, None after a kernel change.
+K_HITS_DRAM_BYTES_PER_HIT = 4.26
+LANES_PER_SM_CLK = {"mulwide": 32, "int": 64, "fp32": 128, "mufu": 16}
+
+
+def alu_bound_hits_per_s():
+    t = 0.0
+    for k, n in OPS_PER_HIT.items():
+        t += n / (LANES_PER_SM_CLK[k] * SMS * SM_MAX_MHZ * 1e6)
+    return 1.0 / t
 
 
 def peaks():
@@ -240,12 +264,15 @@ def main():
 
     hit_ms = float(np.mean([s["hits"] for s in t_stage]))
     stage_ms = {k: float(np.mean([s[k] for s in t_stage])) for k in fcs.STAGES}
-    alu_peak = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12  # Tops/s (lane-ops)
-    achieved = H * OPS_PER_HIT / (hit_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                "frac": achieved / alu_peak, "traffic": None,
-                "kernel": "k_hits", "ops_per_hit": OPS_PER_HIT, "hits_per_launch": H,
-                "kernel_ms": hit_ms, "peak_note": "152 SMs x 128 lanes x 2070 MHz (derived)"}
+    achieved = H / (hit_ms * 1e-3) / 1e9
+    peak = alu_bound_hits_per_s() / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G hits/s",
+                "frac": achieved / peak,
+                "traffic": (K_HITS_DRAM_BYTES_PER_HIT * H if K_HITS_DRAM_BYTES_PER_HIT else None),
+                "traffic_note": "dram bytes per launch scaled by hits from the 16-event ncu capture",
+                "kernel": "k_hits", "hits_per_launch": H,
+                "kernel_ms": hit_ms, "ops_per_hit": OPS_PER_HIT, "lanes_per_sm_clk": LANES_PER_SM_CLK,
+                "peak_note": "derived: sum over pipes of ops/hit / (lanes x 152 SMs x 2070 MHz)"}
 
     extra = {}
     if args.extra and rank == 0:
@@ -286,6 +313,17 @@ def main():
         e2e = {"value": H / float(np.mean(tt)), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * float(np.mean(tt))}
 
+    # unit throughputs on this GPU (roofline denominators), measured after the timed region
+    pipes = None
+    if rank == 0:
+        acc_cells = n_ev * geo.n_cells
+        pipes = {"philox_blocks_per_s": fcs.fcs_microbench(fcs.MB_PHILOX, 0, 256),
+                 "mulwide_per_s": fcs.fcs_microbench(fcs.MB_MULWIDE, 0, 1024),
+                 "lop3_steps_per_s": fcs.fcs_microbench(fcs.MB_LOP3, 0, 1024),
+                 "ffma_per_s": fcs.fcs_microbench(fcs.MB_FFMA, 0, 1024),
+                 "red_f32_random_per_s": fcs.fcs_microbench(fcs.MB_RED, acc_cells, 64),
+                 "red_array_floats": acc_cells}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(geo, prm, parts, args.cpu_seconds)
@@ -309,7 +347,7 @@ def main():
                 "events_per_s": n_ev * world / (ms * 1e-3),
                 "autotune": tune,
                 "stages_ms": stage_ms,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "roofline": roofline, "pipes": pipes, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches_per_step * args.steps, "wall_s": wall}
         line.update(extra)
         print(json.dumps(line), flush=True)

@@ -263,6 +263,18 @@ int fcs_autotune(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
                  uint64_t seed, int64_t first_event, int32_t reps, fcs_config* config,
                  float* ms, cudaStream_t s);
 
+/* Throughput microbenchmarks of the units the hit path uses (the roofline
+ * denominators): kind FCS_MB_PHILOX = Philox4x32-10 blocks/s; FCS_MB_MULWIDE =
+ * 32x32->64-bit integer multiplies/s (each followed by a 2-input XOR);
+ * FCS_MB_LOP3 = shift + 3-input XOR + add steps/s; FCS_MB_FFMA = FP32 FMAs/s;
+ * FCS_MB_RED = float reductions into global memory at uniformly random
+ * addresses of a `size`-float array per second.  A full grid (4 waves of
+ * 256-thread blocks) runs `iters` iterations per thread, once to warm up and
+ * once timed with CUDA events on stream s; *rate receives operations per
+ * second.  Allocates and frees its own device buffer.  Synchronous. */
+enum fcs_microbench_kind { FCS_MB_PHILOX = 0, FCS_MB_MULWIDE = 1, FCS_MB_LOP3 = 2, FCS_MB_FFMA = 3, FCS_MB_RED = 4 };
+int fcs_microbench(int32_t kind, int64_t size, int32_t iters, double* rate, cudaStream_t s);
+
 /* Size of the library's static device scratch used by
  * fcs_simulate_events_static (16 MiB, held on every GPU that loads the
  * library until the process exits). */

@@ -660,7 +660,7 @@ int fcs_load_params(fcs_params** out, const fcs_geo* geo, const float* frac, con
   if ((rc = current_device(&prm->device)) != FCS_OK) return fail(rc);
   float *d_frac, *d_mhe, *d_re, *d_ae, *d_lf, *d_w = nullptr;
   uint32_t* d_thr;
-  uint16_t* d_guide;
+  uint2* d_guide;
   int32_t* d_bad = nullptr;
   if ((rc = dev_alloc(&d_frac, n_entries, &prm->allocs)) || (rc = dev_alloc(&d_mhe, n_entries, &prm->allocs)) ||
       (rc = dev_alloc(&d_re, NR + 1, &prm->allocs)) || (rc = dev_alloc(&d_ae, NA + 1, &prm->allocs)) ||

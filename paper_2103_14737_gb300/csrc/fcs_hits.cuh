@@ -42,8 +42,11 @@ struct HitKParams {
 
 // ---- shape bin: inverse CDF by guide table and binary search --------------
 __device__ __forceinline__ int sample_bin(const ParamDev& p, int32_t entry, uint32_t x0) {
-  const uint16_t gg = __ldg(p.guide + (size_t)entry * kGuideCells + (x0 >> 25));
-  int lo = gg & 0xFF, hi = gg >> 8;
+  const uint2 gg = __ldg(p.guide + (size_t)entry * kGuideCells + (x0 >> 25));
+  int lo = gg.y & 0xFF, hi = (gg.y >> 8) & 0xFF;
+  if (lo == hi) return lo;
+  if (x0 < gg.x) return lo;  // the first candidate's threshold comes with the guide cell
+  lo += 1;
   const uint32_t* T = p.thr + (size_t)entry * kNBins;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
@@ -110,8 +113,8 @@ static __device__ __noinline__ int32_t cell_fp64(const GeoDev& g, const ParamDev
 struct HitSmemTables {
   RegionF reg[kMaxRegions];
   int32_t lrb[kMaxLayers + 1];
-  float rlo[kNR], rw[kNR], rhi[kNR];
-  float alo[kNA], aw[kNA];  // alpha_lo - pi and bin widths
+  float4 rb[kNR];  // r bin: lo, width, hi
+  float2 ab[kNA];  // alpha bin: lo - pi, width
 };
 
 __device__ __forceinline__ void load_tables(HitSmemTables& t, const GeoDev& g, const ParamDev& p) {
@@ -119,14 +122,11 @@ __device__ __forceinline__ void load_tables(HitSmemTables& t, const GeoDev& g, c
   for (int i = threadIdx.x; i <= g.n_layers; i += blockDim.x) t.lrb[i] = g.lrb[i];
   if (threadIdx.x < kNR) {
     const float lo = p.r_edges[threadIdx.x], hi = p.r_edges[threadIdx.x + 1];
-    t.rlo[threadIdx.x] = lo;
-    t.rw[threadIdx.x] = hi - lo;
-    t.rhi[threadIdx.x] = hi;
+    t.rb[threadIdx.x] = make_float4(lo, hi - lo, hi, 0.0f);
   }
   if (threadIdx.x < kNA) {
     const double lo = p.a_edges[threadIdx.x], hi = p.a_edges[threadIdx.x + 1];
-    t.alo[threadIdx.x] = (float)(lo - 3.141592653589793);
-    t.aw[threadIdx.x] = (float)(hi - lo);
+    t.ab[threadIdx.x] = make_float2((float)(lo - 3.141592653589793), (float)(hi - lo));
   }
 }
 
@@ -157,7 +157,7 @@ struct TileTask {
   uint32_t ctr_z;   // particle in event
   uint32_t ctr_w;   // event number of the random stream
   uint32_t row_off; // accumulation row offset (atomic) or row * n_cells (deterministic)
-  int32_t layer;
+  uint32_t lay;     // layer | first region << 8 | end region << 20
 };
 static_assert(sizeof(TileTask) == 48, "TileTask layout");
 
@@ -165,19 +165,21 @@ template <typename TT>
 __device__ __forceinline__ FastHit fast_cell(const HitSmemTables& tb, const TT& T, uint4 x, int bin) {
   const int ir = bin >> 3, ia = bin & 7;
   const float ur = u24f(x.y), ua = u24f(x.z);
-  const float r = fmaf(ur, tb.rw[ir], tb.rlo[ir]);
-  const float ap = fmaf(ua, tb.aw[ia], tb.alo[ia]);  // alpha - pi
+  const float4 rbin = tb.rb[ir];
+  const float2 abin = tb.ab[ia];
+  const float r = fmaf(ur, rbin.y, rbin.x);
+  const float ap = fmaf(ua, abin.y, abin.x);  // alpha - pi
   float sn, cs;
   __sincosf(ap, &sn, &cs);
   const float de = (r * -cs) * T.s_eta;
   const float dp = (r * -sn) * T.s_phi;
   const float eta = T.eta_c + de;
   const float phi = T.phi_c + dp;
-  const float rh = tb.rhi[ir];
+  const float rh = rbin.z;
   const float be = fmaf(rh * fabsf(T.s_eta), 0x1p-17f, fabsf(eta) * 0x1p-21f);
   const float bp = fmaf(rh * fabsf(T.s_phi), 0x1p-17f, fabsf(phi) * 0x1p-21f);
   bool sure = (fabsf(eta) < 1.0e30f) && (fabsf(phi) < 1.0e30f);
-  const int rb = tb.lrb[T.layer], re = tb.lrb[T.layer + 1];
+  const int rb = (T.lay >> 8) & 0xFFF, re = T.lay >> 20;
   int rr = rb;
   for (int q = rb + 1; q < re; ++q) {
     const float sp = tb.reg[q].split;
@@ -320,7 +322,7 @@ __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKPara
         q.ctr_z = (uint32_t)r.particle;
         q.ctr_w = kp.first_event_lo + (uint32_t)r.event;
         q.row_off = (uint32_t)(r.event - kp.ev_lo) * row_stride;
-        q.layer = r.layer;
+        q.lay = (uint32_t)r.layer | ((uint32_t)tb.lrb[r.layer] << 8) | ((uint32_t)tb.lrb[r.layer + 1] << 20);
         s_task[j] = q;
         if (j > 0 && s < TILE) s_owner[s] = (int16_t)j;
       }
@@ -354,7 +356,7 @@ __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKPara
         T.ctr_z = (uint32_t)r.particle;
         T.ctr_w = kp.first_event_lo + (uint32_t)r.event;
         T.row_off = (uint32_t)(r.event - kp.ev_lo) * row_stride;
-        T.layer = r.layer;
+        T.lay = (uint32_t)r.layer | ((uint32_t)tb.lrb[r.layer] << 8) | ((uint32_t)tb.lrb[r.layer + 1] << 20);
       }
       const uint32_t hit = (uint32_t)(i - T.rel);
       const uint4 x = philox4x32_10(make_uint4(hit, T.ctr_y, T.ctr_z, T.ctr_w), kp.k0, kp.k1);
@@ -390,7 +392,7 @@ __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKPara
             w.recheck[pos] = make_uint2((uint32_t)(t0 + tl), hit);
           } else {
             const int32_t ev = (int32_t)(T.ctr_w - kp.first_event_lo);
-            const int32_t c = cell_fp64(kp.g, kp.p, T.layer, T.eta_c, T.phi_c, x, bin);
+            const int32_t c = cell_fp64(kp.g, kp.p, (int32_t)(T.lay & 0xFF), T.eta_c, T.phi_c, x, bin);
             deposit_single(kp, ev, T.Ehit, t0 + tl, c, DET);
             atomicAdd((unsigned long long*)&w.sizes->n_inline, 1ull);
             atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_RECHECK_SPILL);

@@ -6,7 +6,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/fcs.h"
+#include "fcs.h"  // include/ is on the include path (build.py)
 
 namespace fcs {
 
@@ -74,7 +74,7 @@ struct ParamDev {
   const float* frac;     // [n_entries]
   const float* mhe;      // [n_entries]
   const uint32_t* thr;   // [n_entries][128] inverse-CDF thresholds
-  const uint16_t* guide; // [n_entries][128]: lo | hi << 8 search bounds per guide cell
+  const uint2* guide;    // [n_entries][128]: (T[lo], lo | hi << 8) per guide cell
   const float* r_edges;  // [17]
   const float* a_edges;  // [9]
 };
@@ -158,7 +158,7 @@ struct Launch {
 };
 
 // fcs_params.cu
-cudaError_t launch_build_tables(const float* shape_w, int n_entries, uint32_t* thr, uint16_t* guide,
+cudaError_t launch_build_tables(const float* shape_w, int n_entries, uint32_t* thr, uint2* guide,
                                 int32_t* bad, cudaStream_t s);
 
 // fcs_scan.cu: exclusive scan of n int64 values (n on the host or device).

@@ -9,21 +9,22 @@
 // Guide table (Chen and Asau's indexed search): for guide cell j (the words
 // with x >> 25 == j) lo_j is the bin of x = j << 25 and hi_j the bin of
 // x = (j + 1) << 25 (K for the last cell); the bin of every x in the cell lies
-// in [lo_j, hi_j], so a hit needs one guide load and a binary search over
-// hi_j - lo_j thresholds (usually none or one) instead of seven.
+// in [lo_j, hi_j].  Each cell stores (T[lo_j], lo_j | hi_j << 8), so when
+// hi_j - lo_j <= 1 (most cells) one 8-byte load decides the bin; wider cells
+// finish with a binary search over the thresholds.
 #include "fcs_internal.cuh"
 
 namespace fcs {
 namespace {
 
 __global__ void k_build_tables(const float* __restrict__ shape_w, int n_entries,
-                               uint32_t* __restrict__ thr, uint16_t* __restrict__ guide,
+                               uint32_t* __restrict__ thr, uint2* __restrict__ guide,
                                int32_t* __restrict__ bad) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_entries) return;
   const float* w = shape_w + (int64_t)e * kNBins;
   uint32_t* T = thr + (int64_t)e * kNBins;
-  uint16_t* G = guide + (int64_t)e * kGuideCells;
+  uint2* G = guide + (int64_t)e * kGuideCells;
   double C = 0.0;
   int K = -1;
   for (int k = 0; k < kNBins; ++k) {
@@ -33,7 +34,7 @@ __global__ void k_build_tables(const float* __restrict__ shape_w, int n_entries,
   }
   if (!(C > 0.0) || K < 0) {
     for (int k = 0; k < kNBins; ++k) T[k] = 0xFFFFFFFFu;
-    for (int j = 0; j < kGuideCells; ++j) G[j] = 0;
+    for (int j = 0; j < kGuideCells; ++j) G[j] = make_uint2(0xFFFFFFFFu, 0u);
     bad[e] = 1;
     return;
   }
@@ -61,14 +62,14 @@ __global__ void k_build_tables(const float* __restrict__ shape_w, int n_entries,
     } else {
       lo = K;
     }
-    if (j > 0) G[j - 1] = (uint16_t)(lo_prev | (lo << 8));
+    if (j > 0) G[j - 1] = make_uint2(T[lo_prev], (uint32_t)(lo_prev | (lo << 8)));
     lo_prev = lo;
   }
 }
 
 }  // namespace
 
-cudaError_t launch_build_tables(const float* shape_w, int n_entries, uint32_t* thr, uint16_t* guide,
+cudaError_t launch_build_tables(const float* shape_w, int n_entries, uint32_t* thr, uint2* guide,
                                 int32_t* bad, cudaStream_t s) {
   if (n_entries <= 0) return cudaSuccess;
   const int threads = 128;

@@ -30,7 +30,7 @@ MODE_ATOMIC, MODE_DETERMINISTIC = 0, 1
 EXPORTED = ("fcs_version", "fcs_last_error", "fcs_load_geometry", "fcs_geometry_info", "fcs_free_geometry",
             "fcs_load_params", "fcs_free_params", "fcs_workspace_create", "fcs_workspace_reserve",
             "fcs_workspace_status", "fcs_workspace_timings", "fcs_workspace_free", "fcs_simulate_events", "fcs_simulate_events_host",
-            "fcs_simulate_events_static", "fcs_autotune", "fcs_simulate_backward")
+            "fcs_simulate_events_static", "fcs_autotune", "fcs_microbench", "fcs_simulate_backward")
 
 
 class FcsError(RuntimeError):
@@ -74,8 +74,9 @@ def load_library(build_if_missing: bool = True):
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB
-        if build_if_missing:
+        # FCS_LIBRARY selects another build of the same ABI (e.g. a tuned variant)
+        path = os.environ.get("FCS_LIBRARY") or _build.LIB
+        if build_if_missing and not os.environ.get("FCS_LIBRARY"):
             path = _build.build()
         if not os.path.exists(path):
             raise RuntimeError(f"libfcs.so not found at {path}; run __graft_entry__.build()")
@@ -102,6 +103,7 @@ def load_library(build_if_missing: bool = True):
                                                i64, vp, vp]
         L.fcs_simulate_events_static.argtypes = [vp, vp, vp, i64, i32, u64, i64, vp, vp, vp, i64, vp, vp]
         L.fcs_autotune.argtypes = [vp, vp, vp, vp, i64, i32, u64, i64, i32, vp, vp, vp]
+        L.fcs_microbench.argtypes = [i32, i64, i32, vp, vp]
         L.fcs_simulate_backward.argtypes = [vp, vp, vp, vp, i64, i32, u64, i64, vp, vp, vp, vp, vp]
         # every other entry point returns an int status (the ctypes default restype)
         _lib = L
@@ -251,6 +253,16 @@ def fcs_simulate_events_host(geo, prm, ws, type_, E, eta, phi, event_offsets, se
     if check and rc != FCS_OK:
         _check(rc)
     return rc, st
+
+
+MB_PHILOX, MB_MULWIDE, MB_LOP3, MB_FFMA, MB_RED = range(5)
+
+
+def fcs_microbench(kind, size=0, iters=256):
+    """Operations per second of one unit microbenchmark (see include/fcs.h)."""
+    rate = C.c_double()
+    _check(load_library().fcs_microbench(int(kind), int(size), int(iters), C.byref(rate), _stream()))
+    return rate.value
 
 
 AUTOTUNE_BLOCKS = (128, 256, 512)
