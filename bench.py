@@ -197,16 +197,19 @@ def main():
     import torch
     import torch.distributed as dist
     from paper_2103_14737_gb300 import fcs, synth
+    from paper_2103_14737_gb300.shard import max_over_ranks, shard_events
 
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     geo = synth.geometry()
     prm = synth.params(geo)
-    # weak scaling: rank r simulates its own 64 events (random-stream events r*64 ...)
+    # weak scaling: the job is world x 64 events; rank r simulates its contiguous
+    # share (random-stream events first_event ...), with no data-path collective
     n_ev = args.events
+    first_event, n_mine = shard_events(n_ev * world, rank, world)
+    assert n_mine == n_ev
     parts = synth.pileup(seed=SEED + rank, n_events=n_ev)
-    first_event = rank * n_ev
     sim = fcs.Simulator(geo, prm)
     d = sim.to_device(parts)
     # autotune the hit kernel's launch shape on this workload (not timed)
@@ -255,11 +258,7 @@ def main():
     clocks = clk.stop()
     if world > 1:
         dist.barrier()
-    ms = float(np.mean(t_step))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean(t_step)))
     value = H * world / (ms * 1e-3)
 
     hit_ms = float(np.mean([s["hits"] for s in t_stage]))
