@@ -393,3 +393,170 @@ int32_t orc_simulate(const orc_geometry* g, const orc_params* P, int64_t n_parti
   free(touched);
   return status;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Gradients by reweighting (the differentiable form of the hit loop).  For a */
+/* seed, the base parametrisation fixes every hit: its task's count n, its    */
+/* shape bin b and its cell.  Perturbed parameters change only the hits'     */
+/* energies: E * f / n (FP64) for the layer fraction f of the task's entry,  */
+/* times the shape likelihood ratio p_b(w) / p_b(w0) with p_b(w) = w_b /      */
+/* sum(w).  walk_hits visits the hits in orc_simulate's order with the same  */
+/* element functions.                                                         */
+/* ------------------------------------------------------------------------- */
+typedef struct orc_hit {
+  int32_t event;  /* batch-local */
+  int64_t entry;  /* parametrisation entry including the layer */
+  int64_t n;      /* hits of the task */
+  float E;        /* particle energy, MeV */
+  int32_t bin, cell;
+} orc_hit;
+
+typedef void (*orc_hit_fn)(void* user, const orc_hit* h);
+
+static int32_t walk_hits(const orc_geometry* g, const orc_params* P, int64_t n_particles,
+                         const int32_t* type, const float* E, const float* eta, const float* phi,
+                         int32_t n_events, const int64_t* event_offsets, uint64_t seed,
+                         int64_t first_event, orc_hit_fn fn, void* user) {
+  if (P->NL != g->n_layers) return -1;
+  if (event_offsets[0] != 0 || event_offsets[n_events] != n_particles) return -1;
+  const int32_t NB = P->NR * P->NA;
+  uint32_t* T = (uint32_t*)malloc((size_t)NB * sizeof(uint32_t));
+  if (!T) return -1;
+  const uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+  int32_t status = 0;
+  for (int32_t e = 0; e < n_events; ++e) {
+    const uint32_t ev = (uint32_t)(first_event + e);
+    for (int64_t p = event_offsets[e]; p < event_offsets[e + 1]; ++p) {
+      const uint32_t pin = (uint32_t)(p - event_offsets[e]);
+      if (type[p] < 0 || type[p] >= P->NT || !(E[p] > 0.0f) || !isfinite(E[p]) ||
+          !isfinite(eta[p]) || !isfinite(phi[p])) {
+        status = -1;
+        continue;
+      }
+      const int32_t base = orc_param_entry(P, type[p], E[p], eta[p]);
+      for (int32_t l = 0; l < P->NL; ++l) {
+        const int64_t entry = (int64_t)base * P->NL + l;
+        const float El = E[p] * P->frac[entry];
+        if (!(El > 0.0f)) continue;
+        const float mu = El / P->mean_hit_E[entry];
+        int64_t n = orc_poisson((double)mu, key, (uint32_t)l, pin, ev);
+        if (n < 1) n = 1;
+        int32_t K = -1;
+        if (orc_thresholds(P->shape_w + entry * NB, NB, T, &K) != 0) { status = -1; continue; }
+        double s_eta, s_phi;
+        orc_scales(g, l, (double)eta[p], &s_eta, &s_phi);
+        orc_hit hit = {e, entry, n, E[p], 0, 0};
+        for (int64_t h = 0; h < n; ++h) {
+          const uint32_t ctr[4] = {(uint32_t)h, (uint32_t)l | ((uint32_t)PURPOSE_HIT << 16), pin, ev};
+          uint32_t x[4];
+          orc_philox(ctr, key, x);
+          const int32_t bin = orc_sample_bin(T, K, x[0]);
+          const int32_t ir = bin / P->NA, ia = bin % P->NA;
+          const double r_lo = (double)P->r_edges[ir], r_hi = (double)P->r_edges[ir + 1];
+          const double a_lo = (double)P->a_edges[ia], a_hi = (double)P->a_edges[ia + 1];
+          const double r = r_lo + u24(x[1]) * (r_hi - r_lo);
+          const double alpha = a_lo + u24(x[2]) * (a_hi - a_lo);
+          const double heta = (double)eta[p] + (r * cos(alpha)) * s_eta;
+          const double hphi = (double)phi[p] + (r * sin(alpha)) * s_phi;
+          hit.bin = bin;
+          hit.cell = orc_cell(g, l, heta, hphi);
+          fn(user, &hit);
+        }
+      }
+    }
+  }
+  free(T);
+  return status;
+}
+
+static double weight_sum(const orc_params* P, int64_t entry) {
+  const int32_t NB = P->NR * P->NA;
+  double W = 0.0;
+  for (int32_t k = 0; k < NB; ++k) W = W + (double)P->shape_w[entry * NB + k];
+  return W;
+}
+
+typedef struct rw_ctx {
+  const orc_params* P;
+  int32_t n_cells;
+  int64_t f_entry, w_entry;
+  int32_t w_bin;
+  double f_delta, w_delta, W0;
+  double* cells;
+} rw_ctx;
+
+static void rw_hit(void* user, const orc_hit* h) {
+  rw_ctx* c = (rw_ctx*)user;
+  const int32_t NB = c->P->NR * c->P->NA;
+  double f = (double)c->P->frac[h->entry];
+  if (h->entry == c->f_entry) f = f + c->f_delta;
+  double ratio = 1.0;
+  if (h->entry == c->w_entry) {
+    const double w0 = (double)c->P->shape_w[h->entry * NB + h->bin];
+    const double w1 = w0 + (h->bin == c->w_bin ? c->w_delta : 0.0);
+    ratio = (w1 / (c->W0 + c->w_delta)) / (w0 / c->W0);
+  }
+  c->cells[(int64_t)h->event * c->n_cells + h->cell] += (((double)h->E * f) / (double)h->n) * ratio;
+}
+
+int32_t orc_reweighted_cells(const orc_geometry* g, const orc_params* P, int64_t n_particles,
+                             const int32_t* type, const float* E, const float* eta,
+                             const float* phi, int32_t n_events, const int64_t* event_offsets,
+                             uint64_t seed, int64_t first_event, int64_t f_entry, double f_delta,
+                             int64_t w_entry, int32_t w_bin, double w_delta, double* cells) {
+  rw_ctx c = {P, g->n_cells, f_entry, w_entry, w_bin, f_delta, w_delta, 1.0, cells};
+  if (w_entry >= 0) c.W0 = weight_sum(P, w_entry);
+  return walk_hits(g, P, n_particles, type, E, eta, phi, n_events, event_offsets, seed, first_event,
+                   rw_hit, &c);
+}
+
+typedef struct bw_ctx {
+  const orc_params* P;
+  int32_t n_cells;
+  const double* g;
+  double* d_frac;
+  double* A;
+} bw_ctx;
+
+static void bw_hit(void* user, const orc_hit* h) {
+  bw_ctx* c = (bw_ctx*)user;
+  const int32_t NB = c->P->NR * c->P->NA;
+  const double gc = c->g[(int64_t)h->event * c->n_cells + h->cell];
+  /* dE_hit / df = E / n; the hit energy itself weights the shape score */
+  c->d_frac[h->entry] += ((double)h->E / (double)h->n) * gc;
+  c->A[h->entry * NB + h->bin] += (((double)h->E * (double)c->P->frac[h->entry]) / (double)h->n) * gc;
+}
+
+/* d_frac, d_w: accumulated (the caller zeroes them).  With A[e][k] the sum of  */
+/* E_hit * dL/dE_cell over the hits of entry e in bin k and W = sum(w[e]):     */
+/*   dL/df[e]    = sum over its hits of (E / n) dL/dE_cell                     */
+/*   dL/dw[e][k] = A[e][k] / w[e][k] - sum_j A[e][j] / W   (first term 0 when  */
+/*                 w[e][k] == 0: such bins have no hits)                        */
+int32_t orc_backward(const orc_geometry* g, const orc_params* P, int64_t n_particles,
+                     const int32_t* type, const float* E, const float* eta, const float* phi,
+                     int32_t n_events, const int64_t* event_offsets, uint64_t seed,
+                     int64_t first_event, const double* dL_dcells, double* d_frac, double* d_w) {
+  const int32_t NB = P->NR * P->NA;
+  const int64_t n_entries = (int64_t)P->NT * P->NE * P->NH * P->NL;
+  double* A = (double*)calloc((size_t)n_entries * (size_t)NB, sizeof(double));
+  if (!A) return -1;
+  bw_ctx c = {P, g->n_cells, dL_dcells, d_frac, A};
+  const int32_t st = walk_hits(g, P, n_particles, type, E, eta, phi, n_events, event_offsets, seed,
+                               first_event, bw_hit, &c);
+  for (int64_t e = 0; e < n_entries; ++e) {
+    double S = 0.0;
+    int any = 0;
+    for (int32_t k = 0; k < NB; ++k) {
+      S = S + A[e * NB + k];
+      any |= A[e * NB + k] != 0.0;
+    }
+    if (!any) continue;
+    const double W = weight_sum(P, e);
+    for (int32_t k = 0; k < NB; ++k) {
+      const double w = (double)P->shape_w[e * NB + k];
+      d_w[e * NB + k] += (w > 0.0 ? A[e * NB + k] / w : 0.0) - S / W;
+    }
+  }
+  free(A);
+  return st;
+}

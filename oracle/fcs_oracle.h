@@ -102,6 +102,23 @@ int32_t orc_simulate(const orc_geometry* g, const orc_params* P, int64_t n_parti
                      int32_t n_events, const int64_t* event_offsets, uint64_t seed,
                      int64_t first_event, orc_outputs* out);
 
+/* Differentiable form (gradients by reweighting hit energies, hit positions
+ * held fixed for the seed).  orc_reweighted_cells: FP64 cells [n_events][n_cells]
+ * (accumulated) of the hits of P with the layer fraction of entry f_entry
+ * moved by f_delta and the weight of (w_entry, w_bin) moved by w_delta
+ * (entries < 0: no change).  orc_backward: gradients of a loss with the given
+ * dL/dE_cell [n_events][n_cells] with respect to the layer fractions
+ * [entries] and shape weights [entries][NR * NA] (accumulated). */
+int32_t orc_reweighted_cells(const orc_geometry* g, const orc_params* P, int64_t n_particles,
+                             const int32_t* type, const float* E, const float* eta,
+                             const float* phi, int32_t n_events, const int64_t* event_offsets,
+                             uint64_t seed, int64_t first_event, int64_t f_entry, double f_delta,
+                             int64_t w_entry, int32_t w_bin, double w_delta, double* cells);
+int32_t orc_backward(const orc_geometry* g, const orc_params* P, int64_t n_particles,
+                     const int32_t* type, const float* E, const float* eta, const float* phi,
+                     int32_t n_events, const int64_t* event_offsets, uint64_t seed,
+                     int64_t first_event, const double* dL_dcells, double* d_frac, double* d_w);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,6 +96,13 @@ def lib():
             L.orc_simulate.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp, C.c_int32, vp, C.c_uint64,
                                        C.c_int64, vp]
             L.orc_simulate.restype = C.c_int32
+            L.orc_reweighted_cells.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp, C.c_int32, vp, C.c_uint64,
+                                               C.c_int64, C.c_int64, C.c_double, C.c_int64, C.c_int32,
+                                               C.c_double, vp]
+            L.orc_reweighted_cells.restype = C.c_int32
+            L.orc_backward.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp, C.c_int32, vp, C.c_uint64, C.c_int64,
+                                       vp, vp, vp]
+            L.orc_backward.restype = C.c_int32
     return _lib
 
 
@@ -263,3 +270,42 @@ def simulate(ogeo: OracleGeometry, oprm: OracleParams, parts, seed: int, first_e
             if a is not None:
                 setattr(res, name, a[:k])
     return res
+
+
+# ----------------------------------------------------------------------------
+# Gradients by reweighting
+# ----------------------------------------------------------------------------
+def _parts(parts):
+    return (np.ascontiguousarray(parts.type, dtype=np.int32), np.ascontiguousarray(parts.E, dtype=np.float32),
+            np.ascontiguousarray(parts.eta, dtype=np.float32), np.ascontiguousarray(parts.phi, dtype=np.float32),
+            np.ascontiguousarray(parts.event_offsets, dtype=np.int64))
+
+
+def reweighted_cells(ogeo: OracleGeometry, oprm: OracleParams, parts, seed: int, first_event: int = 0,
+                     f_entry: int = -1, f_delta: float = 0.0, w_entry: int = -1, w_bin: int = 0,
+                     w_delta: float = 0.0) -> np.ndarray:
+    """FP64 cells of the base hits with one layer fraction and/or one shape
+    weight moved (hit counts, bins and cells held fixed)."""
+    t, E, eta, phi, off = _parts(parts)
+    ne = len(off) - 1
+    cells = np.zeros((ne, ogeo.n_cells), dtype=np.float64)
+    rc = lib().orc_reweighted_cells(ogeo.ptr, oprm.ptr, len(E), _p(t), _p(E), _p(eta), _p(phi), ne, _p(off),
+                                    seed & 0xFFFFFFFFFFFFFFFF, first_event, f_entry, f_delta, w_entry, w_bin,
+                                    w_delta, _p(cells))
+    assert rc == 0, rc
+    return cells
+
+
+def backward(ogeo: OracleGeometry, oprm: OracleParams, parts, seed: int, dL_dcells: np.ndarray,
+             first_event: int = 0):
+    """(dL/dfrac [entries], dL/dshape_w [entries][128]) in FP64."""
+    t, E, eta, phi, off = _parts(parts)
+    ne = len(off) - 1
+    g = np.ascontiguousarray(dL_dcells, dtype=np.float64).reshape(ne, ogeo.n_cells)
+    n_entries = oprm.frac.size
+    d_frac = np.zeros(n_entries, dtype=np.float64)
+    d_w = np.zeros((n_entries, oprm.w.shape[-2] * oprm.w.shape[-1]), dtype=np.float64)
+    rc = lib().orc_backward(ogeo.ptr, oprm.ptr, len(E), _p(t), _p(E), _p(eta), _p(phi), ne, _p(off),
+                            seed & 0xFFFFFFFFFFFFFFFF, first_event, _p(g), _p(d_frac), _p(d_w))
+    assert rc == 0, rc
+    return d_frac, d_w
