@@ -281,6 +281,29 @@ def main():
         ts, tst = timed(max(5, args.steps // 2), 2, batched=0)
         extra["per_event_launches"] = {"hits_per_s": H / (np.mean(ts) * 1e-3), "ms_per_step": float(np.mean(ts)),
                                        "batched_speedup": float(np.mean(ts)) / ms}
+        # the adjoint (gradients of the layer fractions and shape weights) over the
+        # same events, for a fixed dL/dE_cell (dense float32 rows, 48 MB)
+        gcell = torch.randn((n_ev, geo.n_cells), generator=torch.Generator("cuda").manual_seed(3), device="cuda")
+        gf = torch.zeros(sim.n_entries, dtype=torch.float32, device="cuda")
+        gw = torch.zeros(sim.n_entries * 128, dtype=torch.float32, device="cuda")
+        kw = dict(first_event=first_event, d_frac=gf, d_shape_w=gw, hits_per_thread=args.hpt, block=args.block)
+        sim.backward(d, SEED, gcell, **kw)  # sizes the workspace (not timed)
+        for _ in range(2):
+            sim.backward(d, SEED, gcell, sync=0, **kw)
+        Kb = max(5, args.steps // 2)
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(Kb)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(Kb)]
+        for k in range(Kb):
+            flush.zero_()
+            st[k].record()
+            sim.backward(d, SEED, gcell, sync=0, **kw)
+            en[k].record()
+        torch.cuda.synchronize()
+        rc, stt = fcs.fcs_workspace_status(sim.ws)
+        assert rc == 0, (rc, stt.as_dict())
+        tb = float(np.mean([a.elapsed_time(b) for a, b in zip(st, en)]))
+        extra["backward"] = {"hits_per_s": H / (tb * 1e-3), "ms_per_step": tb, "forward_ms_per_step": ms,
+                             "outputs": "dL/dfrac and dL/dshape_w of all entries, FP32, accumulated"}
 
     # end to end through the host-buffer entry point (copies inside the timed region)
     e2e = None

@@ -178,6 +178,15 @@ int fcs_load_params(fcs_params** out, const fcs_geo* geo, const float* frac,
                     const float* mean_hit_E, const float* shape_w, const float* r_edges,
                     const float* a_edges, int32_t NT, int32_t NE, int32_t NH, int32_t NR,
                     int32_t NA, double eta_bin_scale, int32_t ebin_log2_min, cudaStream_t s);
+/* Replaces the parametrisation's tables from DEVICE arrays of the shapes of
+ * fcs_load_params (a training step's update); NULL keeps an array.  The new
+ * values are checked on the device with fcs_load_params' rules first (the
+ * call waits for stream s for that); on a violation it returns FCS_E_ARG and
+ * nothing changes.  Then the copies and the rebuild of the inverse-CDF tables
+ * are enqueued on s: the source arrays must stay valid until s reaches them,
+ * and simulation calls on other streams must be ordered after them. */
+int fcs_update_params(fcs_params* prm, const float* frac, const float* mean_hit_E,
+                      const float* shape_w, cudaStream_t s);
 void fcs_free_params(fcs_params* prm);
 
 /* Workspace: the intermediate device buffers of a simulation call (task
@@ -306,14 +315,38 @@ int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* prm,
                                int32_t* cell_ids, float* cell_E, int64_t* event_offsets_out,
                                int64_t capacity, fcs_stats* stats, cudaStream_t s);
 
-/* Gradient of a cell-energy loss with respect to the layer-fraction table
- * and the shape weights, by reweighting hit energies with hit positions held
- * fixed for the seed.  Not implemented yet: returns FCS_E_UNSUPPORTED. */
+/* Adjoint of fcs_simulate_events: the gradient of a loss L of the dense cell
+ * energies with respect to the layer-fraction table and the shape weights.
+ * The hit energy E_hit = E f_l / n of Sec. 4 (Listing 1) is the only place
+ * where the parameters enter once the seed fixes each hit's task, count n,
+ * shape bin b and cell; the fraction enters linearly (dE_hit/df_l = E / n)
+ * and the shape weights through the likelihood ratio p_b(w) / p_b(w0) of the
+ * drawn bin, p_b = w_b / sum(w).  With A[e][b] = the sum of E_hit dL/dE_cell
+ * over entry e's hits drawn in bin b (FP64):
+ *   d_frac[e]       += sum_b A[e][b] / frac[e]
+ *   d_shape_w[e][b] += A[e][b] / w_b - sum_j A[e][j] / sum_j w_j
+ *                      (the first term is 0 where w_b = 0: no hits there)
+ * Only entries that received hits change.  Hits are regenerated on the
+ * device exactly as by the forward call with the same seed, first_event and
+ * particles (FP64 recheck included), so no hit list is stored.
+ *   dL_dcells: device [n_events][n_cells] FP32, the layout of cells_out.
+ *   d_frac: device, shaped like frac; d_shape_w: device, shaped like
+ *     shape_w; FP32, accumulated into (the caller zeroes them); either may
+ *     be NULL.
+ *   config: mode is ignored; batched, hits_per_thread, block and sync as for
+ *     fcs_simulate_events; use_graph must be 0; timing is ignored.
+ *   stats: host, optional (n_tasks, n_hits, n_recheck, device_flags).
+ * The scores use a FP64 array of the workspace (8 bytes x 128 x entries),
+ * allocated by the first call.  With sync != 0 the call waits for the stream
+ * and returns the device status like fcs_simulate_events; with sync == 0 it
+ * returns after enqueueing (the workspace must be reserved) and
+ * fcs_workspace_status reports the status.  On a device error the gradients
+ * are incomplete.  FCS_E_RANGE if n_events (batched) x n_cells >= 2^32. */
 int fcs_simulate_backward(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
                           const fcs_particles* particles, int64_t n_particles,
                           int32_t n_events, uint64_t seed, int64_t first_event,
                           const fcs_config* config, const float* dL_dcells, float* d_frac,
-                          float* d_shape_w, cudaStream_t s);
+                          float* d_shape_w, fcs_stats* stats, cudaStream_t s);
 
 #ifdef __cplusplus
 }

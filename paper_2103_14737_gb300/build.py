@@ -20,7 +20,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfcs.so")
 
 SOURCES = ["fcs_api.cu", "fcs_scan.cu", "fcs_params.cu", "fcs_tasks.cu", "fcs_hits.cu", "fcs_hits_det.cu",
-           "fcs_compact.cu", "fcs_sort.cu", "fcs_micro.cu"]
+           "fcs_compact.cu", "fcs_sort.cu", "fcs_micro.cu", "fcs_grad.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--cudart", "shared", "-Xcompiler", "-fPIC,-ffp-contract=off",
                      "-I", INCLUDE]

@@ -78,6 +78,9 @@ struct fcs_geo {
 struct fcs_params {
   int device = -1;
   ParamDev d{};
+  float* w = nullptr;           // device shape weights (the tables' source)
+  int32_t* bad = nullptr;       // per-entry flags of the table build
+  uint32_t* check = nullptr;    // validation word of fcs_update_params
   std::vector<void*> allocs;
   ~fcs_params() {
     for (void* p : allocs) cudaFree(p);
@@ -160,6 +163,12 @@ struct fcs_workspace {
   int64_t* head_flags = nullptr;
   int64_t* head_off = nullptr;
   int64_t hf_cap = 0, ho_cap = 0;
+  // gradient scores [n_entries][128] (FP64) and their entry flags; zero
+  // between backward calls (the finalize kernel clears what it reads)
+  double* grad_acc = nullptr;
+  uint8_t* grad_touched = nullptr;
+  int64_t ga_cap = 0, gt_cap = 0;
+  bool grad_dirty = false;  // a backward call stopped before its finalize
   // staging for the host-buffer entry point
   void* stage = nullptr;
   int64_t stage_cap = 0;
@@ -176,7 +185,7 @@ struct fcs_workspace {
     if (graph) cudaGraphExecDestroy(graph);
     for (cudaEvent_t e : tev) cudaEventDestroy(e);
     void* ps[] = {d_sizes, pcount, poff, tasks, tmu, tn, th, tlist, pdefer, gmap, recheck, acc, chunk_counts, chunk_offsets,
-                  block_sums, keys, keys_alt, head_flags, head_off, stage};
+                  block_sums, keys, keys_alt, head_flags, head_off, stage, grad_acc, grad_touched};
     for (void* p : ps)
       if (p) cudaFree(p);
     if (h_sizes) cudaFreeHost(h_sizes);
@@ -671,14 +680,9 @@ int fcs_load_params(fcs_params** out, const fcs_geo* geo, const float* frac, con
   // log k! for the FP32 Poisson acceptance test, from the host's FP64 lgamma
   std::vector<float> lf(kLfactEntries);
   for (int k = 0; k < kLfactEntries; ++k) lf[k] = (float)std::lgamma((double)k + 1.0);
-  if ((rc = dev_alloc(&d_w, n_entries * kNBins)) || (rc = dev_alloc(&d_bad, n_entries))) {
-    if (d_w) cudaFree(d_w);
+  if ((rc = dev_alloc(&d_w, n_entries * kNBins, &prm->allocs)) || (rc = dev_alloc(&d_bad, n_entries, &prm->allocs)) ||
+      (rc = dev_alloc(&prm->check, 1, &prm->allocs)))
     return fail(rc);
-  }
-  auto cleanup_tmp = [&]() {
-    cudaFree(d_w);
-    cudaFree(d_bad);
-  };
   cudaError_t e = cudaSuccess;
   if ((e = cudaMemcpyAsync(d_frac, frac, n_entries * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_mhe, mean_hit_E, n_entries * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
@@ -688,10 +692,10 @@ int fcs_load_params(fcs_params** out, const fcs_geo* geo, const float* frac, con
       (e = cudaMemcpyAsync(d_w, shape_w, n_entries * kNBins * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = launch_build_tables(d_w, (int)n_entries, d_thr, d_guide, d_bad, s)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess) {
-    cleanup_tmp();
     return fail(set_err(FCS_E_CUDA, "parametrisation upload: %s", cudaGetErrorString(e)));
   }
-  cleanup_tmp();
+  prm->w = d_w;
+  prm->bad = d_bad;
   ParamDev& d = prm->d;
   d.NT = NT;
   d.NE = NE;
@@ -706,12 +710,40 @@ int fcs_load_params(fcs_params** out, const fcs_geo* geo, const float* frac, con
   d.lfact = d_lf;
   d.n_entries = (int32_t)n_entries;
   d.frac = d_frac;
+  d.shape_w = d_w;
   d.mhe = d_mhe;
   d.thr = d_thr;
   d.guide = d_guide;
   d.r_edges = d_re;
   d.a_edges = d_ae;
   *out = prm;
+  return ok();
+}
+
+int fcs_update_params(fcs_params* prm, const float* frac, const float* mean_hit_E, const float* shape_w,
+                      cudaStream_t s) {
+  if (!prm) return set_err(FCS_E_ARG, "params is NULL");
+  int dev = 0;
+  FCS_TRY(current_device(&dev));
+  if (dev != prm->device) return set_err(FCS_E_ARG, "the parametrisation lives on another device");
+  ParamDev& d = prm->d;
+  const int64_t n = d.n_entries;
+  FCS_CUDA(cudaMemsetAsync(prm->check, 0, sizeof(uint32_t), s));
+  FCS_CUDA(launch_check_params(frac ? frac : d.frac, mean_hit_E ? mean_hit_E : d.mhe, shape_w ? shape_w : prm->w,
+                               (int)n, prm->check, s));
+  uint32_t bad = 0;
+  FCS_CUDA(cudaMemcpyAsync(&bad, prm->check, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  FCS_CUDA(cudaStreamSynchronize(s));
+  if (bad & 1u) return set_err(FCS_E_ARG, "frac must be finite and >= 0");
+  if (bad & 2u) return set_err(FCS_E_ARG, "mean_hit_E must be finite and > 0 where frac > 0");
+  if (bad & 4u) return set_err(FCS_E_ARG, "shape_w must be finite and >= 0");
+  if (bad & 8u) return set_err(FCS_E_ARG, "shape_w of an entry with frac > 0 sums to 0");
+  if (frac) FCS_CUDA(cudaMemcpyAsync((void*)d.frac, frac, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (mean_hit_E) FCS_CUDA(cudaMemcpyAsync((void*)d.mhe, mean_hit_E, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (shape_w) {
+    FCS_CUDA(cudaMemcpyAsync(prm->w, shape_w, n * kNBins * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    FCS_CUDA(launch_build_tables(prm->w, (int)n, (uint32_t*)d.thr, (uint2*)d.guide, prm->bad, s));
+  }
   return ok();
 }
 
@@ -986,9 +1018,72 @@ int fcs_simulate_events_host(const fcs_geo* geo, const fcs_params* prm, fcs_work
   return ok();
 }
 
-int fcs_simulate_backward(const fcs_geo*, const fcs_params*, fcs_workspace*, const fcs_particles*, int64_t, int32_t,
-                          uint64_t, int64_t, const fcs_config*, const float*, float*, float*, cudaStream_t) {
-  return set_err(FCS_E_UNSUPPORTED, "fcs_simulate_backward is not implemented yet");
+int fcs_simulate_backward(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
+                          const fcs_particles* particles, int64_t n_particles, int32_t n_events, uint64_t seed,
+                          int64_t first_event, const fcs_config* config, const float* dL_dcells, float* d_frac,
+                          float* d_shape_w, fcs_stats* stats, cudaStream_t s) {
+  if (!geo || !prm || !ws) return set_err(FCS_E_ARG, "geo, params and workspace are required");
+  FCS_TRY(check_particles(particles, n_particles));
+  if (n_particles < 0 || n_events < 0) return set_err(FCS_E_ARG, "negative size");
+  if (prm->d.NL != geo->d.n_layers) return set_err(FCS_E_ARG, "parametrisation and geometry disagree on layers");
+  if (n_events > 0 && !dL_dcells) return set_err(FCS_E_ARG, "dL_dcells is required");
+  fcs_config cfg{};
+  cfg.batched = 1;
+  cfg.sync = 1;
+  if (config) cfg = *config;
+  FCS_TRY(validate_config(cfg));
+  if (cfg.use_graph) return set_err(FCS_E_ARG, "the backward pass runs without graph capture (use_graph = 0)");
+  int dev = 0;
+  FCS_TRY(current_device(&dev));
+  if (dev != geo->device || dev != prm->device || (ws->device >= 0 && ws->device != dev))
+    return set_err(FCS_E_ARG, "geometry, parametrisation and workspace must live on the current device");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (n_events == 0) return ok();
+  const int32_t rows = cfg.batched ? n_events : 1;
+  if ((int64_t)rows * geo->d.n_cells >= (int64_t(1) << 32))
+    return set_err(FCS_E_RANGE, "%d events x %d cells exceed 2^32; split the batch", rows, geo->d.n_cells);
+  FCS_TRY(ws_reserve_static(ws, geo, n_particles, 1, FCS_MODE_ATOMIC));
+  const int64_t n_scores = (int64_t)prm->d.n_entries * kNBins;
+  if (n_scores > ws->ga_cap || prm->d.n_entries > ws->gt_cap || ws->grad_dirty) {
+    FCS_TRY(grow(&ws->grad_acc, &ws->ga_cap, n_scores, true));
+    FCS_TRY(grow(&ws->grad_touched, &ws->gt_cap, (int64_t)prm->d.n_entries, true));
+    if (ws->grad_dirty) {
+      FCS_CUDA(cudaMemset(ws->grad_acc, 0, (size_t)ws->ga_cap * sizeof(double)));
+      FCS_CUDA(cudaMemset(ws->grad_touched, 0, (size_t)ws->gt_cap));
+      ws->grad_dirty = false;
+    }
+  }
+  ws->timed_ranges = 0;
+  const HitCfg hc = hit_cfg(cfg);
+  const Launch L{s, ws->num_sms};
+  const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
+  const ScanTmp tmp{ws->block_sums};
+  ws->grad_dirty = true;
+  k_call_begin<<<1, 1, 0, s>>>(ws->d_sizes);
+  for (int32_t lo = 0; lo < n_events; lo += rows) {
+    const int32_t hi = lo + rows;
+    k_range_begin<<<1, 1, 0, s>>>(ws->d_sizes, particles->event_offsets, lo, hi, n_particles, ws->pcap);
+    WsDev w = ws->view();
+    FCS_CUDA(launch_task_counts(geo->d, prm->d, *particles, lo, hi, k0, k1, first_event, w, tmp, L));
+    if (cfg.sync) {
+      FCS_CUDA(cudaMemcpyAsync(ws->h_sizes, ws->d_sizes, sizeof(Sizes), cudaMemcpyDeviceToHost, s));
+      FCS_CUDA(cudaStreamSynchronize(s));
+      FCS_TRY(ws_reserve_hits(ws, ws->h_sizes->n_hits, FCS_MODE_ATOMIC));
+      w = ws->view();
+    }
+    FCS_CUDA(launch_task_finish(w, nullptr, L));
+    const float* g = dL_dcells + (int64_t)lo * geo->d.n_cells;
+    FCS_CUDA(launch_hits_grad(geo->d, prm->d, w, lo, k0, k1, first_event, hc, g, ws->grad_acc, ws->grad_touched, L));
+    FCS_CUDA(launch_recheck_grad(geo->d, prm->d, w, lo, k0, k1, first_event, g, ws->grad_acc, ws->grad_touched, L));
+    k_range_end<<<1, 1, 0, s>>>(ws->d_sizes);
+  }
+  FCS_CUDA(launch_grad_finalize(prm->d, ws->grad_acc, ws->grad_touched, d_frac, d_shape_w, L));
+  FCS_CUDA(cudaGetLastError());
+  ws->grad_dirty = false;
+  if (!cfg.sync) return ok();
+  FCS_CUDA(cudaMemcpyAsync(ws->h_sizes, ws->d_sizes, sizeof(Sizes), cudaMemcpyDeviceToHost, s));
+  FCS_CUDA(cudaStreamSynchronize(s));
+  return status_from(*ws->h_sizes, stats);
 }
 
 }  // extern "C"

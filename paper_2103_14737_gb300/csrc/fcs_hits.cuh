@@ -38,6 +38,10 @@ struct HitKParams {
   int32_t* dbg_hit_cell;
   int16_t* dbg_hit_bin;
   int64_t dbg_hit_cap;
+  // gradient mode
+  const float* grad_in;  // dL/dE_cell of the range's events, row stride n_cells
+  double* grad_acc;      // [n_entries][128] sum of E_hit dL/dE_cell per (entry, shape bin)
+  uint8_t* grad_touched; // [n_entries] set where grad_acc has contributions
 };
 
 // ---- shape bin: inverse CDF by guide table and binary search --------------
@@ -232,11 +236,35 @@ __device__ __forceinline__ void emit_warp(bool ok, unsigned long long gkey, cons
   }
 }
 
+// Sum of v over each group of lanes with equal keys, added by the group's
+// first lane to grad_acc[key] in FP64 (key = entry * 128 + bin).  s_v: this
+// warp's 32 floats of shared memory; groups sum in ascending lane order.
+__device__ __forceinline__ void grad_warp(bool ok, uint32_t key, float v, float* s_v, const HitKParams& kp) {
+  const int lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(0xffffffffu, ok);
+  s_v[lane] = v;
+  __syncwarp();
+  if (ok) {
+    const unsigned peers = __match_any_sync(m, key);
+    if (lane == __ffs(peers) - 1) {
+      float sum = 0.0f;
+      for (unsigned q = peers; q; q &= q - 1) sum += s_v[__ffs(q) - 1];
+      atomicAdd(kp.grad_acc + key, (double)sum);
+      kp.grad_touched[key >> 7] = 1;
+    }
+  }
+  __syncwarp();
+}
+
 __device__ __forceinline__ void deposit_single(const HitKParams& kp, int32_t event, float Ehit, int64_t task_rel,
-                                               int32_t cell, bool det) {
+                                               int32_t cell, int mode, int32_t entry, int bin) {
   const int64_t row = event - kp.ev_lo;
-  if (!det) {
+  if (mode == kModeAtomic) {
     atomicAdd(kp.w.acc + row * kp.g.acc_stride + cell, Ehit);
+  } else if (mode == kModeGrad) {
+    const float v = __fmul_rn(Ehit, __ldg(kp.grad_in + row * kp.g.n_cells + cell));
+    atomicAdd(kp.grad_acc + ((int64_t)entry << 7) + bin, (double)v);
+    kp.grad_touched[entry] = 1;
   } else {
     const unsigned long long gkey =
         ((unsigned long long)(row * kp.g.n_cells + cell) << kp.key_task_bits) | (unsigned long long)task_rel;
@@ -274,8 +302,9 @@ __device__ __forceinline__ void owner_scan(int16_t* s_owner, int* s_wmax) {
   for (int k = 0; k < HPT; ++k) s_owner[tid * HPT + k] = (int16_t)max(v[k], excl);
 }
 
-template <int BLOCK, int HPT, bool DET>
+template <int BLOCK, int HPT, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKParams kp) {
+  constexpr bool DET = MODE == kModeDet;
   constexpr int TILE = BLOCK * HPT;
   static_assert(TILE % kGranule == 0, "tiles must start on granules");
   static_assert(TILE <= 4096, "owner index and 32-bit match keys need TILE + 1 < 2^13");
@@ -284,6 +313,7 @@ __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKPara
   __shared__ int16_t s_owner[TILE];
   __shared__ int s_wmax[BLOCK / 32];
   __shared__ unsigned long long s_tile;
+  __shared__ float s_gv[MODE == kModeGrad ? BLOCK : 1];
   load_tables(tb, kp.g, kp.p);
   for (int i = threadIdx.x; i < TILE; i += BLOCK) s_owner[i] = 0;
   const WsDev& w = kp.w;
@@ -293,7 +323,7 @@ __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKPara
   const unsigned long long n_tiles = (unsigned long long)((H + TILE - 1) / TILE);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t hit_dbg_base = kp.dbg_hit_cell || kp.dbg_hit_bin ? w.sizes->hit_base : 0;
-  const uint32_t row_stride = DET ? (uint32_t)kp.g.n_cells : (uint32_t)kp.g.acc_stride;
+  const uint32_t row_stride = MODE == kModeAtomic ? (uint32_t)kp.g.acc_stride : (uint32_t)kp.g.n_cells;
   if (threadIdx.x == 0) s_tile = atomicAdd(&w.sizes->queue, 1ull);
   __syncthreads();
   unsigned long long tile = s_tile;
@@ -364,7 +394,11 @@ __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKPara
       const FastHit f = fast_cell(tb, T, x, bin);
       const bool ok = valid && f.sure;
       const bool need = valid && !f.sure;
-      if (!DET) {
+      if constexpr (MODE == kModeGrad) {
+        // dL/dE_cell of the hit's cell times its energy, summed per (entry, bin)
+        const float v = ok ? __fmul_rn(T.Ehit, __ldg(kp.grad_in + T.row_off + f.cell)) : 0.0f;
+        grad_warp(ok, ((uint32_t)T.entry << 7) | (uint32_t)bin, v, s_gv + warp * 32, kp);
+      } else if constexpr (!DET) {
         // (cell, task-in-tile) identifies (address, hit energy): 19 + 13 bits
         const unsigned m = __ballot_sync(0xffffffffu, ok);
         if (ok) {
@@ -393,7 +427,7 @@ __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKPara
           } else {
             const int32_t ev = (int32_t)(T.ctr_w - kp.first_event_lo);
             const int32_t c = cell_fp64(kp.g, kp.p, (int32_t)(T.lay & 0xFF), T.eta_c, T.phi_c, x, bin);
-            deposit_single(kp, ev, T.Ehit, t0 + tl, c, DET);
+            deposit_single(kp, ev, T.Ehit, t0 + tl, c, MODE, T.entry, bin);
             atomicAdd((unsigned long long*)&w.sizes->n_inline, 1ull);
             atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_RECHECK_SPILL);
             if (kp.dbg_hit_cell && hit_dbg_base + h0 + i < kp.dbg_hit_cap) kp.dbg_hit_cell[hit_dbg_base + h0 + i] = c;
@@ -415,7 +449,7 @@ __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKPara
 }
 
 // FP64 recheck of the queued hits (grid-stride over the queue).
-template <bool DET>
+template <int MODE>
 __global__ void __launch_bounds__(128) k_recheck(const __grid_constant__ HitKParams kp) {
   const WsDev& w = kp.w;
   const int64_t n = min(w.sizes->n_recheck, w.recheck_cap);
@@ -430,13 +464,13 @@ __global__ void __launch_bounds__(128) k_recheck(const __grid_constant__ HitKPar
         kp.k0, kp.k1);
     const int bin = sample_bin(kp.p, T.entry, x.x);
     const int32_t c = cell_fp64(kp.g, kp.p, T.layer, T.eta_c, T.phi_c, x, bin);
-    deposit_single(kp, T.event, T.Ehit, q.x, c, DET);
+    deposit_single(kp, T.event, T.Ehit, q.x, c, MODE, T.entry, bin);
     const int64_t h = hit_dbg_base + T.hit_begin + q.y;
     if (kp.dbg_hit_cell && h < kp.dbg_hit_cap) kp.dbg_hit_cell[h] = c;
   }
 }
 
-template <bool DET>
+template <int MODE>
 cudaError_t launch_hits_t(const HitKParams& kp, const HitCfg& hc, const Launch& L);
 
 }  // namespace fcs

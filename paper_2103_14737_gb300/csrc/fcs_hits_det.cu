@@ -3,6 +3,6 @@
 #include "fcs_hits_impl.cuh"
 
 namespace fcs {
-template cudaError_t launch_hits_t<true>(const HitKParams&, const HitCfg&, const Launch&);
-template cudaError_t launch_recheck_t<true>(const HitKParams&, const Launch&);
+template cudaError_t launch_hits_t<kModeDet>(const HitKParams&, const HitCfg&, const Launch&);
+template cudaError_t launch_recheck_t<kModeDet>(const HitKParams&, const Launch&);
 }  // namespace fcs

@@ -72,6 +72,7 @@ struct ParamDev {
   int32_t n_lfact;       // entries of lfact
   const float* lfact;    // [n_lfact] FP32 of lgamma(k + 1) (host libm, rounded once)
   const float* frac;     // [n_entries]
+  const float* shape_w;  // [n_entries][128] shape weights (the gradient's likelihood ratios)
   const float* mhe;      // [n_entries]
   const uint32_t* thr;   // [n_entries][128] inverse-CDF thresholds
   const uint2* guide;    // [n_entries][128]: (T[lo], lo | hi << 8) per guide cell
@@ -177,7 +178,12 @@ cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_par
                                int64_t first_event, WsDev w, ScanTmp tmp, const Launch& L);
 cudaError_t launch_task_finish(WsDev w, const fcs_debug* dbg, const Launch& L);
 
-// fcs_hits.cu
+// fcs_hits.cu: what the hit kernel does with a certified hit
+enum HitMode : int {
+  kModeAtomic = 0,  // float atomics into the accumulation rows
+  kModeDet = 1,     // (cell, task, count) records for the sort-by-cell reduction
+  kModeGrad = 2,    // gather dL/dE_cell, add E_hit dL/dE_cell to the (entry, bin) score
+};
 struct HitCfg {
   int block;
   int hpt;
@@ -190,6 +196,20 @@ cudaError_t launch_recheck(const GeoDev& g, const ParamDev& p, WsDev w, int32_t 
                            uint32_t k1, int64_t first_event, int det, int key_task_bits,
                            const fcs_debug* dbg, const Launch& L);
 int hits_max_smem_tasks();
+
+// fcs_grad.cu: the adjoint of the hit loop.  grad_in: dL/dE_cell rows of the
+// range (row stride n_cells); grad_acc: FP64 [n_entries][128] scores;
+// touched: [n_entries] flags of entries with scores.
+cudaError_t launch_hits_grad(const GeoDev& g, const ParamDev& p, WsDev w, int32_t ev_lo, uint32_t k0,
+                             uint32_t k1, int64_t first_event, const HitCfg& hc, const float* grad_in,
+                             double* grad_acc, uint8_t* touched, const Launch& L);
+cudaError_t launch_recheck_grad(const GeoDev& g, const ParamDev& p, WsDev w, int32_t ev_lo, uint32_t k0,
+                                uint32_t k1, int64_t first_event, const float* grad_in, double* grad_acc,
+                                uint8_t* touched, const Launch& L);
+cudaError_t launch_grad_finalize(const ParamDev& p, double* grad_acc, uint8_t* touched, float* d_frac,
+                                 float* d_shape_w, const Launch& L);
+cudaError_t launch_check_params(const float* frac, const float* mean_hit_E, const float* shape_w,
+                                int n_entries, uint32_t* bad, cudaStream_t s);
 
 // fcs_compact.cu
 cudaError_t launch_compact(const GeoDev& g, WsDev w, int32_t rows, int32_t ev_lo,

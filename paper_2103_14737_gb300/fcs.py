@@ -30,7 +30,8 @@ MODE_ATOMIC, MODE_DETERMINISTIC = 0, 1
 EXPORTED = ("fcs_version", "fcs_last_error", "fcs_load_geometry", "fcs_geometry_info", "fcs_free_geometry",
             "fcs_load_params", "fcs_free_params", "fcs_workspace_create", "fcs_workspace_reserve",
             "fcs_workspace_status", "fcs_workspace_timings", "fcs_workspace_free", "fcs_simulate_events", "fcs_simulate_events_host",
-            "fcs_simulate_events_static", "fcs_autotune", "fcs_microbench", "fcs_simulate_backward")
+            "fcs_simulate_events_static", "fcs_autotune", "fcs_microbench", "fcs_simulate_backward",
+            "fcs_update_params")
 
 
 class FcsError(RuntimeError):
@@ -104,7 +105,8 @@ def load_library(build_if_missing: bool = True):
         L.fcs_simulate_events_static.argtypes = [vp, vp, vp, i64, i32, u64, i64, vp, vp, vp, i64, vp, vp]
         L.fcs_autotune.argtypes = [vp, vp, vp, vp, i64, i32, u64, i64, i32, vp, vp, vp]
         L.fcs_microbench.argtypes = [i32, i64, i32, vp, vp]
-        L.fcs_simulate_backward.argtypes = [vp, vp, vp, vp, i64, i32, u64, i64, vp, vp, vp, vp, vp]
+        L.fcs_simulate_backward.argtypes = [vp, vp, vp, vp, i64, i32, u64, i64, vp, vp, vp, vp, vp, vp]
+        L.fcs_update_params.argtypes = [vp, vp, vp, vp, vp]
         # every other entry point returns an int status (the ctypes default restype)
         _lib = L
         return L
@@ -301,13 +303,22 @@ def fcs_simulate_events_static(geo, prm, particles: fcs_particles, n_particles, 
 
 
 def fcs_simulate_backward(geo, prm, ws, particles: fcs_particles, n_particles, n_events, seed, first_event,
-                          config, dL_dcells, d_frac, d_shape_w):
-    """Adjoint entry point; the library does not implement it yet (FCS_E_UNSUPPORTED)."""
+                          config, dL_dcells, d_frac, d_shape_w, check=True):
+    """Adjoint of fcs_simulate_events: accumulates dL/dfrac and dL/dshape_w
+    (device tensors or None) for dL/dE_cell given as dense device rows."""
     L = load_library()
+    st = fcs_stats()
     rc = L.fcs_simulate_backward(geo, prm, ws, C.byref(particles), int(n_particles), int(n_events),
                                  int(seed) & 0xFFFFFFFFFFFFFFFF, int(first_event), C.byref(config), _ptr(dL_dcells),
-                                 _ptr(d_frac), _ptr(d_shape_w), _stream())
-    _check(rc)
+                                 _ptr(d_frac), _ptr(d_shape_w), C.byref(st), _stream())
+    if check and rc != FCS_OK:
+        _check(rc)
+    return rc, st
+
+
+def fcs_update_params(prm, frac=None, mean_hit_E=None, shape_w=None):
+    """Replaces tables of a loaded parametrisation from device tensors."""
+    _check(load_library().fcs_update_params(prm, _ptr(frac), _ptr(mean_hit_E), _ptr(shape_w), _stream()))
 
 
 # ---------------------------------------------------------------------------
@@ -326,6 +337,7 @@ class Simulator:
         self.n_cells = fcs_geometry_info(self.geo)[0]
         self.prm = fcs_load_params(self.geo, prm.frac, prm.mean_hit_E, prm.shape_w, prm.r_edges, prm.a_edges,
                                    prm.eta_bin_scale, prm.ebin_log2_min)
+        self.n_entries = int(np.prod(np.shape(prm.frac)))
         self.ws = fcs_workspace_create()
 
     def close(self):
@@ -398,9 +410,42 @@ class Simulator:
                 dbg.hit_capacity = debug_hits
         cfg = make_config(mode, batched, hits_per_thread, block, sync, use_graph, timing)
         rc, st = fcs_simulate_events(self.geo, self.prm, self.ws, parts, n_particles, n_events, seed, first_event,
-                                     cfg, outputs.get("cells"), outputs["cell_ids"], outputs["cell_E"],
-                                     outputs["event_offsets"], outputs["cell_ids"].numel(), dbg, check=check)
+                                     cfg, outputs.get("cells"), outputs.get("cell_ids"), outputs.get("cell_E"),
+                                     outputs.get("event_offsets"),
+                                     outputs["cell_ids"].numel() if outputs.get("cell_ids") is not None else 0, dbg,
+                                     check=check)
         res["status"] = rc
         res["stats"] = st.as_dict()
         res["_keep"] = (parts, dbg, cfg)
         return res
+
+    def update_params(self, frac=None, mean_hit_E=None, shape_w=None):
+        """Loads new tables from contiguous float32 device tensors (None keeps one)."""
+        for t in (frac, mean_hit_E, shape_w):
+            if t is not None and (not t.is_cuda or t.dtype.itemsize != 4 or not t.is_contiguous()):
+                raise ValueError("update_params wants contiguous float32 CUDA tensors")
+        fcs_update_params(self.prm, frac, mean_hit_E, shape_w)
+
+    def backward(self, dparts, seed, dL_dcells, first_event=0, d_frac=None, d_shape_w=None, batched=1,
+                 hits_per_thread=0, block=0, sync=1, check=True):
+        """Gradients of a loss with dL/dE_cell = dL_dcells ([n_events][n_cells]
+        float32 on the device) with respect to the layer fractions and shape
+        weights; accumulated into d_frac / d_shape_w (flat float32 device
+        tensors, allocated zeroed when None)."""
+        import torch
+        dev = dparts["E"].device
+        n_events = dparts["event_offsets"].numel() - 1
+        n_particles = dparts["E"].numel()
+        if d_frac is None:
+            d_frac = torch.zeros(self.n_entries, dtype=torch.float32, device=dev)
+        if d_shape_w is None:
+            d_shape_w = torch.zeros(self.n_entries * 128, dtype=torch.float32, device=dev)
+        g = dL_dcells.contiguous()
+        if g.dtype != torch.float32 or g.numel() != n_events * self.n_cells:
+            raise ValueError("dL_dcells must be float32 [n_events][n_cells]")
+        parts = fcs_particles(dparts["type"].data_ptr(), dparts["E"].data_ptr(), dparts["eta"].data_ptr(),
+                              dparts["phi"].data_ptr(), dparts["event_offsets"].data_ptr())
+        cfg = make_config(MODE_ATOMIC, batched, hits_per_thread, block, sync, 0, 0)
+        rc, st = fcs_simulate_backward(self.geo, self.prm, self.ws, parts, n_particles, n_events, seed, first_event,
+                                       cfg, g, d_frac, d_shape_w, check=check)
+        return dict(d_frac=d_frac, d_shape_w=d_shape_w, status=rc, stats=st.as_dict(), _keep=(parts, cfg, g))

@@ -284,6 +284,14 @@ def _hard_scatter(rng, n=400):
     return t, E, eta, phi
 
 
+def replicate(parts: Particles, n: int) -> Particles:
+    """The events of ``parts`` repeated n times; each copy draws its own random
+    numbers through its event number (n simulation seeds of the same event)."""
+    return _concat([(parts.type, parts.E, parts.eta, parts.phi)] * n) if parts.n_events == 1 else \
+        _concat([(parts.type[a:b], parts.E[a:b], parts.eta[a:b], parts.phi[a:b])
+                 for _ in range(n) for a, b in zip(parts.event_offsets[:-1], parts.event_offsets[1:])])
+
+
 def ttbar_like(seed: int = 1, n_events: int = 1, n: int = 400) -> Particles:
     """400-particle ttbar-like events without pile-up."""
     rng = np.random.default_rng(seed)

@@ -88,4 +88,5 @@ def test_params_and_simulate_validation(lib):
     assert lib.fcs_simulate_events(None, None, None, C.byref(parts), 0, 1, 1, 0, C.byref(cfg), None, None, None,
                                    None, 0, C.byref(st), None, None) == fcs.FCS_E_ARG
     assert lib.fcs_simulate_backward(None, None, None, None, 0, 0, 0, 0, None, None, None, None,
-                                     None) == fcs.FCS_E_UNSUPPORTED
+                                     None, None) == fcs.FCS_E_ARG
+    assert lib.fcs_update_params(None, None, None, None, None) == fcs.FCS_E_ARG
