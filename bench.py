@@ -55,7 +55,7 @@ SMS, SM_MAX_MHZ = 152, 2070.0
 # DRAM bytes per hit of the hit kernel, from the committed ncu summary of its
 # 16-event capture (traffic grows with the hits): valid for the kernel version
 # captured there, None after a kernel change.
-K_HITS_DRAM_BYTES_PER_HIT = 4.26
+K_HITS_DRAM_BYTES_PER_HIT = None
 LANES_PER_SM_CLK = {"mulwide": 32, "int": 64, "fp32": 128, "mufu": 16}
 
 
@@ -122,24 +122,51 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def _oracle_events(og, op, parts, events, threads):
+    """Runs the oracle on whole events (event-parallel over host threads; the
+    oracle is plain C called through ctypes, which releases the GIL).
+    Returns the hits simulated."""
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import oracle as O
+
+    def one(e):
+        return O.simulate(og, op, parts.event(e), seed=SEED, first_event=e, tasks=False, canon=False).n_hits
+
+    if threads <= 1:
+        return sum(one(e) for e in events)
+    with ThreadPoolExecutor(threads) as ex:
+        return sum(ex.map(one, events))
+
+
 def cpu_baseline(geo, prm, parts, seconds=10.0):
-    """The oracle as it stands, single threaded, on whole events of the same
-    workload until `seconds` of CPU work."""
+    """The oracle as it stands on whole events of the same workload: one
+    thread for about seconds / 3, then event-parallel on every host core for
+    the rest (events taken round-robin from the batch)."""
     from oracle import oracle as O
     og, op = O.OracleGeometry(geo), O.OracleParams(prm)
-    hits, ev, t0 = 0, 0, time.perf_counter()
-    while ev < parts.n_events and time.perf_counter() - t0 < seconds:
-        r = O.simulate(og, op, parts.event(ev), seed=SEED, first_event=ev, tasks=False, canon=False)
-        hits += r.n_hits
-        ev += 1
-    dt = time.perf_counter() - t0
-    return {"value": hits / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{ev} whole events of {WORKLOAD} ({hits} hits, {dt:.1f} s, 1 thread)",
-            "events_per_s": ev / dt}
+    cores = os.cpu_count() or 1
+    hits1, ev1, t0 = 0, 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds / 3:
+        hits1 += _oracle_events(og, op, parts, [ev1 % parts.n_events], 1)
+        ev1 += 1
+    dt1 = time.perf_counter() - t0
+    hitsN, evN, t0 = 0, 0, time.perf_counter()
+    while time.perf_counter() - t0 < 2 * seconds / 3:
+        batch = [(evN + k) % parts.n_events for k in range(cores)]
+        hitsN += _oracle_events(og, op, parts, batch, cores)
+        evN += cores
+    dtN = time.perf_counter() - t0
+    return {"value": hitsN / dtN, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{evN} whole events of {WORKLOAD} ({hitsN} hits, {dtN:.1f} s) event-parallel on {cores} "
+                      f"threads",
+            "events_per_s": evN / dtN,
+            "single_thread": {"value": hits1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"{ev1} whole events ({hits1} hits, {dt1:.1f} s)"}}
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the CPU oracle, each step one whole pile-up event."""
+    """--impl reference: the CPU oracle; each step simulates one whole pile-up
+    event per host core, event-parallel."""
     from paper_2103_14737_gb300 import synth
     from oracle import oracle as O
     if rank != 0:
@@ -148,27 +175,144 @@ def run_reference(args, rank, world):
     prm = synth.params(geo)
     parts = synth.workload(WORKLOAD, seed=SEED)
     og, op = O.OracleGeometry(geo), O.OracleParams(prm)
+    cores = os.cpu_count() or 1
     hits = 0
     times = []
     for k in range(args.warmup + args.steps):
-        e = k % parts.n_events
+        batch = [(k * cores + j) % parts.n_events for j in range(cores)]
         t0 = time.perf_counter()
-        r = O.simulate(og, op, parts.event(e), seed=SEED, first_event=e, tasks=False, canon=False)
+        h = _oracle_events(og, op, parts, batch, cores)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             times.append(dt)
-            hits += r.n_hits
+            hits += h
     tot = sum(times)
     v = hits / tot
+    sample = f"{cores} whole events of {WORKLOAD} per step, event-parallel on {cores} threads"
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": "one whole event per step, oracle, 1 thread"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} whole events of {WORKLOAD}"},
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_sweep(args):
+    """--sweep: the 1024-event pile-up batch (about 1.5e9 hits) swept over event
+    waves, hit-kernel launch shapes, atomic vs deterministic accumulation and
+    multiplicity bucketing; plus the launch latency of a one-particle call
+    eagerly and as a graph, and per-event vs batched launches.  One JSON line."""
+    import torch
+    from paper_2103_14737_gb300 import fcs, synth
+    n_ev = args.sweep_events
+    geo = synth.geometry()
+    prm = synth.params(geo)
+    parts = synth.pileup(seed=SEED, n_events=n_ev)
+    sim = fcs.Simulator(geo, prm)
+    d = sim.to_device(parts)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {"mode": "sweep", "workload": f"pileup{n_ev}", "events": n_ev, "particles": parts.n,
+           "l2": "flushed between steps (256 MB write)", "timing": "CUDA events, graph replay, mean of K steps"}
+
+    def t_call(dd, K=5, W=3, **kw):
+        r = sim.simulate(dd, SEED, outputs=dict(cells=None), **kw)  # sizes the workspace (not timed)
+        for _ in range(W):
+            sim.simulate(dd, SEED, sync=0, use_graph=1, outputs=dict(cells=None), **kw)
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        for k in range(K):
+            flush.zero_()
+            st[k].record()
+            sim.simulate(dd, SEED, sync=0, use_graph=1, outputs=dict(cells=None), **kw)
+            en[k].record()
+        torch.cuda.synchronize()
+        rc, stt = fcs.fcs_workspace_status(sim.ws)
+        assert rc == 0, (rc, stt.as_dict())
+        ms = float(np.mean([a.elapsed_time(b) for a, b in zip(st, en)]))
+        return ms, r["stats"]["n_hits"]
+
+    clk = ClockSampler(0)
+    clk.start()
+    # event waves (atomic mode, default launch shape)
+    waves = {}
+    for w in (16, 32, 64, 128, 256, 512, 0):
+        ms, H = t_call(d, wave_events=w)
+        waves[str(w or n_ev)] = {"ms": ms, "hits_per_s": H / (ms * 1e-3)}
+    out["hits"] = H
+    best_w = int(max(waves, key=lambda k: waves[k]["hits_per_s"]))
+    out["waves_atomic"] = waves
+    out["best_wave"] = best_w
+    # launch shapes at the best wave
+    b, h, table = sim.autotune(d, SEED, reps=3, wave_events=best_w)
+    out["shapes_hits_ms_at_best_wave"] = {f"{k[0]}x{k[1]}": v for k, v in table.items()}
+    out["best_shape"] = f"{b}x{h}"
+    ms, _ = t_call(d, wave_events=best_w, block=b, hits_per_thread=h)
+    out["atomic"] = {"ms": ms, "hits_per_s": H / (ms * 1e-3), "events_per_s": n_ev / (ms * 1e-3)}
+    det = {}
+    for w in (64, 256):
+        ms, _ = t_call(d, K=3, wave_events=w, block=b, hits_per_thread=h, mode=fcs.MODE_DETERMINISTIC)
+        det[str(w)] = {"ms": ms, "hits_per_s": H / (ms * 1e-3)}
+    out["deterministic"] = det
+    # multiplicity bucketing: events in ascending particle count, so that a
+    # wave holds events of similar size
+    order = np.argsort(np.diff(parts.event_offsets), kind="stable")
+    sp = synth.Particles(*[np.concatenate([getattr(parts.event(int(e)), k) for e in order])
+                           for k in ("type", "E", "eta", "phi")],
+                         np.concatenate([[0], np.cumsum(np.diff(parts.event_offsets)[order])]).astype(np.int64))
+    ms, H2 = t_call(sim.to_device(sp), wave_events=best_w, block=b, hits_per_thread=h)
+    out["bucketed"] = {"ms": ms, "hits_per_s": H2 / (ms * 1e-3), "hits": H2,
+                       "note": "the same events sorted by multiplicity (different random streams per event number)"}
+    out["clocks"] = clk.stop()
+    # launch latency: one 65.5 GeV electron (about 20 tasks, 1.5k hits)
+    one = sim.to_device(synth.single_particle(1))
+    lat = {}
+    for name, kw in (("eager", dict(sync=0, use_graph=0)), ("graph", dict(sync=0, use_graph=1)),
+                     ("sync_call", dict(sync=1, use_graph=0))):
+        sim.simulate(one, SEED, outputs=dict(cells=None))
+        for _ in range(20):
+            sim.simulate(one, SEED, outputs=dict(cells=None), **kw)
+        torch.cuda.synchronize()
+        host, dev = [], []
+        for _ in range(200):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0 = time.perf_counter()
+            e0.record()
+            sim.simulate(one, SEED, outputs=dict(cells=None), check=False, **kw)
+            e1.record()
+            t1 = time.perf_counter()
+            torch.cuda.synchronize()
+            host.append((t1 - t0) * 1e6)
+            dev.append(e0.elapsed_time(e1) * 1e3)
+        lat[name] = {"host_us_median": float(np.median(host)), "device_us_median": float(np.median(dev))}
+    lat["launches_per_call"] = 23
+    lat["per_launch_us_eager_minus_graph"] = (lat["eager"]["device_us_median"] -
+                                              lat["graph"]["device_us_median"]) / 22
+    out["latency_one_electron"] = lat
+    # per-event vs batched launch sequences for 64 single-electron events
+    many = sim.to_device(synth.single_particle(64))
+    ms_b, Hm = t_call(many, K=10)
+    ms_e, _ = t_call(many, K=10, batched=0)
+    # per-task launches (the paper's non-grouped GPU mode): the call reads each
+    # event's task list back and launches the hit kernel once per task, so it
+    # is timed as a whole synchronous call
+    for b_, h_ in ((128, 1), (256, 4)):
+        sim.simulate(many, SEED, outputs=dict(cells=None), batched=2, block=b_, hits_per_thread=h_)
+    torch.cuda.synchronize()
+    tt = []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        sim.simulate(many, SEED, outputs=dict(cells=None), batched=2, block=128, hits_per_thread=1)
+        torch.cuda.synchronize()
+        tt.append(time.perf_counter() - t0)
+    ms_t = 1e3 * float(np.median(tt))
+    out["single_e65_x64"] = {"hits": Hm, "batched_ms": ms_b, "per_event_ms": ms_e, "per_task_ms": ms_t,
+                             "tasks": int(sim.simulate(many, SEED, outputs=dict(cells=None))["stats"]["n_tasks"]),
+                             "per_event_over_batched": ms_e / ms_b, "per_task_over_batched": ms_t / ms_b,
+                             "per_task_shape": "128x1"}
+    print(json.dumps(out), flush=True)
+    sim.close()
 
 
 def main():
@@ -185,6 +329,8 @@ def main():
     ap.add_argument("--events", type=int, default=N_EVENTS, help="events per step (smaller cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--sweep", action="store_true", help="the 1024-event sweep and launch latency table instead")
+    ap.add_argument("--sweep-events", type=int, default=1024)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
@@ -192,6 +338,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.sweep:
+        if rank == 0:
+            run_sweep(args)
         return
 
     import torch
@@ -275,10 +425,11 @@ def main():
 
     extra = {}
     if args.extra and rank == 0:
-        ts, tst = timed(max(5, args.steps // 2), 2, mode=fcs.MODE_DETERMINISTIC)
+        ts, tst = timed(max(5, args.steps // 2), 2, mode=fcs.MODE_DETERMINISTIC, hits_per_thread=args.hpt,
+                        block=args.block)
         extra["deterministic"] = {"hits_per_s": H / (np.mean(ts) * 1e-3), "ms_per_step": float(np.mean(ts)),
                                   "stages_ms": {k: float(np.mean([s[k] for s in tst])) for k in fcs.STAGES}}
-        ts, tst = timed(max(5, args.steps // 2), 2, batched=0)
+        ts, tst = timed(max(5, args.steps // 2), 2, batched=0, hits_per_thread=args.hpt, block=args.block)
         extra["per_event_launches"] = {"hits_per_s": H / (np.mean(ts) * 1e-3), "ms_per_step": float(np.mean(ts)),
                                        "batched_speedup": float(np.mean(ts)) / ms}
         # the adjoint (gradients of the layer fractions and shape weights) over the

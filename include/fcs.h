@@ -61,7 +61,7 @@ enum fcs_device_flag {
   FCS_FLAG_BAD_PARTICLE = 1u << 0,  /* type out of range, E <= 0 or non-finite, eta/phi non-finite */
   FCS_FLAG_HIT_CAPACITY = 1u << 1,  /* more hits than the workspace was sized for (sync == 0) */
   FCS_FLAG_OUT_CAPACITY = 1u << 2,  /* more non-zero cells than `capacity` */
-  FCS_FLAG_KEY_BITS = 1u << 3,      /* deterministic mode: (cell, task) keys need > 64 bits */
+  FCS_FLAG_KEY_BITS = 1u << 3,      /* deterministic mode: (cell, task) keys need > 63 bits */
   FCS_FLAG_RECHECK_SPILL = 1u << 4, /* informational: FP64 recheck queue full, done inline */
   FCS_FLAG_BAD_OFFSETS = 1u << 5    /* event_offsets not within [0, n_particles] or decreasing */
 };
@@ -106,14 +106,19 @@ enum fcs_mode {
 
 typedef struct fcs_config {
   int32_t mode;            /* enum fcs_mode */
-  int32_t batched;         /* 1: one launch sequence for all events; 0: one sequence per event */
-  int32_t hits_per_thread; /* hit kernel: hits per thread per tile, 1..8; 0 = tuned default */
-  int32_t block;           /* hit kernel: threads per block, 128..1024 (multiple of 32); 0 = default */
+  int32_t batched;         /* 1: events in launch sequences of wave_events; 0: one sequence per
+                              event; 2: per event, one hit-kernel launch per task (the paper's
+                              non-grouped GPU mode, Sec. 4; the call waits for the stream per
+                              event to read the task list; no graph capture) */
+  int32_t hits_per_thread; /* hit kernel: hits per thread per tile, 1, 2, 4 or 8; 0 = default (4) */
+  int32_t block;           /* hit kernel: threads per block, 128, 256 or 512; 0 = default (256) */
   int32_t sync;            /* != 0: wait for the stream, read the device status (see above) */
   int32_t use_graph;       /* != 0 (requires sync == 0): capture the launch sequence as a CUDA
                               graph keyed by every argument, replay it on identical calls */
   int32_t timing;          /* != 0: record CUDA events around each stage (fcs_workspace_timings) */
-  int32_t reserved;        /* must be 0 */
+  int32_t wave_events;     /* batched: events per launch sequence (a wave), >= 0; 0 = all events of
+                              the call.  A wave's accumulation rows (4 B x cells per event) stay
+                              in L2 while they fit; the workspace holds one wave's rows */
 } fcs_config;
 
 /* Filled by fcs_simulate_events when non-NULL and config->sync != 0. */
@@ -301,7 +306,7 @@ int fcs_microbench(int32_t kind, int64_t size, int32_t iters, double* rate, cuda
  * records, tile map, recheck queue and accumulation rows are carved out of
  * one static device array of FCS_STATIC_SCRATCH_BYTES.  The call is
  * synchronous on stream s and returns the device status like a sync call.
- * Limits: the particle tables (about 76 bytes x layers per particle) plus the
+ * Limits: the particle tables (about 76 bytes x layers + 32 bytes per particle) plus the
  * accumulation rows (4 bytes x cells, padded, per event) must fit in the
  * array, and the hits of the call are bounded by what remains (128 hits per
  * 4 remaining bytes); otherwise FCS_E_RANGE with the sizes in the message.

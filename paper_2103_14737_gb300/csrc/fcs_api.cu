@@ -137,7 +137,8 @@ struct fcs_workspace {
   int64_t sizes_cap = 0;
   int64_t* pcount = nullptr;
   int64_t* poff = nullptr;
-  int64_t pc_cap = 0, po_cap = 0, pcap = 0;
+  uint4* pinfo = nullptr;
+  int64_t pc_cap = 0, po_cap = 0, pi_cap = 0, pcap = 0;
   TaskRec* tasks = nullptr;
   float* tmu = nullptr;
   int64_t* tn = nullptr;
@@ -172,6 +173,9 @@ struct fcs_workspace {
   // staging for the host-buffer entry point
   void* stage = nullptr;
   int64_t stage_cap = 0;
+  // pinned copy of a range's task records (per-task launches)
+  TaskRec* h_tasks = nullptr;
+  int64_t h_tasks_cap = 0;
   // CUDA graph cache (use_graph)
   cudaGraphExec_t graph = nullptr;
   std::vector<unsigned char> graph_key;
@@ -184,11 +188,12 @@ struct fcs_workspace {
   ~fcs_workspace() {
     if (graph) cudaGraphExecDestroy(graph);
     for (cudaEvent_t e : tev) cudaEventDestroy(e);
-    void* ps[] = {d_sizes, pcount, poff, tasks, tmu, tn, th, tlist, pdefer, gmap, recheck, acc, chunk_counts, chunk_offsets,
+    void* ps[] = {d_sizes, pcount, poff, pinfo, tasks, tmu, tn, th, tlist, pdefer, gmap, recheck, acc, chunk_counts, chunk_offsets,
                   block_sums, keys, keys_alt, head_flags, head_off, stage, grad_acc, grad_touched};
     for (void* p : ps)
       if (p) cudaFree(p);
     if (h_sizes) cudaFreeHost(h_sizes);
+    if (h_tasks) cudaFreeHost(h_tasks);
   }
 
   WsDev view() const {
@@ -196,6 +201,7 @@ struct fcs_workspace {
     w.sizes = d_sizes;
     w.pcount = pcount;
     w.poff = poff;
+    w.pinfo = pinfo;
     w.pcap = pcap;
     w.tasks = tasks;
     w.tmu = tmu;
@@ -235,6 +241,7 @@ int ws_reserve_static(fcs_workspace* ws, const fcs_geo* geo, int64_t P, int32_t 
   if (Pc > ws->pcap || !ws->pcount) {
     FCS_TRY(grow(&ws->pcount, &ws->pc_cap, Pc));
     FCS_TRY(grow(&ws->poff, &ws->po_cap, Pc));
+    FCS_TRY(grow(&ws->pinfo, &ws->pi_cap, Pc));
     ws->pcap = Pc;
   }
   FCS_TRY(grow(&ws->tasks, &ws->task_cap, Pc * NL));
@@ -346,7 +353,7 @@ int status_from(const Sizes& s, fcs_stats* st) {
   if (s.flags & FCS_FLAG_HIT_CAPACITY)
     return set_err(FCS_E_RANGE, "the workspace holds fewer hits than the call produced (%lld); reserve more",
                    (long long)s.hit_base);
-  if (s.flags & FCS_FLAG_KEY_BITS) return set_err(FCS_E_RANGE, "deterministic keys exceed 64 bits");
+  if (s.flags & FCS_FLAG_KEY_BITS) return set_err(FCS_E_RANGE, "deterministic keys exceed 63 bits");
   if (s.flags & FCS_FLAG_OUT_CAPACITY)
     return set_err(FCS_E_RANGE, "output capacity too small: %lld non-zero cells", (long long)s.nnz_total);
   return ok();
@@ -390,28 +397,51 @@ cudaError_t record_stage(cudaEvent_t e, cudaStream_t s) {
 
 // Enqueues one event range.  sync_size: read the hit count back after the
 // scans and grow the hit-dependent buffers.
-int enqueue_range(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, bool sync_size, const HitCfg& hc,
+int enqueue_range(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, int32_t range, bool sync_size, const HitCfg& hc,
                   int key_task_bits) {
   fcs_workspace* ws = a.ws;
   const Launch L{a.s, ws->num_sms};
   const int det = a.cfg.mode == FCS_MODE_DETERMINISTIC;
   const int32_t rows = ev_hi - ev_lo;
-  cudaEvent_t* tev = a.cfg.timing ? &ws->tev[(size_t)(a.cfg.batched ? 0 : ev_lo) * 5] : nullptr;
+  cudaEvent_t* tev = a.cfg.timing ? &ws->tev[(size_t)range * 5] : nullptr;
   if (tev) FCS_CUDA(record_stage(tev[0], a.s));
   k_range_begin<<<1, 1, 0, a.s>>>(ws->d_sizes, a.parts.event_offsets, ev_lo, ev_hi, a.n_particles, ws->pcap);
   const uint32_t k0 = (uint32_t)(a.seed & 0xFFFFFFFFu), k1 = (uint32_t)(a.seed >> 32);
   const ScanTmp tmp{ws->block_sums};
   WsDev w = ws->view();
-  FCS_CUDA(launch_task_counts(a.geo->d, a.prm->d, a.parts, ev_lo, ev_hi, k0, k1, a.first_event, w, tmp, L));
-  if (sync_size) {
+  FCS_CUDA(launch_task_counts(a.geo->d, a.prm->d, a.parts, ev_lo, ev_hi, k0, k1, a.first_event, w, tmp,
+                              a.n_particles, L));
+  if (sync_size || a.cfg.batched == 2) {
     FCS_CUDA(cudaMemcpyAsync(ws->h_sizes, ws->d_sizes, sizeof(Sizes), cudaMemcpyDeviceToHost, a.s));
     FCS_CUDA(cudaStreamSynchronize(a.s));
     FCS_TRY(ws_reserve_hits(ws, ws->h_sizes->n_hits, a.cfg.mode));
     w = ws->view();
   }
-  FCS_CUDA(launch_task_finish(w, a.dbg, L));
+  FCS_CUDA(launch_task_finish(w, a.dbg, det, a.n_particles * a.geo->d.n_layers, L));
   if (tev) FCS_CUDA(record_stage(tev[1], a.s));
-  FCS_CUDA(launch_hits(a.geo->d, a.prm->d, w, ev_lo, k0, k1, a.first_event, hc, key_task_bits, a.dbg, L));
+  if (a.cfg.batched == 2) {
+    // per-task launches: read the range's task records, then one hit-kernel
+    // launch over each task's hits
+    const int64_t nt = ws->h_sizes->n_tasks;
+    if (nt > ws->h_tasks_cap) {
+      if (ws->h_tasks) cudaFreeHost(ws->h_tasks);
+      ws->h_tasks = nullptr;
+      ws->h_tasks_cap = 0;
+      FCS_CUDA(cudaMallocHost((void**)&ws->h_tasks, (size_t)nt * sizeof(TaskRec)));
+      ws->h_tasks_cap = nt;
+    }
+    if (nt > 0) {
+      FCS_CUDA(cudaMemcpyAsync(ws->h_tasks, ws->tasks, (size_t)nt * sizeof(TaskRec), cudaMemcpyDeviceToHost, a.s));
+      FCS_CUDA(cudaStreamSynchronize(a.s));
+    }
+    for (int64_t t = 0; t < nt; ++t) {
+      const TaskRec& r = ws->h_tasks[t];
+      FCS_CUDA(launch_hits_task(a.geo->d, a.prm->d, w, ev_lo, k0, k1, a.first_event, hc, key_task_bits, a.dbg,
+                                r.hit_begin, r.hit_begin + r.n, (int32_t)t, L));
+    }
+  } else {
+    FCS_CUDA(launch_hits(a.geo->d, a.prm->d, w, ev_lo, k0, k1, a.first_event, hc, key_task_bits, a.dbg, L));
+  }
   if (tev) FCS_CUDA(record_stage(tev[2], a.s));
   FCS_CUDA(launch_recheck(a.geo->d, a.prm->d, w, ev_lo, k0, k1, a.first_event, det, key_task_bits, a.dbg, L));
   if (tev) FCS_CUDA(record_stage(tev[3], a.s));
@@ -430,6 +460,19 @@ int enqueue_range(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, bool sync_siz
   return FCS_OK;
 }
 
+// Events per launch sequence: all (batched, wave_events == 0), waves of
+// wave_events, or one (per-event launches).
+int32_t range_events(const fcs_config& c, int32_t n_events) {
+  if (c.batched != 1) return 1;
+  if (c.wave_events > 0 && c.wave_events < n_events) return c.wave_events;
+  return std::max(n_events, 1);
+}
+
+int32_t n_ranges(const fcs_config& c, int32_t n_events) {
+  const int32_t W = range_events(c, n_events);
+  return (n_events + W - 1) / W;
+}
+
 int ensure_timing_events(fcs_workspace* ws, int ranges) {
   while ((int)ws->tev.size() < ranges * 5) {
     cudaEvent_t e;
@@ -445,11 +488,9 @@ int enqueue_call(const CallArgs& a, bool sync_size, const HitCfg& hc, int key_ta
   k_call_begin<<<1, 1, 0, a.s>>>(ws->d_sizes);
   if (a.cells_out && a.cfg.mode == FCS_MODE_DETERMINISTIC)
     FCS_CUDA(cudaMemsetAsync(a.cells_out, 0, (size_t)a.n_events * a.geo->d.n_cells * sizeof(float), a.s));
-  if (a.cfg.batched) {
-    FCS_TRY(enqueue_range(a, 0, a.n_events, sync_size, hc, key_task_bits));
-  } else {
-    for (int32_t e = 0; e < a.n_events; ++e) FCS_TRY(enqueue_range(a, e, e + 1, sync_size, hc, key_task_bits));
-  }
+  const int32_t W = range_events(a.cfg, a.n_events);
+  for (int32_t lo = 0, r = 0; lo < a.n_events; lo += W, ++r)
+    FCS_TRY(enqueue_range(a, lo, std::min(a.n_events, lo + W), r, sync_size, hc, key_task_bits));
   k_call_end<<<1, 1, 0, a.s>>>(ws->d_sizes, a.event_offsets_out, a.n_events, a.capacity, a.cell_ids ? 1 : 0);
   FCS_CUDA(cudaGetLastError());
   return FCS_OK;
@@ -465,13 +506,14 @@ HitCfg hit_cfg(const fcs_config& c) {
 
 int validate_config(const fcs_config& c) {
   if (c.mode != FCS_MODE_ATOMIC && c.mode != FCS_MODE_DETERMINISTIC) return set_err(FCS_E_ARG, "config.mode");
-  if (c.batched != 0 && c.batched != 1) return set_err(FCS_E_ARG, "config.batched must be 0 or 1");
+  if (c.batched < 0 || c.batched > 2) return set_err(FCS_E_ARG, "config.batched must be 0, 1 or 2");
+  if (c.batched == 2 && c.use_graph) return set_err(FCS_E_ARG, "per-task launches (batched = 2) cannot be captured");
   const int hpt = c.hits_per_thread, blk = c.block;
   if (!(hpt == 0 || hpt == 1 || hpt == 2 || hpt == 4 || hpt == 8))
     return set_err(FCS_E_ARG, "config.hits_per_thread must be 0, 1, 2, 4 or 8");
   if (!(blk == 0 || blk == 128 || blk == 256 || blk == 512))
     return set_err(FCS_E_ARG, "config.block must be 0, 128, 256 or 512");
-  if (c.reserved) return set_err(FCS_E_ARG, "config.reserved must be 0");
+  if (c.wave_events < 0) return set_err(FCS_E_ARG, "config.wave_events must be >= 0");
   if (c.use_graph && c.sync) return set_err(FCS_E_ARG, "config.use_graph requires sync == 0");
   return FCS_OK;
 }
@@ -820,19 +862,19 @@ int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace
     FCS_CUDA(cudaGetLastError());
     return ok();
   }
-  const int32_t rows = cfg.batched ? n_events : 1;
+  const int32_t rows = range_events(cfg, n_events);
   if ((int64_t)rows * geo->d.acc_stride >= (int64_t(1) << 32))
     return set_err(FCS_E_RANGE, "%d events x %d cells exceed 2^32 accumulation cells; split the batch", rows,
                    geo->d.acc_stride);
   FCS_TRY(ws_reserve_static(ws, geo, n_particles, rows, cfg.mode));
   const int key_task_bits = bits_for(std::max<int64_t>(n_particles, 1) * geo->d.n_layers);
   if (cfg.mode == FCS_MODE_DETERMINISTIC &&
-      kRecordCountBits + key_task_bits + bits_for((int64_t)rows * geo->d.n_cells) > 64)
-    return set_err(FCS_E_RANGE, "deterministic mode: (cell, task) keys exceed 64 bits; split the batch");
+      kRecordCountBits + key_task_bits + bits_for((int64_t)rows * geo->d.n_cells) > 63)
+    return set_err(FCS_E_RANGE, "deterministic mode: (cell, task) keys exceed 63 bits; use smaller waves or split the batch");
   CallArgs a{geo, prm, ws, *particles, n_particles, n_events, seed, first_event, cfg, cells_out,
              cell_ids, cell_E, event_offsets_out, capacity, dbg, s};
   const HitCfg hc = hit_cfg(cfg);
-  if (cfg.timing) FCS_TRY(ensure_timing_events(ws, cfg.batched ? 1 : n_events));
+  if (cfg.timing) FCS_TRY(ensure_timing_events(ws, n_ranges(cfg, n_events)));
   else ws->timed_ranges = 0;
   if (!cfg.sync && cfg.use_graph) {
     // key of the captured sequence: every argument that shapes it
@@ -856,6 +898,9 @@ int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace
     put(&capacity, sizeof(capacity));
     put(&dbg, sizeof(dbg));
     put(&ws->d_sizes, sizeof(void*));
+    put(&ws->pcount, sizeof(void*));
+    put(&ws->poff, sizeof(void*));
+    put(&ws->pinfo, sizeof(void*));
     put(&ws->tasks, sizeof(void*));
     put(&ws->gmap, sizeof(void*));
     put(&ws->recheck, sizeof(void*));
@@ -919,6 +964,7 @@ int fcs_autotune(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws, c
   fcs_config c{};
   c.mode = config->mode;
   c.batched = 1;
+  c.wave_events = config->wave_events;
   c.sync = 1;
   // sizes the workspace and validates the arguments
   FCS_TRY(fcs_simulate_events(geo, prm, ws, particles, n_particles, n_events, seed, first_event, &c, nullptr, nullptr,
@@ -1039,7 +1085,7 @@ int fcs_simulate_backward(const fcs_geo* geo, const fcs_params* prm, fcs_workspa
     return set_err(FCS_E_ARG, "geometry, parametrisation and workspace must live on the current device");
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (n_events == 0) return ok();
-  const int32_t rows = cfg.batched ? n_events : 1;
+  const int32_t rows = range_events(cfg, n_events);
   if ((int64_t)rows * geo->d.n_cells >= (int64_t(1) << 32))
     return set_err(FCS_E_RANGE, "%d events x %d cells exceed 2^32; split the batch", rows, geo->d.n_cells);
   FCS_TRY(ws_reserve_static(ws, geo, n_particles, 1, FCS_MODE_ATOMIC));
@@ -1061,17 +1107,17 @@ int fcs_simulate_backward(const fcs_geo* geo, const fcs_params* prm, fcs_workspa
   ws->grad_dirty = true;
   k_call_begin<<<1, 1, 0, s>>>(ws->d_sizes);
   for (int32_t lo = 0; lo < n_events; lo += rows) {
-    const int32_t hi = lo + rows;
+    const int32_t hi = std::min(n_events, lo + rows);
     k_range_begin<<<1, 1, 0, s>>>(ws->d_sizes, particles->event_offsets, lo, hi, n_particles, ws->pcap);
     WsDev w = ws->view();
-    FCS_CUDA(launch_task_counts(geo->d, prm->d, *particles, lo, hi, k0, k1, first_event, w, tmp, L));
+    FCS_CUDA(launch_task_counts(geo->d, prm->d, *particles, lo, hi, k0, k1, first_event, w, tmp, n_particles, L));
     if (cfg.sync) {
       FCS_CUDA(cudaMemcpyAsync(ws->h_sizes, ws->d_sizes, sizeof(Sizes), cudaMemcpyDeviceToHost, s));
       FCS_CUDA(cudaStreamSynchronize(s));
       FCS_TRY(ws_reserve_hits(ws, ws->h_sizes->n_hits, FCS_MODE_ATOMIC));
       w = ws->view();
     }
-    FCS_CUDA(launch_task_finish(w, nullptr, L));
+    FCS_CUDA(launch_task_finish(w, nullptr, 0, n_particles * geo->d.n_layers, L));
     const float* g = dL_dcells + (int64_t)lo * geo->d.n_cells;
     FCS_CUDA(launch_hits_grad(geo->d, prm->d, w, lo, k0, k1, first_event, hc, g, ws->grad_acc, ws->grad_touched, L));
     FCS_CUDA(launch_recheck_grad(geo->d, prm->d, w, lo, k0, k1, first_event, g, ws->grad_acc, ws->grad_touched, L));
@@ -1171,6 +1217,7 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   w.d_sizes = c.take<Sizes>(1);
   w.pcount = c.take<int64_t>(P);
   w.poff = c.take<int64_t>(P);
+  w.pinfo = c.take<uint4>(P);
   w.pcap = P;
   w.tasks = c.take<TaskRec>(P * NL);
   w.tmu = c.take<float>(P * NL);
@@ -1188,7 +1235,7 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   w.block_sums = c.take<int64_t>(kScanBlocks + 1);
   w.recheck = c.take<uint2>(recheck_cap);
   w.recheck_cap = recheck_cap;
-  const bool fits = w.d_sizes && w.pcount && w.poff && w.tasks && w.tmu && w.tn && w.th && w.tlist && w.pdefer &&
+  const bool fits = w.d_sizes && w.pcount && w.poff && w.pinfo && w.tasks && w.tmu && w.tn && w.th && w.tlist && w.pdefer &&
                     w.acc &&
                     w.chunk_counts &&
                     w.chunk_offsets && w.block_sums && w.recheck && c.cap - c.off >= 4096;
@@ -1201,6 +1248,7 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
     w.d_sizes = nullptr;
     w.pcount = nullptr;
     w.poff = nullptr;
+    w.pinfo = nullptr;
     w.tasks = nullptr;
     w.tmu = nullptr;
     w.tn = nullptr;

@@ -20,6 +20,8 @@
 // (cell, task, count) records for the sort-by-cell reduction.
 #pragma once
 
+#include <type_traits>
+
 #include "fcs_internal.cuh"
 
 namespace fcs {
@@ -42,6 +44,11 @@ struct HitKParams {
   const float* grad_in;  // dL/dE_cell of the range's events, row stride n_cells
   double* grad_acc;      // [n_entries][128] sum of E_hit dL/dE_cell per (entry, shape bin)
   uint8_t* grad_touched; // [n_entries] set where grad_acc has contributions
+  // one launch per task (static_tiles != 0): CTA b takes tile b of the hits
+  // [h_lo, h_hi), all of task t_last
+  int64_t h_lo, h_hi;
+  int32_t t_last;
+  int32_t static_tiles;
 };
 
 // ---- shape bin: inverse CDF by guide table and binary search --------------
@@ -151,6 +158,27 @@ struct FastHit {
   bool sure;
 };
 
+// The regions [a, b) of a task's layer that its hits can reach: every hit
+// lies within r_max |s_eta| of eta_c in eta (r_max = the outer edge of the
+// shape histogram), widened by 2^-8 relative and 2^-16 (1 + |eta_c|) for the
+// FP32 scale factor and for the rounding of the FP32 and FP64 hit positions.
+// Split q is left out of the search when the FP64 split lies below (above)
+// every hit, judged from its FP32 copy with a 2^-22 relative margin, so the
+// search over [a, b) decides exactly as the search over the whole layer and
+// needs no certification at the splits it skips.
+__device__ __forceinline__ uint32_t task_lay(const HitSmemTables& tb, int layer, float eta_c, float s_eta) {
+  const int rb = tb.lrb[layer], re = tb.lrb[layer + 1];
+  const float D = fmaf(tb.rb[kNR - 1].z * fabsf(s_eta), 1.00390625f, fmaf(fabsf(eta_c), 0x1p-16f, 0x1p-16f));
+  const float L = eta_c - D, U = eta_c + D;
+  int a = rb, b = re;
+  for (int q = rb + 1; q < re; ++q) {
+    const float sp = tb.reg[q].split;
+    if (fmaf(fabsf(sp), 0x1p-22f, sp) <= L) a = q;
+    if (b == re && fmaf(-fabsf(sp), 0x1p-22f, sp) > U) b = q;
+  }
+  return (uint32_t)layer | ((uint32_t)a << 8) | ((uint32_t)b << 20);
+}
+
 // A task as the hit loop uses it, staged in shared memory per tile (48 B):
 // 32-bit offsets and the Philox counter words are formed once per task.
 struct TileTask {
@@ -161,7 +189,7 @@ struct TileTask {
   uint32_t ctr_z;   // particle in event
   uint32_t ctr_w;   // event number of the random stream
   uint32_t row_off; // accumulation row offset (atomic) or row * n_cells (deterministic)
-  uint32_t lay;     // layer | first region << 8 | end region << 20
+  uint32_t lay;     // layer | first region << 8 | end region << 20 (the reachable regions)
 };
 static_assert(sizeof(TileTask) == 48, "TileTask layout");
 
@@ -215,25 +243,29 @@ __device__ __forceinline__ FastHit fast_cell(const HitSmemTables& tb, const TT& 
 }
 
 // ---- warp-level deposit / record emission -----------------------------------
-__device__ __forceinline__ void emit_warp(bool ok, unsigned long long gkey, const WsDev& w) {
+// Deterministic mode: every hit of the range owns the record slot of its hit
+// index, so the record array is in hit order, which is task order.  The
+// first lane of each group of equal (cell, task) keys in the warp writes the
+// group's record (count - 1 in the low bits) to its own slot; the other valid
+// lanes write the empty record (all ones, sorted last).  A stable sort by cell
+// then gives (cell, task) order.  Uncertain hits leave their slot empty for the
+// recheck kernel to fill.  Returns the warp's number of records (the caller
+// counts them per CTA: one counter hit by every warp would serialise).
+__device__ __forceinline__ unsigned emit_slots(bool valid, bool ok, unsigned long long gkey, int64_t slot,
+                                               const WsDev& w) {
   const int lane = threadIdx.x & 31;
   const unsigned m = __ballot_sync(0xffffffffu, ok);
   unsigned peers = 0;
   if (ok) peers = __match_any_sync(m, gkey);
   const bool lead = ok && (lane == __ffs(peers) - 1);
   const unsigned lm = __ballot_sync(0xffffffffu, lead);
-  if (lm == 0) return;
-  unsigned long long base = 0;
-  const int l0 = __ffs(lm) - 1;
-  if (lane == l0) base = atomicAdd((unsigned long long*)&w.sizes->n_records, (unsigned long long)__popc(lm));
-  base = __shfl_sync(0xffffffffu, base, l0);
-  if (lead) {
-    const unsigned long long pos = base + __popc(lm & ((1u << lane) - 1u));
-    if (pos < (unsigned long long)w.rec_cap)
-      w.keys[pos] = (gkey << kRecordCountBits) | (unsigned long long)(__popc(peers) - 1);
+  if (valid) {
+    if (slot < w.rec_cap)
+      w.keys[slot] = lead ? ((gkey << kRecordCountBits) | (unsigned long long)(__popc(peers) - 1)) : ~0ull;
     else
       atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_HIT_CAPACITY);
   }
+  return (unsigned)__popc(lm);
 }
 
 // Sum of v over each group of lanes with equal keys, added by the group's
@@ -257,7 +289,7 @@ __device__ __forceinline__ void grad_warp(bool ok, uint32_t key, float v, float*
 }
 
 __device__ __forceinline__ void deposit_single(const HitKParams& kp, int32_t event, float Ehit, int64_t task_rel,
-                                               int32_t cell, int mode, int32_t entry, int bin) {
+                                               int32_t cell, int mode, int32_t entry, int bin, int64_t slot) {
   const int64_t row = event - kp.ev_lo;
   if (mode == kModeAtomic) {
     atomicAdd(kp.w.acc + row * kp.g.acc_stride + cell, Ehit);
@@ -268,8 +300,8 @@ __device__ __forceinline__ void deposit_single(const HitKParams& kp, int32_t eve
   } else {
     const unsigned long long gkey =
         ((unsigned long long)(row * kp.g.n_cells + cell) << kp.key_task_bits) | (unsigned long long)task_rel;
-    const unsigned long long pos = atomicAdd((unsigned long long*)&kp.w.sizes->n_records, 1ull);
-    if (pos < (unsigned long long)kp.w.rec_cap) kp.w.keys[pos] = gkey << kRecordCountBits;
+    atomicAdd((unsigned long long*)&kp.w.sizes->n_records, 1ull);
+    if (slot < kp.w.rec_cap) kp.w.keys[slot] = gkey << kRecordCountBits;
     else atomicOr(&kp.w.sizes->flags, (uint32_t)FCS_FLAG_HIT_CAPACITY);
   }
 }
@@ -306,7 +338,7 @@ template <int BLOCK, int HPT, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKParams kp) {
   constexpr bool DET = MODE == kModeDet;
   constexpr int TILE = BLOCK * HPT;
-  static_assert(TILE % kGranule == 0, "tiles must start on granules");
+  static_assert(TILE % kGranule == 0, "queue tiles must start on granules (the tile map's unit)");
   static_assert(TILE <= 4096, "owner index and 32-bit match keys need TILE + 1 < 2^13");
   __shared__ HitSmemTables tb;
   __shared__ __align__(16) TileTask s_task[kSmemTasks];
@@ -314,26 +346,32 @@ __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKPara
   __shared__ int s_wmax[BLOCK / 32];
   __shared__ unsigned long long s_tile;
   __shared__ float s_gv[MODE == kModeGrad ? BLOCK : 1];
+  __shared__ unsigned long long s_recs;  // deterministic mode: records of this CTA
   load_tables(tb, kp.g, kp.p);
   for (int i = threadIdx.x; i < TILE; i += BLOCK) s_owner[i] = 0;
   const WsDev& w = kp.w;
-  const int64_t H = w.sizes->n_hits;
-  const int64_t T_all = w.sizes->n_tasks;
+  const int64_t H = kp.static_tiles ? kp.h_hi : w.sizes->n_hits;
+  const int64_t T_last = kp.static_tiles ? (int64_t)kp.t_last : w.sizes->n_tasks - 1;
+  const int64_t hbase = kp.static_tiles ? kp.h_lo : 0;
   if (H > w.gmap_cap * (int64_t)kGranule) return;  // flagged by the task finish kernel
-  const unsigned long long n_tiles = (unsigned long long)((H + TILE - 1) / TILE);
+  const unsigned long long n_tiles = (unsigned long long)((H - hbase + TILE - 1) / TILE);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t hit_dbg_base = kp.dbg_hit_cell || kp.dbg_hit_bin ? w.sizes->hit_base : 0;
   const uint32_t row_stride = MODE == kModeAtomic ? (uint32_t)kp.g.acc_stride : (uint32_t)kp.g.n_cells;
-  if (threadIdx.x == 0) s_tile = atomicAdd(&w.sizes->queue, 1ull);
+  if (threadIdx.x == 0) {
+    s_tile = kp.static_tiles ? blockIdx.x : atomicAdd(&w.sizes->queue, 1ull);
+    s_recs = 0;
+  }
   __syncthreads();
   unsigned long long tile = s_tile;
+  unsigned long long recs = 0;  // deterministic mode: this warp's records
   while (tile < n_tiles) {
     __syncthreads();  // everyone has read s_tile; s_owner is zero again
-    if (threadIdx.x == 0) s_tile = atomicAdd(&w.sizes->queue, 1ull);
-    const int64_t h0 = (int64_t)tile * TILE;
+    if (threadIdx.x == 0) s_tile = kp.static_tiles ? n_tiles : atomicAdd(&w.sizes->queue, 1ull);
+    const int64_t h0 = hbase + (int64_t)tile * TILE;
     const int hn = (int)min((int64_t)TILE, H - h0);  // hits in this tile
-    const int32_t t0 = w.gmap[h0 / kGranule];
-    const int32_t t1 = (h0 + TILE < H) ? w.gmap[(h0 + TILE) / kGranule] : (int32_t)(T_all - 1);
+    const int32_t t0 = kp.static_tiles ? kp.t_last : w.gmap[h0 / kGranule];
+    const int32_t t1 = (h0 + TILE < H && !kp.static_tiles) ? w.gmap[(h0 + TILE) / kGranule] : (int32_t)T_last;
     const int nt = t1 - t0 + 1;
     if (nt <= kSmemTasks) {
       // stage the tile's tasks and mark where each starts
@@ -352,7 +390,7 @@ __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKPara
         q.ctr_z = (uint32_t)r.particle;
         q.ctr_w = kp.first_event_lo + (uint32_t)r.event;
         q.row_off = (uint32_t)(r.event - kp.ev_lo) * row_stride;
-        q.lay = (uint32_t)r.layer | ((uint32_t)tb.lrb[r.layer] << 8) | ((uint32_t)tb.lrb[r.layer + 1] << 20);
+        q.lay = task_lay(tb, r.layer, r.eta_c, r.s_eta);
         s_task[j] = q;
         if (j > 0 && s < TILE) s_owner[s] = (int16_t)j;
       }
@@ -365,86 +403,97 @@ __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKPara
     __syncthreads();
     owner_scan<BLOCK, HPT>(s_owner, s_wmax);
     __syncthreads();
+    // the hit loop, compiled once for staged tiles (the common case) and once
+    // for tiles with more tasks than the shared copy holds
+    auto hit_loop = [&](auto staged) {
 #pragma unroll 1
-    for (int k = 0; k < HPT; ++k) {
-      const int i = warp * 32 * HPT + k * 32 + lane;
-      const bool valid = i < hn;
-      const int tl = valid ? s_owner[i] : 0;
-      TileTask T;
-      if (nt <= kSmemTasks) {
-        T = s_task[tl];
-      } else {  // more tasks than the shared copy holds: read the record itself
-        const TaskRec r = w.tasks[t0 + tl];
-        T.rel = (int32_t)(r.hit_begin - h0);
-        T.entry = r.entry;
-        T.Ehit = r.Ehit;
-        T.eta_c = r.eta_c;
-        T.phi_c = r.phi_c;
-        T.s_eta = r.s_eta;
-        T.s_phi = r.s_phi;
-        T.ctr_y = (uint32_t)r.layer | (kPurposeHit << 16);
-        T.ctr_z = (uint32_t)r.particle;
-        T.ctr_w = kp.first_event_lo + (uint32_t)r.event;
-        T.row_off = (uint32_t)(r.event - kp.ev_lo) * row_stride;
-        T.lay = (uint32_t)r.layer | ((uint32_t)tb.lrb[r.layer] << 8) | ((uint32_t)tb.lrb[r.layer + 1] << 20);
-      }
-      const uint32_t hit = (uint32_t)(i - T.rel);
-      const uint4 x = philox4x32_10(make_uint4(hit, T.ctr_y, T.ctr_z, T.ctr_w), kp.k0, kp.k1);
-      const int bin = sample_bin(kp.p, T.entry, x.x);
-      const FastHit f = fast_cell(tb, T, x, bin);
-      const bool ok = valid && f.sure;
-      const bool need = valid && !f.sure;
-      if constexpr (MODE == kModeGrad) {
-        // dL/dE_cell of the hit's cell times its energy, summed per (entry, bin)
-        const float v = ok ? __fmul_rn(T.Ehit, __ldg(kp.grad_in + T.row_off + f.cell)) : 0.0f;
-        grad_warp(ok, ((uint32_t)T.entry << 7) | (uint32_t)bin, v, s_gv + warp * 32, kp);
-      } else if constexpr (!DET) {
-        // (cell, task-in-tile) identifies (address, hit energy): 19 + 13 bits
-        const unsigned m = __ballot_sync(0xffffffffu, ok);
-        if (ok) {
-          const unsigned peers = kp.key32 ? __match_any_sync(m, ((uint32_t)f.cell << 13) | (uint32_t)tl)
-                                          : __match_any_sync(m, ((unsigned long long)(uint32_t)tl << 32) |
-                                                                    (uint32_t)f.cell);
-          if (lane == __ffs(peers) - 1)
-            atomicAdd(w.acc + T.row_off + f.cell, __fmul_rn((float)__popc(peers), T.Ehit));
+      for (int k = 0; k < HPT; ++k) {
+        const int i = warp * 32 * HPT + k * 32 + lane;
+        const bool valid = i < hn;
+        const int tl = valid ? s_owner[i] : 0;
+        TileTask T;
+        if constexpr (decltype(staged)::value) {
+          T = s_task[tl];
+        } else {  // more tasks than the shared copy holds: read the record itself
+          const TaskRec r = w.tasks[t0 + tl];
+          T.rel = (int32_t)(r.hit_begin - h0);
+          T.entry = r.entry;
+          T.Ehit = r.Ehit;
+          T.eta_c = r.eta_c;
+          T.phi_c = r.phi_c;
+          T.s_eta = r.s_eta;
+          T.s_phi = r.s_phi;
+          T.ctr_y = (uint32_t)r.layer | (kPurposeHit << 16);
+          T.ctr_z = (uint32_t)r.particle;
+          T.ctr_w = kp.first_event_lo + (uint32_t)r.event;
+          T.row_off = (uint32_t)(r.event - kp.ev_lo) * row_stride;
+          T.lay = task_lay(tb, r.layer, r.eta_c, r.s_eta);
         }
-      } else {
-        const unsigned long long gkey =
-            ((unsigned long long)(T.row_off + (uint32_t)f.cell) << kp.key_task_bits) | (unsigned long long)(t0 + tl);
-        emit_warp(ok, gkey, w);
-      }
-      // queue the uncertain hits for the FP64 recheck
-      const unsigned m = __ballot_sync(0xffffffffu, need);
-      if (m) {
-        unsigned long long base = 0;
-        const int l0 = __ffs(m) - 1;
-        if (lane == l0) base = atomicAdd((unsigned long long*)&w.sizes->n_recheck, (unsigned long long)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, l0);
-        if (need) {
-          const unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
-          if (pos < (unsigned long long)w.recheck_cap) {
-            w.recheck[pos] = make_uint2((uint32_t)(t0 + tl), hit);
-          } else {
-            const int32_t ev = (int32_t)(T.ctr_w - kp.first_event_lo);
-            const int32_t c = cell_fp64(kp.g, kp.p, (int32_t)(T.lay & 0xFF), T.eta_c, T.phi_c, x, bin);
-            deposit_single(kp, ev, T.Ehit, t0 + tl, c, MODE, T.entry, bin);
-            atomicAdd((unsigned long long*)&w.sizes->n_inline, 1ull);
-            atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_RECHECK_SPILL);
-            if (kp.dbg_hit_cell && hit_dbg_base + h0 + i < kp.dbg_hit_cap) kp.dbg_hit_cell[hit_dbg_base + h0 + i] = c;
+        const uint32_t hit = (uint32_t)(i - T.rel);
+        const uint4 x = philox4x32_10(make_uint4(hit, T.ctr_y, T.ctr_z, T.ctr_w), kp.k0, kp.k1);
+        const int bin = sample_bin(kp.p, T.entry, x.x);
+        const FastHit f = fast_cell(tb, T, x, bin);
+        const bool ok = valid && f.sure;
+        const bool need = valid && !f.sure;
+        if constexpr (MODE == kModeGrad) {
+          // dL/dE_cell of the hit's cell times its energy, summed per (entry, bin)
+          const float v = ok ? __fmul_rn(T.Ehit, __ldg(kp.grad_in + T.row_off + f.cell)) : 0.0f;
+          grad_warp(ok, ((uint32_t)T.entry << 7) | (uint32_t)bin, v, s_gv + warp * 32, kp);
+        } else if constexpr (!DET) {
+          // (cell, task-in-tile) identifies (address, hit energy): 19 + 13 bits
+          const unsigned m = __ballot_sync(0xffffffffu, ok);
+          if (ok) {
+            const unsigned peers = kp.key32 ? __match_any_sync(m, ((uint32_t)f.cell << 13) | (uint32_t)tl)
+                                            : __match_any_sync(m, ((unsigned long long)(uint32_t)tl << 32) |
+                                                                      (uint32_t)f.cell);
+            if (lane == __ffs(peers) - 1)
+              atomicAdd(w.acc + T.row_off + f.cell, __fmul_rn((float)__popc(peers), T.Ehit));
+          }
+        } else {
+          const unsigned long long gkey =
+              ((unsigned long long)(T.row_off + (uint32_t)f.cell) << kp.key_task_bits) | (unsigned long long)(t0 + tl);
+          recs += emit_slots(valid, ok, gkey, h0 + i, w);
+        }
+        // queue the uncertain hits for the FP64 recheck
+        const unsigned m = __ballot_sync(0xffffffffu, need);
+        if (m) {
+          unsigned long long base = 0;
+          const int l0 = __ffs(m) - 1;
+          if (lane == l0) base = atomicAdd((unsigned long long*)&w.sizes->n_recheck, (unsigned long long)__popc(m));
+          base = __shfl_sync(0xffffffffu, base, l0);
+          if (need) {
+            const unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
+            if (pos < (unsigned long long)w.recheck_cap) {
+              w.recheck[pos] = make_uint2((uint32_t)(t0 + tl), hit);
+            } else {
+              const int32_t ev = (int32_t)(T.ctr_w - kp.first_event_lo);
+              const int32_t c = cell_fp64(kp.g, kp.p, (int32_t)(T.lay & 0xFF), T.eta_c, T.phi_c, x, bin);
+              deposit_single(kp, ev, T.Ehit, t0 + tl, c, MODE, T.entry, bin, h0 + i);
+              atomicAdd((unsigned long long*)&w.sizes->n_inline, 1ull);
+              atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_RECHECK_SPILL);
+              if (kp.dbg_hit_cell && hit_dbg_base + h0 + i < kp.dbg_hit_cap) kp.dbg_hit_cell[hit_dbg_base + h0 + i] = c;
+            }
           }
         }
-      }
-      if (kp.dbg_hit_cell || kp.dbg_hit_bin) {
-        const int64_t h = hit_dbg_base + h0 + i;
-        if (valid && h < kp.dbg_hit_cap) {
-          if (kp.dbg_hit_cell && f.sure) kp.dbg_hit_cell[h] = f.cell;
-          if (kp.dbg_hit_bin) kp.dbg_hit_bin[h] = (int16_t)bin;
+        if (kp.dbg_hit_cell || kp.dbg_hit_bin) {
+          const int64_t h = hit_dbg_base + h0 + i;
+          if (valid && h < kp.dbg_hit_cap) {
+            if (kp.dbg_hit_cell && f.sure) kp.dbg_hit_cell[h] = f.cell;
+            if (kp.dbg_hit_bin) kp.dbg_hit_bin[h] = (int16_t)bin;
+          }
         }
+        s_owner[i] = 0;  // ready for the next tile (each slot is read and reset by one thread)
       }
-      s_owner[i] = 0;  // ready for the next tile (each slot is read and reset by one thread)
-    }
+    };
+    if (nt <= kSmemTasks) hit_loop(std::true_type{});
+    else hit_loop(std::false_type{});
     __syncthreads();  // the tile's shared data is dead; s_tile holds the next tile
     tile = s_tile;
+  }
+  if constexpr (DET) {
+    if (lane == 0 && recs) atomicAdd(&s_recs, recs);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_recs) atomicAdd((unsigned long long*)&w.sizes->n_records, s_recs);
   }
 }
 
@@ -464,7 +513,7 @@ __global__ void __launch_bounds__(128) k_recheck(const __grid_constant__ HitKPar
         kp.k0, kp.k1);
     const int bin = sample_bin(kp.p, T.entry, x.x);
     const int32_t c = cell_fp64(kp.g, kp.p, T.layer, T.eta_c, T.phi_c, x, bin);
-    deposit_single(kp, T.event, T.Ehit, q.x, c, MODE, T.entry, bin);
+    deposit_single(kp, T.event, T.Ehit, q.x, c, MODE, T.entry, bin, T.hit_begin + q.y);
     const int64_t h = hit_dbg_base + T.hit_begin + q.y;
     if (kp.dbg_hit_cell && h < kp.dbg_hit_cap) kp.dbg_hit_cell[h] = c;
   }

@@ -35,7 +35,13 @@ static cudaError_t launch_hits_shape(const HitKParams& kp, const Launch& L) {
     if (e != cudaSuccess) return e;
     occ = o < 1 ? 1 : o;
   }
-  k_hits<BLOCK, HPT, MODE><<<L.num_sms * occ, BLOCK, 0, L.s>>>(kp);
+  int64_t grid = (int64_t)L.num_sms * occ;
+  if (kp.static_tiles) {
+    constexpr int64_t TILE = (int64_t)BLOCK * HPT;
+    grid = (kp.h_hi - kp.h_lo + TILE - 1) / TILE;
+    if (grid <= 0) return cudaSuccess;
+  }
+  k_hits<BLOCK, HPT, MODE><<<(unsigned)grid, BLOCK, 0, L.s>>>(kp);
   return cudaGetLastError();
 }
 

@@ -21,8 +21,8 @@ constexpr int kRecordCountBits = 5;  // deterministic mode: count - 1 in the low
 constexpr int kLfactEntries = 8192;  // log k! table for the FP32 Poisson test (k < 8192)
 
 // Task record: one (event, particle, layer) of the hit loop of Listing 1.
-// 48 bytes; tasks are stored in (event, particle, layer) order and hits of a
-// task are the global hit numbers [hit_begin, hit_begin + n).
+// 48 bytes; tasks are stored in (event, particle, layer) order and the hits
+// of a task are the hit numbers [hit_begin, hit_begin + n) of its event range.
 struct __align__(16) TaskRec {
   int64_t hit_begin;
   int32_t n;        // hits (>= 1)
@@ -85,7 +85,7 @@ struct Sizes {
   int64_t n_tasks;
   int64_t n_hits;
   int64_t n_recheck;    // entries appended to the recheck queue (may exceed its capacity)
-  int64_t n_records;    // deterministic mode records
+  int64_t n_records;    // deterministic mode: non-empty record slots
   int64_t nnz;          // non-zero cells of the current event range
   int64_t nnz_total;    // running output size over the call (per-event mode)
   int64_t n_inline;     // recheck hits done inline because the queue was full
@@ -108,9 +108,11 @@ struct WsDev {
   Sizes* sizes;
   int64_t* pcount;     // [pcap] tasks per particle
   int64_t* poff;       // [pcap] exclusive offsets
+  uint4* pinfo;        // [pcap] per particle: entry (without layer), event, layer mask, 0
   int64_t pcap;        // particle capacity
   TaskRec* tasks;      // [task_cap]
-  float* tmu;          // [task_cap] Poisson mean of each task
+  float* tmu;          // [task_cap] Poisson mean of each task; its hit energy after the task
+                       // finish in deterministic mode (a compact copy for the fold)
   int64_t* tn;         // [task_cap] hits of each task
   int64_t* th;         // [task_cap] first hit of each task (exclusive scan of tn)
   int32_t* tlist;      // [task_cap] task indices grouped by Poisson method
@@ -119,7 +121,7 @@ struct WsDev {
   uint2* recheck;      // [recheck_cap] (task, hit in task)
   float* acc;          // [rows][acc_stride] zero-maintained accumulation rows
   int64_t task_cap, gmap_cap, recheck_cap, rows_cap;
-  uint64_t* keys;      // deterministic mode records [rec_cap]
+  uint64_t* keys;      // deterministic mode record slots, one per hit [rec_cap]
   uint64_t* keys_alt;  // ping-pong buffer [rec_cap]
   int64_t rec_cap;
 };
@@ -173,10 +175,12 @@ cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, const int64_t* n_de
 
 // fcs_tasks.cu: tasks, Poisson counts and the two scans (task and hit offsets);
 // then the records' hit offsets, the tile map and the validation dumps.
+// n_part_max: an upper bound of the range's particles (sizes the grids).
 cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_particles& parts,
                                int32_t ev_lo, int32_t ev_hi, uint32_t k0, uint32_t k1,
-                               int64_t first_event, WsDev w, ScanTmp tmp, const Launch& L);
-cudaError_t launch_task_finish(WsDev w, const fcs_debug* dbg, const Launch& L);
+                               int64_t first_event, WsDev w, ScanTmp tmp, int64_t n_part_max,
+                               const Launch& L);
+cudaError_t launch_task_finish(WsDev w, const fcs_debug* dbg, int det, int64_t n_task_max, const Launch& L);
 
 // fcs_hits.cu: what the hit kernel does with a certified hit
 enum HitMode : int {
@@ -192,6 +196,11 @@ struct HitCfg {
 cudaError_t launch_hits(const GeoDev& g, const ParamDev& p, WsDev w, int32_t ev_lo, uint32_t k0,
                         uint32_t k1, int64_t first_event, const HitCfg& hc, int key_task_bits,
                         const fcs_debug* dbg, const Launch& L);
+// One launch over the hits [h_lo, h_hi) of one task (the paper's per-task
+// kernel launches, Sec. 4), a CTA per tile.
+cudaError_t launch_hits_task(const GeoDev& g, const ParamDev& p, WsDev w, int32_t ev_lo, uint32_t k0, uint32_t k1,
+                             int64_t first_event, const HitCfg& hc, int key_task_bits, const fcs_debug* dbg,
+                             int64_t h_lo, int64_t h_hi, int32_t task, const Launch& L);
 cudaError_t launch_recheck(const GeoDev& g, const ParamDev& p, WsDev w, int32_t ev_lo, uint32_t k0,
                            uint32_t k1, int64_t first_event, int det, int key_task_bits,
                            const fcs_debug* dbg, const Launch& L);

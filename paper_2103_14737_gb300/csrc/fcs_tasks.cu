@@ -3,6 +3,8 @@
 // per task the Poisson hit count (get_number_of_hits) and the float hit
 // energy; task records in (event, particle, layer) order and the tile -> task
 // map.  Flat per-task kernels keep the Poisson draws of a warp together.
+#include <algorithm>
+
 #include "fcs_internal.cuh"
 
 namespace fcs {
@@ -261,24 +263,51 @@ __device__ __forceinline__ int32_t event_of(const int64_t* off, int32_t ev_lo, i
   return lo;
 }
 
-// Tasks of a particle: the layers with a non-zero float layer energy.
-__global__ void k_particle_count(const ParamDev p, const fcs_particles parts, int32_t ev_lo, WsDev w) {
+// Layer mask of a particle: bit l set where the float layer energy
+// fl32(E f_l) is > 0 (a task).  The fraction row is read with 16-byte loads,
+// all issued before the tests, when the layer count is a multiple of 4.
+__device__ __forceinline__ uint32_t layer_mask(const ParamDev& p, int64_t row, float E) {
+  const int NL = p.NL;
+  uint32_t mask = 0;
+  if ((NL & 3) == 0) {
+    const float4* f4 = reinterpret_cast<const float4*>(p.frac + row);
+    float4 f[kMaxLayers / 4];
+#pragma unroll
+    for (int c = 0; c < kMaxLayers / 4; ++c) f[c] = (4 * c < NL) ? __ldg(f4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < kMaxLayers / 4; ++c) {
+      mask |= (uint32_t)(__fmul_rn(E, f[c].x) > 0.0f) << (4 * c);
+      mask |= (uint32_t)(__fmul_rn(E, f[c].y) > 0.0f) << (4 * c + 1);
+      mask |= (uint32_t)(__fmul_rn(E, f[c].z) > 0.0f) << (4 * c + 2);
+      mask |= (uint32_t)(__fmul_rn(E, f[c].w) > 0.0f) << (4 * c + 3);
+    }
+  } else {
+    for (int l = 0; l < NL; ++l) mask |= (uint32_t)(__fmul_rn(E, p.frac[row + l]) > 0.0f) << l;
+  }
+  return mask;
+}
+
+// Per particle: its checks, parametrisation entry, event and layer mask; the
+// task count feeds the scan of task offsets.
+__global__ void __launch_bounds__(128) k_particle_count(const ParamDev p, const fcs_particles parts, int32_t ev_lo,
+                                                        int32_t ev_hi, WsDev w) {
   const int64_t pb = parts.event_offsets[ev_lo];
   const int64_t P = w.sizes->n_part;  // checked against the capacity and n_particles
-  const int NL = p.NL;
   for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < P;
        li += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = pb + li;
     const int32_t t = parts.type[i];
     const float E = parts.E[i], eta = parts.eta[i], phi = parts.phi[i];
-    int64_t cnt = 0;
+    uint4 info = make_uint4(0u, 0u, 0u, 0u);
     if (!particle_ok(p, t, E, eta, phi)) {
       atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_BAD_PARTICLE);
     } else {
-      const int64_t base = (int64_t)param_entry(p, t, E, eta) * NL;
-      for (int l = 0; l < NL; ++l) cnt += __fmul_rn(E, p.frac[base + l]) > 0.0f;
+      const int32_t entry = param_entry(p, t, E, eta);
+      info = make_uint4((uint32_t)entry, (uint32_t)event_of(parts.event_offsets, ev_lo, ev_hi, i),
+                        layer_mask(p, (int64_t)entry * p.NL, E), 0u);
     }
-    w.pcount[li] = cnt;
+    w.pcount[li] = __popc(info.z);
+    w.pinfo[li] = info;
   }
 }
 
@@ -286,8 +315,8 @@ __global__ void k_particle_count(const ParamDev p, const fcs_particles parts, in
 // layer energy waits in Ehit and the Poisson mean in tmu.  Each task index is
 // also filed in tlist by draw method (inversion from the front, PTRS from the
 // back), with one list reservation per warp.
-__global__ void k_task_init(const GeoDev g, const ParamDev p, const fcs_particles parts, int32_t ev_lo,
-                            int32_t ev_hi, WsDev w) {
+__global__ void __launch_bounds__(128) k_task_init(const GeoDev g, const ParamDev p, const fcs_particles parts,
+                                                   int32_t ev_lo, WsDev w) {
   const int64_t pb = parts.event_offsets[ev_lo];
   const int64_t P = w.sizes->n_part;
   const int NL = p.NL;
@@ -295,26 +324,25 @@ __global__ void k_task_init(const GeoDev g, const ParamDev p, const fcs_particle
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base_i = (int64_t)blockIdx.x * blockDim.x; base_i < P; base_i += stride) {
     const int64_t li = base_i + threadIdx.x;
-    const bool active = li < P && w.pcount[li] > 0;
-    int32_t n_inv = 0, n_ptrs = 0;
-    int64_t t_first = 0;
+    const uint4 info = li < P ? w.pinfo[li] : make_uint4(0u, 0u, 0u, 0u);
+    uint32_t inv_bits = 0;  // bit j: task j of the particle draws by inversion
     int32_t n_mine = 0;
-    if (active) {
+    int64_t t_first = 0;
+    if (info.z) {
       const int64_t i = pb + li;
-      const int32_t t = parts.type[i];
       const float E = parts.E[i], eta = parts.eta[i], phi = parts.phi[i];
-      const int32_t e = event_of(parts.event_offsets, ev_lo, ev_hi, i);
+      const int32_t e = (int32_t)info.y;
       const int32_t pin = (int32_t)(i - parts.event_offsets[e]);
-      const int64_t base = (int64_t)param_entry(p, t, E, eta) * NL;
-      int64_t to = w.poff[li];
-      t_first = to;
+      const int64_t base = (int64_t)info.x * NL;
+      t_first = w.poff[li];
       // FP32 scale factors of the (r, alpha) -> (eta, phi) map; the FP64 recheck
       // recomputes them in double exactly as the oracle does.
       const float ae = fabsf(eta);
       const float ch = coshf(eta), sh = sinhf(ae), th = tanhf(ae);
-      for (int l = 0; l < NL; ++l) {
-        const float El = __fmul_rn(E, p.frac[base + l]);
-        if (!(El > 0.0f)) continue;
+      for (uint32_t m = info.z; m; m &= m - 1) {
+        const int l = __ffs(m) - 1;
+        const float El = __fmul_rn(E, __ldg(p.frac + base + l));
+        const float mu = __fdiv_rn(El, __ldg(p.mhe + base + l));
         TaskRec r;
         r.hit_begin = 0;
         r.n = 0;
@@ -327,25 +355,23 @@ __global__ void k_task_init(const GeoDev g, const ParamDev p, const fcs_particle
           r.s_phi = 1.0f / R;
           r.s_eta = 1.0f / (R * ch);
         } else {
-          const float m = (th * sh) / R;
+          const float mm = (th * sh) / R;
           r.s_phi = sh / R;
-          r.s_eta = (eta < 0.0f) ? m : -m;
+          r.s_eta = (eta < 0.0f) ? mm : -mm;
         }
         r.particle = pin;
         r.event = e;
         r.layer = l;
-        if (to < w.task_cap) {
-          w.tasks[to] = r;
-          const float mu = __fdiv_rn(El, p.mhe[base + l]);
-          w.tmu[to] = mu;
-          if (mu < 10.0f) ++n_inv;
-          else ++n_ptrs;
-          ++n_mine;
-        }
-        to += 1;
+        const int64_t to = t_first + n_mine;
+        if (to >= w.task_cap) break;  // cannot happen: the capacity is particles x layers
+        w.tasks[to] = r;
+        w.tmu[to] = mu;
+        inv_bits |= (uint32_t)(mu < 10.0f) << n_mine;
+        ++n_mine;
       }
     }
     // warp-level reservation in both lists
+    const int32_t n_inv = __popc(inv_bits), n_ptrs = n_mine - n_inv;
     int32_t xi = n_inv, xp = n_ptrs;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -364,7 +390,7 @@ __global__ void k_task_init(const GeoDev g, const ParamDev p, const fcs_particle
     bp = __shfl_sync(0xffffffffu, bp, 31) + (unsigned long long)(xp - n_ptrs);
     for (int32_t j = 0; j < n_mine; ++j) {
       const int64_t t = t_first + j;
-      if (w.tmu[t] < 10.0f) w.tlist[bi++] = (int32_t)t;
+      if ((inv_bits >> j) & 1u) w.tlist[bi++] = (int32_t)t;
       else w.tlist[w.task_cap - 1 - (int64_t)(bp++)] = (int32_t)t;
     }
   }
@@ -419,7 +445,7 @@ __global__ void __launch_bounds__(128) k_task_poisson64(WsDev w, uint32_t k0, ui
 
 // One thread per task: hit offsets, counts and hit energy; the tile map
 // (granule -> task containing its first hit); validation dumps.
-__global__ void k_task_finish(WsDev w, fcs_debug dbg, int has_dbg) {
+__global__ void k_task_finish(WsDev w, fcs_debug dbg, int has_dbg, int det) {
   const int64_t T = min(w.sizes->n_tasks, w.task_cap);
   const int64_t H = w.sizes->n_hits;
   const bool map_ok = H <= w.gmap_cap * (int64_t)kGranule;
@@ -433,6 +459,7 @@ __global__ void k_task_finish(WsDev w, fcs_debug dbg, int has_dbg) {
     r.hit_begin = b;
     r.n = n;
     r.Ehit = Ehit;
+    if (det) w.tmu[t] = Ehit;
     if (map_ok)
       for (int64_t gi = (b + kGranule - 1) / kGranule; gi * kGranule < b + n; ++gi) w.gmap[gi] = (int32_t)t;
     if (has_dbg) {
@@ -448,25 +475,34 @@ __global__ void k_task_finish(WsDev w, fcs_debug dbg, int has_dbg) {
   }
 }
 
+// Blocks of 128 threads for n items, at most 16 per SM (a full SM's worth).
+int grid_for(int64_t n, const Launch& L) {
+  const int64_t b = (std::max<int64_t>(n, 1) + 127) / 128;
+  return (int)std::min<int64_t>(b, (int64_t)L.num_sms * 16);
+}
+
 }  // namespace
 
 cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_particles& parts, int32_t ev_lo,
                                int32_t ev_hi, uint32_t k0, uint32_t k1, int64_t first_event, WsDev w, ScanTmp tmp,
-                               const Launch& L) {
-  k_particle_count<<<L.num_sms * 4, 128, 0, L.s>>>(p, parts, ev_lo, w);
+                               int64_t n_part_max, const Launch& L) {
+  // one thread per particle / task where the grid allows (these kernels wait
+  // on dependent loads: more threads in flight, not fewer, hide them)
+  const int gp = grid_for(n_part_max, L), gt = grid_for(n_part_max * p.NL, L);
+  k_particle_count<<<gp, 128, 0, L.s>>>(p, parts, ev_lo, ev_hi, w);
   cudaError_t e = launch_scan_i64(w.pcount, w.poff, &w.sizes->n_part, 0, &w.sizes->n_tasks, 0, tmp, L.s);
   if (e != cudaSuccess) return e;
-  k_task_init<<<L.num_sms * 4, 128, 0, L.s>>>(g, p, parts, ev_lo, ev_hi, w);
-  k_task_poisson<<<L.num_sms * 8, 128, 0, L.s>>>(w, k0, k1, (uint32_t)first_event, p.lfact, p.n_lfact);
+  k_task_init<<<gp, 128, 0, L.s>>>(g, p, parts, ev_lo, w);
+  k_task_poisson<<<gt, 128, 0, L.s>>>(w, k0, k1, (uint32_t)first_event, p.lfact, p.n_lfact);
   k_task_poisson64<<<L.num_sms * 2, 128, 0, L.s>>>(w, k0, k1, (uint32_t)first_event);
   // the scan counts the tasks actually written (n_tasks <= task_cap by construction)
   return launch_scan_i64(w.tn, w.th, &w.sizes->n_tasks, 0, &w.sizes->n_hits, 0, tmp, L.s);
 }
 
-cudaError_t launch_task_finish(WsDev w, const fcs_debug* dbg, const Launch& L) {
+cudaError_t launch_task_finish(WsDev w, const fcs_debug* dbg, int det, int64_t n_task_max, const Launch& L) {
   fcs_debug d{};
   if (dbg) d = *dbg;
-  k_task_finish<<<L.num_sms * 8, 128, 0, L.s>>>(w, d, dbg ? 1 : 0);
+  k_task_finish<<<grid_for(n_task_max, L), 128, 0, L.s>>>(w, d, dbg ? 1 : 0, det);
   return cudaGetLastError();
 }
 

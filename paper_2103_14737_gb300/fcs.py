@@ -48,7 +48,7 @@ class fcs_particles(C.Structure):
 class fcs_config(C.Structure):
     _fields_ = [("mode", C.c_int32), ("batched", C.c_int32), ("hits_per_thread", C.c_int32),
                 ("block", C.c_int32), ("sync", C.c_int32), ("use_graph", C.c_int32),
-                ("timing", C.c_int32), ("reserved", C.c_int32)]
+                ("timing", C.c_int32), ("wave_events", C.c_int32)]
 
 
 class fcs_stats(C.Structure):
@@ -214,10 +214,11 @@ def fcs_workspace_free(ws):
     load_library().fcs_workspace_free(ws)
 
 
-def make_config(mode=MODE_ATOMIC, batched=1, hits_per_thread=0, block=0, sync=1, use_graph=0, timing=0):
+def make_config(mode=MODE_ATOMIC, batched=1, hits_per_thread=0, block=0, sync=1, use_graph=0, timing=0,
+                wave_events=0):
     c = fcs_config()
-    c.mode, c.batched, c.hits_per_thread, c.block, c.sync, c.use_graph, c.timing = \
-        mode, batched, hits_per_thread, block, sync, use_graph, timing
+    c.mode, c.batched, c.hits_per_thread, c.block, c.sync, c.use_graph, c.timing, c.wave_events = \
+        mode, batched, hits_per_thread, block, sync, use_graph, timing, wave_events
     return c
 
 
@@ -272,11 +273,11 @@ AUTOTUNE_HPT = (1, 2, 4, 8)
 
 
 def fcs_autotune(geo, prm, ws, particles: fcs_particles, n_particles, n_events, seed, first_event, reps=3,
-                 mode=MODE_ATOMIC):
+                 mode=MODE_ATOMIC, wave_events=0):
     """Times every (block, hits_per_thread) shape of the hit kernel on this
     workload; returns (block, hits_per_thread, {(block, hpt): median ms})."""
     L = load_library()
-    cfg = make_config(mode=mode)
+    cfg = make_config(mode=mode, wave_events=wave_events)
     ms = (C.c_float * 12)()
     _check(L.fcs_autotune(geo, prm, ws, C.byref(particles), int(n_particles), int(n_events),
                           int(seed) & 0xFFFFFFFFFFFFFFFF, int(first_event), int(reps), C.byref(cfg), ms, _stream()))
@@ -357,11 +358,11 @@ class Simulator:
         except Exception:
             pass
 
-    def autotune(self, dparts, seed, first_event=0, reps=3, mode=MODE_ATOMIC):
+    def autotune(self, dparts, seed, first_event=0, reps=3, mode=MODE_ATOMIC, wave_events=0):
         parts = fcs_particles(dparts["type"].data_ptr(), dparts["E"].data_ptr(), dparts["eta"].data_ptr(),
                               dparts["phi"].data_ptr(), dparts["event_offsets"].data_ptr())
         return fcs_autotune(self.geo, self.prm, self.ws, parts, dparts["E"].numel(),
-                            dparts["event_offsets"].numel() - 1, seed, first_event, reps, mode)
+                            dparts["event_offsets"].numel() - 1, seed, first_event, reps, mode, wave_events)
 
     @staticmethod
     def to_device(parts, device="cuda"):
@@ -375,7 +376,7 @@ class Simulator:
 
     def simulate(self, dparts, seed, first_event=0, mode=MODE_ATOMIC, batched=1, hits_per_thread=0, block=0,
                  sync=1, use_graph=0, dense=False, capacity=None, debug_tasks=0, debug_hits=0, outputs=None,
-                 check=True, timing=0):
+                 check=True, timing=0, wave_events=0):
         """Runs one call.  dparts: dict of device tensors (see to_device).
         Returns a dict with cell_ids, cell_E, event_offsets (device tensors),
         cells (dense, if requested), stats, status and debug dumps."""
@@ -408,7 +409,7 @@ class Simulator:
                 dbg.hit_cell = res["hit_cell"].data_ptr()
                 dbg.hit_bin = res["hit_bin"].data_ptr()
                 dbg.hit_capacity = debug_hits
-        cfg = make_config(mode, batched, hits_per_thread, block, sync, use_graph, timing)
+        cfg = make_config(mode, batched, hits_per_thread, block, sync, use_graph, timing, wave_events)
         rc, st = fcs_simulate_events(self.geo, self.prm, self.ws, parts, n_particles, n_events, seed, first_event,
                                      cfg, outputs.get("cells"), outputs.get("cell_ids"), outputs.get("cell_E"),
                                      outputs.get("event_offsets"),
@@ -427,7 +428,7 @@ class Simulator:
         fcs_update_params(self.prm, frac, mean_hit_E, shape_w)
 
     def backward(self, dparts, seed, dL_dcells, first_event=0, d_frac=None, d_shape_w=None, batched=1,
-                 hits_per_thread=0, block=0, sync=1, check=True):
+                 hits_per_thread=0, block=0, sync=1, check=True, wave_events=0):
         """Gradients of a loss with dL/dE_cell = dL_dcells ([n_events][n_cells]
         float32 on the device) with respect to the layer fractions and shape
         weights; accumulated into d_frac / d_shape_w (flat float32 device
@@ -445,7 +446,7 @@ class Simulator:
             raise ValueError("dL_dcells must be float32 [n_events][n_cells]")
         parts = fcs_particles(dparts["type"].data_ptr(), dparts["E"].data_ptr(), dparts["eta"].data_ptr(),
                               dparts["phi"].data_ptr(), dparts["event_offsets"].data_ptr())
-        cfg = make_config(MODE_ATOMIC, batched, hits_per_thread, block, sync, 0, 0)
+        cfg = make_config(MODE_ATOMIC, batched, hits_per_thread, block, sync, 0, 0, wave_events)
         rc, st = fcs_simulate_backward(self.geo, self.prm, self.ws, parts, n_particles, n_events, seed, first_event,
                                        cfg, g, d_frac, d_shape_w, check=check)
         return dict(d_frac=d_frac, d_shape_w=d_shape_w, status=rc, stats=st.as_dict(), _keep=(parts, cfg, g))

@@ -113,6 +113,41 @@ def test_launch_shapes(sim, ogeo, oprm, block, hpt):
     assert np.array_equal(got2["cells"].cpu().numpy().view(np.uint32), ref.cells_canon.view(np.uint32))
 
 
+@pytest.mark.parametrize("mode", [fcs.MODE_ATOMIC, fcs.MODE_DETERMINISTIC])
+@pytest.mark.parametrize("wave", [1, 2, 3])
+def test_event_waves(sim, ogeo, oprm, mode, wave):
+    """Launch sequences of `wave` events (a ragged last wave): the same tasks,
+    cells and compacted output as the oracle."""
+    parts = synth.pileup(seed=14, n_events=5, mu_pu=8)
+    d = sim.to_device(parts)
+    ref = O.simulate(ogeo, oprm, parts, seed=9, first_event=3)
+    for timing in (0, 1):
+        got = sim.simulate(d, 9, first_event=3, mode=mode, wave_events=wave, dense=True, debug_tasks=ref.n_tasks,
+                           timing=timing)
+        check_tasks_hits(ref, got)
+        cells = got["cells"].cpu().numpy()
+        if mode == fcs.MODE_DETERMINISTIC:
+            assert np.array_equal(cells.view(np.uint32), ref.cells_canon.view(np.uint32))
+            check_compacted(got, cells.astype(np.float64), 5)
+        else:
+            check_cells_atomic(ref, got, 5)
+    t = fcs.fcs_workspace_timings(sim.ws)
+    assert t["total"] > 0
+
+
+@pytest.mark.parametrize("block,hpt", [(128, 1), (256, 4)])
+def test_per_task_launches(sim, ogeo, oprm, block, hpt):
+    """One hit-kernel launch per task (the paper's non-grouped GPU mode): every
+    hit once, the same cells as the oracle."""
+    parts = synth.replicate(synth.ttbar_like(2, 1, n=40), 2)
+    ref, got = run_both(sim, ogeo, oprm, parts, seed=4, batched=2, hpt=hpt, block=block)
+    check_tasks_hits(ref, got)
+    check_cells_atomic(ref, got, 2)
+    got = sim.simulate(sim.to_device(parts), 4, mode=fcs.MODE_DETERMINISTIC, batched=2, hits_per_thread=hpt,
+                       block=block, dense=True)
+    assert np.array_equal(got["cells"].cpu().numpy().view(np.uint32), ref.cells_canon.view(np.uint32))
+
+
 def test_poisson_counts_wide_mu(sim, ogeo, oprm):
     """Hit counts over mu from ~1e-2 to ~1e5 (inversion, FP32-certified PTRS,
     the FP64-only large-mu path) equal the oracle's draw for draw."""
