@@ -513,7 +513,8 @@ def main():
                            "events_per_step": n_ev, "particles_per_step": parts.n,
                            "hits_per_step": H, "tasks_per_step": ref["stats"]["n_tasks"],
                            "nonzero_cells_per_step": ref["stats"]["n_nonzero"],
-                           "recheck_hits_per_step": ref["stats"]["n_recheck"], "mode": "atomic",
+                           "recheck_hits_per_step": ref["stats"]["n_recheck"],
+                           "poisson_fp64_per_step": ref["stats"]["n_poisson_fp64"], "mode": "atomic",
                            "hit_kernel_shape": f"{args.block or 256}x{args.hpt or 4}",
                            "launch": "batched, CUDA graph", "l2": "flushed between steps (256 MB write)",
                            "parallelism": f"replicas x{world} (events sharded, no collective)"},

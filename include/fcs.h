@@ -237,8 +237,9 @@ void fcs_workspace_free(fcs_workspace* ws);
  *     holds the size needed and the call returns FCS_E_RANGE (sync) or sets
  *     FCS_FLAG_OUT_CAPACITY (async).
  * dbg: optional validation dumps (NULL in production).
- * Errors: FCS_E_ARG for bad arguments, FCS_E_RANGE as above or when a
- * sync == 0 call needs more workspace than reserved, FCS_E_DEVICE_CHECK when
+ * Errors: FCS_E_ARG for bad arguments, FCS_E_RANGE as above, when a
+ * sync == 0 call needs more workspace than reserved or for 2^24 or more
+ * events in one call, FCS_E_DEVICE_CHECK when
  * a particle fails its checks (its tasks are skipped), FCS_E_CUDA / OOM. */
 int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
                         const fcs_particles* particles, int64_t n_particles, int32_t n_events,

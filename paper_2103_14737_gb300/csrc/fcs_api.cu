@@ -143,7 +143,6 @@ struct fcs_workspace {
   float* tmu = nullptr;
   int64_t* tn = nullptr;
   int64_t* th = nullptr;
-  int32_t* tlist = nullptr;
   int32_t* pdefer = nullptr;
   int64_t task_cap = 0, tmu_cap = 0, tn_cap = 0, th_cap = 0, tl_cap = 0, pd_cap = 0;
   int32_t* gmap = nullptr;
@@ -161,9 +160,8 @@ struct fcs_workspace {
   uint64_t* keys = nullptr;
   uint64_t* keys_alt = nullptr;
   int64_t k_cap = 0, ka_cap = 0, rec_cap = 0;
-  int64_t* head_flags = nullptr;
-  int64_t* head_off = nullptr;
-  int64_t hf_cap = 0, ho_cap = 0;
+  int64_t* cell_off = nullptr;  // deterministic mode: each cell's first record
+  int64_t co_cells_cap = 0;
   // gradient scores [n_entries][128] (FP64) and their entry flags; zero
   // between backward calls (the finalize kernel clears what it reads)
   double* grad_acc = nullptr;
@@ -173,8 +171,8 @@ struct fcs_workspace {
   // staging for the host-buffer entry point
   void* stage = nullptr;
   int64_t stage_cap = 0;
-  // pinned copy of a range's task records (per-task launches)
-  TaskRec* h_tasks = nullptr;
+  // pinned copy of a range's first hits and hit counts (per-task launches)
+  int64_t* h_tasks = nullptr;
   int64_t h_tasks_cap = 0;
   // CUDA graph cache (use_graph)
   cudaGraphExec_t graph = nullptr;
@@ -188,8 +186,8 @@ struct fcs_workspace {
   ~fcs_workspace() {
     if (graph) cudaGraphExecDestroy(graph);
     for (cudaEvent_t e : tev) cudaEventDestroy(e);
-    void* ps[] = {d_sizes, pcount, poff, pinfo, tasks, tmu, tn, th, tlist, pdefer, gmap, recheck, acc, chunk_counts, chunk_offsets,
-                  block_sums, keys, keys_alt, head_flags, head_off, stage, grad_acc, grad_touched};
+    void* ps[] = {d_sizes, pcount, poff, pinfo, tasks, tmu, tn, th, pdefer, gmap, recheck, acc, chunk_counts, chunk_offsets,
+                  block_sums, keys, keys_alt, cell_off, stage, grad_acc, grad_touched};
     for (void* p : ps)
       if (p) cudaFree(p);
     if (h_sizes) cudaFreeHost(h_sizes);
@@ -207,7 +205,6 @@ struct fcs_workspace {
     w.tmu = tmu;
     w.tn = tn;
     w.th = th;
-    w.tlist = tlist;
     w.pdefer = pdefer;
     w.gmap = gmap;
     w.recheck = recheck;
@@ -248,7 +245,6 @@ int ws_reserve_static(fcs_workspace* ws, const fcs_geo* geo, int64_t P, int32_t 
   FCS_TRY(grow(&ws->tmu, &ws->tmu_cap, Pc * NL));
   FCS_TRY(grow(&ws->tn, &ws->tn_cap, Pc * NL));
   FCS_TRY(grow(&ws->th, &ws->th_cap, Pc * NL));
-  FCS_TRY(grow(&ws->tlist, &ws->tl_cap, Pc * NL));
   FCS_TRY(grow(&ws->pdefer, &ws->pd_cap, Pc * NL));
   const int32_t stride = geo->d.acc_stride;
   if (stride != ws->acc_stride || rows > ws->rows_cap || !ws->acc) {
@@ -265,11 +261,8 @@ int ws_reserve_static(fcs_workspace* ws, const fcs_geo* geo, int64_t P, int32_t 
   FCS_TRY(grow(&ws->chunk_counts, &ws->cc_cap, chunks));
   FCS_TRY(grow(&ws->chunk_offsets, &ws->co_cap, chunks));
   FCS_TRY(grow(&ws->block_sums, &ws->bs_cap, kScanBlocks + 1));
-  if (mode == FCS_MODE_DETERMINISTIC) {
-    const int64_t he = det_hist_entries(ws->num_sms);
-    FCS_TRY(grow(&ws->head_flags, &ws->hf_cap, std::max<int64_t>(he, ws->rec_cap)));
-    FCS_TRY(grow(&ws->head_off, &ws->ho_cap, std::max<int64_t>(1, ws->rec_cap)));
-  }
+  if (mode == FCS_MODE_DETERMINISTIC)
+    FCS_TRY(grow(&ws->cell_off, &ws->co_cells_cap, (int64_t)std::max(rows, 1) * stride));
   return FCS_OK;
 }
 
@@ -290,9 +283,6 @@ int ws_reserve_hits(fcs_workspace* ws, int64_t H, int mode) {
       ws->ka_cap = c2;
       ws->rec_cap = cap;
     }
-    const int64_t he = det_hist_entries(ws->num_sms);
-    FCS_TRY(grow(&ws->head_flags, &ws->hf_cap, std::max<int64_t>(he, ws->rec_cap)));
-    FCS_TRY(grow(&ws->head_off, &ws->ho_cap, ws->rec_cap));
   }
   return FCS_OK;
 }
@@ -315,8 +305,6 @@ __global__ void k_range_begin(Sizes* s, const int64_t* __restrict__ off, int32_t
   s->n_recheck = 0;
   s->n_records = 0;
   s->n_rec_used = 0;
-  s->n_inv = 0;
-  s->n_ptrs = 0;
   s->n_pdefer = 0;
   s->queue = 0;
 }
@@ -420,24 +408,25 @@ int enqueue_range(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, int32_t range
   FCS_CUDA(launch_task_finish(w, a.dbg, det, a.n_particles * a.geo->d.n_layers, L));
   if (tev) FCS_CUDA(record_stage(tev[1], a.s));
   if (a.cfg.batched == 2) {
-    // per-task launches: read the range's task records, then one hit-kernel
-    // launch over each task's hits
+    // per-task launches: read the range's first hits and hit counts, then
+    // one hit-kernel launch over each task's hits
     const int64_t nt = ws->h_sizes->n_tasks;
-    if (nt > ws->h_tasks_cap) {
+    if (2 * nt > ws->h_tasks_cap) {
       if (ws->h_tasks) cudaFreeHost(ws->h_tasks);
       ws->h_tasks = nullptr;
       ws->h_tasks_cap = 0;
-      FCS_CUDA(cudaMallocHost((void**)&ws->h_tasks, (size_t)nt * sizeof(TaskRec)));
-      ws->h_tasks_cap = nt;
+      FCS_CUDA(cudaMallocHost((void**)&ws->h_tasks, (size_t)(2 * nt) * sizeof(int64_t)));
+      ws->h_tasks_cap = 2 * nt;
     }
     if (nt > 0) {
-      FCS_CUDA(cudaMemcpyAsync(ws->h_tasks, ws->tasks, (size_t)nt * sizeof(TaskRec), cudaMemcpyDeviceToHost, a.s));
+      FCS_CUDA(cudaMemcpyAsync(ws->h_tasks, ws->th, (size_t)nt * sizeof(int64_t), cudaMemcpyDeviceToHost, a.s));
+      FCS_CUDA(cudaMemcpyAsync(ws->h_tasks + nt, ws->tn, (size_t)nt * sizeof(int64_t), cudaMemcpyDeviceToHost, a.s));
       FCS_CUDA(cudaStreamSynchronize(a.s));
     }
     for (int64_t t = 0; t < nt; ++t) {
-      const TaskRec& r = ws->h_tasks[t];
-      FCS_CUDA(launch_hits_task(a.geo->d, a.prm->d, w, ev_lo, k0, k1, a.first_event, hc, key_task_bits, a.dbg,
-                                r.hit_begin, r.hit_begin + r.n, (int32_t)t, L));
+      const int64_t hb = ws->h_tasks[t];
+      FCS_CUDA(launch_hits_task(a.geo->d, a.prm->d, w, ev_lo, k0, k1, a.first_event, hc, key_task_bits, a.dbg, hb,
+                                hb + ws->h_tasks[nt + t], (int32_t)t, L));
     }
   } else {
     FCS_CUDA(launch_hits(a.geo->d, a.prm->d, w, ev_lo, k0, k1, a.first_event, hc, key_task_bits, a.dbg, L));
@@ -445,16 +434,9 @@ int enqueue_range(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, int32_t range
   if (tev) FCS_CUDA(record_stage(tev[2], a.s));
   FCS_CUDA(launch_recheck(a.geo->d, a.prm->d, w, ev_lo, k0, k1, a.first_event, det, key_task_bits, a.dbg, L));
   if (tev) FCS_CUDA(record_stage(tev[3], a.s));
-  if (!det) {
-    FCS_CUDA(launch_compact(a.geo->d, w, rows, ev_lo, ws->chunk_counts, ws->chunk_offsets, tmp, a.cells_out,
-                            a.cell_ids, a.cell_E, a.event_offsets_out, a.n_events, a.capacity, L));
-  } else {
-    const int cellbits = bits_for((int64_t)rows * a.geo->d.n_cells);
-    const int total = kRecordCountBits + key_task_bits + cellbits;
-    FCS_CUDA(launch_det_reduce(a.geo->d, w, rows, ev_lo, key_task_bits, total, nullptr, ws->hf_cap,
-                               ws->head_flags, ws->head_off, tmp, a.cells_out, a.cell_ids, a.cell_E,
-                               a.event_offsets_out, a.n_events, a.capacity, L));
-  }
+  if (det) FCS_CUDA(launch_det_reduce(a.geo->d, w, rows, key_task_bits, ws->cell_off, tmp, L));
+  FCS_CUDA(launch_compact(a.geo->d, w, rows, ev_lo, ws->chunk_counts, ws->chunk_offsets, tmp, a.cells_out,
+                          a.cell_ids, a.cell_E, a.event_offsets_out, a.n_events, a.capacity, L));
   if (tev) FCS_CUDA(record_stage(tev[4], a.s));
   k_range_end<<<1, 1, 0, a.s>>>(ws->d_sizes);
   return FCS_OK;
@@ -486,8 +468,6 @@ int ensure_timing_events(fcs_workspace* ws, int ranges) {
 int enqueue_call(const CallArgs& a, bool sync_size, const HitCfg& hc, int key_task_bits) {
   fcs_workspace* ws = a.ws;
   k_call_begin<<<1, 1, 0, a.s>>>(ws->d_sizes);
-  if (a.cells_out && a.cfg.mode == FCS_MODE_DETERMINISTIC)
-    FCS_CUDA(cudaMemsetAsync(a.cells_out, 0, (size_t)a.n_events * a.geo->d.n_cells * sizeof(float), a.s));
   const int32_t W = range_events(a.cfg, a.n_events);
   for (int32_t lo = 0, r = 0; lo < a.n_events; lo += W, ++r)
     FCS_TRY(enqueue_range(a, lo, std::min(a.n_events, lo + W), r, sync_size, hc, key_task_bits));
@@ -845,6 +825,7 @@ int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace
   if (!geo || !prm || !ws) return set_err(FCS_E_ARG, "geo, params and workspace are required");
   FCS_TRY(check_particles(particles, n_particles));
   if (n_particles < 0 || n_events < 0 || capacity < 0) return set_err(FCS_E_ARG, "negative size");
+  if (n_events >= kMaxEventsPerCall) return set_err(FCS_E_RANGE, "at most 2^24 - 1 events per call");
   if (prm->d.NL != geo->d.n_layers) return set_err(FCS_E_ARG, "parametrisation and geometry disagree on layers");
   if ((cell_ids == nullptr) != (cell_E == nullptr)) return set_err(FCS_E_ARG, "cell_ids and cell_E go together");
   fcs_config cfg{};
@@ -869,7 +850,7 @@ int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace
   FCS_TRY(ws_reserve_static(ws, geo, n_particles, rows, cfg.mode));
   const int key_task_bits = bits_for(std::max<int64_t>(n_particles, 1) * geo->d.n_layers);
   if (cfg.mode == FCS_MODE_DETERMINISTIC &&
-      kRecordCountBits + key_task_bits + bits_for((int64_t)rows * geo->d.n_cells) > 63)
+      kRecordCountBits + key_task_bits + bits_for((int64_t)rows * geo->d.acc_stride) > 63)
     return set_err(FCS_E_RANGE, "deterministic mode: (cell, task) keys exceed 63 bits; use smaller waves or split the batch");
   CallArgs a{geo, prm, ws, *particles, n_particles, n_events, seed, first_event, cfg, cells_out,
              cell_ids, cell_E, event_offsets_out, capacity, dbg, s};
@@ -906,7 +887,7 @@ int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace
     put(&ws->recheck, sizeof(void*));
     put(&ws->acc, sizeof(void*));
     put(&ws->keys, sizeof(void*));
-    put(&ws->head_flags, sizeof(void*));
+    put(&ws->cell_off, sizeof(void*));
     if (!ws->graph || key != ws->graph_key) {
       if (ws->graph) {
         cudaGraphExecDestroy(ws->graph);
@@ -1071,6 +1052,7 @@ int fcs_simulate_backward(const fcs_geo* geo, const fcs_params* prm, fcs_workspa
   if (!geo || !prm || !ws) return set_err(FCS_E_ARG, "geo, params and workspace are required");
   FCS_TRY(check_particles(particles, n_particles));
   if (n_particles < 0 || n_events < 0) return set_err(FCS_E_ARG, "negative size");
+  if (n_events >= kMaxEventsPerCall) return set_err(FCS_E_RANGE, "at most 2^24 - 1 events per call");
   if (prm->d.NL != geo->d.n_layers) return set_err(FCS_E_ARG, "parametrisation and geometry disagree on layers");
   if (n_events > 0 && !dL_dcells) return set_err(FCS_E_ARG, "dL_dcells is required");
   fcs_config cfg{};
@@ -1195,6 +1177,7 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   if (!geo || !prm) return set_err(FCS_E_ARG, "geo and params are required");
   FCS_TRY(check_particles(particles, n_particles));
   if (n_particles < 0 || n_events < 1 || capacity < 0) return set_err(FCS_E_ARG, "bad size");
+  if (n_events >= kMaxEventsPerCall) return set_err(FCS_E_RANGE, "at most 2^24 - 1 events per call");
   if (!event_offsets_out) return set_err(FCS_E_ARG, "event_offsets_out is required");
   if ((cell_ids == nullptr) != (cell_E == nullptr)) return set_err(FCS_E_ARG, "cell_ids and cell_E go together");
   if (prm->d.NL != geo->d.n_layers) return set_err(FCS_E_ARG, "parametrisation and geometry disagree on layers");
@@ -1223,7 +1206,6 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   w.tmu = c.take<float>(P * NL);
   w.tn = c.take<int64_t>(P * NL);
   w.th = c.take<int64_t>(P * NL);
-  w.tlist = c.take<int32_t>(P * NL);
   w.pdefer = c.take<int32_t>(P * NL);
   w.task_cap = P * NL;
   w.acc = c.take<float>((int64_t)n_events * geo->d.acc_stride);
@@ -1235,7 +1217,7 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   w.block_sums = c.take<int64_t>(kScanBlocks + 1);
   w.recheck = c.take<uint2>(recheck_cap);
   w.recheck_cap = recheck_cap;
-  const bool fits = w.d_sizes && w.pcount && w.poff && w.pinfo && w.tasks && w.tmu && w.tn && w.th && w.tlist && w.pdefer &&
+  const bool fits = w.d_sizes && w.pcount && w.poff && w.pinfo && w.tasks && w.tmu && w.tn && w.th && w.pdefer &&
                     w.acc &&
                     w.chunk_counts &&
                     w.chunk_offsets && w.block_sums && w.recheck && c.cap - c.off >= 4096;
@@ -1253,7 +1235,6 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
     w.tmu = nullptr;
     w.tn = nullptr;
     w.th = nullptr;
-    w.tlist = nullptr;
     w.pdefer = nullptr;
     w.acc = nullptr;
     w.chunk_counts = nullptr;

@@ -71,22 +71,41 @@ __global__ void __launch_bounds__(kCThreads) k_compact_write(
   __syncthreads();
   int pre = 0;
   for (int w = 0; w < warp; ++w) pre += s_w[w];
-  int64_t pos = offsets[(int64_t)row * cpr + chunk] + pre + x - cnt;
+  // the block's pairs go through shared memory so that the output is written
+  // with consecutive threads on consecutive positions
+  __shared__ int32_t s_id[kChunk];
+  __shared__ float s_E[kChunk];
+  int lpos = pre + x - cnt;
 #pragma unroll
   for (int k = 0; k < kCItems; ++k) {
     if (mask & (1u << k)) {
-      if (pos < capacity) {
-        if (cell_ids) cell_ids[pos] = (int32_t)(c0 + k);
-        if (cell_E) cell_E[pos] = v[k];
-      }
-      ++pos;
+      s_id[lpos] = (int32_t)(c0 + k);
+      s_E[lpos] = v[k];
+      ++lpos;
+    }
+  }
+  __shared__ int s_total;
+  if (threadIdx.x == kCThreads - 1) s_total = lpos;  // the last thread ends the block's run
+  __syncthreads();
+  const int total = s_total;
+  const int64_t base = offsets[(int64_t)row * cpr + chunk];
+  for (int j = threadIdx.x; j < total; j += kCThreads) {
+    const int64_t pos = base + j;
+    if (pos < capacity) {
+      if (cell_ids) cell_ids[pos] = s_id[j];
+      if (cell_E) cell_E[pos] = s_E[j];
     }
   }
   if (cells_out && c0 < n_cells) {
     float* dst = cells_out + (int64_t)(ev_lo + row) * n_cells + c0;
+    if (c0 + kCItems <= n_cells && (n_cells & 3) == 0) {
+      reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+      reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+    } else {
 #pragma unroll
-    for (int k = 0; k < kCItems; ++k)
-      if (c0 + k < n_cells) dst[k] = v[k];
+      for (int k = 0; k < kCItems; ++k)
+        if (c0 + k < n_cells) dst[k] = v[k];
+    }
   }
   if (chunk == 0 && threadIdx.x == 0 && event_offsets_out)
     event_offsets_out[ev_lo + row] = offsets[(int64_t)row * cpr];

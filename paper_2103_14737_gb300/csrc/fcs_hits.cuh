@@ -193,6 +193,29 @@ struct TileTask {
 };
 static_assert(sizeof(TileTask) == 48, "TileTask layout");
 
+// The tile's view of task t: hit offset relative to the tile start h0, the
+// float hit energy fl32(El / n), the Philox counter words and the accumulation
+// row.
+__device__ __forceinline__ TileTask make_tile_task(const HitSmemTables& tb, const WsDev& w, int64_t t, int64_t h0,
+                                                   uint32_t first_event_lo, int32_t ev_lo, uint32_t row_stride) {
+  const TaskRec r = w.tasks[t];
+  const int32_t layer = r.layer(), event = r.event();
+  TileTask q;
+  q.rel = (int32_t)(w.th[t] - h0);
+  q.entry = r.entry;
+  q.Ehit = __fdiv_rn(r.El, (float)w.tn[t]);
+  q.eta_c = r.eta_c;
+  q.phi_c = r.phi_c;
+  q.s_eta = r.s_eta;
+  q.s_phi = r.s_phi;
+  q.ctr_y = (uint32_t)layer | (kPurposeHit << 16);
+  q.ctr_z = (uint32_t)r.particle;
+  q.ctr_w = first_event_lo + (uint32_t)event;
+  q.row_off = (uint32_t)(event - ev_lo) * row_stride;
+  q.lay = task_lay(tb, layer, r.eta_c, r.s_eta);
+  return q;
+}
+
 template <typename TT>
 __device__ __forceinline__ FastHit fast_cell(const HitSmemTables& tb, const TT& T, uint4 x, int bin) {
   const int ir = bin >> 3, ia = bin & 7;
@@ -244,15 +267,15 @@ __device__ __forceinline__ FastHit fast_cell(const HitSmemTables& tb, const TT& 
 
 // ---- warp-level deposit / record emission -----------------------------------
 // Deterministic mode: every hit of the range owns the record slot of its hit
-// index, so the record array is in hit order, which is task order.  The
-// first lane of each group of equal (cell, task) keys in the warp writes the
-// group's record (count - 1 in the low bits) to its own slot; the other valid
-// lanes write the empty record (all ones, sorted last).  A stable sort by cell
-// then gives (cell, task) order.  Uncertain hits leave their slot empty for the
-// recheck kernel to fill.  Returns the warp's number of records (the caller
-// counts them per CTA: one counter hit by every warp would serialise).
-__device__ __forceinline__ unsigned emit_slots(bool valid, bool ok, unsigned long long gkey, int64_t slot,
-                                               const WsDev& w) {
+// index.  The first lane of each group of equal (cell, task) keys in the warp
+// writes the group's record (count - 1 in the low bits) to its own slot and
+// counts it in the cell's uint32 counter (the accumulation row); the other
+// valid lanes write the empty record (all ones).  Uncertain hits leave their
+// slot empty for the recheck kernel to fill.  Returns the warp's number of
+// records (the caller counts them per CTA: one counter hit by every warp would
+// serialise).
+__device__ __forceinline__ unsigned emit_slots(bool valid, bool ok, unsigned long long gkey, uint32_t cell,
+                                               int64_t slot, const WsDev& w) {
   const int lane = threadIdx.x & 31;
   const unsigned m = __ballot_sync(0xffffffffu, ok);
   unsigned peers = 0;
@@ -260,10 +283,12 @@ __device__ __forceinline__ unsigned emit_slots(bool valid, bool ok, unsigned lon
   const bool lead = ok && (lane == __ffs(peers) - 1);
   const unsigned lm = __ballot_sync(0xffffffffu, lead);
   if (valid) {
-    if (slot < w.rec_cap)
+    if (slot < w.rec_cap) {
       w.keys[slot] = lead ? ((gkey << kRecordCountBits) | (unsigned long long)(__popc(peers) - 1)) : ~0ull;
-    else
+      if (lead) atomicAdd(reinterpret_cast<uint32_t*>(w.acc) + cell, 1u);
+    } else {
       atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_HIT_CAPACITY);
+    }
   }
   return (unsigned)__popc(lm);
 }
@@ -298,11 +323,15 @@ __device__ __forceinline__ void deposit_single(const HitKParams& kp, int32_t eve
     atomicAdd(kp.grad_acc + ((int64_t)entry << 7) + bin, (double)v);
     kp.grad_touched[entry] = 1;
   } else {
-    const unsigned long long gkey =
-        ((unsigned long long)(row * kp.g.n_cells + cell) << kp.key_task_bits) | (unsigned long long)task_rel;
-    atomicAdd((unsigned long long*)&kp.w.sizes->n_records, 1ull);
-    if (slot < kp.w.rec_cap) kp.w.keys[slot] = gkey << kRecordCountBits;
-    else atomicOr(&kp.w.sizes->flags, (uint32_t)FCS_FLAG_HIT_CAPACITY);
+    const uint32_t c = (uint32_t)(row * kp.g.acc_stride + cell);
+    const unsigned long long gkey = ((unsigned long long)c << kp.key_task_bits) | (unsigned long long)task_rel;
+    if (slot < kp.w.rec_cap) {
+      atomicAdd((unsigned long long*)&kp.w.sizes->n_records, 1ull);
+      kp.w.keys[slot] = gkey << kRecordCountBits;
+      atomicAdd(reinterpret_cast<uint32_t*>(kp.w.acc) + c, 1u);
+    } else {
+      atomicOr(&kp.w.sizes->flags, (uint32_t)FCS_FLAG_HIT_CAPACITY);
+    }
   }
 }
 
@@ -357,7 +386,8 @@ __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKPara
   const unsigned long long n_tiles = (unsigned long long)((H - hbase + TILE - 1) / TILE);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t hit_dbg_base = kp.dbg_hit_cell || kp.dbg_hit_bin ? w.sizes->hit_base : 0;
-  const uint32_t row_stride = MODE == kModeAtomic ? (uint32_t)kp.g.acc_stride : (uint32_t)kp.g.n_cells;
+  // accumulation rows (atomic, deterministic) or dL/dE_cell rows (gradient)
+  const uint32_t row_stride = MODE == kModeGrad ? (uint32_t)kp.g.n_cells : (uint32_t)kp.g.acc_stride;
   if (threadIdx.x == 0) {
     s_tile = kp.static_tiles ? blockIdx.x : atomicAdd(&w.sizes->queue, 1ull);
     s_recs = 0;
@@ -376,27 +406,14 @@ __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKPara
     if (nt <= kSmemTasks) {
       // stage the tile's tasks and mark where each starts
       for (int j = threadIdx.x; j < nt; j += BLOCK) {
-        const TaskRec r = w.tasks[t0 + j];
-        const int64_t s = r.hit_begin - h0;
-        TileTask q;
-        q.rel = (int32_t)s;
-        q.entry = r.entry;
-        q.Ehit = r.Ehit;
-        q.eta_c = r.eta_c;
-        q.phi_c = r.phi_c;
-        q.s_eta = r.s_eta;
-        q.s_phi = r.s_phi;
-        q.ctr_y = (uint32_t)r.layer | (kPurposeHit << 16);
-        q.ctr_z = (uint32_t)r.particle;
-        q.ctr_w = kp.first_event_lo + (uint32_t)r.event;
-        q.row_off = (uint32_t)(r.event - kp.ev_lo) * row_stride;
-        q.lay = task_lay(tb, r.layer, r.eta_c, r.s_eta);
+        const TileTask q = make_tile_task(tb, w, t0 + j, h0, kp.first_event_lo, kp.ev_lo, row_stride);
+        const int64_t s = q.rel;
         s_task[j] = q;
         if (j > 0 && s < TILE) s_owner[s] = (int16_t)j;
       }
     } else {
       for (int j = threadIdx.x + 1; j < nt; j += BLOCK) {
-        const int64_t s = w.tasks[t0 + j].hit_begin - h0;
+        const int64_t s = w.th[t0 + j] - h0;
         if (s < TILE) s_owner[s] = (int16_t)j;
       }
     }
@@ -415,19 +432,7 @@ __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKPara
         if constexpr (decltype(staged)::value) {
           T = s_task[tl];
         } else {  // more tasks than the shared copy holds: read the record itself
-          const TaskRec r = w.tasks[t0 + tl];
-          T.rel = (int32_t)(r.hit_begin - h0);
-          T.entry = r.entry;
-          T.Ehit = r.Ehit;
-          T.eta_c = r.eta_c;
-          T.phi_c = r.phi_c;
-          T.s_eta = r.s_eta;
-          T.s_phi = r.s_phi;
-          T.ctr_y = (uint32_t)r.layer | (kPurposeHit << 16);
-          T.ctr_z = (uint32_t)r.particle;
-          T.ctr_w = kp.first_event_lo + (uint32_t)r.event;
-          T.row_off = (uint32_t)(r.event - kp.ev_lo) * row_stride;
-          T.lay = task_lay(tb, r.layer, r.eta_c, r.s_eta);
+          T = make_tile_task(tb, w, t0 + tl, h0, kp.first_event_lo, kp.ev_lo, row_stride);
         }
         const uint32_t hit = (uint32_t)(i - T.rel);
         const uint4 x = philox4x32_10(make_uint4(hit, T.ctr_y, T.ctr_z, T.ctr_w), kp.k0, kp.k1);
@@ -450,9 +455,9 @@ __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKPara
               atomicAdd(w.acc + T.row_off + f.cell, __fmul_rn((float)__popc(peers), T.Ehit));
           }
         } else {
-          const unsigned long long gkey =
-              ((unsigned long long)(T.row_off + (uint32_t)f.cell) << kp.key_task_bits) | (unsigned long long)(t0 + tl);
-          recs += emit_slots(valid, ok, gkey, h0 + i, w);
+          const uint32_t cg = T.row_off + (uint32_t)f.cell;
+          const unsigned long long gkey = ((unsigned long long)cg << kp.key_task_bits) | (unsigned long long)(t0 + tl);
+          recs += emit_slots(valid, ok, gkey, cg, h0 + i, w);
         }
         // queue the uncertain hits for the FP64 recheck
         const unsigned m = __ballot_sync(0xffffffffu, need);
@@ -507,14 +512,15 @@ __global__ void __launch_bounds__(128) k_recheck(const __grid_constant__ HitKPar
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint2 q = w.recheck[i];
     const TaskRec T = w.tasks[q.x];
+    const int32_t layer = T.layer(), event = T.event();
+    const int64_t hb = w.th[q.x];
     const uint4 x = philox4x32_10(
-        make_uint4(q.y, (uint32_t)T.layer | (kPurposeHit << 16), (uint32_t)T.particle,
-                   kp.first_event_lo + (uint32_t)T.event),
+        make_uint4(q.y, (uint32_t)layer | (kPurposeHit << 16), (uint32_t)T.particle, kp.first_event_lo + (uint32_t)event),
         kp.k0, kp.k1);
     const int bin = sample_bin(kp.p, T.entry, x.x);
-    const int32_t c = cell_fp64(kp.g, kp.p, T.layer, T.eta_c, T.phi_c, x, bin);
-    deposit_single(kp, T.event, T.Ehit, q.x, c, MODE, T.entry, bin, T.hit_begin + q.y);
-    const int64_t h = hit_dbg_base + T.hit_begin + q.y;
+    const int32_t c = cell_fp64(kp.g, kp.p, layer, T.eta_c, T.phi_c, x, bin);
+    deposit_single(kp, event, __fdiv_rn(T.El, (float)w.tn[q.x]), q.x, c, MODE, T.entry, bin, hb + q.y);
+    const int64_t h = hit_dbg_base + hb + q.y;
     if (kp.dbg_hit_cell && h < kp.dbg_hit_cap) kp.dbg_hit_cell[h] = c;
   }
 }

@@ -58,7 +58,8 @@ cudaError_t launch_hits_t(const HitKParams& kp, const HitCfg& hc, const Launch& 
 
 template <int MODE>
 cudaError_t launch_recheck_t(const HitKParams& kp, const Launch& L) {
-  k_recheck<MODE><<<L.num_sms * 2, 128, 0, L.s>>>(kp);
+  // FP64 work: one warp per block spreads the queue over every SM's FP64 pipe
+  k_recheck<MODE><<<L.num_sms * 8, 32, 0, L.s>>>(kp);
   return cudaGetLastError();
 }
 

@@ -21,20 +21,23 @@ constexpr int kRecordCountBits = 5;  // deterministic mode: count - 1 in the low
 constexpr int kLfactEntries = 8192;  // log k! table for the FP32 Poisson test (k < 8192)
 
 // Task record: one (event, particle, layer) of the hit loop of Listing 1.
-// 48 bytes; tasks are stored in (event, particle, layer) order and the hits
-// of a task are the hit numbers [hit_begin, hit_begin + n) of its event range.
+// 32 bytes (one sector); tasks are stored in (event, particle, layer) order.
+// The hit count n and first hit live in the per-task arrays tn and th (the
+// hits of task t are the hit numbers [th[t], th[t] + tn[t]) of its event
+// range); the hit energy is fl32(El / n) (Listing 1: float Ehit = E(layer) /
+// nhit), formed where a kernel needs it.
 struct __align__(16) TaskRec {
-  int64_t hit_begin;
-  int32_t n;        // hits (>= 1)
-  int32_t entry;    // parametrisation entry including the layer
-  float Ehit;       // hit energy, MeV (Listing 1: float Ehit = E(layer) / nhit)
+  int32_t entry;       // parametrisation entry including the layer
+  float El;            // layer energy fl32(E f_l), MeV
   float eta_c, phi_c;
   float s_eta, s_phi;  // FP32 scale factors of the (r, alpha) -> (eta, phi) map
   int32_t particle;    // index within the event
-  int32_t event;       // batch-local event index
-  int32_t layer;
+  uint32_t ev_layer;   // batch-local event << 8 | layer
+  __device__ __forceinline__ int32_t event() const { return (int32_t)(ev_layer >> 8); }
+  __device__ __forceinline__ int32_t layer() const { return (int32_t)(ev_layer & 0xFFu); }
 };
-static_assert(sizeof(TaskRec) == 48, "TaskRec layout");
+static_assert(sizeof(TaskRec) == 32, "TaskRec layout");
+constexpr int32_t kMaxEventsPerCall = 1 << 24;  // batch-local events fit the record's 24 bits
 
 // FP32 view of a region for the fast path (shared-memory staged).
 struct RegionF {
@@ -94,8 +97,6 @@ struct Sizes {
   int64_t recheck_total;  // recheck hits over the call
   int64_t n_part;       // particles of the current event range (checked against the capacity)
   int64_t n_rec_used;   // deterministic records sorted (n_records clamped to the capacity)
-  int64_t n_inv;        // tasks queued for the inversion draw (front of tlist)
-  int64_t n_ptrs;       // tasks queued for the PTRS draw (back of tlist)
   int64_t n_pdefer;     // draws deferred to FP64 in the current range
   unsigned long long queue;  // hit-kernel work-queue counter (tiles handed out)
   uint32_t flags;       // fcs_device_flag bits
@@ -115,7 +116,6 @@ struct WsDev {
                        // finish in deterministic mode (a compact copy for the fold)
   int64_t* tn;         // [task_cap] hits of each task
   int64_t* th;         // [task_cap] first hit of each task (exclusive scan of tn)
-  int32_t* tlist;      // [task_cap] task indices grouped by Poisson method
   int32_t* pdefer;     // [task_cap] tasks whose draw is redone in FP64
   int32_t* gmap;       // [gmap_cap] granule -> task
   uint2* recheck;      // [recheck_cap] (task, hit in task)
@@ -172,6 +172,8 @@ constexpr int kScanBlocks = 512;
 cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, const int64_t* n_dev, int64_t n_host,
                             int64_t* total_dst, int64_t total_add_base_from_dst, ScanTmp tmp,
                             cudaStream_t s);
+// Exclusive scan of n uint32 values into int64 (no base, no total).
+cudaError_t launch_scan_u32(const uint32_t* in, int64_t* out, int64_t n, ScanTmp tmp, cudaStream_t s);
 
 // fcs_tasks.cu: tasks, Poisson counts and the two scans (task and hit offsets);
 // then the records' hit offsets, the tile map and the validation dumps.
@@ -229,12 +231,11 @@ cudaError_t launch_compact(const GeoDev& g, WsDev w, int32_t rows, int32_t ev_lo
 
 // fcs_sort.cu
 int64_t compact_chunks(int32_t n_cells, int32_t rows);
-cudaError_t launch_det_reduce(const GeoDev& g, WsDev w, int32_t rows, int32_t ev_lo,
-                              int key_task_bits, int key_total_bits, uint32_t* unused,
-                              int64_t hist_cap, int64_t* head_flags, int64_t* head_offsets,
-                              ScanTmp tmp, float* cells_out, int32_t* cell_ids, float* cell_E,
-                              int64_t* event_offsets_out, int32_t n_events_total,
-                              int64_t capacity, const Launch& L);
-int64_t det_hist_entries(int num_sms);
+// Deterministic mode: the records of the range (hit slots) grouped by cell
+// and folded into the accumulation rows, whose uint32 record counters the
+// hit kernel filled.  cell_off: [rows * acc_stride] scratch.  The compaction
+// then runs as in atomic mode.
+cudaError_t launch_det_reduce(const GeoDev& g, WsDev w, int32_t rows, int key_task_bits, int64_t* cell_off,
+                              ScanTmp tmp, const Launch& L);
 
 }  // namespace fcs

@@ -42,14 +42,15 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* s_warp, i
   return warp_excl + x - v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int64_t* __restrict__ in,
+template <typename In>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const In* __restrict__ in,
                                                             const int64_t* n_dev, int64_t n_host,
                                                             int64_t* __restrict__ block_sums) {
   const int64_t n = load_n(n_dev, n_host);
   const int64_t chunk = (n + kScanBlocks - 1) / kScanBlocks;
   const int64_t b = (int64_t)blockIdx.x * chunk, e = min(b + chunk, n);
   int64_t acc = 0;
-  for (int64_t i = b + threadIdx.x; i < e; i += kScanThreads) acc += in[i];
+  for (int64_t i = b + threadIdx.x; i < e; i += kScanThreads) acc += (int64_t)in[i];
 #pragma unroll
   for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   __shared__ int64_t s[kScanThreads / 32];
@@ -98,32 +99,52 @@ __global__ void __launch_bounds__(kScanBlocks) k_scan_blocks(int64_t* block_sums
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(const int64_t* __restrict__ in,
+// Tiles of kScanTile elements move through shared memory: coalesced loads
+// and stores of the tile, while each thread scans kScanItems consecutive
+// elements of it.  Element j sits at j + j / kScanItems (one pad word per
+// thread's run keeps the per-thread accesses off a single bank).
+template <typename In>
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const In* __restrict__ in,
                                                           int64_t* __restrict__ out,
                                                           const int64_t* n_dev, int64_t n_host,
                                                           const int64_t* __restrict__ block_sums) {
   __shared__ int64_t s_warp[kScanThreads / 32];
+  __shared__ int64_t s_tile[kScanTile + kScanTile / kScanItems];
   const int64_t n = load_n(n_dev, n_host);
   const int64_t chunk = (n + kScanBlocks - 1) / kScanBlocks;
   const int64_t b = (int64_t)blockIdx.x * chunk, e = min(b + chunk, n);
   int64_t carry = block_sums[blockIdx.x];
   for (int64_t t0 = b; t0 < e; t0 += kScanTile) {
-    int64_t v[kScanItems];
-    int64_t sum = 0;
-    const int64_t i0 = t0 + (int64_t)threadIdx.x * kScanItems;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-      v[k] = (i0 + k < e) ? in[i0 + k] : 0;
+      const int j = k * kScanThreads + threadIdx.x;
+      const int64_t i = t0 + j;
+      s_tile[j + j / kScanItems] = i < e ? (int64_t)in[i] : 0;
+    }
+    __syncthreads();
+    int64_t v[kScanItems];
+    int64_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      v[k] = s_tile[threadIdx.x * (kScanItems + 1) + k];
       sum += v[k];
     }
     int64_t tile_total;
-    int64_t run = carry + block_excl_scan(sum, s_warp, &tile_total);
+    int64_t run = carry + block_excl_scan(sum, s_warp, &tile_total);  // synchronises the block
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-      if (i0 + k < e) out[i0 + k] = run;
+      s_tile[threadIdx.x * (kScanItems + 1) + k] = run;
       run += v[k];
     }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      const int j = k * kScanThreads + threadIdx.x;
+      const int64_t i = t0 + j;
+      if (i < e) out[i] = s_tile[j + j / kScanItems];
+    }
     carry += tile_total;
+    __syncthreads();  // the tile buffer is reused
   }
 }
 
@@ -132,13 +153,23 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const int64_t* __res
 // out[i] = base + sum_{j<i} in[j]; base = *total_dst if base_from_dst != 0
 // (a running total in device memory) else 0.  Writes base + sum to
 // *total_dst when total_dst is non-NULL.  in and out may alias.
-cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, const int64_t* n_dev, int64_t n_host,
-                            int64_t* total_dst, int64_t base_from_dst, ScanTmp tmp, cudaStream_t s) {
-  k_scan_reduce<<<kScanBlocks, kScanThreads, 0, s>>>(in, n_dev, n_host, tmp.block_sums);
+template <typename In>
+static cudaError_t launch_scan(const In* in, int64_t* out, const int64_t* n_dev, int64_t n_host,
+                               int64_t* total_dst, int64_t base_from_dst, ScanTmp tmp, cudaStream_t s) {
+  k_scan_reduce<In><<<kScanBlocks, kScanThreads, 0, s>>>(in, n_dev, n_host, tmp.block_sums);
   k_scan_blocks<<<1, kScanBlocks, 0, s>>>(tmp.block_sums, base_from_dst ? total_dst : nullptr,
                                           total_dst);
-  k_scan_down<<<kScanBlocks, kScanThreads, 0, s>>>(in, out, n_dev, n_host, tmp.block_sums);
+  k_scan_down<In><<<kScanBlocks, kScanThreads, 0, s>>>(in, out, n_dev, n_host, tmp.block_sums);
   return cudaGetLastError();
+}
+
+cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, const int64_t* n_dev, int64_t n_host,
+                            int64_t* total_dst, int64_t base_from_dst, ScanTmp tmp, cudaStream_t s) {
+  return launch_scan(in, out, n_dev, n_host, total_dst, base_from_dst, tmp, s);
+}
+
+cudaError_t launch_scan_u32(const uint32_t* in, int64_t* out, int64_t n, ScanTmp tmp, cudaStream_t s) {
+  return launch_scan(in, out, nullptr, n, nullptr, 0, tmp, s);
 }
 
 }  // namespace fcs

@@ -311,120 +311,162 @@ __global__ void __launch_bounds__(128) k_particle_count(const ParamDev p, const 
   }
 }
 
-// Task records in (event, particle, layer) order, without hit counts; the
-// layer energy waits in Ehit and the Poisson mean in tmu.  Each task index is
-// also filed in tlist by draw method (inversion from the front, PTRS from the
-// back), with one list reservation per warp.
+// Task records in (event, particle, layer) order and their Poisson means.
+// A warp takes 32 consecutive particles, whose tasks are consecutive too
+// (poff), and fills them 32 at a time: lane s of a round builds the task in
+// slot s of the warp's range, so each round writes 32 consecutive 32-byte
+// records.  The owner of a slot is found by a binary search over the lanes'
+// inclusive task counts (shuffles); its data comes by shuffle from the lane
+// that loaded the particle.
 __global__ void __launch_bounds__(128) k_task_init(const GeoDev g, const ParamDev p, const fcs_particles parts,
                                                    int32_t ev_lo, WsDev w) {
   const int64_t pb = parts.event_offsets[ev_lo];
   const int64_t P = w.sizes->n_part;
   const int NL = p.NL;
   const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base_i = (int64_t)blockIdx.x * blockDim.x; base_i < P; base_i += stride) {
-    const int64_t li = base_i + threadIdx.x;
-    const uint4 info = li < P ? w.pinfo[li] : make_uint4(0u, 0u, 0u, 0u);
-    uint32_t inv_bits = 0;  // bit j: task j of the particle draws by inversion
-    int32_t n_mine = 0;
-    int64_t t_first = 0;
-    if (info.z) {
-      const int64_t i = pb + li;
-      const float E = parts.E[i], eta = parts.eta[i], phi = parts.phi[i];
-      const int32_t e = (int32_t)info.y;
-      const int32_t pin = (int32_t)(i - parts.event_offsets[e]);
-      const int64_t base = (int64_t)info.x * NL;
-      t_first = w.poff[li];
-      // FP32 scale factors of the (r, alpha) -> (eta, phi) map; the FP64 recheck
-      // recomputes them in double exactly as the oracle does.
-      const float ae = fabsf(eta);
-      const float ch = coshf(eta), sh = sinhf(ae), th = tanhf(ae);
-      for (uint32_t m = info.z; m; m &= m - 1) {
-        const int l = __ffs(m) - 1;
-        const float El = __fmul_rn(E, __ldg(p.frac + base + l));
-        const float mu = __fdiv_rn(El, __ldg(p.mhe + base + l));
-        TaskRec r;
-        r.hit_begin = 0;
-        r.n = 0;
-        r.entry = (int32_t)(base + l);
-        r.Ehit = El;
-        r.eta_c = eta;
-        r.phi_c = phi;
-        const float R = g.rz32[l];
-        if (g.barrel[l]) {
-          r.s_phi = 1.0f / R;
-          r.s_eta = 1.0f / (R * ch);
-        } else {
-          const float mm = (th * sh) / R;
-          r.s_phi = sh / R;
-          r.s_eta = (eta < 0.0f) ? mm : -mm;
-        }
-        r.particle = pin;
-        r.event = e;
-        r.layer = l;
-        const int64_t to = t_first + n_mine;
-        if (to >= w.task_cap) break;  // cannot happen: the capacity is particles x layers
-        w.tasks[to] = r;
-        w.tmu[to] = mu;
-        inv_bits |= (uint32_t)(mu < 10.0f) << n_mine;
-        ++n_mine;
-      }
-    }
-    // warp-level reservation in both lists
-    const int32_t n_inv = __popc(inv_bits), n_ptrs = n_mine - n_inv;
-    int32_t xi = n_inv, xp = n_ptrs;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t wb = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; wb < P; wb += warps * 32) {
+    const int64_t li = wb + lane;
+    const bool have = li < P;
+    const uint4 info = have ? w.pinfo[li] : make_uint4(0u, 0u, 0u, 0u);
+    const int cnt = __popc(info.z);
+    int incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int32_t yi = __shfl_up_sync(0xffffffffu, xi, o), yp = __shfl_up_sync(0xffffffffu, xp, o);
-      if (lane >= o) {
-        xi += yi;
-        xp += yp;
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) continue;
+    const int64_t tbase = __shfl_sync(0xffffffffu, w.poff[have ? li : wb], 0);
+    // the particle this lane loaded (lanes without tasks load nothing)
+    float E = 0.0f, eta = 0.0f, phi = 0.0f, ch = 0.0f, sh = 0.0f, th = 0.0f;
+    int32_t pin = 0;
+    if (cnt) {
+      const int64_t i = pb + li;
+      E = parts.E[i];
+      eta = parts.eta[i];
+      phi = parts.phi[i];
+      pin = (int32_t)(i - parts.event_offsets[info.y]);
+      // FP32 scale factors of the (r, alpha) -> (eta, phi) map; the FP64
+      // recheck recomputes them in double exactly as the oracle does
+      const float ae = fabsf(eta);
+      ch = coshf(eta);
+      sh = sinhf(ae);
+      th = tanhf(ae);
+    }
+    for (int s0 = 0; s0 < total; s0 += 32) {
+      const int sl = s0 + lane;
+      int o = 0;  // owner: the first lane whose inclusive count exceeds sl
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int v = __shfl_sync(0xffffffffu, incl, o + step - 1);
+        if (v <= sl) o += step;
       }
-    }
-    unsigned long long bi = 0, bp = 0;
-    if (lane == 31) {
-      if (xi) bi = atomicAdd((unsigned long long*)&w.sizes->n_inv, (unsigned long long)xi);
-      if (xp) bp = atomicAdd((unsigned long long*)&w.sizes->n_ptrs, (unsigned long long)xp);
-    }
-    bi = __shfl_sync(0xffffffffu, bi, 31) + (unsigned long long)(xi - n_inv);
-    bp = __shfl_sync(0xffffffffu, bp, 31) + (unsigned long long)(xp - n_ptrs);
-    for (int32_t j = 0; j < n_mine; ++j) {
-      const int64_t t = t_first + j;
-      if ((inv_bits >> j) & 1u) w.tlist[bi++] = (int32_t)t;
-      else w.tlist[w.task_cap - 1 - (int64_t)(bp++)] = (int32_t)t;
+      o = min(o, 31);
+      const int j = sl - (__shfl_sync(0xffffffffu, incl, o) - __shfl_sync(0xffffffffu, cnt, o));
+      const uint32_t entry = __shfl_sync(0xffffffffu, info.x, o);
+      const uint32_t ev = __shfl_sync(0xffffffffu, info.y, o);
+      const uint32_t mask = __shfl_sync(0xffffffffu, info.z, o);
+      const float oE = __shfl_sync(0xffffffffu, E, o), oeta = __shfl_sync(0xffffffffu, eta, o);
+      const float ophi = __shfl_sync(0xffffffffu, phi, o);
+      const float och = __shfl_sync(0xffffffffu, ch, o), osh = __shfl_sync(0xffffffffu, sh, o);
+      const float oth = __shfl_sync(0xffffffffu, th, o);
+      const int32_t opin = __shfl_sync(0xffffffffu, pin, o);
+      const int64_t to = tbase + sl;
+      if (sl >= total || to >= w.task_cap) continue;  // the capacity is particles x layers: never
+      const int l = (int)__fns(mask, 0u, j + 1);
+      const int64_t e = (int64_t)entry * NL + l;
+      const float El = __fmul_rn(oE, __ldg(p.frac + e));
+      TaskRec r;
+      r.entry = (int32_t)e;
+      r.El = El;
+      r.eta_c = oeta;
+      r.phi_c = ophi;
+      const float R = g.rz32[l];
+      if (g.barrel[l]) {
+        r.s_phi = 1.0f / R;
+        r.s_eta = 1.0f / (R * och);
+      } else {
+        const float mm = (oth * osh) / R;
+        r.s_phi = osh / R;
+        r.s_eta = (oeta < 0.0f) ? mm : -mm;
+      }
+      r.particle = opin;
+      r.ev_layer = (ev << 8) | (uint32_t)l;
+      w.tasks[to] = r;
+      w.tmu[to] = __fdiv_rn(El, __ldg(p.mhe + e));
     }
   }
 }
 
-// One thread per task: n = max(1, Poisson(mu)) in FP32, inversion tasks
-// first, then PTRS tasks, from the grouped index list.  Draws the FP32 path
-// cannot certify are queued for k_task_poisson64, so that FP64 work runs in
-// full warps instead of stalling a warp for one lane.
-__global__ void k_task_poisson(WsDev w, uint32_t k0, uint32_t k1, uint32_t first_event_lo, const float* lfact,
-                               int32_t n_lfact) {
-  const int64_t n_inv = w.sizes->n_inv, n_all = n_inv + w.sizes->n_ptrs;
+// n = max(1, Poisson(mu)) in FP32.  Each warp takes windows of 128
+// consecutive tasks, lists the window's inversion tasks (mu < 10) from the
+// front and its PTRS tasks from the back of a per-warp shared array, and
+// draws them 32 at a time, inversion rounds first: a round runs one method,
+// and warps never wait for one another.  Draws the FP32 path cannot certify
+// are queued for k_task_poisson64, so that FP64 work runs in full warps
+// instead of stalling a warp for one lane.
+constexpr int kPoisWarps = 4;
+constexpr int kPoisWin = 128;
+
+// One round: lane j draws for list entry j (< n) of the window; list entry j
+// is s_list[j] (inversion list) or s_list[kPoisWin - 1 - j] (PTRS list).
+__device__ __forceinline__ void poisson_round(const WsDev& w, int64_t win, const int* s_list, const float* s_mu,
+                                              int j, int n, bool back, uint32_t k0, uint32_t k1,
+                                              uint32_t first_event_lo, const float* lfact, int32_t n_lfact) {
   const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < n_all; j0 += stride) {
-    const int64_t j = j0 + threadIdx.x;
-    int32_t k = 0;
-    int64_t t = 0;
-    if (j < n_all) {
-      t = (j < n_inv) ? w.tlist[j] : w.tlist[w.task_cap - 1 - (j - n_inv)];
-      const TaskRec& r = w.tasks[t];
-      k = poisson_draw_fp32(w.tmu[t], (uint32_t)r.layer, (uint32_t)r.particle, first_event_lo + (uint32_t)r.event,
-                            k0, k1, lfact, n_lfact);
-      w.tn[t] = (k < 1) ? 1 : k;  // provisional for deferred draws
+  int32_t k = 0;
+  int64_t tt = 0;
+  if (j < n) {
+    const int idx = s_list[back ? kPoisWin - 1 - j : j];
+    tt = win + idx;
+    const TaskRec& r = w.tasks[tt];
+    k = poisson_draw_fp32(s_mu[idx], (uint32_t)r.layer(), (uint32_t)r.particle, first_event_lo + (uint32_t)r.event(),
+                          k0, k1, lfact, n_lfact);
+    w.tn[tt] = (k < 1) ? 1 : k;  // provisional for deferred draws
+  }
+  const bool defer = j < n && k < 0;
+  const unsigned m = __ballot_sync(0xffffffffu, defer);
+  if (m) {
+    unsigned long long b = 0;
+    const int l0 = __ffs(m) - 1;
+    if (lane == l0) b = atomicAdd((unsigned long long*)&w.sizes->n_pdefer, (unsigned long long)__popc(m));
+    b = __shfl_sync(0xffffffffu, b, l0);
+    if (defer) w.pdefer[b + __popc(m & ((1u << lane) - 1u))] = (int32_t)tt;
+  }
+}
+
+__global__ void __launch_bounds__(32 * kPoisWarps) k_task_poisson(WsDev w, uint32_t k0, uint32_t k1,
+                                                                   uint32_t first_event_lo, const float* lfact,
+                                                                   int32_t n_lfact) {
+  __shared__ int s_list[kPoisWarps][kPoisWin];  // inversion tasks from the front, PTRS from the back
+  __shared__ float s_mu[kPoisWarps][kPoisWin];
+  const int64_t T = min(w.sizes->n_tasks, w.task_cap);
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t nw = (int64_t)gridDim.x * kPoisWarps;
+  for (int64_t win = ((int64_t)blockIdx.x * kPoisWarps + wi) * kPoisWin; win < T; win += nw * kPoisWin) {
+    int n_i = 0, n_p = 0;
+#pragma unroll
+    for (int c = 0; c < kPoisWin / 32; ++c) {
+      const int idx = c * 32 + lane;
+      const int64_t t = win + idx;
+      const float mu = t < T ? w.tmu[t] : 0.0f;
+      const bool inv = t < T && mu < 10.0f, pt = t < T && !(mu < 10.0f);
+      const unsigned bi = __ballot_sync(0xffffffffu, inv), bp = __ballot_sync(0xffffffffu, pt);
+      s_mu[wi][idx] = mu;
+      if (inv) s_list[wi][n_i + __popc(bi & lt)] = idx;
+      if (pt) s_list[wi][kPoisWin - 1 - (n_p + __popc(bp & lt))] = idx;
+      n_i += __popc(bi);
+      n_p += __popc(bp);
     }
-    const bool defer = j < n_all && k < 0;
-    const unsigned m = __ballot_sync(0xffffffffu, defer);
-    if (m) {
-      unsigned long long b = 0;
-      const int l0 = __ffs(m) - 1;
-      if (lane == l0) b = atomicAdd((unsigned long long*)&w.sizes->n_pdefer, (unsigned long long)__popc(m));
-      b = __shfl_sync(0xffffffffu, b, l0);
-      if (defer) w.pdefer[b + __popc(m & ((1u << lane) - 1u))] = (int32_t)t;
-    }
+    __syncwarp();
+    for (int r0 = 0; r0 < n_i; r0 += 32)
+      poisson_round(w, win, s_list[wi], s_mu[wi], r0 + lane, n_i, false, k0, k1, first_event_lo, lfact, n_lfact);
+    for (int r0 = 0; r0 < n_p; r0 += 32)
+      poisson_round(w, win, s_list[wi], s_mu[wi], r0 + lane, n_p, true, k0, k1, first_event_lo, lfact, n_lfact);
+    __syncwarp();  // the window's lists are reused
   }
 }
 
@@ -435,16 +477,17 @@ __global__ void __launch_bounds__(128) k_task_poisson64(WsDev w, uint32_t k0, ui
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
     const int32_t t = w.pdefer[q];
     const TaskRec& r = w.tasks[t];
-    int64_t k = poisson_draw((double)w.tmu[t], (uint32_t)r.layer, (uint32_t)r.particle,
-                             first_event_lo + (uint32_t)r.event, k0, k1);
+    int64_t k = poisson_draw((double)w.tmu[t], (uint32_t)r.layer(), (uint32_t)r.particle,
+                             first_event_lo + (uint32_t)r.event(), k0, k1);
     if (k < 1) k = 1;
     if (k > 0x7FFFFFFF) k = 0x7FFFFFFF;
     w.tn[t] = k;
   }
 }
 
-// One thread per task: hit offsets, counts and hit energy; the tile map
-// (granule -> task containing its first hit); validation dumps.
+// One thread per task: the tile map (granule -> task containing its first
+// hit); in deterministic mode the hit energy into tmu (the fold's compact
+// copy); validation dumps.
 __global__ void k_task_finish(WsDev w, fcs_debug dbg, int has_dbg, int det) {
   const int64_t T = min(w.sizes->n_tasks, w.task_cap);
   const int64_t H = w.sizes->n_hits;
@@ -452,24 +495,23 @@ __global__ void k_task_finish(WsDev w, fcs_debug dbg, int has_dbg, int det) {
   if (!map_ok && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_HIT_CAPACITY);
   const int64_t task_base = w.sizes->task_base;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x) {
-    TaskRec& r = w.tasks[t];
-    const int32_t n = (int32_t)w.tn[t];
+    const int64_t n = w.tn[t];
     const int64_t b = w.th[t];
-    const float Ehit = __fdiv_rn(r.Ehit, (float)n);
-    r.hit_begin = b;
-    r.n = n;
-    r.Ehit = Ehit;
-    if (det) w.tmu[t] = Ehit;
     if (map_ok)
       for (int64_t gi = (b + kGranule - 1) / kGranule; gi * kGranule < b + n; ++gi) w.gmap[gi] = (int32_t)t;
-    if (has_dbg) {
-      const int64_t dt = task_base + t;
-      if (dt < dbg.task_capacity) {
-        if (dbg.task_event) dbg.task_event[dt] = r.event;
-        if (dbg.task_particle) dbg.task_particle[dt] = r.particle;
-        if (dbg.task_layer) dbg.task_layer[dt] = r.layer;
-        if (dbg.task_n) dbg.task_n[dt] = n;
-        if (dbg.task_Ehit) dbg.task_Ehit[dt] = Ehit;
+    if (det || has_dbg) {
+      const TaskRec& r = w.tasks[t];
+      const float Ehit = __fdiv_rn(r.El, (float)n);
+      if (det) w.tmu[t] = Ehit;
+      if (has_dbg) {
+        const int64_t dt = task_base + t;
+        if (dt < dbg.task_capacity) {
+          if (dbg.task_event) dbg.task_event[dt] = r.event();
+          if (dbg.task_particle) dbg.task_particle[dt] = r.particle;
+          if (dbg.task_layer) dbg.task_layer[dt] = r.layer();
+          if (dbg.task_n) dbg.task_n[dt] = (int32_t)n;
+          if (dbg.task_Ehit) dbg.task_Ehit[dt] = Ehit;
+        }
       }
     }
   }
@@ -488,13 +530,18 @@ cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_par
                                int64_t n_part_max, const Launch& L) {
   // one thread per particle / task where the grid allows (these kernels wait
   // on dependent loads: more threads in flight, not fewer, hide them)
-  const int gp = grid_for(n_part_max, L), gt = grid_for(n_part_max * p.NL, L);
+  const int gp = grid_for(n_part_max, L);
   k_particle_count<<<gp, 128, 0, L.s>>>(p, parts, ev_lo, ev_hi, w);
   cudaError_t e = launch_scan_i64(w.pcount, w.poff, &w.sizes->n_part, 0, &w.sizes->n_tasks, 0, tmp, L.s);
   if (e != cudaSuccess) return e;
   k_task_init<<<gp, 128, 0, L.s>>>(g, p, parts, ev_lo, w);
-  k_task_poisson<<<gt, 128, 0, L.s>>>(w, k0, k1, (uint32_t)first_event, p.lfact, p.n_lfact);
-  k_task_poisson64<<<L.num_sms * 2, 128, 0, L.s>>>(w, k0, k1, (uint32_t)first_event);
+  const int gpois = (int)std::min<int64_t>(
+      (std::max<int64_t>(n_part_max * p.NL, 1) + kPoisWarps * kPoisWin - 1) / (kPoisWarps * kPoisWin),
+      (int64_t)L.num_sms * 16);
+  k_task_poisson<<<gpois, 32 * kPoisWarps, 0, L.s>>>(w, k0, k1, (uint32_t)first_event, p.lfact, p.n_lfact);
+  // the FP64 pipe is narrow: one warp per block spreads the few deferred draws
+  // over every SM
+  k_task_poisson64<<<L.num_sms * 8, 32, 0, L.s>>>(w, k0, k1, (uint32_t)first_event);
   // the scan counts the tasks actually written (n_tasks <= task_cap by construction)
   return launch_scan_i64(w.tn, w.th, &w.sizes->n_tasks, 0, &w.sizes->n_hits, 0, tmp, L.s);
 }

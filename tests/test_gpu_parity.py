@@ -102,6 +102,17 @@ def test_deterministic_bit_exact(sim, ogeo, oprm, batched):
     check_compacted(got, cells.astype(np.float64), 3)
 
 
+def test_deterministic_hot_cells(sim, ogeo, oprm):
+    """1 TeV electrons: tens of thousands of hits in a few tasks, so the core
+    cells collect hundreds of records (the long-segment sort of the fold)."""
+    parts = synth.single_particle(2, E=float(2 ** 20), eta=-1.1)
+    ref, got = run_both(sim, ogeo, oprm, parts, seed=3, mode=fcs.MODE_DETERMINISTIC, hits=False)
+    check_tasks_hits(ref, got)
+    cells = got["cells"].cpu().numpy()
+    assert np.array_equal(cells.view(np.uint32), ref.cells_canon.view(np.uint32))
+    assert ref.n_hits > 20000
+
+
 @pytest.mark.parametrize("block,hpt", [(128, 1), (128, 8), (256, 2), (256, 4), (512, 1), (512, 8)])
 def test_launch_shapes(sim, ogeo, oprm, block, hpt):
     parts = synth.pileup(seed=6, n_events=2, mu_pu=10)
