@@ -80,7 +80,7 @@ static double u53(uint32_t a, uint32_t b) {
 }
 
 /* Counter layout: (index, layer | purpose << 16, particle in event, event). */
-enum { PURPOSE_HIT = 0, PURPOSE_POISSON = 1 };
+enum { PURPOSE_HIT = 0, PURPOSE_POISSON = 1, PURPOSE_EBIN = 2 };
 
 static void draw_pair(const uint32_t key[2], uint32_t i, uint32_t layer, uint32_t particle,
                       uint32_t event, double* u, double* v) {
@@ -165,6 +165,28 @@ int32_t orc_param_entry(const orc_params* P, int32_t type, float E, float eta) {
   int32_t hb;
   if (ae >= (double)(P->NH - 1)) hb = P->NH - 1;
   else hb = (int32_t)floor(ae);
+  return (type * P->NE + eb) * P->NH + hb;
+}
+
+/* Energy-bin interpolation (a reading: the paper selects "the optimal"     */
+/* parametrisation, Sec. 1, and leaves interpolation out).  The bins' points */
+/* are the powers of two 2^k; E = m 2^k, m in [1, 2), takes bin k + 1 with  */
+/* probability m - 1 (linear in E between the two points).                  */
+int32_t orc_param_entry_rng(const orc_params* P, int32_t type, float E, float eta, const uint32_t key[2],
+                            uint32_t particle, uint32_t event) {
+  const int32_t base = orc_param_entry(P, type, E, eta);
+  if (!P->energy_interp) return base;
+  int ex = 0;
+  const double m = 2.0 * frexp((double)E, &ex); /* E = m * 2^(ex - 1), m in [1, 2) */
+  const uint32_t ctr[4] = {0u, (uint32_t)PURPOSE_EBIN << 16, particle, event};
+  uint32_t x[4];
+  orc_philox(ctr, key, x);
+  const double u = (double)x[0] * (1.0 / 4294967296.0);
+  if (!(u < m - 1.0)) return base;
+  int32_t eb = (ex - 1) - P->ebin_log2_min + 1;
+  if (eb < 0) eb = 0;
+  if (eb > P->NE - 1) eb = P->NE - 1;
+  const int32_t hb = base % P->NH;
   return (type * P->NE + eb) * P->NH + hb;
 }
 
@@ -309,7 +331,7 @@ int32_t orc_simulate(const orc_geometry* g, const orc_params* P, int64_t n_parti
         status = -1;
         continue;
       }
-      const int32_t base = orc_param_entry(P, type[p], E[p], eta[p]);
+      const int32_t base = orc_param_entry_rng(P, type[p], E[p], eta[p], key, pin, ev);
       for (int32_t l = 0; l < P->NL; ++l) {
         const int64_t entry = (int64_t)base * P->NL + l;
         const float El = E[p] * P->frac[entry];
@@ -433,7 +455,7 @@ static int32_t walk_hits(const orc_geometry* g, const orc_params* P, int64_t n_p
         status = -1;
         continue;
       }
-      const int32_t base = orc_param_entry(P, type[p], E[p], eta[p]);
+      const int32_t base = orc_param_entry_rng(P, type[p], E[p], eta[p], key, pin, ev);
       for (int32_t l = 0; l < P->NL; ++l) {
         const int64_t entry = (int64_t)base * P->NL + l;
         const float El = E[p] * P->frac[entry];

@@ -48,7 +48,7 @@ typedef struct orc_params {
   const float* a_edges;    /* [NA + 1] */
   double eta_bin_scale;    /* eta bins per unit |eta| */
   int32_t ebin_log2_min;   /* energy bin 0 starts at 2^ebin_log2_min MeV */
-  int32_t pad;
+  int32_t energy_interp;   /* 1: probabilistic energy-bin interpolation (orc_energy_bin) */
 } orc_params;
 
 const char* orc_version(void);
@@ -66,6 +66,13 @@ void orc_poisson_n(int64_t n, const double* mu, const uint32_t key[2], const uin
 
 /* Parametrisation entry (without the layer index) for a particle. */
 int32_t orc_param_entry(const orc_params* P, int32_t type, float E, float eta);
+/* The same with the energy bin interpolated when P->energy_interp: E = m 2^k
+ * (m in [1, 2)) lies the fraction x = m - 1 of the way from the bin's point
+ * 2^k to the next bin's 2^(k+1), and takes the next bin when the uniform
+ * u = x0 2^-32 of Philox block (0, 2 << 16, particle in event, event) is
+ * below x (exact in FP64). */
+int32_t orc_param_entry_rng(const orc_params* P, int32_t type, float E, float eta, const uint32_t key[2],
+                            uint32_t particle, uint32_t event);
 
 /* Inverse-CDF thresholds of one shape histogram; returns -1 if all weights are 0. */
 int32_t orc_thresholds(const float* w, int32_t nb, uint32_t* T, int32_t* k_last);

@@ -58,7 +58,7 @@ class _Params(C.Structure):
                 ("NR", C.c_int32), ("NA", C.c_int32),
                 ("frac", C.c_void_p), ("mean_hit_E", C.c_void_p), ("shape_w", C.c_void_p),
                 ("r_edges", C.c_void_p), ("a_edges", C.c_void_p),
-                ("eta_bin_scale", C.c_double), ("ebin_log2_min", C.c_int32), ("pad", C.c_int32)]
+                ("eta_bin_scale", C.c_double), ("ebin_log2_min", C.c_int32), ("energy_interp", C.c_int32)]
 
 
 class _Outputs(C.Structure):
@@ -96,6 +96,8 @@ def lib():
             L.orc_simulate.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp, C.c_int32, vp, C.c_uint64,
                                        C.c_int64, vp]
             L.orc_simulate.restype = C.c_int32
+            L.orc_param_entry_rng.argtypes = [vp, C.c_int32, C.c_float, C.c_float, vp, C.c_uint32, C.c_uint32]
+            L.orc_param_entry_rng.restype = C.c_int32
             L.orc_reweighted_cells.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp, C.c_int32, vp, C.c_uint64,
                                                C.c_int64, C.c_int64, C.c_double, C.c_int64, C.c_int32,
                                                C.c_double, vp]
@@ -128,7 +130,7 @@ class OracleGeometry:
 
 
 class OracleParams:
-    def __init__(self, prm):
+    def __init__(self, prm, energy_interp: int = 0):
         self.frac = np.ascontiguousarray(prm.frac, dtype=np.float32)
         self.mhe = np.ascontiguousarray(prm.mean_hit_E, dtype=np.float32)
         self.w = np.ascontiguousarray(prm.shape_w, dtype=np.float32)
@@ -138,7 +140,7 @@ class OracleParams:
         NR, NA = self.w.shape[-2:]
         self.s = _Params(NT, NE, NH, NL, NR, NA, self.frac.ctypes.data, self.mhe.ctypes.data,
                          self.w.ctypes.data, self.re.ctypes.data, self.ae.ctypes.data,
-                         float(prm.eta_bin_scale), int(prm.ebin_log2_min), 0)
+                         float(prm.eta_bin_scale), int(prm.ebin_log2_min), int(energy_interp))
 
     @property
     def ptr(self):
@@ -174,6 +176,12 @@ def poisson(mu, seed: int, layer, particle, event) -> np.ndarray:
 
 def param_entry(oprm: OracleParams, ptype: int, E: float, eta: float) -> int:
     return int(lib().orc_param_entry(oprm.ptr, ptype, E, eta))
+
+
+def param_entry_rng(oprm: OracleParams, ptype: int, E: float, eta: float, seed: int, particle: int,
+                    event: int) -> int:
+    k = key_of(seed)
+    return int(lib().orc_param_entry_rng(oprm.ptr, ptype, E, eta, _p(k), particle, event))
 
 
 def thresholds(w: np.ndarray):

@@ -16,10 +16,12 @@
 //      record array;
 //   2. scatter: every record takes a place in its cell's segment; the
 //      counter, counted down, hands out the places and ends at zero;
-//   3. fold: one thread per cell sorts its segment by (task, count), merges
-//      the records of a task (their counts add exactly) and folds; the float
-//      result goes to the accumulation row, where the compaction of the
-//      atomic mode picks it up and re-zeroes it.
+//   3. fold: one thread per cell sorts its segment by (task, count) (in
+//      registers with an odd-even transposition network up to 8 records,
+//      insertion sort in place up to 32, heapsort beyond), merges the records
+//      of a task (their counts add exactly) and folds; the float result goes
+//      to the accumulation row, where the compaction of the atomic mode picks
+//      it up and re-zeroes it.
 // Only the order of places inside a segment depends on scheduling, and the
 // sort removes it, so the cells are bit-reproducible.
 #include "fcs_internal.cuh"
@@ -28,7 +30,8 @@ namespace fcs {
 namespace {
 
 constexpr uint64_t kEmpty = ~0ull;
-constexpr int kInsertionMax = 32;  // longer segments take heapsort
+constexpr int kRegSortMax = 8;         // segments sorted in registers
+constexpr int kInsertionMax = 32;      // then insertion sort in place, heapsort beyond
 
 __global__ void __launch_bounds__(256) k_det_scatter(const uint64_t* __restrict__ slots, const Sizes* sz, int64_t cap,
                                                      int cell_shift, uint32_t* __restrict__ counters,
@@ -63,8 +66,8 @@ __device__ __forceinline__ void sift_down(uint64_t* a, int64_t root, int64_t n) 
   }
 }
 
-// Ascending sort of a[0, n) in place.
-__device__ __forceinline__ void sort_segment(uint64_t* a, int64_t n) {
+// Ascending sort of a[0, n) in place (n > kRegSortMax).
+__device__ __noinline__ void sort_segment(uint64_t* a, int64_t n) {
   if (n <= kInsertionMax) {
     for (int64_t i = 1; i < n; ++i) {
       const uint64_t v = a[i];
@@ -86,6 +89,53 @@ __device__ __forceinline__ void sort_segment(uint64_t* a, int64_t n) {
   }
 }
 
+__device__ __forceinline__ void cmp_swap(uint64_t& x, uint64_t& y) {
+  const uint64_t lo = x < y ? x : y, hi = x < y ? y : x;
+  x = lo;
+  y = hi;
+}
+
+// One step of the fold of a cell's records in ascending order: per task the
+// summed count times the task's hit energy, added in task order.
+struct Fold {
+  float E = 0.0f;
+  int64_t prev_task = -1;
+  int64_t cnt = 0;
+  __device__ __forceinline__ void add(uint64_t k, uint64_t task_mask, const float* __restrict__ task_ehit) {
+    const int64_t task = (int64_t)((k >> kRecordCountBits) & task_mask);
+    const int64_t c = (int64_t)(k & ((1u << kRecordCountBits) - 1u)) + 1;
+    if (task != prev_task) {
+      if (prev_task >= 0) E = __fadd_rn(E, __fmul_rn((float)cnt, task_ehit[prev_task]));
+      prev_task = task;
+      cnt = 0;
+    }
+    cnt += c;
+  }
+  __device__ __forceinline__ float result(const float* __restrict__ task_ehit) const {
+    return __fadd_rn(E, __fmul_rn((float)cnt, task_ehit[prev_task]));
+  }
+};
+
+// Up to N records: loaded into registers (padded with the largest key),
+// sorted by an N-round odd-even transposition network, folded.
+template <int N>
+__device__ __forceinline__ float fold_small(const uint64_t* __restrict__ seg, int n, uint64_t task_mask,
+                                            const float* __restrict__ task_ehit) {
+  uint64_t r[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) r[j] = j < n ? seg[j] : ~0ull;
+#pragma unroll
+  for (int round = 0; round < N; ++round) {
+#pragma unroll
+    for (int j = round & 1; j + 1 < N; j += 2) cmp_swap(r[j], r[j + 1]);
+  }
+  Fold f;
+#pragma unroll
+  for (int j = 0; j < N; ++j)
+    if (j < n) f.add(r[j], task_mask, task_ehit);
+  return f.result(task_ehit);
+}
+
 __global__ void __launch_bounds__(256) k_det_fold(uint64_t* __restrict__ recs, const int64_t* __restrict__ cell_off,
                                                   int64_t n_cells_all, const Sizes* sz, int64_t cap,
                                                   uint64_t task_mask, const float* __restrict__ task_ehit,
@@ -96,22 +146,18 @@ __global__ void __launch_bounds__(256) k_det_fold(uint64_t* __restrict__ recs, c
     const int64_t a = cell_off[c], b = (c + 1 < n_cells_all) ? cell_off[c + 1] : total;
     if (a >= b) continue;
     uint64_t* seg = recs + a;
-    sort_segment(seg, b - a);
-    float E = 0.0f;
-    int64_t prev_task = -1;
-    int64_t cnt = 0;
-    for (int64_t j = 0; j < b - a; ++j) {
-      const uint64_t k = seg[j];
-      const int64_t task = (int64_t)((k >> kRecordCountBits) & task_mask);
-      const int64_t n = (int64_t)(k & ((1u << kRecordCountBits) - 1u)) + 1;
-      if (task != prev_task) {
-        if (prev_task >= 0) E = __fadd_rn(E, __fmul_rn((float)cnt, task_ehit[prev_task]));
-        prev_task = task;
-        cnt = 0;
-      }
-      cnt += n;
+    const int64_t n = b - a;
+    float E;
+    if (n <= 4) {
+      E = fold_small<4>(seg, (int)n, task_mask, task_ehit);
+    } else if (n <= kRegSortMax) {
+      E = fold_small<kRegSortMax>(seg, (int)n, task_mask, task_ehit);
+    } else {
+      sort_segment(seg, n);
+      Fold f;
+      for (int64_t j = 0; j < n; ++j) f.add(seg[j], task_mask, task_ehit);
+      E = f.result(task_ehit);
     }
-    E = __fadd_rn(E, __fmul_rn((float)cnt, task_ehit[prev_task]));
     acc[c] = E;
   }
 }
