@@ -119,6 +119,11 @@ typedef struct fcs_config {
   int32_t wave_events;     /* batched: events per launch sequence (a wave), >= 0; 0 = all events of
                               the call.  A wave's accumulation rows (4 B x cells per event) stay
                               in L2 while they fit; the workspace holds one wave's rows */
+  int32_t energy_interp;   /* 1: probabilistic energy-bin interpolation.  A particle of energy
+                              E = m 2^k (m in [1, 2)) takes the next energy bin with probability
+                              m - 1: when word 0 of Philox block (0, 2 << 16, particle in event,
+                              event) is below (mantissa bits of E) << 9.  0: the bin of E */
+  int32_t reserved;        /* must be 0 */
 } fcs_config;
 
 /* Filled by fcs_simulate_events when non-NULL and config->sync != 0. */

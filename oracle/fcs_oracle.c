@@ -28,6 +28,7 @@
  */
 #include "fcs_oracle.h"
 
+#include <float.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -175,7 +176,7 @@ int32_t orc_param_entry(const orc_params* P, int32_t type, float E, float eta) {
 int32_t orc_param_entry_rng(const orc_params* P, int32_t type, float E, float eta, const uint32_t key[2],
                             uint32_t particle, uint32_t event) {
   const int32_t base = orc_param_entry(P, type, E, eta);
-  if (!P->energy_interp) return base;
+  if (!P->energy_interp || E < FLT_MIN) return base; /* subnormal energies are not interpolated */
   int ex = 0;
   const double m = 2.0 * frexp((double)E, &ex); /* E = m * 2^(ex - 1), m in [1, 2) */
   const uint32_t ctr[4] = {0u, (uint32_t)PURPOSE_EBIN << 16, particle, event};

@@ -70,7 +70,7 @@ int32_t orc_param_entry(const orc_params* P, int32_t type, float E, float eta);
  * (m in [1, 2)) lies the fraction x = m - 1 of the way from the bin's point
  * 2^k to the next bin's 2^(k+1), and takes the next bin when the uniform
  * u = x0 2^-32 of Philox block (0, 2 << 16, particle in event, event) is
- * below x (exact in FP64). */
+ * below x (exact in FP64); subnormal E keeps its bin. */
 int32_t orc_param_entry_rng(const orc_params* P, int32_t type, float E, float eta, const uint32_t key[2],
                             uint32_t particle, uint32_t event);
 

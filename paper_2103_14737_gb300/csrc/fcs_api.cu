@@ -398,7 +398,7 @@ int enqueue_range(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, int32_t range
   const ScanTmp tmp{ws->block_sums};
   WsDev w = ws->view();
   FCS_CUDA(launch_task_counts(a.geo->d, a.prm->d, a.parts, ev_lo, ev_hi, k0, k1, a.first_event, w, tmp,
-                              a.n_particles, L));
+                              a.n_particles, a.cfg.energy_interp, L));
   if (sync_size || a.cfg.batched == 2) {
     FCS_CUDA(cudaMemcpyAsync(ws->h_sizes, ws->d_sizes, sizeof(Sizes), cudaMemcpyDeviceToHost, a.s));
     FCS_CUDA(cudaStreamSynchronize(a.s));
@@ -494,6 +494,8 @@ int validate_config(const fcs_config& c) {
   if (!(blk == 0 || blk == 128 || blk == 256 || blk == 512))
     return set_err(FCS_E_ARG, "config.block must be 0, 128, 256 or 512");
   if (c.wave_events < 0) return set_err(FCS_E_ARG, "config.wave_events must be >= 0");
+  if (c.energy_interp != 0 && c.energy_interp != 1) return set_err(FCS_E_ARG, "config.energy_interp must be 0 or 1");
+  if (c.reserved) return set_err(FCS_E_ARG, "config.reserved must be 0");
   if (c.use_graph && c.sync) return set_err(FCS_E_ARG, "config.use_graph requires sync == 0");
   return FCS_OK;
 }
@@ -946,6 +948,7 @@ int fcs_autotune(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws, c
   c.mode = config->mode;
   c.batched = 1;
   c.wave_events = config->wave_events;
+  c.energy_interp = config->energy_interp;
   c.sync = 1;
   // sizes the workspace and validates the arguments
   FCS_TRY(fcs_simulate_events(geo, prm, ws, particles, n_particles, n_events, seed, first_event, &c, nullptr, nullptr,
@@ -1092,7 +1095,8 @@ int fcs_simulate_backward(const fcs_geo* geo, const fcs_params* prm, fcs_workspa
     const int32_t hi = std::min(n_events, lo + rows);
     k_range_begin<<<1, 1, 0, s>>>(ws->d_sizes, particles->event_offsets, lo, hi, n_particles, ws->pcap);
     WsDev w = ws->view();
-    FCS_CUDA(launch_task_counts(geo->d, prm->d, *particles, lo, hi, k0, k1, first_event, w, tmp, n_particles, L));
+    FCS_CUDA(launch_task_counts(geo->d, prm->d, *particles, lo, hi, k0, k1, first_event, w, tmp, n_particles,
+                                cfg.energy_interp, L));
     if (cfg.sync) {
       FCS_CUDA(cudaMemcpyAsync(ws->h_sizes, ws->d_sizes, sizeof(Sizes), cudaMemcpyDeviceToHost, s));
       FCS_CUDA(cudaStreamSynchronize(s));

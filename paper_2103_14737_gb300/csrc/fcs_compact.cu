@@ -10,7 +10,8 @@ namespace fcs {
 namespace {
 
 constexpr int kCThreads = 256;
-constexpr int kCItems = 8;  // two float4 per thread
+constexpr int kCItems = 16;  // four float4 per thread (rows are padded to 64 cells)
+constexpr int kCVec = kCItems / 4;
 constexpr int kChunk = kCThreads * kCItems;
 
 __global__ void __launch_bounds__(kCThreads) k_compact_count(const float* __restrict__ acc, int32_t n_cells,
@@ -21,10 +22,16 @@ __global__ void __launch_bounds__(kCThreads) k_compact_count(const float* __rest
   const float4* src = reinterpret_cast<const float4*>(acc + (int64_t)row * stride + c0);
   int cnt = 0;
   if (c0 < n_cells) {
-    const float4 a = src[0], b = src[1];
-    const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    float4 a[kCVec];
 #pragma unroll
-    for (int k = 0; k < kCItems; ++k) cnt += (c0 + k < n_cells) && (v[k] != 0.0f);
+    for (int q = 0; q < kCVec; ++q) a[q] = src[q];
+#pragma unroll
+    for (int q = 0; q < kCVec; ++q) {
+      cnt += (c0 + 4 * q < n_cells) && (a[q].x != 0.0f);
+      cnt += (c0 + 4 * q + 1 < n_cells) && (a[q].y != 0.0f);
+      cnt += (c0 + 4 * q + 2 < n_cells) && (a[q].z != 0.0f);
+      cnt += (c0 + 4 * q + 3 < n_cells) && (a[q].w != 0.0f);
+    }
   }
   cnt = __reduce_add_sync(0xffffffffu, cnt);
   __shared__ int s[kCThreads / 32];
@@ -44,14 +51,22 @@ __global__ void __launch_bounds__(kCThreads) k_compact_write(
   const int chunk = blockIdx.x, row = blockIdx.y;
   const int64_t c0 = (int64_t)chunk * kChunk + threadIdx.x * kCItems;
   float4* src = reinterpret_cast<float4*>(acc + (int64_t)row * stride + c0);
-  float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  float v[kCItems];
+#pragma unroll
+  for (int k = 0; k < kCItems; ++k) v[k] = 0.0f;
   if (c0 < n_cells) {
-    const float4 a = src[0], b = src[1];
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    float4 a[kCVec];
+#pragma unroll
+    for (int q = 0; q < kCVec; ++q) a[q] = src[q];
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    src[0] = z;
-    src[1] = z;
+#pragma unroll
+    for (int q = 0; q < kCVec; ++q) {
+      v[4 * q] = a[q].x;
+      v[4 * q + 1] = a[q].y;
+      v[4 * q + 2] = a[q].z;
+      v[4 * q + 3] = a[q].w;
+      src[q] = z;
+    }
   }
   unsigned mask = 0;
 #pragma unroll
@@ -99,8 +114,9 @@ __global__ void __launch_bounds__(kCThreads) k_compact_write(
   if (cells_out && c0 < n_cells) {
     float* dst = cells_out + (int64_t)(ev_lo + row) * n_cells + c0;
     if (c0 + kCItems <= n_cells && (n_cells & 3) == 0) {
-      reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
-      reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+#pragma unroll
+      for (int q = 0; q < kCVec; ++q)
+        reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     } else {
 #pragma unroll
       for (int k = 0; k < kCItems; ++k)

@@ -146,6 +146,7 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 // (index, layer | purpose << 16, particle in event, event).
 constexpr uint32_t kPurposeHit = 0u;
 constexpr uint32_t kPurposePoisson = 1u;
+constexpr uint32_t kPurposeEnergyBin = 2u;
 
 __device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
   return __dmul_rn(__dadd_rn(__dmul_rn((double)(a >> 5), 67108864.0), (double)(b >> 6)),
@@ -181,7 +182,7 @@ cudaError_t launch_scan_u32(const uint32_t* in, int64_t* out, int64_t n, ScanTmp
 cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_particles& parts,
                                int32_t ev_lo, int32_t ev_hi, uint32_t k0, uint32_t k1,
                                int64_t first_event, WsDev w, ScanTmp tmp, int64_t n_part_max,
-                               const Launch& L);
+                               int energy_interp, const Launch& L);
 cudaError_t launch_task_finish(WsDev w, const fcs_debug* dbg, int det, int64_t n_task_max, const Launch& L);
 
 // fcs_hits.cu: what the hit kernel does with a certified hit

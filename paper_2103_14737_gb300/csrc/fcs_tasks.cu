@@ -287,10 +287,25 @@ __device__ __forceinline__ uint32_t layer_mask(const ParamDev& p, int64_t row, f
   return mask;
 }
 
+// Energy-bin interpolation: E = m 2^k (m in [1, 2)) takes the next energy
+// bin (clamped to the last) with probability m - 1, decided exactly in
+// integers: word 0 of Philox block (0, 2 << 16, particle in event, event)
+// below the 23 mantissa bits of E shifted left by 9.
+__device__ __forceinline__ int32_t interp_entry(const ParamDev& p, int32_t entry, float E, uint32_t pin,
+                                                uint32_t event, uint32_t k0, uint32_t k1) {
+  const uint32_t x0 = philox4x32_10(make_uint4(0u, kPurposeEnergyBin << 16, pin, event), k0, k1).x;
+  const uint32_t bits = __float_as_uint(E);
+  if ((bits >> 23) == 0 || x0 >= ((bits & 0x7FFFFFu) << 9)) return entry;  // subnormal E: m < 1
+  const int32_t hb = entry % p.NH, teb = entry / p.NH;
+  const int32_t eb = teb % p.NE, t = teb / p.NE;
+  return (t * p.NE + min(eb + 1, p.NE - 1)) * p.NH + hb;
+}
+
 // Per particle: its checks, parametrisation entry, event and layer mask; the
 // task count feeds the scan of task offsets.
 __global__ void __launch_bounds__(128) k_particle_count(const ParamDev p, const fcs_particles parts, int32_t ev_lo,
-                                                        int32_t ev_hi, WsDev w) {
+                                                        int32_t ev_hi, WsDev w, int energy_interp, uint32_t k0,
+                                                        uint32_t k1, uint32_t first_event_lo) {
   const int64_t pb = parts.event_offsets[ev_lo];
   const int64_t P = w.sizes->n_part;  // checked against the capacity and n_particles
   for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < P;
@@ -302,9 +317,11 @@ __global__ void __launch_bounds__(128) k_particle_count(const ParamDev p, const 
     if (!particle_ok(p, t, E, eta, phi)) {
       atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_BAD_PARTICLE);
     } else {
-      const int32_t entry = param_entry(p, t, E, eta);
-      info = make_uint4((uint32_t)entry, (uint32_t)event_of(parts.event_offsets, ev_lo, ev_hi, i),
-                        layer_mask(p, (int64_t)entry * p.NL, E), 0u);
+      int32_t entry = param_entry(p, t, E, eta);
+      const int32_t e = event_of(parts.event_offsets, ev_lo, ev_hi, i);
+      if (energy_interp)
+        entry = interp_entry(p, entry, E, (uint32_t)(i - parts.event_offsets[e]), first_event_lo + (uint32_t)e, k0, k1);
+      info = make_uint4((uint32_t)entry, (uint32_t)e, layer_mask(p, (int64_t)entry * p.NL, E), 0u);
     }
     w.pcount[li] = __popc(info.z);
     w.pinfo[li] = info;
@@ -527,11 +544,11 @@ int grid_for(int64_t n, const Launch& L) {
 
 cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_particles& parts, int32_t ev_lo,
                                int32_t ev_hi, uint32_t k0, uint32_t k1, int64_t first_event, WsDev w, ScanTmp tmp,
-                               int64_t n_part_max, const Launch& L) {
+                               int64_t n_part_max, int energy_interp, const Launch& L) {
   // one thread per particle / task where the grid allows (these kernels wait
   // on dependent loads: more threads in flight, not fewer, hide them)
   const int gp = grid_for(n_part_max, L);
-  k_particle_count<<<gp, 128, 0, L.s>>>(p, parts, ev_lo, ev_hi, w);
+  k_particle_count<<<gp, 128, 0, L.s>>>(p, parts, ev_lo, ev_hi, w, energy_interp, k0, k1, (uint32_t)first_event);
   cudaError_t e = launch_scan_i64(w.pcount, w.poff, &w.sizes->n_part, 0, &w.sizes->n_tasks, 0, tmp, L.s);
   if (e != cudaSuccess) return e;
   k_task_init<<<gp, 128, 0, L.s>>>(g, p, parts, ev_lo, w);

@@ -48,7 +48,8 @@ class fcs_particles(C.Structure):
 class fcs_config(C.Structure):
     _fields_ = [("mode", C.c_int32), ("batched", C.c_int32), ("hits_per_thread", C.c_int32),
                 ("block", C.c_int32), ("sync", C.c_int32), ("use_graph", C.c_int32),
-                ("timing", C.c_int32), ("wave_events", C.c_int32)]
+                ("timing", C.c_int32), ("wave_events", C.c_int32), ("energy_interp", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class fcs_stats(C.Structure):
@@ -215,10 +216,11 @@ def fcs_workspace_free(ws):
 
 
 def make_config(mode=MODE_ATOMIC, batched=1, hits_per_thread=0, block=0, sync=1, use_graph=0, timing=0,
-                wave_events=0):
+                wave_events=0, energy_interp=0):
     c = fcs_config()
     c.mode, c.batched, c.hits_per_thread, c.block, c.sync, c.use_graph, c.timing, c.wave_events = \
         mode, batched, hits_per_thread, block, sync, use_graph, timing, wave_events
+    c.energy_interp = energy_interp
     return c
 
 
@@ -376,7 +378,7 @@ class Simulator:
 
     def simulate(self, dparts, seed, first_event=0, mode=MODE_ATOMIC, batched=1, hits_per_thread=0, block=0,
                  sync=1, use_graph=0, dense=False, capacity=None, debug_tasks=0, debug_hits=0, outputs=None,
-                 check=True, timing=0, wave_events=0):
+                 check=True, timing=0, wave_events=0, energy_interp=0):
         """Runs one call.  dparts: dict of device tensors (see to_device).
         Returns a dict with cell_ids, cell_E, event_offsets (device tensors),
         cells (dense, if requested), stats, status and debug dumps."""
@@ -409,7 +411,7 @@ class Simulator:
                 dbg.hit_cell = res["hit_cell"].data_ptr()
                 dbg.hit_bin = res["hit_bin"].data_ptr()
                 dbg.hit_capacity = debug_hits
-        cfg = make_config(mode, batched, hits_per_thread, block, sync, use_graph, timing, wave_events)
+        cfg = make_config(mode, batched, hits_per_thread, block, sync, use_graph, timing, wave_events, energy_interp)
         rc, st = fcs_simulate_events(self.geo, self.prm, self.ws, parts, n_particles, n_events, seed, first_event,
                                      cfg, outputs.get("cells"), outputs.get("cell_ids"), outputs.get("cell_E"),
                                      outputs.get("event_offsets"),
@@ -428,7 +430,7 @@ class Simulator:
         fcs_update_params(self.prm, frac, mean_hit_E, shape_w)
 
     def backward(self, dparts, seed, dL_dcells, first_event=0, d_frac=None, d_shape_w=None, batched=1,
-                 hits_per_thread=0, block=0, sync=1, check=True, wave_events=0):
+                 hits_per_thread=0, block=0, sync=1, check=True, wave_events=0, energy_interp=0):
         """Gradients of a loss with dL/dE_cell = dL_dcells ([n_events][n_cells]
         float32 on the device) with respect to the layer fractions and shape
         weights; accumulated into d_frac / d_shape_w (flat float32 device
@@ -446,7 +448,7 @@ class Simulator:
             raise ValueError("dL_dcells must be float32 [n_events][n_cells]")
         parts = fcs_particles(dparts["type"].data_ptr(), dparts["E"].data_ptr(), dparts["eta"].data_ptr(),
                               dparts["phi"].data_ptr(), dparts["event_offsets"].data_ptr())
-        cfg = make_config(MODE_ATOMIC, batched, hits_per_thread, block, sync, 0, 0, wave_events)
+        cfg = make_config(MODE_ATOMIC, batched, hits_per_thread, block, sync, 0, 0, wave_events, energy_interp)
         rc, st = fcs_simulate_backward(self.geo, self.prm, self.ws, parts, n_particles, n_events, seed, first_event,
                                        cfg, g, d_frac, d_shape_w, check=check)
         return dict(d_frac=d_frac, d_shape_w=d_shape_w, status=rc, stats=st.as_dict(), _keep=(parts, cfg, g))

@@ -36,7 +36,7 @@ def test_exports_every_declared_symbol(lib):
 def test_struct_layouts():
     assert synth.REGION_DTYPE.itemsize == 48 and synth.LAYER_DTYPE.itemsize == 16
     assert C.sizeof(fcs.fcs_particles) == 40
-    assert C.sizeof(fcs.fcs_config) == 32
+    assert C.sizeof(fcs.fcs_config) == 40
     assert C.sizeof(fcs.fcs_stats) == 40
     assert C.sizeof(fcs.fcs_debug) == 72
 

@@ -74,6 +74,19 @@ def test_backward_vs_oracle(sim, ogeo, oprm, prm, case):
     check_grad(r["d_frac"], r["d_shape_w"], ref_f, ref_w, sc_f, sc_w)
 
 
+def test_backward_energy_interpolation(sim, ogeo, prm):
+    """The adjoint with interpolated energy bins follows the forward's entries."""
+    oprm_i = O.OracleParams(prm, energy_interp=1)
+    parts, seed = synth.ttbar_like(6, 2, n=100), 13
+    rng = np.random.default_rng(8)
+    g = rng.normal(size=(parts.n_events, sim.n_cells)).astype(np.float32)
+    r = sim.backward(sim.to_device(parts), seed, torch.as_tensor(g, device="cuda"), energy_interp=1)
+    torch.cuda.synchronize()
+    ref_f, ref_w = O.backward(ogeo, oprm_i, parts, seed, g.astype(np.float64))
+    sc_f, sc_w = grad_scales(ogeo, oprm_i, prm, parts, seed, g.astype(np.float64))
+    check_grad(r["d_frac"], r["d_shape_w"], ref_f, ref_w, sc_f, sc_w)
+
+
 def test_backward_accumulates_and_offsets(sim, ogeo, oprm, prm):
     """Outputs accumulate; first_event selects the random streams."""
     parts, seed, fe = synth.ttbar_like(4, 1), 3, 1000

@@ -159,6 +159,24 @@ def test_per_task_launches(sim, ogeo, oprm, block, hpt):
     assert np.array_equal(got["cells"].cpu().numpy().view(np.uint32), ref.cells_canon.view(np.uint32))
 
 
+@pytest.mark.parametrize("mode", [fcs.MODE_ATOMIC, fcs.MODE_DETERMINISTIC])
+def test_energy_interpolation(sim, ogeo, prm, mode):
+    """Probabilistic energy-bin interpolation: tasks, hits and cells as the
+    oracle with the same option."""
+    oprm_i = O.OracleParams(prm, energy_interp=1)
+    parts = synth.pileup(seed=15, n_events=3, mu_pu=10)
+    ref = O.simulate(ogeo, oprm_i, parts, seed=6, first_event=2, hit_cap=10**7)
+    got = sim.simulate(sim.to_device(parts), 6, first_event=2, mode=mode, dense=True, energy_interp=1,
+                       debug_tasks=ref.n_tasks, debug_hits=ref.n_hits)
+    check_tasks_hits(ref, got)
+    if mode == fcs.MODE_DETERMINISTIC:
+        assert np.array_equal(got["cells"].cpu().numpy().view(np.uint32), ref.cells_canon.view(np.uint32))
+    else:
+        check_cells_atomic(ref, got, 3)
+    plain = O.simulate(ogeo, O.OracleParams(prm), parts, seed=6, first_event=2)
+    assert plain.n_tasks != ref.n_tasks or not np.array_equal(plain.task_n, ref.task_n)
+
+
 def test_poisson_counts_wide_mu(sim, ogeo, oprm):
     """Hit counts over mu from ~1e-2 to ~1e5 (inversion, FP32-certified PTRS,
     the FP64-only large-mu path) equal the oracle's draw for draw."""
