@@ -202,8 +202,11 @@ void fcs_free_params(fcs_params* prm);
 /* Workspace: the intermediate device buffers of a simulation call (task
  * records, tile map, FP64-recheck queue, accumulation array, sort keys).  The
  * library allocates them with cudaMalloc and grows them on demand during
- * sync calls; fcs_workspace_reserve sizes them ahead of sync == 0 calls and
- * graph capture.  Pointers stay fixed until the next growth. */
+ * sync calls: the first sync call on a workspace reads the hit count back
+ * mid-call to size it; later sync calls run without that round trip and, if
+ * a call outgrows the workspace, grow it and run the call once more.
+ * fcs_workspace_reserve sizes them ahead of sync == 0 calls and graph
+ * capture.  Pointers stay fixed until the next growth. */
 int fcs_workspace_create(fcs_workspace** out);
 int fcs_workspace_reserve(fcs_workspace* ws, const fcs_geo* geo, int64_t n_particles,
                           int32_t n_events, int64_t n_hits, int32_t mode);
@@ -257,8 +260,11 @@ int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace
  * particle arrays (host SoA, same layout as fcs_particles, event_offsets on
  * the host) are copied to the device, simulated, and the compacted result
  * copied back into host cell_ids / cell_E / event_offsets_out (capacity
- * entries).  Always synchronous.  Pinned host memory gives the fastest
- * copies; pageable memory works. */
+ * entries).  Always synchronous.  When every output array is mapped pinned
+ * host memory (cudaMallocHost, cudaHostAlloc(Mapped) or a registered range;
+ * the device address is taken with cudaPointerGetAttributes), the compaction
+ * kernel writes the results there directly and no device-to-host copy runs.
+ * Pageable memory works through device staging and copies. */
 int fcs_simulate_events_host(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
                              const int32_t* type, const float* E, const float* eta,
                              const float* phi, const int64_t* event_offsets,

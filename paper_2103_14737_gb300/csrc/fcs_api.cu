@@ -500,6 +500,17 @@ int validate_config(const fcs_config& c) {
   return FCS_OK;
 }
 
+// Device address of a mapped pinned host allocation, else NULL.
+void* mapped_host(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return (at.type == cudaMemoryTypeHost && at.devicePointer) ? at.devicePointer : nullptr;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -922,13 +933,18 @@ int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace
     FCS_CUDA(cudaGraphLaunch(ws->graph, s));
     return ok();
   }
-  FCS_TRY(enqueue_call(a, cfg.sync != 0 && cfg.batched, hc, key_task_bits));
+  // A sync call reads the hit count back mid-call only while the workspace has
+  // never been sized for hits; later calls run optimistically and are redone
+  // once, with the workspace grown, if they outgrow it (a call that overflows
+  // deposits nothing beyond the flag and leaves the accumulation rows zero).
+  const bool size_mid_call = cfg.sync != 0 && cfg.batched == 1 && ws->gmap_cap == 0;
+  FCS_TRY(enqueue_call(a, size_mid_call, hc, key_task_bits));
   if (!cfg.sync) return ok();
   FCS_CUDA(cudaMemcpyAsync(ws->h_sizes, ws->d_sizes, sizeof(Sizes), cudaMemcpyDeviceToHost, s));
   FCS_CUDA(cudaStreamSynchronize(s));
-  if ((ws->h_sizes->flags & FCS_FLAG_HIT_CAPACITY) && !cfg.batched) {
-    // per-event sync call that outgrew the workspace: size it for the largest
-    // event seen (the whole call's hits bound it) and run again
+  if (ws->h_sizes->flags & FCS_FLAG_HIT_CAPACITY) {
+    // the call outgrew the workspace: size it for the whole call's hits (they
+    // bound every event range's) and run again
     FCS_TRY(ws_reserve_hits(ws, ws->h_sizes->hit_base, cfg.mode));
     FCS_TRY(enqueue_call(a, false, hc, key_task_bits));
     FCS_CUDA(cudaMemcpyAsync(ws->h_sizes, ws->d_sizes, sizeof(Sizes), cudaMemcpyDeviceToHost, s));
@@ -1032,6 +1048,33 @@ int fcs_simulate_events_host(const fcs_geo* geo, const fcs_params* prm, fcs_work
   FCS_CUDA(cudaMemcpyAsync(d_off, event_offsets, (size_t)(n_events + 1) * 8, cudaMemcpyHostToDevice, s));
   fcs_particles parts{d_type, d_E, d_eta, d_phi, d_off};
   fcs_stats st{};
+  // Output buffers in mapped pinned host memory (cudaMallocHost, or torch's
+  // pin_memory) are written by the compaction kernel directly, over the
+  // CPU-GPU link, instead of through device staging and copies.
+  int64_t* m_oout = (int64_t*)mapped_host(event_offsets_out);
+  int32_t* m_ids = cell_ids ? (int32_t*)mapped_host(cell_ids) : nullptr;
+  float* m_cE = cell_ids ? (float*)mapped_host(cell_E) : nullptr;
+  const bool direct = m_oout && (!cell_ids || (m_ids && m_cE));
+  if (direct) {
+    // once the workspace is sized, replay the call's CUDA graph and read the
+    // status; a call that outgrew the workspace runs again synchronously
+    if (cfg.batched == 1 && ws->gmap_cap > 0) {
+      fcs_config gcfg = cfg;
+      gcfg.sync = 0;
+      gcfg.use_graph = 1;
+      gcfg.timing = 0;
+      FCS_TRY(fcs_simulate_events(geo, prm, ws, &parts, n_particles, n_events, seed, first_event, &gcfg, nullptr,
+                                  m_ids, m_cE, m_oout, capacity, nullptr, nullptr, s));
+      FCS_CUDA(cudaMemcpyAsync(ws->h_sizes, ws->d_sizes, sizeof(Sizes), cudaMemcpyDeviceToHost, s));
+      FCS_CUDA(cudaStreamSynchronize(s));
+      if (!(ws->h_sizes->flags & FCS_FLAG_HIT_CAPACITY)) return status_from(*ws->h_sizes, stats);
+      FCS_TRY(ws_reserve_hits(ws, ws->h_sizes->hit_base, cfg.mode));
+    }
+    const int rc = fcs_simulate_events(geo, prm, ws, &parts, n_particles, n_events, seed, first_event, &cfg, nullptr,
+                                       m_ids, m_cE, m_oout, capacity, &st, nullptr, s);
+    if (stats) *stats = st;
+    return rc;
+  }
   const int rc = fcs_simulate_events(geo, prm, ws, &parts, n_particles, n_events, seed, first_event, &cfg, nullptr,
                                      cell_ids ? d_ids : nullptr, cell_ids ? d_cE : nullptr, d_oout, capacity, &st,
                                      nullptr, s);

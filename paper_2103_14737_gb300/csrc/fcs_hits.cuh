@@ -182,13 +182,13 @@ __device__ __forceinline__ uint32_t task_lay(const HitSmemTables& tb, int layer,
 // A task as the hit loop uses it, staged in shared memory per tile (48 B):
 // 32-bit offsets and the Philox counter words are formed once per task.
 struct TileTask {
-  int32_t rel;      // hit_begin - first hit of the tile (<= 0 for the tile's first task)
+  int32_t rel;      // first hit of the task - first hit of the tile (<= 0 for the tile's first task)
   int32_t entry;    // parametrisation entry (with layer)
   float Ehit, eta_c, phi_c, s_eta, s_phi;
   uint32_t ctr_y;   // layer | purpose << 16
   uint32_t ctr_z;   // particle in event
   uint32_t ctr_w;   // event number of the random stream
-  uint32_t row_off; // accumulation row offset (atomic) or row * n_cells (deterministic)
+  uint32_t row_off; // row * acc_stride (atomic, deterministic) or row * n_cells (gradient)
   uint32_t lay;     // layer | first region << 8 | end region << 20 (the reachable regions)
 };
 static_assert(sizeof(TileTask) == 48, "TileTask layout");

@@ -1,6 +1,6 @@
 // fcs_scan.cu - device-wide exclusive scan of int64 counts (reduce, scan of
 // block sums, downsweep).  Used for particle -> task / hit offsets, the
-// compaction offsets and the radix-sort digit offsets.  The element count may
+// compaction offsets and the deterministic mode's cell offsets.  The element count may
 // live in device memory, so the launches need no host synchronisation.
 #include "fcs_internal.cuh"
 

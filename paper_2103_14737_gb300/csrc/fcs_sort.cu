@@ -33,10 +33,14 @@ constexpr uint64_t kEmpty = ~0ull;
 constexpr int kRegSortMax = 8;         // segments sorted in registers
 constexpr int kInsertionMax = 32;      // then insertion sort in place, heapsort beyond
 
+// A range that outgrew the workspace (FCS_FLAG_HIT_CAPACITY) has slots the
+// hit kernel did not write: the scatter and the fold then do nothing (the
+// call reports the overflow; the compaction still re-zeroes the rows).
 __global__ void __launch_bounds__(256) k_det_scatter(const uint64_t* __restrict__ slots, const Sizes* sz, int64_t cap,
                                                      int cell_shift, uint32_t* __restrict__ counters,
-                                                     const int64_t* __restrict__ cell_off,
+                                                     const int64_t* __restrict__ cell_off, int64_t n_cells_all,
                                                      uint64_t* __restrict__ out) {
+  if (sz->flags & FCS_FLAG_HIT_CAPACITY) return;
   const int64_t n = min(sz->n_hits, cap);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
@@ -47,8 +51,9 @@ __global__ void __launch_bounds__(256) k_det_scatter(const uint64_t* __restrict_
     for (int j = 0; j < 4; ++j) {
       if (k[j] == kEmpty) continue;
       const uint64_t c = k[j] >> cell_shift;
+      if (c >= (uint64_t)n_cells_all) continue;  // cannot happen for records of this range
       const int64_t pos = cell_off[c] + (int64_t)atomicSub(counters + c, 1u) - 1;
-      out[pos] = k[j];
+      if (pos >= 0 && pos < cap) out[pos] = k[j];
     }
   }
 }
@@ -140,10 +145,11 @@ __global__ void __launch_bounds__(256) k_det_fold(uint64_t* __restrict__ recs, c
                                                   int64_t n_cells_all, const Sizes* sz, int64_t cap,
                                                   uint64_t task_mask, const float* __restrict__ task_ehit,
                                                   float* __restrict__ acc) {
+  if (sz->flags & FCS_FLAG_HIT_CAPACITY) return;
   const int64_t total = min(sz->n_records, cap);
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells_all;
        c += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t a = cell_off[c], b = (c + 1 < n_cells_all) ? cell_off[c + 1] : total;
+    const int64_t a = cell_off[c], b = min((c + 1 < n_cells_all) ? cell_off[c + 1] : total, cap);
     if (a >= b) continue;
     uint64_t* seg = recs + a;
     const int64_t n = b - a;
@@ -173,7 +179,7 @@ cudaError_t launch_det_reduce(const GeoDev& g, WsDev w, int32_t rows, int key_ta
   const int cell_shift = kRecordCountBits + key_task_bits;
   const uint64_t task_mask = (key_task_bits >= 64) ? ~0ull : ((1ull << key_task_bits) - 1ull);
   k_det_scatter<<<L.num_sms * 8, 256, 0, L.s>>>(w.keys, w.sizes, w.rec_cap, cell_shift, counters, cell_off,
-                                                w.keys_alt);
+                                                n_cells_all, w.keys_alt);
   k_det_fold<<<L.num_sms * 8, 256, 0, L.s>>>(w.keys_alt, cell_off, n_cells_all, w.sizes, w.rec_cap, task_mask,
                                              w.tmu, w.acc);
   return cudaGetLastError();

@@ -286,6 +286,43 @@ def test_host_entry_point_matches(sim):
     assert np.array_equal(E[:n].view(np.uint32), ref["cell_E"][:n].cpu().numpy().view(np.uint32))
 
 
+def test_host_entry_point_pinned_outputs(sim):
+    """Mapped pinned host outputs are written by the device directly."""
+    parts = synth.pileup(seed=16, n_events=3, mu_pu=20)
+    ref = sim.simulate(sim.to_device(parts), 4, mode=fcs.MODE_DETERMINISTIC)
+    cap = ref["stats"]["n_nonzero"] + 10
+    ids = torch.full((cap,), -1, dtype=torch.int32).pin_memory()
+    E = torch.zeros(cap, dtype=torch.float32).pin_memory()
+    off = torch.zeros(4, dtype=torch.int64).pin_memory()
+    cfg = fcs.make_config(mode=fcs.MODE_DETERMINISTIC)
+    rc, st = fcs.fcs_simulate_events_host(sim.geo, sim.prm, sim.ws, parts.type, parts.E, parts.eta, parts.phi,
+                                          parts.event_offsets, 4, 0, cfg, ids.numpy(), E.numpy(), off.numpy())
+    n = st.n_nonzero
+    assert rc == 0 and n == ref["stats"]["n_nonzero"]
+    assert np.array_equal(off.numpy(), ref["event_offsets"].cpu().numpy())
+    assert np.array_equal(ids.numpy()[:n], ref["cell_ids"][:n].cpu().numpy())
+    assert np.array_equal(E.numpy()[:n].view(np.uint32), ref["cell_E"][:n].cpu().numpy().view(np.uint32))
+    assert (ids.numpy()[n:] == -1).all()
+
+
+def test_sync_call_outgrows_workspace(geo, prm, ogeo, oprm):
+    """A fresh workspace is sized by its first call; a larger later call
+    overflows it, grows it and runs again with the same results."""
+    s = fcs.Simulator(geo, prm)
+    try:
+        small = synth.single_particle(1)
+        s.simulate(s.to_device(small), 2, mode=fcs.MODE_DETERMINISTIC)
+        big = synth.pileup(seed=17, n_events=2, mu_pu=30)
+        got = s.simulate(s.to_device(big), 5, mode=fcs.MODE_DETERMINISTIC, dense=True)
+        ref = O.simulate(ogeo, oprm, big, seed=5)
+        assert got["stats"]["n_hits"] == ref.n_hits
+        assert np.array_equal(got["cells"].cpu().numpy().view(np.uint32), ref.cells_canon.view(np.uint32))
+        got2 = s.simulate(s.to_device(big), 5, dense=True)
+        check_cells_atomic(ref, got2, 2)
+    finally:
+        s.close()
+
+
 def test_autotune_picks_a_valid_shape(sim, ogeo, oprm):
     parts = synth.pileup(seed=13, n_events=2, mu_pu=20)
     d = sim.to_device(parts)
