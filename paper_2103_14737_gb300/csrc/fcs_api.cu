@@ -304,7 +304,7 @@ __global__ void k_range_begin(Sizes* s, const int64_t* __restrict__ off, int32_t
   s->n_hits = 0;
   s->n_recheck = 0;
   s->n_records = 0;
-  s->n_rec_used = 0;
+  s->n_big = 0;
   s->n_pdefer = 0;
   s->queue = 0;
 }

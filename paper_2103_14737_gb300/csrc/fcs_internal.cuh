@@ -96,7 +96,7 @@ struct Sizes {
   int64_t hit_base;     //   (per-event mode; offsets of the debug dumps)
   int64_t recheck_total;  // recheck hits over the call
   int64_t n_part;       // particles of the current event range (checked against the capacity)
-  int64_t n_rec_used;   // deterministic records sorted (n_records clamped to the capacity)
+  int64_t n_big;        // deterministic mode: cells with more records than one thread sorts
   int64_t n_pdefer;     // draws deferred to FP64 in the current range
   unsigned long long queue;  // hit-kernel work-queue counter (tiles handed out)
   uint32_t flags;       // fcs_device_flag bits

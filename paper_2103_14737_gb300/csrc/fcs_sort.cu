@@ -16,12 +16,12 @@
 //      record array;
 //   2. scatter: every record takes a place in its cell's segment; the
 //      counter, counted down, hands out the places and ends at zero;
-//   3. fold: one thread per cell sorts its segment by (task, count) (in
-//      registers with an odd-even transposition network up to 8 records,
-//      insertion sort in place up to 32, heapsort beyond), merges the records
-//      of a task (their counts add exactly) and folds; the float result goes
-//      to the accumulation row, where the compaction of the atomic mode picks
-//      it up and re-zeroes it.
+//   3. fold: one thread per cell sorts its segment by (task, count) in place
+//      (insertion, up to 32 records), merges the records of a task (their
+//      counts add exactly) and folds; a warp per longer segment sorts it in
+//      shared memory (bitonic) before its first lane folds.  The float result
+//      goes to the accumulation row, where the compaction of the atomic mode
+//      picks it up and re-zeroes it.
 // Only the order of places inside a segment depends on scheduling, and the
 // sort removes it, so the cells are bit-reproducible.
 #include "fcs_internal.cuh"
@@ -30,8 +30,7 @@ namespace fcs {
 namespace {
 
 constexpr uint64_t kEmpty = ~0ull;
-constexpr int kRegSortMax = 8;         // segments sorted in registers
-constexpr int kInsertionMax = 32;      // then insertion sort in place, heapsort beyond
+constexpr int kInsertionMax = 32;  // segments sorted in place by insertion up to here, heapsort beyond
 
 // A range that outgrew the workspace (FCS_FLAG_HIT_CAPACITY) has slots the
 // hit kernel did not write: the scatter and the fold then do nothing (the
@@ -71,7 +70,7 @@ __device__ __forceinline__ void sift_down(uint64_t* a, int64_t root, int64_t n) 
   }
 }
 
-// Ascending sort of a[0, n) in place (n > kRegSortMax).
+// Ascending sort of a[0, n) in place.
 __device__ __noinline__ void sort_segment(uint64_t* a, int64_t n) {
   if (n <= kInsertionMax) {
     for (int64_t i = 1; i < n; ++i) {
@@ -92,12 +91,6 @@ __device__ __noinline__ void sort_segment(uint64_t* a, int64_t n) {
     a[e] = t;
     sift_down(a, 0, e);
   }
-}
-
-__device__ __forceinline__ void cmp_swap(uint64_t& x, uint64_t& y) {
-  const uint64_t lo = x < y ? x : y, hi = x < y ? y : x;
-  x = lo;
-  y = hi;
 }
 
 // One step of the fold of a cell's records in ascending order: per task the
@@ -121,50 +114,96 @@ struct Fold {
   }
 };
 
-// Up to N records: loaded into registers (padded with the largest key),
-// sorted by an N-round odd-even transposition network, folded.
-template <int N>
-__device__ __forceinline__ float fold_small(const uint64_t* __restrict__ seg, int n, uint64_t task_mask,
-                                            const float* __restrict__ task_ehit) {
-  uint64_t r[N];
-#pragma unroll
-  for (int j = 0; j < N; ++j) r[j] = j < n ? seg[j] : ~0ull;
-#pragma unroll
-  for (int round = 0; round < N; ++round) {
-#pragma unroll
-    for (int j = round & 1; j + 1 < N; j += 2) cmp_swap(r[j], r[j + 1]);
-  }
-  Fold f;
-#pragma unroll
-  for (int j = 0; j < N; ++j)
-    if (j < n) f.add(r[j], task_mask, task_ehit);
-  return f.result(task_ehit);
-}
-
+// One thread per cell: segments of up to kInsertionMax records are sorted in
+// place by insertion and folded; longer ones are listed for k_det_fold_big.
 __global__ void __launch_bounds__(256) k_det_fold(uint64_t* __restrict__ recs, const int64_t* __restrict__ cell_off,
-                                                  int64_t n_cells_all, const Sizes* sz, int64_t cap,
-                                                  uint64_t task_mask, const float* __restrict__ task_ehit,
-                                                  float* __restrict__ acc) {
+                                                  int64_t n_cells_all, Sizes* sz, int64_t cap, uint64_t task_mask,
+                                                  const float* __restrict__ task_ehit, float* __restrict__ acc,
+                                                  int64_t* __restrict__ big) {
   if (sz->flags & FCS_FLAG_HIT_CAPACITY) return;
   const int64_t total = min(sz->n_records, cap);
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells_all;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t a = cell_off[c], b = min((c + 1 < n_cells_all) ? cell_off[c + 1] : total, cap);
     if (a >= b) continue;
-    uint64_t* seg = recs + a;
     const int64_t n = b - a;
-    float E;
-    if (n <= 4) {
-      E = fold_small<4>(seg, (int)n, task_mask, task_ehit);
-    } else if (n <= kRegSortMax) {
-      E = fold_small<kRegSortMax>(seg, (int)n, task_mask, task_ehit);
-    } else {
-      sort_segment(seg, n);
-      Fold f;
-      for (int64_t j = 0; j < n; ++j) f.add(seg[j], task_mask, task_ehit);
-      E = f.result(task_ehit);
+    if (n > kInsertionMax) {
+      big[atomicAdd((unsigned long long*)&sz->n_big, 1ull)] = c;
+      continue;
     }
-    acc[c] = E;
+    uint64_t* seg = recs + a;
+    for (int64_t i = 1; i < n; ++i) {
+      const uint64_t v = seg[i];
+      int64_t j = i - 1;
+      while (j >= 0 && seg[j] > v) {
+        seg[j + 1] = seg[j];
+        --j;
+      }
+      seg[j + 1] = v;
+    }
+    Fold f;
+    for (int64_t j = 0; j < n; ++j) f.add(seg[j], task_mask, task_ehit);
+    acc[c] = f.result(task_ehit);
+  }
+}
+
+// One warp per long segment: a bitonic sort in shared memory (segments of up
+// to kBigMax records; longer ones take heapsort in place), then lane 0 folds.
+constexpr int kBigWarps = 4;
+constexpr int kBigMax = 1024;
+__global__ void __launch_bounds__(32 * kBigWarps) k_det_fold_big(uint64_t* __restrict__ recs,
+                                                                 const int64_t* __restrict__ cell_off,
+                                                                 int64_t n_cells_all, const Sizes* sz, int64_t cap,
+                                                                 uint64_t task_mask, const float* __restrict__ task_ehit,
+                                                                 float* __restrict__ acc,
+                                                                 const int64_t* __restrict__ big) {
+  __shared__ uint64_t s_rec[kBigWarps][kBigMax];
+  if (sz->flags & FCS_FLAG_HIT_CAPACITY) return;
+  const int64_t total = min(sz->n_records, cap);
+  const int64_t n_big = sz->n_big;
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  uint64_t* s = s_rec[wi];
+  for (int64_t q = (int64_t)blockIdx.x * kBigWarps + wi; q < n_big; q += (int64_t)gridDim.x * kBigWarps) {
+    const int64_t c = big[q];
+    const int64_t a = cell_off[c], b = min((c + 1 < n_cells_all) ? cell_off[c + 1] : total, cap);
+    const int64_t n = b - a;
+    uint64_t* seg = recs + a;
+    if (n > kBigMax) {
+      if (lane == 0) {
+        sort_segment(seg, n);
+        Fold f;
+        for (int64_t j = 0; j < n; ++j) f.add(seg[j], task_mask, task_ehit);
+        acc[c] = f.result(task_ehit);
+      }
+      __syncwarp();
+      continue;
+    }
+    int m = 1;
+    while (m < n) m <<= 1;
+    for (int j = lane; j < m; j += 32) s[j] = j < n ? seg[j] : ~0ull;
+    __syncwarp();
+    for (int k = 2; k <= m; k <<= 1) {
+      for (int jj = k >> 1; jj > 0; jj >>= 1) {
+        for (int i = lane; i < m; i += 32) {
+          const int l = i ^ jj;
+          if (l > i) {
+            const uint64_t x = s[i], y = s[l];
+            const bool up = (i & k) == 0;
+            if ((x > y) == up) {
+              s[i] = y;
+              s[l] = x;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    if (lane == 0) {
+      Fold f;
+      for (int64_t j = 0; j < n; ++j) f.add(s[j], task_mask, task_ehit);
+      acc[c] = f.result(task_ehit);
+    }
+    __syncwarp();
   }
 }
 
@@ -180,8 +219,12 @@ cudaError_t launch_det_reduce(const GeoDev& g, WsDev w, int32_t rows, int key_ta
   const uint64_t task_mask = (key_task_bits >= 64) ? ~0ull : ((1ull << key_task_bits) - 1ull);
   k_det_scatter<<<L.num_sms * 8, 256, 0, L.s>>>(w.keys, w.sizes, w.rec_cap, cell_shift, counters, cell_off,
                                                 n_cells_all, w.keys_alt);
-  k_det_fold<<<L.num_sms * 8, 256, 0, L.s>>>(w.keys_alt, cell_off, n_cells_all, w.sizes, w.rec_cap, task_mask,
-                                             w.tmu, w.acc);
+  // the slot array is free after the scatter: it lists the long segments
+  int64_t* big = reinterpret_cast<int64_t*>(w.keys);
+  k_det_fold<<<L.num_sms * 8, 256, 0, L.s>>>(w.keys_alt, cell_off, n_cells_all, w.sizes, w.rec_cap, task_mask, w.tmu,
+                                             w.acc, big);
+  k_det_fold_big<<<L.num_sms * 4, 32 * kBigWarps, 0, L.s>>>(w.keys_alt, cell_off, n_cells_all, w.sizes, w.rec_cap,
+                                                            task_mask, w.tmu, w.acc, big);
   return cudaGetLastError();
 }
 
