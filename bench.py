@@ -37,8 +37,8 @@ SEED = 1
 #   time per hit = sum over pipes of (algorithmic ops per hit / pipe peak),
 # with the algorithmic operation counts of one hit taken from the algorithm
 # (not from compiled code) and each pipe's peak derived from its lanes per SM
-# per clock x 152 SMs x 2070 MHz.  The lane counts of the integer, wide-multiply
-# and MUFU pipes are those the unit microbenchmarks show (fcs_microbench).
+# per clock x 152 SMs x 2070 MHz.  The lane counts are those the unit
+# microbenchmarks show (fcs_microbench; bench.py reports them as measured).
 OPS_PER_HIT = {
     # Philox4x32-10: 10 rounds x 2 (32 x 32 -> 64-bit) multiplies
     "mulwide": 20,
@@ -50,13 +50,18 @@ OPS_PER_HIT = {
     "fp32": 29,
     # sin, cos
     "mufu": 2,
+    # 32-bit shared-memory words read from the staged tables: the hit's region
+    # (eta_lo, 1/deta, phi_lo, 1/dphi, n_eta, n_phi, cell offset), its r bin
+    # (lo, width, hi) and alpha bin (lo, width); the per-task parameters are
+    # per task, not per hit
+    "lds": 12,
 }
 SMS, SM_MAX_MHZ = 152, 2070.0
 # DRAM bytes per hit of the hit kernel, from the committed ncu summary of its
 # 16-event capture (traffic grows with the hits): valid for the kernel version
 # captured there, None after a kernel change.
 K_HITS_DRAM_BYTES_PER_HIT = 4.26
-LANES_PER_SM_CLK = {"mulwide": 32, "int": 64, "fp32": 128, "mufu": 16}
+LANES_PER_SM_CLK = {"mulwide": 32, "int": 64, "fp32": 128, "mufu": 16, "lds": 32}
 
 
 def alu_bound_hits_per_s():
@@ -494,8 +499,17 @@ def main():
                  "mulwide_per_s": fcs.fcs_microbench(fcs.MB_MULWIDE, 0, 1024),
                  "lop3_steps_per_s": fcs.fcs_microbench(fcs.MB_LOP3, 0, 1024),
                  "ffma_per_s": fcs.fcs_microbench(fcs.MB_FFMA, 0, 1024),
+                 "mufu_sin_per_s": fcs.fcs_microbench(fcs.MB_MUFU, 0, 1024),
+                 "lds_words_per_s": fcs.fcs_microbench(fcs.MB_LDS, 0, 1024),
                  "red_f32_random_per_s": fcs.fcs_microbench(fcs.MB_RED, acc_cells, 64),
                  "red_array_floats": acc_cells}
+        # lanes per SM per clock the microbenchmarks reach at the sampled clock
+        mhz = (clocks or {}).get("sm_mhz") or SM_MAX_MHZ
+        per_clk = SMS * mhz * 1e6
+        pipes["lanes_per_sm_clk_measured"] = {
+            "mulwide": pipes["mulwide_per_s"] / per_clk, "int": 3 * pipes["lop3_steps_per_s"] / per_clk,
+            "fp32": pipes["ffma_per_s"] / per_clk, "mufu": pipes["mufu_sin_per_s"] / per_clk,
+            "lds": pipes["lds_words_per_s"] / per_clk}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -294,11 +294,20 @@ int fcs_autotune(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
  * 32x32->64-bit integer multiplies/s (each followed by a 2-input XOR);
  * FCS_MB_LOP3 = shift + 3-input XOR + add steps/s; FCS_MB_FFMA = FP32 FMAs/s;
  * FCS_MB_RED = float reductions into global memory at uniformly random
- * addresses of a `size`-float array per second.  A full grid (4 waves of
+ * addresses of a `size`-float array per second; FCS_MB_MUFU = hardware sines
+ * (__sinf)/s; FCS_MB_LDS = 32-bit words/s read by 128-bit shared-memory loads.  A full grid (4 waves of
  * 256-thread blocks) runs `iters` iterations per thread, once to warm up and
  * once timed with CUDA events on stream s; *rate receives operations per
  * second.  Allocates and frees its own device buffer.  Synchronous. */
-enum fcs_microbench_kind { FCS_MB_PHILOX = 0, FCS_MB_MULWIDE = 1, FCS_MB_LOP3 = 2, FCS_MB_FFMA = 3, FCS_MB_RED = 4 };
+enum fcs_microbench_kind {
+  FCS_MB_PHILOX = 0,
+  FCS_MB_MULWIDE = 1,
+  FCS_MB_LOP3 = 2,
+  FCS_MB_FFMA = 3,
+  FCS_MB_RED = 4,
+  FCS_MB_MUFU = 5,
+  FCS_MB_LDS = 6
+};
 int fcs_microbench(int32_t kind, int64_t size, int32_t iters, double* rate, cudaStream_t s);
 
 /* Size of the library's static device scratch used by

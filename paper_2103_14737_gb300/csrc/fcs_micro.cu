@@ -1,7 +1,8 @@
 // fcs_micro.cu - throughput microbenchmarks of the units the hit path uses,
 // the denominators of its roofline: Philox4x32-10 blocks, 32x32->64-bit
-// integer multiplies (Philox's rounds), 3-input XORs, FP32 FMAs, and float
-// reductions into global memory (the deposit) at random addresses.  Each
+// integer multiplies (Philox's rounds), 3-input XORs, FP32 FMAs, the MUFU
+// sine (the hit's sincos), 32-bit shared-memory loads (the staged tables),
+// and float reductions into global memory (the deposit) at random addresses.  Each
 // kernel runs independent chains in every thread of a full grid and folds its
 // results into one word per thread, so no work can be optimised away.
 #include <cstdio>
@@ -74,6 +75,46 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_ffma(float* out, int iters, f
   out[tid] = acc;
 }
 
+// 8 independent chains of the hardware sine (__sinf).
+__global__ void __launch_bounds__(kMbThreads) k_mb_mufu(float* out, int iters, float seed) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  float a[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = seed + (float)(tid & 255) * 1e-3f + (float)j * 0.1f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = __sinf(a[j]);
+  }
+  float acc = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc += a[j];
+  out[tid] = acc;
+}
+
+// 8 independent 128-bit shared-memory loads per thread and iteration (the
+// hit kernel reads its staged tables with vector loads), lanes on distinct
+// 16-byte slots, folded by XOR; the rate is counted in 32-bit words.
+__global__ void __launch_bounds__(kMbThreads) k_mb_lds(uint32_t* out, int iters, uint32_t seed) {
+  __shared__ uint4 s[1024];
+  for (int i = threadIdx.x; i < 1024; i += blockDim.x)
+    s[i] = make_uint4((uint32_t)i * 2654435761u ^ seed, (uint32_t)i, seed, (uint32_t)i * 7u);
+  __syncthreads();
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint4 acc = make_uint4(tid, 0u, 0u, 0u);
+  for (int i = 0; i < iters; ++i) {
+    const uint32_t base = ((uint32_t)i * 256u + (acc.x & 1u)) & 767u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint4 v = s[base + j * 32 + (threadIdx.x & 31)];
+      acc.x ^= v.x;
+      acc.y ^= v.y;
+      acc.z ^= v.z;
+      acc.w ^= v.w;
+    }
+  }
+  out[tid] = acc.x ^ acc.y ^ acc.z ^ acc.w;
+}
+
 // Float reductions at pseudo-random addresses of an n-float array.
 __global__ void __launch_bounds__(kMbThreads) k_mb_red(float* arr, int64_t n, int iters, uint32_t seed) {
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -112,11 +153,13 @@ extern "C" int fcs_microbench(int32_t kind, int64_t size, int32_t iters, double*
       case FCS_MB_LOP3: k_mb_lop3<<<blocks, kMbThreads, 0, s>>>((uint32_t*)buf, it, 5u); break;
       case FCS_MB_FFMA: k_mb_ffma<<<blocks, kMbThreads, 0, s>>>((float*)buf, it, 0.5f); break;
       case FCS_MB_RED: k_mb_red<<<blocks, kMbThreads, 0, s>>>((float*)buf + threads, arr_n, it, 9u); break;
+      case FCS_MB_MUFU: k_mb_mufu<<<blocks, kMbThreads, 0, s>>>((float*)buf, it, 0.3f); break;
+      case FCS_MB_LDS: k_mb_lds<<<blocks, kMbThreads, 0, s>>>((uint32_t*)buf, it, 13u); break;
       default: break;
     }
   };
   int rc = FCS_OK;
-  if (kind < FCS_MB_PHILOX || kind > FCS_MB_RED) rc = FCS_E_ARG;
+  if (kind < FCS_MB_PHILOX || kind > FCS_MB_LDS) rc = FCS_E_ARG;
   float ms = 0.0f;
   if (rc == FCS_OK) {
     if (kind == FCS_MB_RED) cudaMemsetAsync((float*)buf + threads, 0, (size_t)arr_n * 4, s);
@@ -130,7 +173,7 @@ extern "C" int fcs_microbench(int32_t kind, int64_t size, int32_t iters, double*
   }
   if (rc == FCS_OK && ms > 0.0f) {
     // operations per thread per iteration of each kernel
-    const double per = (kind == FCS_MB_PHILOX) ? 1.0 : (kind == FCS_MB_RED) ? 1.0 : 8.0;
+    const double per = (kind == FCS_MB_PHILOX) ? 1.0 : (kind == FCS_MB_RED) ? 1.0 : (kind == FCS_MB_LDS) ? 32.0 : 8.0;
     *rate = (double)threads * iters * per / (ms * 1e-3);
   }
   cudaEventDestroy(e0);

@@ -332,3 +332,17 @@ def test_autotune_picks_a_valid_shape(sim, ogeo, oprm):
     ref = O.simulate(ogeo, oprm, parts, seed=3)
     got = sim.simulate(d, 3, block=b, hits_per_thread=h, mode=fcs.MODE_DETERMINISTIC, dense=True)
     assert np.array_equal(got["cells"].cpu().numpy().view(np.uint32), ref.cells_canon.view(np.uint32))
+
+
+def test_unit_microbenchmarks(sim):
+    """Every unit microbenchmark returns a positive rate within the pipe's
+    plausible range (lanes per SM per clock at up to 2.1 GHz, 152 SMs)."""
+    per_clk = 152 * 2.1e9
+    limits = {fcs.MB_PHILOX: 8, fcs.MB_MULWIDE: 64, fcs.MB_LOP3: 128, fcs.MB_FFMA: 256, fcs.MB_MUFU: 32,
+              fcs.MB_LDS: 64}
+    for kind, lim in limits.items():
+        r = fcs.fcs_microbench(kind, 0, 64)
+        assert 0 < r < lim * per_clk, (kind, r)
+    assert fcs.fcs_microbench(fcs.MB_RED, 1 << 20, 16) > 0
+    with pytest.raises(fcs.FcsError):
+        fcs.fcs_microbench(99, 0, 1)
