@@ -291,9 +291,10 @@ def run_sweep(args):
             host.append((t1 - t0) * 1e6)
             dev.append(e0.elapsed_time(e1) * 1e3)
         lat[name] = {"host_us_median": float(np.median(host)), "device_us_median": float(np.median(dev))}
-    lat["launches_per_call"] = 23
+    n_launch = fcs.fcs_workspace_graph_kernels(sim.ws)
+    lat["launches_per_call"] = n_launch
     lat["per_launch_us_eager_minus_graph"] = (lat["eager"]["device_us_median"] -
-                                              lat["graph"]["device_us_median"]) / 22
+                                              lat["graph"]["device_us_median"]) / (n_launch - 1)
     out["latency_one_electron"] = lat
     # per-event vs batched launch sequences for 64 single-electron events
     many = sim.to_device(synth.single_particle(64))
@@ -410,6 +411,8 @@ def main():
     t_step, t_stage = timed(args.steps, args.warmup, hits_per_thread=args.hpt, block=args.block)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    # kernels of one step: the kernel nodes of the timed call's CUDA graph
+    launches_per_step = fcs.fcs_workspace_graph_kernels(sim.ws)
     clocks = clk.stop()
     if world > 1:
         dist.barrier()
@@ -515,10 +518,6 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(geo, prm, parts, args.cpu_seconds)
 
-    # kernels of one atomic-mode batched step: call begin/end 2, range begin/end 2,
-    # particle counts 1, task init 1, Poisson FP32 + FP64 2, two scans 6,
-    # task finish 1, hits 1, recheck 1, compaction 5 (count, scan 3, write)
-    launches_per_step = 23
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

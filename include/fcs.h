@@ -213,6 +213,12 @@ int fcs_workspace_reserve(fcs_workspace* ws, const fcs_geo* geo, int64_t n_parti
 /* Reads the device status of the last call on ws (waits for stream s). */
 int fcs_workspace_status(fcs_workspace* ws, fcs_stats* stats, cudaStream_t s);
 
+/* Kernel launches of one replay of the workspace's cached CUDA graph (the
+ * launch sequence of the last call captured with config->use_graph != 0):
+ * the kernel nodes of the captured graph.  n_kernels: host, written.
+ * FCS_E_ARG when no call has been captured on ws. */
+int fcs_workspace_graph_kernels(const fcs_workspace* ws, int64_t* n_kernels);
+
 /* Stage times of the last call on ws that ran with config->timing != 0, in
  * milliseconds, summed over its event ranges (CUDA events on the call's
  * stream; waits for them): ms[FCS_STAGE_TASKS] particle tasks, scans, task

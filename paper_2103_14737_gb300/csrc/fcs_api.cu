@@ -177,6 +177,7 @@ struct fcs_workspace {
   // CUDA graph cache (use_graph)
   cudaGraphExec_t graph = nullptr;
   std::vector<unsigned char> graph_key;
+  int64_t graph_kernels = 0;  // kernel nodes of the cached graph
   // stage timing events: 5 per event range (begin, after tasks, after hits,
   // after recheck, after reduce) of the last timed call; recorded as external
   // events so that a captured call gets event-record nodes in its graph
@@ -213,6 +214,7 @@ struct fcs_workspace {
     w.gmap_cap = gmap_cap;
     w.recheck_cap = recheck_cap;
     w.rows_cap = rows_cap;
+    w.pdefer_cap = pd_cap;
     w.keys = keys;
     w.keys_alt = keys_alt;
     w.rec_cap = rec_cap;
@@ -306,6 +308,8 @@ __global__ void k_range_begin(Sizes* s, const int64_t* __restrict__ off, int32_t
   s->n_records = 0;
   s->n_big = 0;
   s->n_pdefer = 0;
+  s->n_pdefer_ptrs = 0;
+  s->n_pretry = 0;
   s->queue = 0;
 }
 
@@ -703,6 +707,7 @@ int fcs_load_params(fcs_params** out, const fcs_geo* geo, const float* frac, con
   };
   if ((rc = current_device(&prm->device)) != FCS_OK) return fail(rc);
   float *d_frac, *d_mhe, *d_re, *d_ae, *d_lf, *d_w = nullptr;
+  double* d_lf64 = nullptr;
   uint32_t* d_thr;
   uint2* d_guide;
   int32_t* d_bad = nullptr;
@@ -710,11 +715,17 @@ int fcs_load_params(fcs_params** out, const fcs_geo* geo, const float* frac, con
       (rc = dev_alloc(&d_re, NR + 1, &prm->allocs)) || (rc = dev_alloc(&d_ae, NA + 1, &prm->allocs)) ||
       (rc = dev_alloc(&d_thr, n_entries * kNBins, &prm->allocs)) ||
       (rc = dev_alloc(&d_guide, n_entries * kGuideCells, &prm->allocs)) ||
-      (rc = dev_alloc(&d_lf, kLfactEntries, &prm->allocs)))
+      (rc = dev_alloc(&d_lf, kLfactEntries, &prm->allocs)) ||
+      (rc = dev_alloc(&d_lf64, kLfactEntries, &prm->allocs)))
     return fail(rc);
-  // log k! for the FP32 Poisson acceptance test, from the host's FP64 lgamma
+  // log k! from the host's FP64 lgamma: as is for the FP64 Poisson acceptance
+  // test (the value the C definition computes), rounded once for the FP32 test
   std::vector<float> lf(kLfactEntries);
-  for (int k = 0; k < kLfactEntries; ++k) lf[k] = (float)std::lgamma((double)k + 1.0);
+  std::vector<double> lf64(kLfactEntries);
+  for (int k = 0; k < kLfactEntries; ++k) {
+    lf64[k] = std::lgamma((double)k + 1.0);
+    lf[k] = (float)lf64[k];
+  }
   if ((rc = dev_alloc(&d_w, n_entries * kNBins, &prm->allocs)) || (rc = dev_alloc(&d_bad, n_entries, &prm->allocs)) ||
       (rc = dev_alloc(&prm->check, 1, &prm->allocs)))
     return fail(rc);
@@ -724,6 +735,8 @@ int fcs_load_params(fcs_params** out, const fcs_geo* geo, const float* frac, con
       (e = cudaMemcpyAsync(d_re, r_edges, (NR + 1) * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_ae, a_edges, (NA + 1) * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_lf, lf.data(), kLfactEntries * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_lf64, lf64.data(), kLfactEntries * sizeof(double), cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess ||
       (e = cudaMemcpyAsync(d_w, shape_w, n_entries * kNBins * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = launch_build_tables(d_w, (int)n_entries, d_thr, d_guide, d_bad, s)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess) {
@@ -743,6 +756,7 @@ int fcs_load_params(fcs_params** out, const fcs_geo* geo, const float* frac, con
                         : 0;
   d.n_lfact = kLfactEntries;
   d.lfact = d_lf;
+  d.lfact64 = d_lf64;
   d.n_entries = (int32_t)n_entries;
   d.frac = d_frac;
   d.shape_w = d_w;
@@ -809,6 +823,14 @@ int fcs_workspace_status(fcs_workspace* ws, fcs_stats* stats, cudaStream_t s) {
   FCS_CUDA(cudaMemcpyAsync(ws->h_sizes, ws->d_sizes, sizeof(Sizes), cudaMemcpyDeviceToHost, s));
   FCS_CUDA(cudaStreamSynchronize(s));
   return status_from(*ws->h_sizes, stats);
+}
+
+int fcs_workspace_graph_kernels(const fcs_workspace* ws, int64_t* n_kernels) {
+  if (!ws || !n_kernels) return set_err(FCS_E_ARG, "NULL argument");
+  *n_kernels = 0;
+  if (!ws->graph) return set_err(FCS_E_ARG, "no call on this workspace has been captured as a graph");
+  *n_kernels = ws->graph_kernels;
+  return ok();
 }
 
 int fcs_workspace_timings(fcs_workspace* ws, float* ms) {
@@ -922,6 +944,16 @@ int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace
         return rc;
       }
       if (e2 != cudaSuccess) return set_err(FCS_E_CUDA, "graph capture: %s", cudaGetErrorString(e2));
+      int64_t kernels = 0;
+      size_t n_nodes = 0;
+      if (cudaGraphGetNodes(g, nullptr, &n_nodes) == cudaSuccess && n_nodes > 0) {
+        std::vector<cudaGraphNode_t> nodes(n_nodes);
+        if (cudaGraphGetNodes(g, nodes.data(), &n_nodes) == cudaSuccess)
+          for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+          }
+      }
       e = cudaGraphInstantiate(&ws->graph, g, 0);
       cudaGraphDestroy(g);
       if (e != cudaSuccess) {
@@ -929,6 +961,7 @@ int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace
         return set_err(FCS_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
       }
       ws->graph_key = key;
+      ws->graph_kernels = kernels;
     }
     FCS_CUDA(cudaGraphLaunch(ws->graph, s));
     return ok();
@@ -1254,6 +1287,7 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   w.tn = c.take<int64_t>(P * NL);
   w.th = c.take<int64_t>(P * NL);
   w.pdefer = c.take<int32_t>(P * NL);
+  w.pd_cap = P * NL;
   w.task_cap = P * NL;
   w.acc = c.take<float>((int64_t)n_events * geo->d.acc_stride);
   w.rows_cap = n_events;

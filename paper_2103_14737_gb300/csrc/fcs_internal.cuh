@@ -74,6 +74,7 @@ struct ParamDev {
   int32_t n_entries;     // NT * NE * NH * NL
   int32_t n_lfact;       // entries of lfact
   const float* lfact;    // [n_lfact] FP32 of lgamma(k + 1) (host libm, rounded once)
+  const double* lfact64; // [n_lfact] lgamma(k + 1) of the host libm, the FP64 Poisson test's value
   const float* frac;     // [n_entries]
   const float* shape_w;  // [n_entries][128] shape weights (the gradient's likelihood ratios)
   const float* mhe;      // [n_entries]
@@ -97,7 +98,9 @@ struct Sizes {
   int64_t recheck_total;  // recheck hits over the call
   int64_t n_part;       // particles of the current event range (checked against the capacity)
   int64_t n_big;        // deterministic mode: cells with more records than one thread sorts
-  int64_t n_pdefer;     // draws deferred to FP64 in the current range
+  int64_t n_pdefer;     // inversion draws deferred to FP64 in the current range (front of pdefer)
+  int64_t n_pdefer_ptrs;  // PTRS draws deferred to FP64 in the current range (back of pdefer)
+  int64_t n_pretry;     // PTRS draws continued after iteration 0 (their list lives in th)
   unsigned long long queue;  // hit-kernel work-queue counter (tiles handed out)
   uint32_t flags;       // fcs_device_flag bits
   uint32_t n_poisson_fp64;  // Poisson draws that needed an FP64 decision (call total)
@@ -116,11 +119,12 @@ struct WsDev {
                        // finish in deterministic mode (a compact copy for the fold)
   int64_t* tn;         // [task_cap] hits of each task
   int64_t* th;         // [task_cap] first hit of each task (exclusive scan of tn)
-  int32_t* pdefer;     // [task_cap] tasks whose draw is redone in FP64
+  int32_t* pdefer;     // [pdefer_cap] tasks whose draw is redone in FP64: inversion draws from the
+                       // front, PTRS draws from the back (their resume iteration waits in tn)
   int32_t* gmap;       // [gmap_cap] granule -> task
   uint2* recheck;      // [recheck_cap] (task, hit in task)
   float* acc;          // [rows][acc_stride] zero-maintained accumulation rows
-  int64_t task_cap, gmap_cap, recheck_cap, rows_cap;
+  int64_t task_cap, gmap_cap, recheck_cap, rows_cap, pdefer_cap;
   uint64_t* keys;      // deterministic mode record slots, one per hit [rec_cap]
   uint64_t* keys_alt;  // ping-pong buffer [rec_cap]
   int64_t rec_cap;

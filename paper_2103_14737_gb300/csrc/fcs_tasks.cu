@@ -42,8 +42,10 @@ __device__ __forceinline__ PtrsConst64 ptrs_const64(double mu) {
 }
 
 // One PTRS iteration in FP64 from its two 53-bit uniforms: the accepted count,
-// or -1 when the iteration rejects.
-__device__ __noinline__ int64_t ptrs_iter64(double mu, const PtrsConst64& c, double u, double V) {
+// or -1 when the iteration rejects.  log k! = lgamma(k + 1) comes from the
+// host's libm (the table), as in the C definition, for k below the table size.
+__device__ __noinline__ int64_t ptrs_iter64(double mu, const PtrsConst64& c, double u, double V,
+                                            const double* lfact64, int32_t n_lfact) {
   const double U = __dsub_rn(u, 0.5);
   const double us = __dsub_rn(0.5, fabs(U));
   if (us <= 0.0) return -1;
@@ -53,13 +55,17 @@ __device__ __noinline__ int64_t ptrs_iter64(double mu, const PtrsConst64& c, dou
   if (kd < 0.0 || (us < 0.013 && V > us)) return -1;
   const double lhs = __dsub_rn(__dadd_rn(log(V), log(c.invalpha)),
                                log(__dadd_rn(__ddiv_rn(c.a, __dmul_rn(us, us)), c.b)));
-  const double rhs = __dsub_rn(__dadd_rn(-mu, __dmul_rn(kd, c.loglam)), lgamma(__dadd_rn(kd, 1.0)));
+  const double lg = (kd < (double)n_lfact) ? __ldg(lfact64 + (int32_t)kd) : lgamma(__dadd_rn(kd, 1.0));
+  const double rhs = __dsub_rn(__dadd_rn(-mu, __dmul_rn(kd, c.loglam)), lg);
   return (lhs <= rhs) ? (int64_t)kd : -1;
 }
 
-// The whole draw in FP64 (the definition the fast path must reproduce).
+// The whole draw in FP64 (the definition the fast path must reproduce).  A
+// PTRS draw may start at iteration i0 when every earlier iteration is known
+// to reject (the FP32 path certified those rejections).
 __device__ __noinline__ int64_t poisson_draw(double mu, uint32_t layer, uint32_t particle, uint32_t event,
-                                             uint32_t k0, uint32_t k1) {
+                                             uint32_t k0, uint32_t k1, const double* lfact64, int32_t n_lfact,
+                                             uint32_t i0) {
   if (!(mu > 0.0)) return 0;
   if (mu < 10.0) {
     double u, v;
@@ -75,10 +81,10 @@ __device__ __noinline__ int64_t poisson_draw(double mu, uint32_t layer, uint32_t
     return k;
   }
   const PtrsConst64 c = ptrs_const64(mu);
-  for (uint32_t i = 0; i < kPtrsMaxIter; ++i) {
+  for (uint32_t i = i0; i < kPtrsMaxIter; ++i) {
     double u, V;
     draw_pair(i, layer, particle, event, k0, k1, &u, &V);
-    const int64_t k = ptrs_iter64(mu, c, u, V);
+    const int64_t k = ptrs_iter64(mu, c, u, V, lfact64, n_lfact);
     if (k >= 0) return k;
   }
   return (int64_t)floor(mu);
@@ -182,36 +188,50 @@ __device__ __forceinline__ int64_t ptrs_iter32(float mu, const PtrsConst32& c, u
 }
 
 
-// Poisson draw in FP32 where every decision is certified: the count, or -1
-// when a decision is uncertain (or mu is too large for FP32 headroom); the
-// caller then takes poisson_draw, the FP64 definition, for this task.
-__device__ __forceinline__ int32_t poisson_draw_fp32(float mu32, uint32_t layer, uint32_t particle, uint32_t event,
-                                                     uint32_t k0, uint32_t k1, const float* lfact, int32_t n_lfact) {
+// Poisson draw in FP32 where every decision is certified.  Both methods
+// return the count, or -1 - i when a decision of PTRS iteration i (or of the
+// inversion, i = 0) is uncertain or mu is too large for FP32 headroom: the
+// caller then takes poisson_draw, the FP64 definition, for this task from
+// iteration i on.
+//
+// Inversion (mu < 10).  rcp[k] = __frcp_rn(k) for k <= kInvMax (a
+// shared-memory copy: the values the loop would compute).
+__device__ __forceinline__ int32_t poisson_inv_fp32(float mu32, uint32_t layer, uint32_t particle, uint32_t event,
+                                                    uint32_t k0, uint32_t k1, const float* rcp) {
   if (!(mu32 > 0.0f)) return 0;
-  if (mu32 < 10.0f) {
-    const uint4 x = philox4x32_10(make_uint4(0u, layer | (kPurposePoisson << 16), particle, event), k0, k1);
-    const float uf = u53f(x.x, x.y);
-    float p = expf(-mu32);
-    float F = p;
-    int k = 0;
-    while (true) {
-      const float e = (float)(k + 2) * 0x1p-21f;
-      if (uf < F - e) return k;          // u < F_k: stop at k
-      if (!(uf > F + e)) return -1;      // uncertain
-      if (k == kInvMax) return k;        // the definition stops here too
-      k += 1;
-      p = (p * mu32) * __frcp_rn((float)k);
-      F = F + p;
-    }
+  const uint4 x = philox4x32_10(make_uint4(0u, layer | (kPurposePoisson << 16), particle, event), k0, k1);
+  const float uf = u53f(x.x, x.y);
+  float p = expf(-mu32);
+  float F = p;
+  int k = 0;
+  while (true) {
+    const float e = (float)(k + 2) * 0x1p-21f;
+    if (uf < F - e) return k;          // u < F_k: stop at k
+    if (!(uf > F + e)) return -1;      // uncertain
+    if (k == kInvMax) return k;        // the definition stops here too
+    k += 1;
+    p = (p * mu32) * rcp[k];
+    F = F + p;
   }
-  if (mu32 > kPtrsFastMaxMu) return -1;
+}
+
+// PTRS (mu >= 10), iterations [i_begin, i_end).  When every one of them
+// rejects for certain and i_end < kPtrsMaxIter, returns kPoisRetry: the draw
+// continues at iteration i_end (its earlier iterations reject in the
+// definition too).
+constexpr int32_t kPoisRetry = INT32_MIN;
+__device__ __forceinline__ int32_t poisson_ptrs_fp32(float mu32, uint32_t layer, uint32_t particle, uint32_t event,
+                                                     uint32_t k0, uint32_t k1, const float* lfact, int32_t n_lfact,
+                                                     uint32_t i_begin, uint32_t i_end) {
+  if (mu32 > kPtrsFastMaxMu) return -1 - (int32_t)i_begin;
   const PtrsConst32 c = ptrs_const32(mu32, lfact, n_lfact);
-  for (uint32_t i = 0; i < kPtrsMaxIter; ++i) {
+  for (uint32_t i = i_begin; i < i_end; ++i) {
     const uint4 x = philox4x32_10(make_uint4(i, layer | (kPurposePoisson << 16), particle, event), k0, k1);
     const int64_t k = ptrs_iter32(mu32, c, x);
-    if (k == -2) return -1;
+    if (k == -2) return -1 - (int32_t)i;
     if (k >= 0) return (int32_t)k;
   }
+  if (i_end < kPtrsMaxIter) return kPoisRetry;
   return (int32_t)floorf(mu32);
 }
 
@@ -421,37 +441,37 @@ __global__ void __launch_bounds__(128) k_task_init(const GeoDev g, const ParamDe
 // consecutive tasks, lists the window's inversion tasks (mu < 10) from the
 // front and its PTRS tasks from the back of a per-warp shared array, and
 // draws them 32 at a time, inversion rounds first: a round runs one method,
-// and warps never wait for one another.  Draws the FP32 path cannot certify
-// are queued for k_task_poisson64, so that FP64 work runs in full warps
-// instead of stalling a warp for one lane.
+// and warps never wait for one another.  A PTRS round runs iteration 0 only
+// (most draws accept there); the draws it rejects continue in
+// k_task_ptrs_retry, so that one long draw does not hold 31 idle lanes.
+// Draws the FP32 path cannot certify are queued for k_task_poisson64, so that
+// FP64 work runs in full warps instead of stalling a warp for one lane.
 constexpr int kPoisWarps = 4;
 constexpr int kPoisWin = 128;
 
-// One round: lane j draws for list entry j (< n) of the window; list entry j
-// is s_list[j] (inversion list) or s_list[kPoisWin - 1 - j] (PTRS list).
-__device__ __forceinline__ void poisson_round(const WsDev& w, int64_t win, const int* s_list, const float* s_mu,
-                                              int j, int n, bool back, uint32_t k0, uint32_t k1,
-                                              uint32_t first_event_lo, const float* lfact, int32_t n_lfact) {
+// Appends the tasks of the lanes with `push` set to a list: warp-aggregated
+// counter increment, entry q at list[q] (front) or list[cap - 1 - q] (back).
+__device__ __forceinline__ void warp_push(bool push, int64_t task, unsigned long long* counter, int32_t* list,
+                                          bool back, int64_t cap) {
   const int lane = threadIdx.x & 31;
-  int32_t k = 0;
-  int64_t tt = 0;
-  if (j < n) {
-    const int idx = s_list[back ? kPoisWin - 1 - j : j];
-    tt = win + idx;
-    const TaskRec& r = w.tasks[tt];
-    k = poisson_draw_fp32(s_mu[idx], (uint32_t)r.layer(), (uint32_t)r.particle, first_event_lo + (uint32_t)r.event(),
-                          k0, k1, lfact, n_lfact);
-    w.tn[tt] = (k < 1) ? 1 : k;  // provisional for deferred draws
-  }
-  const bool defer = j < n && k < 0;
-  const unsigned m = __ballot_sync(0xffffffffu, defer);
-  if (m) {
-    unsigned long long b = 0;
-    const int l0 = __ffs(m) - 1;
-    if (lane == l0) b = atomicAdd((unsigned long long*)&w.sizes->n_pdefer, (unsigned long long)__popc(m));
-    b = __shfl_sync(0xffffffffu, b, l0);
-    if (defer) w.pdefer[b + __popc(m & ((1u << lane) - 1u))] = (int32_t)tt;
-  }
+  const unsigned m = __ballot_sync(0xffffffffu, push);
+  if (!m) return;
+  unsigned long long b = 0;
+  const int l0 = __ffs(m) - 1;
+  if (lane == l0) b = atomicAdd(counter, (unsigned long long)__popc(m));
+  b = __shfl_sync(0xffffffffu, b, l0);
+  const int64_t q = (int64_t)b + __popc(m & ((1u << lane) - 1u));
+  if (push) list[back ? cap - 1 - q : q] = (int32_t)task;
+}
+
+// Deferral to FP64 by method: inversion draws at the front of pdefer and
+// PTRS draws at its back, so that the FP64 warps run one method; a deferred
+// PTRS draw's tn holds the iteration the FP64 definition resumes at.
+__device__ __forceinline__ void store_count(const WsDev& w, bool valid, int64_t t, int32_t k, bool ptrs) {
+  if (valid && k != kPoisRetry) w.tn[t] = (k < 1) ? (k < 0 ? -1 - k : 1) : k;
+  warp_push(valid && k < 0 && k != kPoisRetry, t,
+            (unsigned long long*)(ptrs ? &w.sizes->n_pdefer_ptrs : &w.sizes->n_pdefer), w.pdefer, ptrs,
+            w.pdefer_cap);
 }
 
 __global__ void __launch_bounds__(32 * kPoisWarps) k_task_poisson(WsDev w, uint32_t k0, uint32_t k1,
@@ -459,10 +479,15 @@ __global__ void __launch_bounds__(32 * kPoisWarps) k_task_poisson(WsDev w, uint3
                                                                    int32_t n_lfact) {
   __shared__ int s_list[kPoisWarps][kPoisWin];  // inversion tasks from the front, PTRS from the back
   __shared__ float s_mu[kPoisWarps][kPoisWin];
+  __shared__ float s_rcp[kInvMax + 1];          // 1 / k, correctly rounded
+  for (int k = threadIdx.x; k <= kInvMax; k += blockDim.x) s_rcp[k] = __frcp_rn((float)k);
+  __syncthreads();
   const int64_t T = min(w.sizes->n_tasks, w.task_cap);
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t nw = (int64_t)gridDim.x * kPoisWarps;
+  // the retry list lives in th, which the scan after the draws overwrites
+  int32_t* retry = reinterpret_cast<int32_t*>(w.th);
   for (int64_t win = ((int64_t)blockIdx.x * kPoisWarps + wi) * kPoisWin; win < T; win += nw * kPoisWin) {
     int n_i = 0, n_p = 0;
 #pragma unroll
@@ -479,23 +504,77 @@ __global__ void __launch_bounds__(32 * kPoisWarps) k_task_poisson(WsDev w, uint3
       n_p += __popc(bp);
     }
     __syncwarp();
-    for (int r0 = 0; r0 < n_i; r0 += 32)
-      poisson_round(w, win, s_list[wi], s_mu[wi], r0 + lane, n_i, false, k0, k1, first_event_lo, lfact, n_lfact);
-    for (int r0 = 0; r0 < n_p; r0 += 32)
-      poisson_round(w, win, s_list[wi], s_mu[wi], r0 + lane, n_p, true, k0, k1, first_event_lo, lfact, n_lfact);
+    for (int r0 = 0; r0 < n_i; r0 += 32) {
+      const int j = r0 + lane;
+      const bool valid = j < n_i;
+      int32_t k = 0;
+      int64_t t = 0;
+      if (valid) {
+        const int idx = s_list[wi][j];
+        t = win + idx;
+        const TaskRec& r = w.tasks[t];
+        k = poisson_inv_fp32(s_mu[wi][idx], (uint32_t)r.layer(), (uint32_t)r.particle,
+                             first_event_lo + (uint32_t)r.event(), k0, k1, s_rcp);
+      }
+      store_count(w, valid, t, k, false);
+    }
+    for (int r0 = 0; r0 < n_p; r0 += 32) {
+      const int j = r0 + lane;
+      const bool valid = j < n_p;
+      int32_t k = 0;
+      int64_t t = 0;
+      if (valid) {
+        const int idx = s_list[wi][kPoisWin - 1 - j];
+        t = win + idx;
+        const TaskRec& r = w.tasks[t];
+        k = poisson_ptrs_fp32(s_mu[wi][idx], (uint32_t)r.layer(), (uint32_t)r.particle,
+                              first_event_lo + (uint32_t)r.event(), k0, k1, lfact, n_lfact, 0u, 1u);
+      }
+      store_count(w, valid, t, k, true);
+      warp_push(valid && k == kPoisRetry, t, (unsigned long long*)&w.sizes->n_pretry, retry, false, 0);
+    }
     __syncwarp();  // the window's lists are reused
   }
 }
 
-// The deferred draws in FP64 (the definition itself).
-__global__ void __launch_bounds__(128) k_task_poisson64(WsDev w, uint32_t k0, uint32_t k1, uint32_t first_event_lo) {
-  const int64_t n = w.sizes->n_pdefer;
+// PTRS draws that rejected at iteration 0, from iteration 1 on (one per
+// lane; the list holds about a tenth of the PTRS draws).
+__global__ void __launch_bounds__(128) k_task_ptrs_retry(WsDev w, uint32_t k0, uint32_t k1, uint32_t first_event_lo,
+                                                          const float* lfact, int32_t n_lfact) {
+  const int64_t n = w.sizes->n_pretry;
+  const int32_t* retry = reinterpret_cast<const int32_t*>(w.th);
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t q0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; q0 < n; q0 += warps * 32) {
+    const int64_t q = q0 + lane;
+    const bool valid = q < n;
+    int32_t k = 0;
+    int64_t t = 0;
+    if (valid) {
+      t = retry[q];
+      const TaskRec& r = w.tasks[t];
+      k = poisson_ptrs_fp32(w.tmu[t], (uint32_t)r.layer(), (uint32_t)r.particle, first_event_lo + (uint32_t)r.event(),
+                            k0, k1, lfact, n_lfact, 1u, kPtrsMaxIter);
+    }
+    store_count(w, valid, t, k, true);
+  }
+}
+
+// The deferred draws in FP64 (the definition itself): the inversion list
+// (front of pdefer), then the PTRS list (back of pdefer), 32 per warp, so
+// that a warp runs one method except at the seam.
+__global__ void __launch_bounds__(128) k_task_poisson64(WsDev w, uint32_t k0, uint32_t k1, uint32_t first_event_lo,
+                                                         const double* lfact64, int32_t n_lfact) {
+  const int64_t n_inv = w.sizes->n_pdefer, n_ptrs = w.sizes->n_pdefer_ptrs;
+  const int64_t n = n_inv + n_ptrs;
   if (blockIdx.x == 0 && threadIdx.x == 0) w.sizes->n_poisson_fp64 += (uint32_t)n;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t t = w.pdefer[q];
+    const bool inv = q < n_inv;
+    const int32_t t = w.pdefer[inv ? q : w.pdefer_cap - 1 - (q - n_inv)];
     const TaskRec& r = w.tasks[t];
+    const uint32_t i0 = inv ? 0u : (uint32_t)w.tn[t];
     int64_t k = poisson_draw((double)w.tmu[t], (uint32_t)r.layer(), (uint32_t)r.particle,
-                             first_event_lo + (uint32_t)r.event(), k0, k1);
+                             first_event_lo + (uint32_t)r.event(), k0, k1, lfact64, n_lfact, i0);
     if (k < 1) k = 1;
     if (k > 0x7FFFFFFF) k = 0x7FFFFFFF;
     w.tn[t] = k;
@@ -556,9 +635,10 @@ cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_par
       (std::max<int64_t>(n_part_max * p.NL, 1) + kPoisWarps * kPoisWin - 1) / (kPoisWarps * kPoisWin),
       (int64_t)L.num_sms * 16);
   k_task_poisson<<<gpois, 32 * kPoisWarps, 0, L.s>>>(w, k0, k1, (uint32_t)first_event, p.lfact, p.n_lfact);
+  k_task_ptrs_retry<<<L.num_sms * 4, 128, 0, L.s>>>(w, k0, k1, (uint32_t)first_event, p.lfact, p.n_lfact);
   // the FP64 pipe is narrow: one warp per block spreads the few deferred draws
   // over every SM
-  k_task_poisson64<<<L.num_sms * 8, 32, 0, L.s>>>(w, k0, k1, (uint32_t)first_event);
+  k_task_poisson64<<<L.num_sms * 8, 32, 0, L.s>>>(w, k0, k1, (uint32_t)first_event, p.lfact64, p.n_lfact);
   // the scan counts the tasks actually written (n_tasks <= task_cap by construction)
   return launch_scan_i64(w.tn, w.th, &w.sizes->n_tasks, 0, &w.sizes->n_hits, 0, tmp, L.s);
 }

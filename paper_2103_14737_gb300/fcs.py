@@ -29,7 +29,8 @@ MODE_ATOMIC, MODE_DETERMINISTIC = 0, 1
 
 EXPORTED = ("fcs_version", "fcs_last_error", "fcs_load_geometry", "fcs_geometry_info", "fcs_free_geometry",
             "fcs_load_params", "fcs_free_params", "fcs_workspace_create", "fcs_workspace_reserve",
-            "fcs_workspace_status", "fcs_workspace_timings", "fcs_workspace_free", "fcs_simulate_events", "fcs_simulate_events_host",
+            "fcs_workspace_status", "fcs_workspace_timings", "fcs_workspace_graph_kernels", "fcs_workspace_free",
+            "fcs_simulate_events", "fcs_simulate_events_host",
             "fcs_simulate_events_static", "fcs_autotune", "fcs_microbench", "fcs_simulate_backward",
             "fcs_update_params")
 
@@ -98,6 +99,7 @@ def load_library(build_if_missing: bool = True):
         L.fcs_workspace_reserve.argtypes = [vp, vp, i64, i32, i64, i32]
         L.fcs_workspace_status.argtypes = [vp, vp, vp]
         L.fcs_workspace_timings.argtypes = [vp, vp]
+        L.fcs_workspace_graph_kernels.argtypes = [vp, vp]
         L.fcs_workspace_free.argtypes = [vp]
         L.fcs_workspace_free.restype = None
         L.fcs_simulate_events.argtypes = [vp, vp, vp, vp, i64, i32, u64, i64, vp, vp, vp, vp, vp, i64, vp, vp, vp]
@@ -209,6 +211,13 @@ def fcs_workspace_timings(ws):
     ms = (C.c_float * len(STAGES))()
     _check(load_library().fcs_workspace_timings(ws, ms))
     return dict(zip(STAGES, [float(v) for v in ms]))
+
+
+def fcs_workspace_graph_kernels(ws):
+    """Kernel launches of one replay of the workspace's cached CUDA graph."""
+    n = C.c_int64()
+    _check(load_library().fcs_workspace_graph_kernels(ws, C.byref(n)))
+    return n.value
 
 
 def fcs_workspace_free(ws):
