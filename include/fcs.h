@@ -52,7 +52,7 @@ enum fcs_status_code {
   FCS_E_OOM = 3,          /* a device allocation of the library failed */
   FCS_E_CUDA = 4,         /* a CUDA runtime call failed (message in fcs_last_error) */
   FCS_E_DEVICE_CHECK = 5, /* a device-side input check failed (bad particle type, NaN, ...) */
-  FCS_E_TIMEOUT = 6,      /* reserved: a bounded device wait gave up */
+  FCS_E_TIMEOUT = 6,      /* a bounded device wait gave up (FCS_FLAG_WAIT_TIMEOUT) */
   FCS_E_UNSUPPORTED = 7   /* the call or option is not implemented */
 };
 
@@ -63,7 +63,8 @@ enum fcs_device_flag {
   FCS_FLAG_OUT_CAPACITY = 1u << 2,  /* more non-zero cells than `capacity` */
   FCS_FLAG_KEY_BITS = 1u << 3,      /* deterministic mode: (cell, task) keys need > 63 bits */
   FCS_FLAG_RECHECK_SPILL = 1u << 4, /* informational: FP64 recheck queue full, done inline */
-  FCS_FLAG_BAD_OFFSETS = 1u << 5    /* event_offsets not within [0, n_particles] or decreasing */
+  FCS_FLAG_BAD_OFFSETS = 1u << 5,   /* event_offsets not within [0, n_particles] or decreasing */
+  FCS_FLAG_WAIT_TIMEOUT = 1u << 6   /* a bounded device wait gave up: the call's results are invalid */
 };
 
 /* ---- geometry (Sec. 4: 187,652 cells, 24 layers, 78 regions, flattened) -- */

@@ -155,8 +155,8 @@ struct fcs_workspace {
   int64_t* chunk_counts = nullptr;
   int64_t* chunk_offsets = nullptr;
   int64_t cc_cap = 0, co_cap = 0;
-  int64_t* block_sums = nullptr;
-  int64_t bs_cap = 0;
+  uint64_t* scan_state = nullptr;  // zero between scans (see ScanTmp)
+  int64_t ss_cap = 0;
   uint64_t* keys = nullptr;
   uint64_t* keys_alt = nullptr;
   int64_t k_cap = 0, ka_cap = 0, rec_cap = 0;
@@ -188,7 +188,7 @@ struct fcs_workspace {
     if (graph) cudaGraphExecDestroy(graph);
     for (cudaEvent_t e : tev) cudaEventDestroy(e);
     void* ps[] = {d_sizes, pcount, poff, pinfo, tasks, tmu, tn, th, pdefer, gmap, recheck, acc, chunk_counts, chunk_offsets,
-                  block_sums, keys, keys_alt, cell_off, stage, grad_acc, grad_touched};
+                  scan_state, keys, keys_alt, cell_off, stage, grad_acc, grad_touched};
     for (void* p : ps)
       if (p) cudaFree(p);
     if (h_sizes) cudaFreeHost(h_sizes);
@@ -219,6 +219,10 @@ struct fcs_workspace {
     w.keys_alt = keys_alt;
     w.rec_cap = rec_cap;
     return w;
+  }
+
+  ScanTmp scan_tmp() const {
+    return ScanTmp{scan_state, ss_cap - 2, d_sizes ? &d_sizes->flags : nullptr, num_sms * 2};
   }
 };
 
@@ -262,7 +266,10 @@ int ws_reserve_static(fcs_workspace* ws, const fcs_geo* geo, int64_t P, int32_t 
   const int64_t chunks = compact_chunks(geo->d.n_cells, std::max(rows, 1));
   FCS_TRY(grow(&ws->chunk_counts, &ws->cc_cap, chunks));
   FCS_TRY(grow(&ws->chunk_offsets, &ws->co_cap, chunks));
-  FCS_TRY(grow(&ws->block_sums, &ws->bs_cap, kScanBlocks + 1));
+  // scan state for the largest array any scan of a call covers (zeroed; the
+  // scans leave it zero)
+  FCS_TRY(grow(&ws->scan_state, &ws->ss_cap,
+               scan_state_words(std::max({Pc * NL, (int64_t)std::max(rows, 1) * stride, chunks})), true));
   if (mode == FCS_MODE_DETERMINISTIC)
     FCS_TRY(grow(&ws->cell_off, &ws->co_cells_cap, (int64_t)std::max(rows, 1) * stride));
   return FCS_OK;
@@ -338,6 +345,8 @@ int status_from(const Sizes& s, fcs_stats* st) {
     st->device_flags = s.flags;
     st->n_poisson_fp64 = s.n_poisson_fp64;
   }
+  if (s.flags & FCS_FLAG_WAIT_TIMEOUT)
+    return set_err(FCS_E_TIMEOUT, "a bounded device wait gave up; the call's results are invalid");
   if (s.flags & FCS_FLAG_BAD_OFFSETS)
     return set_err(FCS_E_ARG, "event_offsets must be non-decreasing within [0, n_particles]");
   if (s.flags & FCS_FLAG_BAD_PARTICLE)
@@ -399,7 +408,7 @@ int enqueue_range(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, int32_t range
   if (tev) FCS_CUDA(record_stage(tev[0], a.s));
   k_range_begin<<<1, 1, 0, a.s>>>(ws->d_sizes, a.parts.event_offsets, ev_lo, ev_hi, a.n_particles, ws->pcap);
   const uint32_t k0 = (uint32_t)(a.seed & 0xFFFFFFFFu), k1 = (uint32_t)(a.seed >> 32);
-  const ScanTmp tmp{ws->block_sums};
+  const ScanTmp tmp = ws->scan_tmp();
   WsDev w = ws->view();
   FCS_CUDA(launch_task_counts(a.geo->d, a.prm->d, a.parts, ev_lo, ev_hi, k0, k1, a.first_event, w, tmp,
                               a.n_particles, a.cfg.energy_interp, L));
@@ -1164,7 +1173,7 @@ int fcs_simulate_backward(const fcs_geo* geo, const fcs_params* prm, fcs_workspa
   const HitCfg hc = hit_cfg(cfg);
   const Launch L{s, ws->num_sms};
   const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
-  const ScanTmp tmp{ws->block_sums};
+  const ScanTmp tmp = ws->scan_tmp();
   ws->grad_dirty = true;
   k_call_begin<<<1, 1, 0, s>>>(ws->d_sizes);
   for (int32_t lo = 0; lo < n_events; lo += rows) {
@@ -1295,13 +1304,14 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   const int64_t chunks = compact_chunks(geo->d.n_cells, n_events);
   w.chunk_counts = c.take<int64_t>(chunks);
   w.chunk_offsets = c.take<int64_t>(chunks);
-  w.block_sums = c.take<int64_t>(kScanBlocks + 1);
+  w.ss_cap = scan_state_words(std::max({P * NL, (int64_t)n_events * geo->d.acc_stride, chunks}));
+  w.scan_state = c.take<uint64_t>(w.ss_cap);
   w.recheck = c.take<uint2>(recheck_cap);
   w.recheck_cap = recheck_cap;
   const bool fits = w.d_sizes && w.pcount && w.poff && w.pinfo && w.tasks && w.tmu && w.tn && w.th && w.pdefer &&
                     w.acc &&
                     w.chunk_counts &&
-                    w.chunk_offsets && w.block_sums && w.recheck && c.cap - c.off >= 4096;
+                    w.chunk_offsets && w.scan_state && w.recheck && c.cap - c.off >= 4096;
   if (fits) {
     // the rest of the array maps tiles to tasks: it bounds the hits per call
     w.gmap_cap = (int64_t)((c.cap - c.off) / sizeof(int32_t));
@@ -1320,7 +1330,7 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
     w.acc = nullptr;
     w.chunk_counts = nullptr;
     w.chunk_offsets = nullptr;
-    w.block_sums = nullptr;
+    w.scan_state = nullptr;
     w.recheck = nullptr;
     w.gmap = nullptr;
   };
@@ -1335,9 +1345,11 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   cfg.mode = FCS_MODE_ATOMIC;
   cfg.batched = 1;
   cfg.sync = 1;
-  // the array keeps the previous call's contents: the accumulation rows must start at zero
+  // the array keeps the previous call's contents: the accumulation rows and
+  // the scan state must start at zero
   int rc = FCS_OK;
   cudaError_t e = cudaMemsetAsync(w.acc, 0, (size_t)n_events * geo->d.acc_stride * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.scan_state, 0, (size_t)w.ss_cap * sizeof(uint64_t), s);
   if (e != cudaSuccess) rc = set_err(FCS_E_CUDA, "clearing the static scratch: %s", cudaGetErrorString(e));
   if (rc == FCS_OK) {
     CallArgs a{geo, prm, &w, *particles, n_particles, n_events, seed, first_event, cfg, nullptr,

@@ -2,6 +2,7 @@
 // the translation units of libfcs (not part of the public ABI).
 #pragma once
 
+#include <algorithm>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -169,11 +170,16 @@ struct Launch {
 cudaError_t launch_build_tables(const float* shape_w, int n_entries, uint32_t* thr, uint2* guide,
                                 int32_t* bad, cudaStream_t s);
 
-// fcs_scan.cu: exclusive scan of n int64 values (n on the host or device).
+// fcs_scan.cu: exclusive scan of n int64 values (n on the host or device),
+// one pass.  The state (ticket, done count, one status word per tile) is zero
+// between scans; scan_state_words(n) words hold a scan of up to n elements.
 struct ScanTmp {
-  int64_t* block_sums;  // [kScanBlocks + 1]
+  uint64_t* state;    // zeroed device words: [0] tile ticket, [1] CTAs done, [2 ..] tile status
+  int64_t cap_tiles;  // tiles the status words cover
+  uint32_t* flags;    // device flag word of the call (FCS_FLAG_WAIT_TIMEOUT)
+  int grid;           // persistent CTAs
 };
-constexpr int kScanBlocks = 512;
+int64_t scan_state_words(int64_t max_elements);
 cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, const int64_t* n_dev, int64_t n_host,
                             int64_t* total_dst, int64_t total_add_base_from_dst, ScanTmp tmp,
                             cudaStream_t s);

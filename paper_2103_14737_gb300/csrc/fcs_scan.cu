@@ -1,18 +1,39 @@
-// fcs_scan.cu - device-wide exclusive scan of int64 counts (reduce, scan of
-// block sums, downsweep).  Used for particle -> task / hit offsets, the
-// compaction offsets and the deterministic mode's cell offsets.  The element count may
-// live in device memory, so the launches need no host synchronisation.
+// fcs_scan.cu - device-wide exclusive scan of counts in one pass (decoupled
+// look-back, Merrill & Garland 2016).  Used for particle -> task / hit
+// offsets, the compaction offsets and the deterministic mode's cell offsets.
+// The element count may live in device memory, so the launch needs no host
+// synchronisation.
+//
+// Persistent CTAs take tiles of kScanTile elements in increasing order from
+// an atomic ticket.  A tile publishes its aggregate, then (after looking back
+// over its predecessors) its inclusive prefix, each as one 64-bit status word
+// [flag:2 | value:62].  A tile waits only on tiles with smaller tickets, which
+// CTAs that are already running hold, so the waits end; each wait is bounded
+// all the same and sets FCS_FLAG_WAIT_TIMEOUT when it gives up.  Input and
+// output move through shared memory (coalesced), each thread scanning
+// kScanItems consecutive elements.  The last CTA to finish resets the ticket
+// and the status words it used, so the state is zero again for the next scan.
 #include "fcs_internal.cuh"
 
 namespace fcs {
 namespace {
 
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
+constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagPrefix = 2ull << 62;
+constexpr uint64_t kValueMask = (1ull << 62) - 1;
+constexpr uint32_t kSpinLimit = 1u << 24;  // status polls before a wait gives up (seconds)
 
 __device__ __forceinline__ int64_t load_n(const int64_t* n_dev, int64_t n_host) {
   return n_dev ? *n_dev : n_host;
+}
+
+__device__ __forceinline__ int64_t warp_sum(int64_t x) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
 }
 
 // Exclusive block scan of one int64 per thread; returns the block total in *total.
@@ -42,84 +63,65 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* s_warp, i
   return warp_excl + x - v;
 }
 
-template <typename In>
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const In* __restrict__ in,
-                                                            const int64_t* n_dev, int64_t n_host,
-                                                            int64_t* __restrict__ block_sums) {
-  const int64_t n = load_n(n_dev, n_host);
-  const int64_t chunk = (n + kScanBlocks - 1) / kScanBlocks;
-  const int64_t b = (int64_t)blockIdx.x * chunk, e = min(b + chunk, n);
-  int64_t acc = 0;
-  for (int64_t i = b + threadIdx.x; i < e; i += kScanThreads) acc += (int64_t)in[i];
-#pragma unroll
-  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  __shared__ int64_t s[kScanThreads / 32];
-  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int64_t t = 0;
-    for (int i = 0; i < kScanThreads / 32; ++i) t += s[i];
-    block_sums[blockIdx.x] = t;
-  }
-}
-
-// One block of kScanBlocks threads: exclusive scan of the block sums plus the
-// optional base; writes the grand total.
-__global__ void __launch_bounds__(kScanBlocks) k_scan_blocks(int64_t* block_sums, const int64_t* base_dev,
-                                                             int64_t* total_dst) {
-  __shared__ int64_t s_warp[kScanBlocks / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t v = block_sums[threadIdx.x];
-  int64_t x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_warp[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    int64_t w = (lane < kScanBlocks / 32) ? s_warp[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
+// Sum of the tiles before tile t, by warp 0: lane l reads the status of tile
+// j - l, 32 tiles per step from the nearest predecessor back, until a tile
+// with its inclusive prefix is found (position -1 counts as a prefix of 0).
+__device__ __forceinline__ int64_t look_back(const uint64_t* status, int64_t t, uint32_t* flags) {
+  const int lane = threadIdx.x & 31;
+  int64_t excl = 0;
+  for (int64_t j = t - 1;; j -= 32) {
+    const int64_t idx = j - lane;
+    uint64_t st = kFlagPrefix;
+    if (idx >= 0) {
+      const volatile uint64_t* p = status + idx;
+      uint32_t spins = 0;
+      st = *p;
+      while ((st >> 62) == 0 && ++spins < kSpinLimit) st = *p;
+      if ((st >> 62) == 0) {  // gave up: the result is invalid, the flag says so
+        atomicOr(flags, (uint32_t)FCS_FLAG_WAIT_TIMEOUT);
+        st = kFlagPrefix;
+      }
     }
-    if (lane < kScanBlocks / 32) s_warp[lane] = w;
-  }
-  __syncthreads();
-  const int64_t base = base_dev ? *base_dev : 0;
-  const int64_t excl = (warp ? s_warp[warp - 1] : 0) + x - v;
-  const int64_t total = s_warp[kScanBlocks / 32 - 1];
-  __syncthreads();  // every thread has read *base_dev before it may be overwritten
-  block_sums[threadIdx.x] = base + excl;
-  if (threadIdx.x == 0) {
-    block_sums[kScanBlocks] = base + total;
-    if (total_dst) *total_dst = base + total;
+    const unsigned pm = __ballot_sync(0xffffffffu, (st >> 62) == 2);
+    const int64_t v = (int64_t)(st & kValueMask);
+    if (pm) {
+      const int first = __ffs(pm) - 1;  // the nearest tile with a prefix
+      return excl + warp_sum(lane <= first ? v : 0);
+    }
+    excl += warp_sum(v);
   }
 }
 
-// Tiles of kScanTile elements move through shared memory: coalesced loads
-// and stores of the tile, while each thread scans kScanItems consecutive
-// elements of it.  Element j sits at j + j / kScanItems (one pad word per
-// thread's run keeps the per-thread accesses off a single bank).
 template <typename In>
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(const In* __restrict__ in,
-                                                          int64_t* __restrict__ out,
-                                                          const int64_t* n_dev, int64_t n_host,
-                                                          const int64_t* __restrict__ block_sums) {
+__global__ void __launch_bounds__(kScanThreads) k_scan(const In* in, int64_t* out, const int64_t* n_dev, int64_t n_host,
+                                                     int64_t* total_dst, int base_from_dst, uint64_t* state,
+                                                     int64_t cap_tiles, uint32_t* flags) {
+  __shared__ int64_t s_tile[kScanTile + kScanTile / kScanItems];  // element j at j + j / kScanItems
   __shared__ int64_t s_warp[kScanThreads / 32];
-  __shared__ int64_t s_tile[kScanTile + kScanTile / kScanItems];
+  __shared__ int64_t s_excl;
+  __shared__ unsigned long long s_ticket;
+  __shared__ int s_last;
+  unsigned long long* ticket = reinterpret_cast<unsigned long long*>(state);
+  unsigned long long* done = ticket + 1;
+  uint64_t* status = state + 2;
   const int64_t n = load_n(n_dev, n_host);
-  const int64_t chunk = (n + kScanBlocks - 1) / kScanBlocks;
-  const int64_t b = (int64_t)blockIdx.x * chunk, e = min(b + chunk, n);
-  int64_t carry = block_sums[blockIdx.x];
-  for (int64_t t0 = b; t0 < e; t0 += kScanTile) {
+  int64_t n_tiles = (n + kScanTile - 1) / kScanTile;
+  if (n_tiles > cap_tiles) {  // the workspace sizes the state for its arrays: never
+    if (threadIdx.x == 0) atomicOr(flags, (uint32_t)FCS_FLAG_WAIT_TIMEOUT);
+    n_tiles = 0;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  while (true) {
+    if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1ull);
+    __syncthreads();
+    const int64_t t = (int64_t)s_ticket;
+    if (t >= n_tiles) break;
+    const int64_t t0 = t * kScanTile;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
       const int j = k * kScanThreads + threadIdx.x;
       const int64_t i = t0 + j;
-      s_tile[j + j / kScanItems] = i < e ? (int64_t)in[i] : 0;
+      s_tile[j + j / kScanItems] = i < n ? (int64_t)in[i] : 0;
     }
     __syncthreads();
     int64_t v[kScanItems];
@@ -130,7 +132,23 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const In* __restrict
       sum += v[k];
     }
     int64_t tile_total;
-    int64_t run = carry + block_excl_scan(sum, s_warp, &tile_total);  // synchronises the block
+    const int64_t thread_excl = block_excl_scan(sum, s_warp, &tile_total);  // synchronises the block
+    if (warp == 0) {
+      int64_t excl;
+      if (t == 0) {
+        excl = base_from_dst ? *total_dst : 0;
+      } else {
+        if (lane == 0) atomicExch(reinterpret_cast<unsigned long long*>(status + t), kFlagAgg | (uint64_t)tile_total);
+        excl = look_back(status, t, flags);
+      }
+      if (lane == 0) {
+        atomicExch(reinterpret_cast<unsigned long long*>(status + t), kFlagPrefix | (uint64_t)(excl + tile_total));
+        s_excl = excl;
+        if (t == n_tiles - 1 && total_dst) *total_dst = excl + tile_total;
+      }
+    }
+    __syncthreads();
+    int64_t run = s_excl + thread_excl;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
       s_tile[threadIdx.x * (kScanItems + 1) + k] = run;
@@ -141,25 +159,43 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const In* __restrict
     for (int k = 0; k < kScanItems; ++k) {
       const int j = k * kScanThreads + threadIdx.x;
       const int64_t i = t0 + j;
-      if (i < e) out[i] = s_tile[j + j / kScanItems];
+      if (i < n) out[i] = s_tile[j + j / kScanItems];
     }
-    carry += tile_total;
-    __syncthreads();  // the tile buffer is reused
+    __syncthreads();  // the tile buffer and s_ticket are reused
+  }
+  // every CTA has left its loop (and its look-backs) before it counts itself
+  // done; the last one resets the state
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(done, 1ull) == (unsigned long long)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    for (int64_t i = threadIdx.x; i < n_tiles; i += kScanThreads) status[i] = 0;
+    if (threadIdx.x == 0) {
+      if (n_tiles == 0 && total_dst && !base_from_dst) *total_dst = 0;
+      *ticket = 0;
+      *done = 0;
+    }
   }
 }
 
 }  // namespace
 
+int64_t scan_state_words(int64_t max_elements) {
+  return 2 + (std::max<int64_t>(max_elements, 1) + kScanTile - 1) / kScanTile;
+}
+
 // out[i] = base + sum_{j<i} in[j]; base = *total_dst if base_from_dst != 0
 // (a running total in device memory) else 0.  Writes base + sum to
-// *total_dst when total_dst is non-NULL.  in and out may alias.
+// *total_dst when total_dst is non-NULL.  in and out may alias (a tile is
+// read whole before it is written).
 template <typename In>
 static cudaError_t launch_scan(const In* in, int64_t* out, const int64_t* n_dev, int64_t n_host,
                                int64_t* total_dst, int64_t base_from_dst, ScanTmp tmp, cudaStream_t s) {
-  k_scan_reduce<In><<<kScanBlocks, kScanThreads, 0, s>>>(in, n_dev, n_host, tmp.block_sums);
-  k_scan_blocks<<<1, kScanBlocks, 0, s>>>(tmp.block_sums, base_from_dst ? total_dst : nullptr,
-                                          total_dst);
-  k_scan_down<In><<<kScanBlocks, kScanThreads, 0, s>>>(in, out, n_dev, n_host, tmp.block_sums);
+  k_scan<In><<<tmp.grid, kScanThreads, 0, s>>>(in, out, n_dev, n_host, total_dst, base_from_dst ? 1 : 0, tmp.state,
+                                               tmp.cap_tiles, tmp.flags);
   return cudaGetLastError();
 }
 
