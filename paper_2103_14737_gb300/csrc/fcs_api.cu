@@ -316,7 +316,6 @@ __global__ void k_range_begin(Sizes* s, const int64_t* __restrict__ off, int32_t
   s->n_big = 0;
   s->n_pdefer = 0;
   s->n_pdefer_ptrs = 0;
-  s->n_pretry = 0;
   s->queue = 0;
 }
 
@@ -418,7 +417,8 @@ int enqueue_range(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, int32_t range
     FCS_TRY(ws_reserve_hits(ws, ws->h_sizes->n_hits, a.cfg.mode));
     w = ws->view();
   }
-  FCS_CUDA(launch_task_finish(w, a.dbg, det, a.n_particles * a.geo->d.n_layers, L));
+  FCS_CUDA(launch_task_finish(w, a.dbg, det, (sync_size || a.cfg.batched == 2) ? 1 : 0,
+                              a.n_particles * a.geo->d.n_layers, L));
   if (tev) FCS_CUDA(record_stage(tev[1], a.s));
   if (a.cfg.batched == 2) {
     // per-task launches: read the range's first hits and hit counts, then
@@ -1188,7 +1188,7 @@ int fcs_simulate_backward(const fcs_geo* geo, const fcs_params* prm, fcs_workspa
       FCS_TRY(ws_reserve_hits(ws, ws->h_sizes->n_hits, FCS_MODE_ATOMIC));
       w = ws->view();
     }
-    FCS_CUDA(launch_task_finish(w, nullptr, 0, n_particles * geo->d.n_layers, L));
+    FCS_CUDA(launch_task_finish(w, nullptr, 0, cfg.sync ? 1 : 0, n_particles * geo->d.n_layers, L));
     const float* g = dL_dcells + (int64_t)lo * geo->d.n_cells;
     FCS_CUDA(launch_hits_grad(geo->d, prm->d, w, lo, k0, k1, first_event, hc, g, ws->grad_acc, ws->grad_touched, L));
     FCS_CUDA(launch_recheck_grad(geo->d, prm->d, w, lo, k0, k1, first_event, g, ws->grad_acc, ws->grad_touched, L));

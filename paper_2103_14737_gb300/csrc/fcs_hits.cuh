@@ -382,7 +382,10 @@ __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKPara
   const int64_t H = kp.static_tiles ? kp.h_hi : w.sizes->n_hits;
   const int64_t T_last = kp.static_tiles ? (int64_t)kp.t_last : w.sizes->n_tasks - 1;
   const int64_t hbase = kp.static_tiles ? kp.h_lo : 0;
-  if (H > w.gmap_cap * (int64_t)kGranule) return;  // flagged by the task finish kernel
+  if (H > w.gmap_cap * (int64_t)kGranule) {  // the tile map is too small for the hits
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_HIT_CAPACITY);
+    return;
+  }
   const unsigned long long n_tiles = (unsigned long long)((H - hbase + TILE - 1) / TILE);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t hit_dbg_base = kp.dbg_hit_cell || kp.dbg_hit_bin ? w.sizes->hit_base : 0;

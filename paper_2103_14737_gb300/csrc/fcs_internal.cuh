@@ -101,7 +101,6 @@ struct Sizes {
   int64_t n_big;        // deterministic mode: cells with more records than one thread sorts
   int64_t n_pdefer;     // inversion draws deferred to FP64 in the current range (front of pdefer)
   int64_t n_pdefer_ptrs;  // PTRS draws deferred to FP64 in the current range (back of pdefer)
-  int64_t n_pretry;     // PTRS draws continued after iteration 0 (their list lives in th)
   unsigned long long queue;  // hit-kernel work-queue counter (tiles handed out)
   uint32_t flags;       // fcs_device_flag bits
   uint32_t n_poisson_fp64;  // Poisson draws that needed an FP64 decision (call total)
@@ -185,6 +184,11 @@ cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, const int64_t* n_de
                             cudaStream_t s);
 // Exclusive scan of n uint32 values into int64 (no base, no total).
 cudaError_t launch_scan_u32(const uint32_t* in, int64_t* out, int64_t n, ScanTmp tmp, cudaStream_t s);
+// The hit offsets th (exclusive scan of the tasks' hit counts tn, *n_tasks of
+// them; total to *n_hits) and the tile map gmap[g] = the task holding hit
+// g * kGranule, for g < gmap_cap.
+cudaError_t launch_scan_hits(const int64_t* tn, int64_t* th, const int64_t* n_tasks, int64_t* n_hits, int32_t* gmap,
+                             int64_t gmap_cap, ScanTmp tmp, cudaStream_t s);
 
 // fcs_tasks.cu: tasks, Poisson counts and the two scans (task and hit offsets);
 // then the records' hit offsets, the tile map and the validation dumps.
@@ -193,7 +197,8 @@ cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_par
                                int32_t ev_lo, int32_t ev_hi, uint32_t k0, uint32_t k1,
                                int64_t first_event, WsDev w, ScanTmp tmp, int64_t n_part_max,
                                int energy_interp, const Launch& L);
-cudaError_t launch_task_finish(WsDev w, const fcs_debug* dbg, int det, int64_t n_task_max, const Launch& L);
+cudaError_t launch_task_finish(WsDev w, const fcs_debug* dbg, int det, int fill_map, int64_t n_task_max,
+                               const Launch& L);
 
 // fcs_hits.cu: what the hit kernel does with a certified hit
 enum HitMode : int {

@@ -13,6 +13,11 @@
 // output move through shared memory (coalesced), each thread scanning
 // kScanItems consecutive elements.  The last CTA to finish resets the ticket
 // and the status words it used, so the state is zero again for the next scan.
+//
+// The scan of the tasks' hit counts also writes the tile map: granule g (hits
+// [g kGranule, (g + 1) kGranule)) -> the task holding hit g kGranule, from
+// each task's first hit and count while the tile is at hand (granules below
+// the map's capacity; the hit kernel reports a map too small for the hits).
 #include "fcs_internal.cuh"
 
 namespace fcs {
@@ -92,10 +97,11 @@ __device__ __forceinline__ int64_t look_back(const uint64_t* status, int64_t t, 
   }
 }
 
-template <typename In>
+template <typename In, bool GMAP>
 __global__ void __launch_bounds__(kScanThreads) k_scan(const In* in, int64_t* out, const int64_t* n_dev, int64_t n_host,
                                                      int64_t* total_dst, int base_from_dst, uint64_t* state,
-                                                     int64_t cap_tiles, uint32_t* flags) {
+                                                     int64_t cap_tiles, uint32_t* flags, int32_t* gmap,
+                                                     int64_t gmap_cap) {
   __shared__ int64_t s_tile[kScanTile + kScanTile / kScanItems];  // element j at j + j / kScanItems
   __shared__ int64_t s_warp[kScanThreads / 32];
   __shared__ int64_t s_excl;
@@ -151,6 +157,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const In* in, int64_t* ou
     int64_t run = s_excl + thread_excl;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
+      if constexpr (GMAP) {
+        const int64_t i = t0 + threadIdx.x * kScanItems + k;  // task i: hits [run, run + v[k])
+        if (i < n) {
+          for (int64_t g = (run + kGranule - 1) / kGranule; g * kGranule < run + v[k] && g < gmap_cap; ++g)
+            gmap[g] = (int32_t)i;
+        }
+      }
       s_tile[threadIdx.x * (kScanItems + 1) + k] = run;
       run += v[k];
     }
@@ -191,11 +204,12 @@ int64_t scan_state_words(int64_t max_elements) {
 // (a running total in device memory) else 0.  Writes base + sum to
 // *total_dst when total_dst is non-NULL.  in and out may alias (a tile is
 // read whole before it is written).
-template <typename In>
+template <typename In, bool GMAP = false>
 static cudaError_t launch_scan(const In* in, int64_t* out, const int64_t* n_dev, int64_t n_host,
-                               int64_t* total_dst, int64_t base_from_dst, ScanTmp tmp, cudaStream_t s) {
-  k_scan<In><<<tmp.grid, kScanThreads, 0, s>>>(in, out, n_dev, n_host, total_dst, base_from_dst ? 1 : 0, tmp.state,
-                                               tmp.cap_tiles, tmp.flags);
+                               int64_t* total_dst, int64_t base_from_dst, ScanTmp tmp, cudaStream_t s,
+                               int32_t* gmap = nullptr, int64_t gmap_cap = 0) {
+  k_scan<In, GMAP><<<tmp.grid, kScanThreads, 0, s>>>(in, out, n_dev, n_host, total_dst, base_from_dst ? 1 : 0,
+                                                     tmp.state, tmp.cap_tiles, tmp.flags, gmap, gmap_cap);
   return cudaGetLastError();
 }
 
@@ -206,6 +220,11 @@ cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, const int64_t* n_de
 
 cudaError_t launch_scan_u32(const uint32_t* in, int64_t* out, int64_t n, ScanTmp tmp, cudaStream_t s) {
   return launch_scan(in, out, nullptr, n, nullptr, 0, tmp, s);
+}
+
+cudaError_t launch_scan_hits(const int64_t* tn, int64_t* th, const int64_t* n_tasks, int64_t* n_hits, int32_t* gmap,
+                             int64_t gmap_cap, ScanTmp tmp, cudaStream_t s) {
+  return launch_scan<int64_t, true>(tn, th, n_tasks, 0, n_hits, 0, tmp, s, gmap, gmap_cap);
 }
 
 }  // namespace fcs

@@ -442,8 +442,9 @@ __global__ void __launch_bounds__(128) k_task_init(const GeoDev g, const ParamDe
 // front and its PTRS tasks from the back of a per-warp shared array, and
 // draws them 32 at a time, inversion rounds first: a round runs one method,
 // and warps never wait for one another.  A PTRS round runs iteration 0 only
-// (most draws accept there); the draws it rejects continue in
-// k_task_ptrs_retry, so that one long draw does not hold 31 idle lanes.
+// (most draws accept there); the warp collects the draws it rejects and
+// continues them from iteration 1 in rounds of 32, so that one long draw does
+// not hold 31 idle lanes.
 // Draws the FP32 path cannot certify are queued for k_task_poisson64, so that
 // FP64 work runs in full warps instead of stalling a warp for one lane.
 constexpr int kPoisWarps = 4;
@@ -480,14 +481,27 @@ __global__ void __launch_bounds__(32 * kPoisWarps) k_task_poisson(WsDev w, uint3
   __shared__ int s_list[kPoisWarps][kPoisWin];  // inversion tasks from the front, PTRS from the back
   __shared__ float s_mu[kPoisWarps][kPoisWin];
   __shared__ float s_rcp[kInvMax + 1];          // 1 / k, correctly rounded
+  __shared__ int32_t s_retry[kPoisWarps][64];   // PTRS draws rejected at iteration 0
   for (int k = threadIdx.x; k <= kInvMax; k += blockDim.x) s_rcp[k] = __frcp_rn((float)k);
   __syncthreads();
   const int64_t T = min(w.sizes->n_tasks, w.task_cap);
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t nw = (int64_t)gridDim.x * kPoisWarps;
-  // the retry list lives in th, which the scan after the draws overwrites
-  int32_t* retry = reinterpret_cast<int32_t*>(w.th);
+  int n_r = 0;  // collected retries (warp-uniform)
+  // one round of retries: lane j continues s_retry[j] (j < cnt) from iteration 1
+  auto retry_round = [&](int cnt) {
+    const bool valid = lane < cnt;
+    int32_t k = 0;
+    int64_t t = 0;
+    if (valid) {
+      t = s_retry[wi][lane];
+      const TaskRec& r = w.tasks[t];
+      k = poisson_ptrs_fp32(w.tmu[t], (uint32_t)r.layer(), (uint32_t)r.particle, first_event_lo + (uint32_t)r.event(),
+                            k0, k1, lfact, n_lfact, 1u, kPtrsMaxIter);
+    }
+    store_count(w, valid, t, k, true);
+  };
   for (int64_t win = ((int64_t)blockIdx.x * kPoisWarps + wi) * kPoisWin; win < T; win += nw * kPoisWin) {
     int n_i = 0, n_p = 0;
 #pragma unroll
@@ -531,33 +545,24 @@ __global__ void __launch_bounds__(32 * kPoisWarps) k_task_poisson(WsDev w, uint3
                               first_event_lo + (uint32_t)r.event(), k0, k1, lfact, n_lfact, 0u, 1u);
       }
       store_count(w, valid, t, k, true);
-      warp_push(valid && k == kPoisRetry, t, (unsigned long long*)&w.sizes->n_pretry, retry, false, 0);
+      const bool rt = valid && k == kPoisRetry;
+      const unsigned rm = __ballot_sync(0xffffffffu, rt);
+      if (rt) s_retry[wi][n_r + __popc(rm & lt)] = (int32_t)t;
+      n_r += __popc(rm);
+      __syncwarp();
+      if (n_r >= 32) {  // a full round; the rest (< 32) moves to the front
+        retry_round(32);
+        const int rest = n_r - 32;
+        const int32_t mv = lane < rest ? s_retry[wi][32 + lane] : 0;
+        __syncwarp();
+        if (lane < rest) s_retry[wi][lane] = mv;
+        __syncwarp();
+        n_r = rest;
+      }
     }
     __syncwarp();  // the window's lists are reused
   }
-}
-
-// PTRS draws that rejected at iteration 0, from iteration 1 on (one per
-// lane; the list holds about a tenth of the PTRS draws).
-__global__ void __launch_bounds__(128) k_task_ptrs_retry(WsDev w, uint32_t k0, uint32_t k1, uint32_t first_event_lo,
-                                                          const float* lfact, int32_t n_lfact) {
-  const int64_t n = w.sizes->n_pretry;
-  const int32_t* retry = reinterpret_cast<const int32_t*>(w.th);
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t q0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; q0 < n; q0 += warps * 32) {
-    const int64_t q = q0 + lane;
-    const bool valid = q < n;
-    int32_t k = 0;
-    int64_t t = 0;
-    if (valid) {
-      t = retry[q];
-      const TaskRec& r = w.tasks[t];
-      k = poisson_ptrs_fp32(w.tmu[t], (uint32_t)r.layer(), (uint32_t)r.particle, first_event_lo + (uint32_t)r.event(),
-                            k0, k1, lfact, n_lfact, 1u, kPtrsMaxIter);
-    }
-    store_count(w, valid, t, k, true);
-  }
+  if (n_r > 0) retry_round(n_r);
 }
 
 // The deferred draws in FP64 (the definition itself): the inversion list
@@ -581,20 +586,21 @@ __global__ void __launch_bounds__(128) k_task_poisson64(WsDev w, uint32_t k0, ui
   }
 }
 
-// One thread per task: the tile map (granule -> task containing its first
-// hit); in deterministic mode the hit energy into tmu (the fold's compact
-// copy); validation dumps.
-__global__ void k_task_finish(WsDev w, fcs_debug dbg, int has_dbg, int det) {
+// One thread per task: in deterministic mode the hit energy into tmu (the
+// fold's compact copy); validation dumps; the tile map (granule -> task
+// holding its first hit) again when the call grew it after the scan that
+// wrote it (fill_map).
+__global__ void k_task_finish(WsDev w, fcs_debug dbg, int has_dbg, int det, int fill_map) {
   const int64_t T = min(w.sizes->n_tasks, w.task_cap);
   const int64_t H = w.sizes->n_hits;
-  const bool map_ok = H <= w.gmap_cap * (int64_t)kGranule;
-  if (!map_ok && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_HIT_CAPACITY);
+  const bool map_ok = fill_map && H <= w.gmap_cap * (int64_t)kGranule;
   const int64_t task_base = w.sizes->task_base;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t n = w.tn[t];
-    const int64_t b = w.th[t];
-    if (map_ok)
+    if (map_ok) {
+      const int64_t b = w.th[t];
       for (int64_t gi = (b + kGranule - 1) / kGranule; gi * kGranule < b + n; ++gi) w.gmap[gi] = (int32_t)t;
+    }
     if (det || has_dbg) {
       const TaskRec& r = w.tasks[t];
       const float Ehit = __fdiv_rn(r.El, (float)n);
@@ -635,18 +641,19 @@ cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_par
       (std::max<int64_t>(n_part_max * p.NL, 1) + kPoisWarps * kPoisWin - 1) / (kPoisWarps * kPoisWin),
       (int64_t)L.num_sms * 16);
   k_task_poisson<<<gpois, 32 * kPoisWarps, 0, L.s>>>(w, k0, k1, (uint32_t)first_event, p.lfact, p.n_lfact);
-  k_task_ptrs_retry<<<L.num_sms * 4, 128, 0, L.s>>>(w, k0, k1, (uint32_t)first_event, p.lfact, p.n_lfact);
   // the FP64 pipe is narrow: one warp per block spreads the few deferred draws
   // over every SM
   k_task_poisson64<<<L.num_sms * 8, 32, 0, L.s>>>(w, k0, k1, (uint32_t)first_event, p.lfact64, p.n_lfact);
   // the scan counts the tasks actually written (n_tasks <= task_cap by construction)
-  return launch_scan_i64(w.tn, w.th, &w.sizes->n_tasks, 0, &w.sizes->n_hits, 0, tmp, L.s);
+  return launch_scan_hits(w.tn, w.th, &w.sizes->n_tasks, &w.sizes->n_hits, w.gmap, w.gmap_cap, tmp, L.s);
 }
 
-cudaError_t launch_task_finish(WsDev w, const fcs_debug* dbg, int det, int64_t n_task_max, const Launch& L) {
+cudaError_t launch_task_finish(WsDev w, const fcs_debug* dbg, int det, int fill_map, int64_t n_task_max,
+                               const Launch& L) {
+  if (!dbg && !det && !fill_map) return cudaSuccess;  // the scan wrote the tile map
   fcs_debug d{};
   if (dbg) d = *dbg;
-  k_task_finish<<<grid_for(n_task_max, L), 128, 0, L.s>>>(w, d, dbg ? 1 : 0, det);
+  k_task_finish<<<grid_for(n_task_max, L), 128, 0, L.s>>>(w, d, dbg ? 1 : 0, det, fill_map);
   return cudaGetLastError();
 }
 

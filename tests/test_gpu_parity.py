@@ -268,14 +268,14 @@ def test_async_graph_replay_matches(sim):
     assert rc == 0 and st.n_nonzero == ref["stats"]["n_nonzero"]
     diff = (outs["cells"] - ref["cells"]).abs()
     assert (diff <= RTOL * ref["cells"].abs() + ATOL).all()
-    # the launch sequence of one event range (15 kernels): range begin,
-    # particle counts, the task-offset scan, task records, Poisson FP32 + PTRS
-    # retries + FP64 (3), the hit-offset scan, task finish, hits, recheck,
+    # the launch sequence of one event range (13 kernels): range begin,
+    # particle counts, the task-offset scan, task records, Poisson FP32 and
+    # FP64 (2), the hit-offset scan with the tile map, hits, recheck,
     # compaction (count, scan, write), range end; plus call begin and end
-    assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 15
+    assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 13
     sim.simulate(d, 21, sync=0, use_graph=1, outputs=outs, wave_events=2)
     torch.cuda.synchronize()
-    assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 2 * 15
+    assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 2 * 13
 
 
 def test_host_entry_point_matches(sim):
