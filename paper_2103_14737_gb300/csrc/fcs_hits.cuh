@@ -26,7 +26,7 @@
 
 namespace fcs {
 
-constexpr int kSmemTasks = 256;
+constexpr int kSmemTasks = 128;  // staged tasks per tile (more: the hit loop reads the records)
 
 struct HitKParams {
   GeoDev g;
@@ -49,6 +49,7 @@ struct HitKParams {
   int64_t h_lo, h_hi;
   int32_t t_last;
   int32_t static_tiles;
+  PhiloxRoundKeys rk;  // the round keys of (k0, k1), read from the parameter bank
 };
 
 // ---- shape bin: inverse CDF by guide table and binary search --------------
@@ -363,8 +364,11 @@ __device__ __forceinline__ void owner_scan(int16_t* s_owner, int* s_wmax) {
   for (int k = 0; k < HPT; ++k) s_owner[tid * HPT + k] = (int16_t)max(v[k], excl);
 }
 
+// Atomic mode asks for 10 CTAs of 128 threads per SM (48 registers): the
+// extra warps hide the guide-table loads; the other modes keep the
+// compiler's choice (a minimum of 0 CTAs is no constraint).
 template <int BLOCK, int HPT, int MODE>
-__global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKParams kp) {
+__global__ void __launch_bounds__(BLOCK, MODE == kModeAtomic ? 1280 / BLOCK : 0) k_hits(const __grid_constant__ HitKParams kp) {
   constexpr bool DET = MODE == kModeDet;
   constexpr int TILE = BLOCK * HPT;
   static_assert(TILE % kGranule == 0, "queue tiles must start on granules (the tile map's unit)");
@@ -438,7 +442,12 @@ __global__ void __launch_bounds__(BLOCK) k_hits(const __grid_constant__ HitKPara
           T = make_tile_task(tb, w, t0 + tl, h0, kp.first_event_lo, kp.ev_lo, row_stride);
         }
         const uint32_t hit = (uint32_t)(i - T.rel);
-        const uint4 x = philox4x32_10(make_uint4(hit, T.ctr_y, T.ctr_z, T.ctr_w), kp.k0, kp.k1);
+        // the atomic and gradient modes read the round keys from the parameters;
+        // the deterministic mode keeps the in-kernel key schedule, with which
+        // its register allocation (and time) is lower
+        uint4 x;
+        if constexpr (DET) x = philox4x32_10(make_uint4(hit, T.ctr_y, T.ctr_z, T.ctr_w), kp.k0, kp.k1);
+        else x = philox4x32_10_rk(make_uint4(hit, T.ctr_y, T.ctr_z, T.ctr_w), kp.rk);
         const int bin = sample_bin(kp.p, T.entry, x.x);
         const FastHit f = fast_cell(tb, T, x, bin);
         const bool ok = valid && f.sure;

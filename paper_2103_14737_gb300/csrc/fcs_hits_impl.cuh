@@ -23,6 +23,7 @@ static inline HitKParams make_hit_params(const GeoDev& g, const ParamDev& p, WsD
   kp.dbg_hit_cell = dbg ? dbg->hit_cell : nullptr;
   kp.dbg_hit_bin = dbg ? dbg->hit_bin : nullptr;
   kp.dbg_hit_cap = dbg ? dbg->hit_capacity : 0;
+  kp.rk = philox_round_keys(k0, k1);
   return kp;
 }
 

@@ -146,6 +146,31 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+// The same generator with the ten round keys (k0 + i W0, k1 + i W1) given,
+// e.g. from kernel parameters, so the key schedule costs no instructions.
+struct PhiloxRoundKeys {
+  uint32_t k[20];  // k[2 i] = k0 + i 0x9E3779B9, k[2 i + 1] = k1 + i 0xBB67AE85
+};
+__host__ __device__ inline PhiloxRoundKeys philox_round_keys(uint32_t k0, uint32_t k1) {
+  PhiloxRoundKeys r;
+  for (int i = 0; i < 10; ++i) {
+    r.k[2 * i] = k0 + (uint32_t)i * 0x9E3779B9u;
+    r.k[2 * i + 1] = k1 + (uint32_t)i * 0xBB67AE85u;
+  }
+  return r;
+}
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const PhiloxRoundKeys& rk) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ rk.k[2 * i], lo1, hi0 ^ c.w ^ rk.k[2 * i + 1], lo0);
+  }
+  return c;
+}
+
 // Counter layout of the method's random streams:
 // (index, layer | purpose << 16, particle in event, event).
 constexpr uint32_t kPurposeHit = 0u;
