@@ -187,19 +187,16 @@ __device__ __forceinline__ int64_t ptrs_iter32(float mu, const PtrsConst32& c, u
   return -2;
 }
 
-
-// Poisson draw in FP32 where every decision is certified.  Both methods
-// return the count, or -1 - i when a decision of PTRS iteration i (or of the
-// inversion, i = 0) is uncertain or mu is too large for FP32 headroom: the
-// caller then takes poisson_draw, the FP64 definition, for this task from
-// iteration i on.
+// Poisson draw in FP32 where every decision is certified; where one is not,
+// the caller takes poisson_draw, the FP64 definition, for the task.
 //
-// Inversion (mu < 10).  rcp[k] = __frcp_rn(k) for k <= kInvMax (a
-// shared-memory copy: the values the loop would compute).
+// Inversion (mu < 10): the count, or -1 when a decision is uncertain.
+// rcp[k] = __frcp_rn(k) for k <= kInvMax (a shared-memory copy: the values
+// the loop would compute).
 __device__ __forceinline__ int32_t poisson_inv_fp32(float mu32, uint32_t layer, uint32_t particle, uint32_t event,
-                                                    uint32_t k0, uint32_t k1, const float* rcp) {
+                                                    const PhiloxRoundKeys& rk, const float* rcp) {
   if (!(mu32 > 0.0f)) return 0;
-  const uint4 x = philox4x32_10(make_uint4(0u, layer | (kPurposePoisson << 16), particle, event), k0, k1);
+  const uint4 x = philox4x32_10_rk(make_uint4(0u, layer | (kPurposePoisson << 16), particle, event), rk);
   const float uf = u53f(x.x, x.y);
   float p = expf(-mu32);
   float F = p;
@@ -215,24 +212,17 @@ __device__ __forceinline__ int32_t poisson_inv_fp32(float mu32, uint32_t layer, 
   }
 }
 
-// PTRS (mu >= 10), iterations [i_begin, i_end).  When every one of them
-// rejects for certain and i_end < kPtrsMaxIter, returns kPoisRetry: the draw
-// continues at iteration i_end (its earlier iterations reject in the
-// definition too).
-constexpr int32_t kPoisRetry = INT32_MIN;
-__device__ __forceinline__ int32_t poisson_ptrs_fp32(float mu32, uint32_t layer, uint32_t particle, uint32_t event,
-                                                     uint32_t k0, uint32_t k1, const float* lfact, int32_t n_lfact,
-                                                     uint32_t i_begin, uint32_t i_end) {
-  if (mu32 > kPtrsFastMaxMu) return -1 - (int32_t)i_begin;
+// PTRS (mu >= 10), iteration i alone: the accepted count, -1 when it rejects
+// for certain (the draw continues at iteration i + 1), -2 when a decision is
+// uncertain or mu is too large for FP32 headroom (the FP64 definition takes
+// the draw from iteration i on).
+__device__ __forceinline__ int32_t ptrs_step_fp32(float mu32, uint32_t layer, uint32_t particle, uint32_t event,
+                                                  const PhiloxRoundKeys& rk, const float* lfact, int32_t n_lfact,
+                                                  uint32_t i) {
+  if (mu32 > kPtrsFastMaxMu) return -2;
   const PtrsConst32 c = ptrs_const32(mu32, lfact, n_lfact);
-  for (uint32_t i = i_begin; i < i_end; ++i) {
-    const uint4 x = philox4x32_10(make_uint4(i, layer | (kPurposePoisson << 16), particle, event), k0, k1);
-    const int64_t k = ptrs_iter32(mu32, c, x);
-    if (k == -2) return -1 - (int32_t)i;
-    if (k >= 0) return (int32_t)k;
-  }
-  if (i_end < kPtrsMaxIter) return kPoisRetry;
-  return (int32_t)floorf(mu32);
+  const uint4 x = philox4x32_10_rk(make_uint4(i, layer | (kPurposePoisson << 16), particle, event), rk);
+  return (int32_t)ptrs_iter32(mu32, c, x);
 }
 
 // Parametrisation entry of a particle (without the layer index).  Energy bin
@@ -441,10 +431,10 @@ __global__ void __launch_bounds__(128) k_task_init(const GeoDev g, const ParamDe
 // consecutive tasks, lists the window's inversion tasks (mu < 10) from the
 // front and its PTRS tasks from the back of a per-warp shared array, and
 // draws them 32 at a time, inversion rounds first: a round runs one method,
-// and warps never wait for one another.  A PTRS round runs iteration 0 only
-// (most draws accept there); the warp collects the draws it rejects and
-// continues them from iteration 1 in rounds of 32, so that one long draw does
-// not hold 31 idle lanes.
+// and warps never wait for one another.  A PTRS round runs one iteration per
+// lane (most draws accept at their first); a draw that rejects goes to the
+// warp's retry list with its next iteration, and the list runs as a round
+// whenever it holds 32, so that one long draw does not hold 31 idle lanes.
 // Draws the FP32 path cannot certify are queued for k_task_poisson64, so that
 // FP64 work runs in full warps instead of stalling a warp for one lane.
 constexpr int kPoisWarps = 4;
@@ -452,6 +442,8 @@ constexpr int kPoisWin = 128;
 
 // Appends the tasks of the lanes with `push` set to a list: warp-aggregated
 // counter increment, entry q at list[q] (front) or list[cap - 1 - q] (back).
+// Deferred draws are listed by method (inversion at the front of pdefer, PTRS
+// at its back) so that the FP64 warps run one method.
 __device__ __forceinline__ void warp_push(bool push, int64_t task, unsigned long long* counter, int32_t* list,
                                           bool back, int64_t cap) {
   const int lane = threadIdx.x & 31;
@@ -465,104 +457,115 @@ __device__ __forceinline__ void warp_push(bool push, int64_t task, unsigned long
   if (push) list[back ? cap - 1 - q : q] = (int32_t)task;
 }
 
-// Deferral to FP64 by method: inversion draws at the front of pdefer and
-// PTRS draws at its back, so that the FP64 warps run one method; a deferred
-// PTRS draw's tn holds the iteration the FP64 definition resumes at.
-__device__ __forceinline__ void store_count(const WsDev& w, bool valid, int64_t t, int32_t k, bool ptrs) {
-  if (valid && k != kPoisRetry) w.tn[t] = (k < 1) ? (k < 0 ? -1 - k : 1) : k;
-  warp_push(valid && k < 0 && k != kPoisRetry, t,
-            (unsigned long long*)(ptrs ? &w.sizes->n_pdefer_ptrs : &w.sizes->n_pdefer), w.pdefer, ptrs,
-            w.pdefer_cap);
-}
-
-__global__ void __launch_bounds__(32 * kPoisWarps) k_task_poisson(WsDev w, uint32_t k0, uint32_t k1,
-                                                                   uint32_t first_event_lo, const float* lfact,
-                                                                   int32_t n_lfact) {
+__global__ void __launch_bounds__(32 * kPoisWarps) k_task_poisson(WsDev w, PhiloxRoundKeys rk, uint32_t first_event_lo,
+                                                                   const float* lfact, int32_t n_lfact) {
   __shared__ int s_list[kPoisWarps][kPoisWin];  // inversion tasks from the front, PTRS from the back
   __shared__ float s_mu[kPoisWarps][kPoisWin];
   __shared__ float s_rcp[kInvMax + 1];          // 1 / k, correctly rounded
-  __shared__ int32_t s_retry[kPoisWarps][64];   // PTRS draws rejected at iteration 0
+  __shared__ int32_t s_rt[kPoisWarps][64];      // retry list: task
+  __shared__ uint8_t s_ri[kPoisWarps][64];      //             and its next PTRS iteration
   for (int k = threadIdx.x; k <= kInvMax; k += blockDim.x) s_rcp[k] = __frcp_rn((float)k);
   __syncthreads();
   const int64_t T = min(w.sizes->n_tasks, w.task_cap);
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t nw = (int64_t)gridDim.x * kPoisWarps;
-  int n_r = 0;  // collected retries (warp-uniform)
-  // one round of retries: lane j continues s_retry[j] (j < cnt) from iteration 1
-  auto retry_round = [&](int cnt) {
-    const bool valid = lane < cnt;
-    int32_t k = 0;
-    int64_t t = 0;
-    if (valid) {
-      t = s_retry[wi][lane];
-      const TaskRec& r = w.tasks[t];
-      k = poisson_ptrs_fp32(w.tmu[t], (uint32_t)r.layer(), (uint32_t)r.particle, first_event_lo + (uint32_t)r.event(),
-                            k0, k1, lfact, n_lfact, 1u, kPtrsMaxIter);
-    }
-    store_count(w, valid, t, k, true);
-  };
-  for (int64_t win = ((int64_t)blockIdx.x * kPoisWarps + wi) * kPoisWin; win < T; win += nw * kPoisWin) {
+  unsigned long long* n_inv_defer = (unsigned long long*)&w.sizes->n_pdefer;
+  unsigned long long* n_ptrs_defer = (unsigned long long*)&w.sizes->n_pdefer_ptrs;
+  int n_r = 0;  // retry list length (warp-uniform, < 64)
+  // the loop runs one window past the warp's last to drain the retry list
+  for (int64_t win = ((int64_t)blockIdx.x * kPoisWarps + wi) * kPoisWin;; win += nw * kPoisWin) {
+    const bool have = win < T;
     int n_i = 0, n_p = 0;
+    if (have) {
 #pragma unroll
-    for (int c = 0; c < kPoisWin / 32; ++c) {
-      const int idx = c * 32 + lane;
-      const int64_t t = win + idx;
-      const float mu = t < T ? w.tmu[t] : 0.0f;
-      const bool inv = t < T && mu < 10.0f, pt = t < T && !(mu < 10.0f);
-      const unsigned bi = __ballot_sync(0xffffffffu, inv), bp = __ballot_sync(0xffffffffu, pt);
-      s_mu[wi][idx] = mu;
-      if (inv) s_list[wi][n_i + __popc(bi & lt)] = idx;
-      if (pt) s_list[wi][kPoisWin - 1 - (n_p + __popc(bp & lt))] = idx;
-      n_i += __popc(bi);
-      n_p += __popc(bp);
-    }
-    __syncwarp();
-    for (int r0 = 0; r0 < n_i; r0 += 32) {
-      const int j = r0 + lane;
-      const bool valid = j < n_i;
-      int32_t k = 0;
-      int64_t t = 0;
-      if (valid) {
-        const int idx = s_list[wi][j];
-        t = win + idx;
-        const TaskRec& r = w.tasks[t];
-        k = poisson_inv_fp32(s_mu[wi][idx], (uint32_t)r.layer(), (uint32_t)r.particle,
-                             first_event_lo + (uint32_t)r.event(), k0, k1, s_rcp);
+      for (int c = 0; c < kPoisWin / 32; ++c) {
+        const int idx = c * 32 + lane;
+        const int64_t t = win + idx;
+        const float mu = t < T ? w.tmu[t] : 0.0f;
+        const bool inv = t < T && mu < 10.0f, pt = t < T && !(mu < 10.0f);
+        const unsigned bi = __ballot_sync(0xffffffffu, inv), bp = __ballot_sync(0xffffffffu, pt);
+        s_mu[wi][idx] = mu;
+        if (inv) s_list[wi][n_i + __popc(bi & lt)] = idx;
+        if (pt) s_list[wi][kPoisWin - 1 - (n_p + __popc(bp & lt))] = idx;
+        n_i += __popc(bi);
+        n_p += __popc(bp);
       }
-      store_count(w, valid, t, k, false);
-    }
-    for (int r0 = 0; r0 < n_p; r0 += 32) {
-      const int j = r0 + lane;
-      const bool valid = j < n_p;
-      int32_t k = 0;
-      int64_t t = 0;
-      if (valid) {
-        const int idx = s_list[wi][kPoisWin - 1 - j];
-        t = win + idx;
-        const TaskRec& r = w.tasks[t];
-        k = poisson_ptrs_fp32(s_mu[wi][idx], (uint32_t)r.layer(), (uint32_t)r.particle,
-                              first_event_lo + (uint32_t)r.event(), k0, k1, lfact, n_lfact, 0u, 1u);
-      }
-      store_count(w, valid, t, k, true);
-      const bool rt = valid && k == kPoisRetry;
-      const unsigned rm = __ballot_sync(0xffffffffu, rt);
-      if (rt) s_retry[wi][n_r + __popc(rm & lt)] = (int32_t)t;
-      n_r += __popc(rm);
       __syncwarp();
-      if (n_r >= 32) {  // a full round; the rest (< 32) moves to the front
-        retry_round(32);
-        const int rest = n_r - 32;
-        const int32_t mv = lane < rest ? s_retry[wi][32 + lane] : 0;
+      for (int r0 = 0; r0 < n_i; r0 += 32) {
+        const int j = r0 + lane;
+        const bool valid = j < n_i;
+        int32_t k = 0;
+        int64_t t = 0;
+        if (valid) {
+          const int idx = s_list[wi][j];
+          t = win + idx;
+          const TaskRec& r = w.tasks[t];
+          k = poisson_inv_fp32(s_mu[wi][idx], (uint32_t)r.layer(), (uint32_t)r.particle,
+                               first_event_lo + (uint32_t)r.event(), rk, s_rcp);
+          w.tn[t] = k < 1 ? 1 : k;  // provisional for a deferred draw
+        }
+        warp_push(valid && k < 0, t, n_inv_defer, w.pdefer, false, w.pdefer_cap);
+      }
+    }
+    // PTRS rounds: new draws of the window 32 at a time, or 32 retries when
+    // the list holds that many (after the warp's last window: all it holds)
+    int p_next = 0;
+    while (p_next < n_p || n_r >= (have ? 32 : 1)) {
+      const bool from_retry = n_r >= 32 || p_next >= n_p;
+      const int cnt = from_retry ? min(n_r, 32) : min(n_p - p_next, 32);
+      const bool valid = lane < cnt;
+      int64_t t = 0;
+      uint32_t it = 0;
+      float mu = 0.0f;
+      if (valid) {
+        if (from_retry) {
+          t = s_rt[wi][lane];
+          it = s_ri[wi][lane];
+          mu = w.tmu[t];
+        } else {
+          const int idx = s_list[wi][kPoisWin - 1 - (p_next + lane)];
+          t = win + idx;
+          mu = s_mu[wi][idx];
+        }
+      }
+      if (from_retry) {  // the entries past the round move to the front
+        const int rest = n_r - cnt;
+        const int32_t mt = lane < rest ? s_rt[wi][cnt + lane] : 0;
+        const uint8_t mi = lane < rest ? s_ri[wi][cnt + lane] : 0;
         __syncwarp();
-        if (lane < rest) s_retry[wi][lane] = mv;
+        if (lane < rest) {
+          s_rt[wi][lane] = mt;
+          s_ri[wi][lane] = mi;
+        }
         __syncwarp();
         n_r = rest;
+      } else {
+        p_next += cnt;
       }
+      int32_t k = 0;
+      if (valid) {
+        const TaskRec& r = w.tasks[t];
+        k = ptrs_step_fp32(mu, (uint32_t)r.layer(), (uint32_t)r.particle, first_event_lo + (uint32_t)r.event(), rk,
+                           lfact, n_lfact, it);
+        if (k == -1 && it + 1 >= kPtrsMaxIter) k = (int32_t)floorf(mu);  // every iteration rejected
+        if (k >= 0) w.tn[t] = k < 1 ? 1 : k;
+        else if (k == -2) w.tn[t] = it;  // the FP64 definition resumes here
+      }
+      warp_push(valid && k == -2, t, n_ptrs_defer, w.pdefer, true, w.pdefer_cap);
+      const bool rt = valid && k == -1;
+      const unsigned rm = __ballot_sync(0xffffffffu, rt);
+      if (rt) {
+        const int q = n_r + __popc(rm & lt);
+        s_rt[wi][q] = (int32_t)t;
+        s_ri[wi][q] = (uint8_t)(it + 1);
+      }
+      n_r += __popc(rm);
+      __syncwarp();
     }
+    if (!have) break;
     __syncwarp();  // the window's lists are reused
   }
-  if (n_r > 0) retry_round(n_r);
 }
 
 // The deferred draws in FP64 (the definition itself): the inversion list
@@ -640,7 +643,8 @@ cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_par
   const int gpois = (int)std::min<int64_t>(
       (std::max<int64_t>(n_part_max * p.NL, 1) + kPoisWarps * kPoisWin - 1) / (kPoisWarps * kPoisWin),
       (int64_t)L.num_sms * 16);
-  k_task_poisson<<<gpois, 32 * kPoisWarps, 0, L.s>>>(w, k0, k1, (uint32_t)first_event, p.lfact, p.n_lfact);
+  k_task_poisson<<<gpois, 32 * kPoisWarps, 0, L.s>>>(w, philox_round_keys(k0, k1), (uint32_t)first_event, p.lfact,
+                                                     p.n_lfact);
   // the FP64 pipe is narrow: one warp per block spreads the few deferred draws
   // over every SM
   k_task_poisson64<<<L.num_sms * 8, 32, 0, L.s>>>(w, k0, k1, (uint32_t)first_event, p.lfact64, p.n_lfact);
