@@ -193,6 +193,38 @@ def test_poisson_counts_wide_mu(sim, ogeo, oprm):
     assert got["stats"]["n_poisson_fp64"] < 0.25 * ref.n_tasks
 
 
+def test_poisson_large_mu_draw_for_draw(sim, prm, oprm):
+    """Hit counts of 6000 particles of 16 GeV to 1 TeV (means from tens to
+    tens of thousands: PTRS draws that reject and continue at later
+    iterations, uncertain FP32 decisions redone in FP64 from the iteration
+    where they arose, and the FP64-only large-mu path) equal the oracle's
+    Poisson function applied to each task's mean, draw for draw."""
+    rng = np.random.default_rng(31)
+    n = 6000
+    E = (2.0 ** rng.uniform(14.0, 20.0, n)).astype(np.float32)
+    ptype = rng.integers(0, 3, n).astype(np.int32)
+    eta = rng.uniform(-2.4, 2.4, n).astype(np.float32)
+    parts = synth.Particles(ptype, E, eta, rng.uniform(-np.pi, np.pi, n).astype(np.float32),
+                            np.array([0, n], dtype=np.int64))
+    got = sim.simulate(sim.to_device(parts), 5, first_event=3, debug_tasks=n * 24)
+    torch.cuda.synchronize()
+    k = got["stats"]["n_tasks"]
+    lay = got["task_layer"].cpu().numpy()[:k]
+    par = got["task_particle"].cpu().numpy()[:k]
+    n_gpu = got["task_n"].cpu().numpy()[:k]
+    NL = prm.frac.shape[-1]
+    frac = prm.frac.reshape(-1, NL)
+    mhe = prm.mean_hit_E.reshape(-1, NL)
+    entry = np.array([O.param_entry(oprm, int(ptype[i]), float(E[i]), float(eta[i])) for i in range(n)])
+    e = entry[par]
+    El = (E[par] * frac[e, lay]).astype(np.float32)  # fl32(E f), then fl32(E_l / mean hit energy)
+    mu = (El / mhe[e, lay]).astype(np.float32)
+    ref = np.maximum(O.poisson(mu.astype(np.float64), 5, lay, par, 3), 1)
+    assert (mu >= 10).sum() > 0.5 * k and (mu > 4096).sum() > 0
+    assert np.array_equal(ref, n_gpu.astype(np.int64))
+    assert got["stats"]["n_poisson_fp64"] > 0
+
+
 def test_pileup_events_parity(sim, ogeo, oprm):
     parts = synth.pileup(seed=8, n_events=2)  # full mu = 200 pile-up events
     ref, got = run_both(sim, ogeo, oprm, parts, seed=1, hits=False)
