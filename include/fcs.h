@@ -214,10 +214,11 @@ int fcs_workspace_reserve(fcs_workspace* ws, const fcs_geo* geo, int64_t n_parti
 /* Reads the device status of the last call on ws (waits for stream s). */
 int fcs_workspace_status(fcs_workspace* ws, fcs_stats* stats, cudaStream_t s);
 
-/* Kernel launches of one replay of the workspace's cached CUDA graph (the
- * launch sequence of the last call captured with config->use_graph != 0):
- * the kernel nodes of the captured graph.  n_kernels: host, written.
- * FCS_E_ARG when no call has been captured on ws. */
+/* Kernel launches of one replay of the CUDA graph the workspace launched
+ * last: a call with config->use_graph != 0, or a host-buffer call replayed in
+ * two waves (fcs_simulate_events_host).  The kernel nodes of the captured
+ * graph.  n_kernels: host, written.  FCS_E_ARG when no call on ws has run as a
+ * graph. */
 int fcs_workspace_graph_kernels(const fcs_workspace* ws, int64_t* n_kernels);
 
 /* Stage times of the last call on ws that ran with config->timing != 0, in
@@ -271,6 +272,14 @@ int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace
  * host memory (cudaMallocHost, cudaHostAlloc(Mapped) or a registered range;
  * the device address is taken with cudaPointerGetAttributes), the compaction
  * kernel writes the results there directly and no device-to-host copy runs.
+ * When the particle arrays are pinned too, the call is in atomic mode in one
+ * launch sequence (wave_events 0), has at least two events and offsets from
+ * 0 to n_particles, and the workspace has been sized by an earlier call, it
+ * runs as two waves of events on three streams (one CUDA graph, replayed
+ * while the arguments stay the same): the second wave's particles are copied
+ * in while the first wave computes, and the first wave's results (the first
+ * three quarters of the events) move to the host while the second computes.
+ * Each wave has its own accumulation rows.
  * Pageable memory works through device staging and copies. */
 int fcs_simulate_events_host(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
                              const int32_t* type, const float* E, const float* eta,

@@ -14,135 +14,141 @@ constexpr int kCItems = 16;  // four float4 per thread (rows are padded to 64 ce
 constexpr int kCVec = kCItems / 4;
 constexpr int kChunk = kCThreads * kCItems;
 
+// Both kernels take the chunks (kChunk cells of one row) t = row * cpr + chunk
+// grid-stride, so a capped grid leaves SMs to concurrent work.
 __global__ void __launch_bounds__(kCThreads) k_compact_count(const float* __restrict__ acc, int32_t n_cells,
-                                                           int32_t stride, int32_t cpr,
+                                                           int32_t stride, int32_t cpr, int64_t n_chunks,
                                                            int64_t* __restrict__ counts) {
-  const int chunk = blockIdx.x, row = blockIdx.y;
-  const int64_t c0 = (int64_t)chunk * kChunk + threadIdx.x * kCItems;
-  const float4* src = reinterpret_cast<const float4*>(acc + (int64_t)row * stride + c0);
-  int cnt = 0;
-  if (c0 < n_cells) {
-    float4 a[kCVec];
-#pragma unroll
-    for (int q = 0; q < kCVec; ++q) a[q] = src[q];
-#pragma unroll
-    for (int q = 0; q < kCVec; ++q) {
-      cnt += (c0 + 4 * q < n_cells) && (a[q].x != 0.0f);
-      cnt += (c0 + 4 * q + 1 < n_cells) && (a[q].y != 0.0f);
-      cnt += (c0 + 4 * q + 2 < n_cells) && (a[q].z != 0.0f);
-      cnt += (c0 + 4 * q + 3 < n_cells) && (a[q].w != 0.0f);
-    }
-  }
-  cnt = __reduce_add_sync(0xffffffffu, cnt);
   __shared__ int s[kCThreads / 32];
-  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = cnt;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int t = 0;
-    for (int i = 0; i < kCThreads / 32; ++i) t += s[i];
-    counts[(int64_t)row * cpr + chunk] = t;
+  for (int64_t t = blockIdx.x; t < n_chunks; t += gridDim.x) {
+    const int chunk = (int)(t % cpr), row = (int)(t / cpr);
+    const int64_t c0 = (int64_t)chunk * kChunk + threadIdx.x * kCItems;
+    const float4* src = reinterpret_cast<const float4*>(acc + (int64_t)row * stride + c0);
+    int cnt = 0;
+    if (c0 < n_cells) {
+      float4 a[kCVec];
+#pragma unroll
+      for (int q = 0; q < kCVec; ++q) a[q] = src[q];
+#pragma unroll
+      for (int q = 0; q < kCVec; ++q) {
+        cnt += (c0 + 4 * q < n_cells) && (a[q].x != 0.0f);
+        cnt += (c0 + 4 * q + 1 < n_cells) && (a[q].y != 0.0f);
+        cnt += (c0 + 4 * q + 2 < n_cells) && (a[q].z != 0.0f);
+        cnt += (c0 + 4 * q + 3 < n_cells) && (a[q].w != 0.0f);
+      }
+    }
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int sum = 0;
+      for (int i = 0; i < kCThreads / 32; ++i) sum += s[i];
+      counts[t] = sum;
+    }
+    __syncthreads();  // s is reused
   }
 }
 
 __global__ void __launch_bounds__(kCThreads) k_compact_write(
-    float* __restrict__ acc, int32_t n_cells, int32_t stride, int32_t cpr, int32_t ev_lo,
+    float* __restrict__ acc, int32_t n_cells, int32_t stride, int32_t cpr, int64_t n_chunks, int32_t ev_lo,
     const int64_t* __restrict__ offsets, float* __restrict__ cells_out, int32_t* __restrict__ cell_ids,
     float* __restrict__ cell_E, int64_t* __restrict__ event_offsets_out, int64_t capacity) {
-  const int chunk = blockIdx.x, row = blockIdx.y;
-  const int64_t c0 = (int64_t)chunk * kChunk + threadIdx.x * kCItems;
-  float4* src = reinterpret_cast<float4*>(acc + (int64_t)row * stride + c0);
-  float v[kCItems];
-#pragma unroll
-  for (int k = 0; k < kCItems; ++k) v[k] = 0.0f;
-  if (c0 < n_cells) {
-    float4 a[kCVec];
-#pragma unroll
-    for (int q = 0; q < kCVec; ++q) a[q] = src[q];
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int q = 0; q < kCVec; ++q) {
-      v[4 * q] = a[q].x;
-      v[4 * q + 1] = a[q].y;
-      v[4 * q + 2] = a[q].z;
-      v[4 * q + 3] = a[q].w;
-      src[q] = z;
-    }
-  }
-  unsigned mask = 0;
-#pragma unroll
-  for (int k = 0; k < kCItems; ++k)
-    if (c0 + k < n_cells && v[k] != 0.0f) mask |= 1u << k;
-  const int cnt = __popc(mask);
-  // block exclusive scan of cnt
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int x = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
   __shared__ int s_w[kCThreads / 32];
-  if (lane == 31) s_w[warp] = x;
-  __syncthreads();
-  int pre = 0;
-  for (int w = 0; w < warp; ++w) pre += s_w[w];
-  // the block's pairs go through shared memory so that the output is written
-  // with consecutive threads on consecutive positions
   __shared__ int32_t s_id[kChunk];
   __shared__ float s_E[kChunk];
-  int lpos = pre + x - cnt;
-#pragma unroll
-  for (int k = 0; k < kCItems; ++k) {
-    if (mask & (1u << k)) {
-      s_id[lpos] = (int32_t)(c0 + k);
-      s_E[lpos] = v[k];
-      ++lpos;
-    }
-  }
   __shared__ int s_total;
-  if (threadIdx.x == kCThreads - 1) s_total = lpos;  // the last thread ends the block's run
-  __syncthreads();
-  const int total = s_total;
-  const int64_t base = offsets[(int64_t)row * cpr + chunk];
-  for (int j = threadIdx.x; j < total; j += kCThreads) {
-    const int64_t pos = base + j;
-    if (pos < capacity) {
-      if (cell_ids) cell_ids[pos] = s_id[j];
-      if (cell_E) cell_E[pos] = s_E[j];
-    }
-  }
-  if (cells_out && c0 < n_cells) {
-    float* dst = cells_out + (int64_t)(ev_lo + row) * n_cells + c0;
-    if (c0 + kCItems <= n_cells && (n_cells & 3) == 0) {
+  for (int64_t t = blockIdx.x; t < n_chunks; t += gridDim.x) {
+    const int chunk = (int)(t % cpr), row = (int)(t / cpr);
+    const int64_t c0 = (int64_t)chunk * kChunk + threadIdx.x * kCItems;
+    float4* src = reinterpret_cast<float4*>(acc + (int64_t)row * stride + c0);
+    float v[kCItems];
 #pragma unroll
-      for (int q = 0; q < kCVec; ++q)
-        reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-    } else {
+    for (int k = 0; k < kCItems; ++k) v[k] = 0.0f;
+    if (c0 < n_cells) {
+      float4 a[kCVec];
 #pragma unroll
-      for (int k = 0; k < kCItems; ++k)
-        if (c0 + k < n_cells) dst[k] = v[k];
+      for (int q = 0; q < kCVec; ++q) a[q] = src[q];
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < kCVec; ++q) {
+        v[4 * q] = a[q].x;
+        v[4 * q + 1] = a[q].y;
+        v[4 * q + 2] = a[q].z;
+        v[4 * q + 3] = a[q].w;
+        src[q] = z;
+      }
     }
+    unsigned mask = 0;
+#pragma unroll
+    for (int k = 0; k < kCItems; ++k)
+      if (c0 + k < n_cells && v[k] != 0.0f) mask |= 1u << k;
+    const int cnt = __popc(mask);
+    // block exclusive scan of cnt
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    int pre = 0;
+    for (int w = 0; w < warp; ++w) pre += s_w[w];
+    // the block's pairs go through shared memory so that the output is written
+    // with consecutive threads on consecutive positions
+    int lpos = pre + x - cnt;
+#pragma unroll
+    for (int k = 0; k < kCItems; ++k) {
+      if (mask & (1u << k)) {
+        s_id[lpos] = (int32_t)(c0 + k);
+        s_E[lpos] = v[k];
+        ++lpos;
+      }
+    }
+    if (threadIdx.x == kCThreads - 1) s_total = lpos;  // the last thread ends the block's run
+    __syncthreads();
+    const int total = s_total;
+    const int64_t base = offsets[t];
+    for (int j = threadIdx.x; j < total; j += kCThreads) {
+      const int64_t pos = base + j;
+      if (pos < capacity) {
+        if (cell_ids) cell_ids[pos] = s_id[j];
+        if (cell_E) cell_E[pos] = s_E[j];
+      }
+    }
+    if (cells_out && c0 < n_cells) {
+      float* dst = cells_out + (int64_t)(ev_lo + row) * n_cells + c0;
+      if (c0 + kCItems <= n_cells && (n_cells & 3) == 0) {
+#pragma unroll
+        for (int q = 0; q < kCVec; ++q)
+          reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < kCItems; ++k)
+          if (c0 + k < n_cells) dst[k] = v[k];
+      }
+    }
+    if (chunk == 0 && threadIdx.x == 0 && event_offsets_out) event_offsets_out[ev_lo + row] = base;
+    __syncthreads();  // the staging arrays are reused
   }
-  if (chunk == 0 && threadIdx.x == 0 && event_offsets_out)
-    event_offsets_out[ev_lo + row] = offsets[(int64_t)row * cpr];
 }
 
 }  // namespace
 
 cudaError_t launch_compact(const GeoDev& g, WsDev w, int32_t rows, int32_t ev_lo, int64_t* chunk_counts,
                            int64_t* chunk_offsets, ScanTmp tmp, float* cells_out, int32_t* cell_ids,
-                           float* cell_E, int64_t* event_offsets_out, int32_t n_events_total,
-                           int64_t capacity, const Launch& L) {
-  (void)n_events_total;
+                           float* cell_E, int64_t* event_offsets_out, int64_t capacity, int max_ctas,
+                           const Launch& L) {
   if (rows <= 0) return cudaSuccess;
   const int cpr = (g.n_cells + kChunk - 1) / kChunk;
-  const dim3 grid(cpr, rows);
-  k_compact_count<<<grid, kCThreads, 0, L.s>>>(w.acc, g.n_cells, g.acc_stride, cpr, chunk_counts);
+  const int64_t n_chunks = (int64_t)rows * cpr;
+  const int grid = (int)std::min<int64_t>(n_chunks, max_ctas > 0 ? max_ctas : ((int64_t)1 << 30));
+  k_compact_count<<<grid, kCThreads, 0, L.s>>>(w.acc, g.n_cells, g.acc_stride, cpr, n_chunks, chunk_counts);
   // offsets continue the call's running output size (per-event mode)
-  cudaError_t e = launch_scan_i64(chunk_counts, chunk_offsets, nullptr, (int64_t)rows * cpr,
-                                  &w.sizes->nnz_total, 1, tmp, L.s);
+  cudaError_t e = launch_scan_i64(chunk_counts, chunk_offsets, nullptr, n_chunks, &w.sizes->nnz_total, 1, tmp, L.s);
   if (e != cudaSuccess) return e;
-  k_compact_write<<<grid, kCThreads, 0, L.s>>>(w.acc, g.n_cells, g.acc_stride, cpr, ev_lo, chunk_offsets,
+  k_compact_write<<<grid, kCThreads, 0, L.s>>>(w.acc, g.n_cells, g.acc_stride, cpr, n_chunks, ev_lo, chunk_offsets,
                                                cells_out, cell_ids, cell_E, event_offsets_out, capacity);
   return cudaGetLastError();
 }

@@ -345,6 +345,40 @@ def test_host_entry_point_pinned_outputs(sim):
     assert (ids.numpy()[n:] == -1).all()
 
 
+def test_host_entry_point_two_waves(sim):
+    """Pinned inputs and outputs: after a sizing call the host entry runs as two
+    waves on three streams (copies in, compute and results out overlapped),
+    one graph of 2 + 2 x 13 kernels; its cells match the deterministic
+    device call (atomic tolerance) and its ids and offsets match exactly, for
+    an odd event count and over repeated calls."""
+    parts = synth.pileup(seed=17, n_events=5, mu_pu=30)
+    ref = sim.simulate(sim.to_device(parts), 6, first_event=2, mode=fcs.MODE_DETERMINISTIC)
+    nnz = ref["stats"]["n_nonzero"]
+    cap = nnz + 16
+    pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(parts, k))).pin_memory()
+           for k in ("type", "E", "eta", "phi", "event_offsets")}
+    ids = torch.full((cap,), -1, dtype=torch.int32).pin_memory()
+    E = torch.zeros(cap, dtype=torch.float32).pin_memory()
+    off = torch.zeros(6, dtype=torch.int64).pin_memory()
+    cfg = fcs.make_config()
+    ref_ids = ref["cell_ids"][:nnz].cpu().numpy()
+    ref_E = ref["cell_E"][:nnz].cpu().numpy().astype(np.float64)
+    for call in range(3):
+        ids.fill_(-1)
+        E.zero_()
+        rc, st = fcs.fcs_simulate_events_host(sim.geo, sim.prm, sim.ws, pin["type"].numpy(), pin["E"].numpy(),
+                                              pin["eta"].numpy(), pin["phi"].numpy(), pin["event_offsets"].numpy(),
+                                              6, 2, cfg, ids.numpy(), E.numpy(), off.numpy())
+        assert rc == 0 and st.n_nonzero == nnz and st.n_hits == ref["stats"]["n_hits"]
+        assert np.array_equal(off.numpy(), ref["event_offsets"].cpu().numpy())
+        assert np.array_equal(ids.numpy()[:nnz], ref_ids)
+        err = np.abs(E.numpy()[:nnz].astype(np.float64) - ref_E)
+        assert (err <= RTOL * np.abs(ref_E) + ATOL).all()
+        assert (ids.numpy()[nnz:] == -1).all()
+        if call > 0:  # the first call may size the workspace synchronously
+            assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 2 * 13
+
+
 def test_sync_call_outgrows_workspace(geo, prm, ogeo, oprm):
     """A fresh workspace is sized by its first call; a larger later call
     overflows it, grows it and runs again with the same results."""
