@@ -317,6 +317,38 @@ def run_sweep(args):
                              "tasks": int(sim.simulate(many, SEED, outputs=dict(cells=None))["stats"]["n_tasks"]),
                              "per_event_over_batched": ms_e / ms_b, "per_task_over_batched": ms_t / ms_b,
                              "per_task_shape": "128x1"}
+    # one training step on 256 events: the forward call (graph replay) and the
+    # adjoint for a fixed dL/dE_cell (dense float32 rows, 193 MB)
+    n256 = min(256, n_ev)
+    d256 = sim.to_device(synth.pileup(seed=SEED, n_events=n256))
+    g256 = torch.randn((n256, geo.n_cells), generator=torch.Generator("cuda").manual_seed(5), device="cuda")
+    gf = torch.zeros(sim.n_entries, dtype=torch.float32, device="cuda")
+    gw = torch.zeros(sim.n_entries * 128, dtype=torch.float32, device="cuda")
+    shape = dict(block=b, hits_per_thread=h)
+    r256 = sim.simulate(d256, SEED, outputs=dict(cells=None), **shape)
+    sim.backward(d256, SEED, g256, d_frac=gf, d_shape_w=gw, **shape)
+    for _ in range(2):
+        sim.simulate(d256, SEED, sync=0, use_graph=1, outputs=dict(cells=None), **shape)
+        sim.backward(d256, SEED, g256, sync=0, d_frac=gf, d_shape_w=gw, **shape)
+    torch.cuda.synchronize()
+    tf, tb = [], []
+    for _ in range(3):
+        flush.zero_()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        sim.simulate(d256, SEED, sync=0, use_graph=1, outputs=dict(cells=None), **shape)
+        e1.record()
+        sim.backward(d256, SEED, g256, sync=0, d_frac=gf, d_shape_w=gw, **shape)
+        e2.record()
+        torch.cuda.synchronize()
+        tf.append(e0.elapsed_time(e1))
+        tb.append(e1.elapsed_time(e2))
+    rc, stt = fcs.fcs_workspace_status(sim.ws)
+    assert rc == 0, (rc, stt.as_dict())
+    H256 = r256["stats"]["n_hits"]
+    out["forward_backward_256"] = {"events": n256, "hits": H256, "forward_ms": float(np.mean(tf)),
+                                   "backward_ms": float(np.mean(tb)),
+                                   "step_hits_per_s": H256 / ((np.mean(tf) + np.mean(tb)) * 1e-3)}
     print(json.dumps(out), flush=True)
     sim.close()
 
@@ -381,11 +413,12 @@ def main():
     outs["cells"] = None
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def timed(K, W, **kw):
+    def timed(K, W, seed=SEED, **kw):
         # one synchronous call sizes the workspace for this mode (not timed)
-        sim.simulate(d, SEED, first_event=first_event, outputs=outs, **kw)
+        r = sim.simulate(d, seed, first_event=first_event, outputs=outs, **kw)
+        timed.n_hits = r["stats"]["n_hits"]
         for _ in range(W):
-            sim.simulate(d, SEED, first_event=first_event, sync=0, use_graph=1, outputs=outs, timing=1, **kw)
+            sim.simulate(d, seed, first_event=first_event, sync=0, use_graph=1, outputs=outs, timing=1, **kw)
         torch.cuda.synchronize()
         t_step, t_hit = [], []
         st = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
@@ -393,7 +426,7 @@ def main():
         for k in range(K):
             flush.zero_()
             st[k].record()
-            sim.simulate(d, SEED, first_event=first_event, sync=0, use_graph=1, outputs=outs, timing=1, **kw)
+            sim.simulate(d, seed, first_event=first_event, sync=0, use_graph=1, outputs=outs, timing=1, **kw)
             en[k].record()
             t_hit.append(fcs.fcs_workspace_timings(sim.ws))  # waits for this step's stage events
         torch.cuda.synchronize()
@@ -463,6 +496,39 @@ def main():
         tb = float(np.mean([a.elapsed_time(b) for a, b in zip(st, en)]))
         extra["backward"] = {"hits_per_s": H / (tb * 1e-3), "ms_per_step": tb, "forward_ms_per_step": ms,
                              "outputs": "dL/dfrac and dL/dshape_w of all entries, FP32, accumulated"}
+        # three more simulation seeds of the same events (the parametrisation keeps its seed)
+        seeds = {}
+        for sd in (2, 3, 4):
+            ts, _ = timed(max(5, args.steps // 4), 2, seed=sd, hits_per_thread=args.hpt, block=args.block)
+            seeds[str(sd)] = {"hits": timed.n_hits, "hits_per_s": timed.n_hits / (np.mean(ts) * 1e-3),
+                              "ms_per_step": float(np.mean(ts))}
+        extra["seeds"] = seeds
+        # the 400-particle hard-scatter event alone, with the standard mean hit
+        # energies (5-200 MeV) and with 0.5-20 MeV ("hi": ten times the hits)
+        one = {}
+        p1 = synth.ttbar_like(SEED, 1)
+        for name, rng_mhe in (("ttbar400", (5.0, 200.0)), ("ttbar400_hi", (0.5, 20.0))):
+            s1 = sim if name == "ttbar400" else fcs.Simulator(geo, synth.params(geo, mean_hit_range=rng_mhe))
+            d1 = s1.to_device(p1)
+            r1 = s1.simulate(d1, SEED, outputs=dict(cells=None), hits_per_thread=args.hpt, block=args.block)
+            for _ in range(3):
+                s1.simulate(d1, SEED, sync=0, use_graph=1, outputs=dict(cells=None), hits_per_thread=args.hpt,
+                            block=args.block)
+            Ko = 20
+            st = [torch.cuda.Event(enable_timing=True) for _ in range(Ko)]
+            en = [torch.cuda.Event(enable_timing=True) for _ in range(Ko)]
+            for k in range(Ko):
+                st[k].record()
+                s1.simulate(d1, SEED, sync=0, use_graph=1, outputs=dict(cells=None), hits_per_thread=args.hpt,
+                            block=args.block)
+                en[k].record()
+            torch.cuda.synchronize()
+            t1 = float(np.median([a.elapsed_time(b) for a, b in zip(st, en)]))
+            one[name] = {"hits": r1["stats"]["n_hits"], "ms_per_event": t1,
+                         "hits_per_s": r1["stats"]["n_hits"] / (t1 * 1e-3), "mean_hit_E_MeV": list(rng_mhe)}
+            if s1 is not sim:
+                s1.close()
+        extra["single_event"] = one
 
     # end to end through the host-buffer entry point (copies inside the timed region)
     e2e = None

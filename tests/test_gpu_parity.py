@@ -92,6 +92,26 @@ def test_ttbar_parity_atomic(sim, ogeo, oprm):
     check_cells_atomic(ref, got, 1)
 
 
+def test_ttbar_high_hit_params(geo, ogeo):
+    """The hard-scatter event with mean hit energies of 0.5-20 MeV instead of
+    5-200 MeV (ten times the hits, about 2M): tasks, hits, per-hit cells and
+    deterministic cells bit-exact, atomic cells within tolerance."""
+    prm_hi = synth.params(geo, mean_hit_range=(0.5, 20.0))
+    s = fcs.Simulator(geo, prm_hi)
+    try:
+        oprm_hi = O.OracleParams(prm_hi)
+        parts = synth.ttbar_like(seed=3)
+        ref, got = run_both(s, ogeo, oprm_hi, parts, seed=11, first_event=1)
+        assert ref.n_hits > 1_000_000
+        check_tasks_hits(ref, got)
+        check_cells_atomic(ref, got, 1)
+        det = s.simulate(s.to_device(parts), 11, first_event=1, mode=fcs.MODE_DETERMINISTIC, dense=True)
+        torch.cuda.synchronize()
+        assert np.array_equal(det["cells"].cpu().numpy().view(np.uint32), ref.cells_canon.view(np.uint32))
+    finally:
+        s.close()
+
+
 @pytest.mark.parametrize("batched", [1, 0])
 def test_deterministic_bit_exact(sim, ogeo, oprm, batched):
     parts = synth.pileup(seed=4, n_events=3, mu_pu=15)
