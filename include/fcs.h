@@ -111,8 +111,8 @@ typedef struct fcs_config {
                               event; 2: per event, one hit-kernel launch per task (the paper's
                               non-grouped GPU mode, Sec. 4; the call waits for the stream per
                               event to read the task list; no graph capture) */
-  int32_t hits_per_thread; /* hit kernel: hits per thread per tile, 1, 2, 4 or 8; 0 = default (4) */
-  int32_t block;           /* hit kernel: threads per block, 128, 256 or 512; 0 = default (256) */
+  int32_t hits_per_thread; /* hit kernel: hits per thread per tile, 1, 2, 4 or 8; 0 = default (8) */
+  int32_t block;           /* hit kernel: threads per block, 128, 256 or 512; 0 = default (128) */
   int32_t sync;            /* != 0: wait for the stream, read the device status (see above) */
   int32_t use_graph;       /* != 0 (requires sync == 0): capture the launch sequence as a CUDA
                               graph keyed by every argument, replay it on identical calls */

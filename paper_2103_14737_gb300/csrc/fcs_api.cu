@@ -1,14 +1,16 @@
 // fcs_api.cu - the C ABI of include/fcs.h: argument validation, device
 // residency of geometry and parametrisation, the workspace, and the launch
 // sequence of a simulation call:
-//   per event range: range setup -> particle tasks (Poisson counts) -> two
-//   scans (task and hit offsets) -> task records -> tile map -> hit kernel ->
-//   FP64 recheck -> compaction (atomic) or sort + fold (deterministic)
-// followed by one finishing kernel.  Batched calls use one range for all
-// events (the grouped simulation of Sec. 4); per-event calls use one range
-// per event, as the paper's per-event GPU path did.  No launch depends on a
-// host-read size except in sync calls, which read the hit count once to size
-// the workspace.
+//   per event range: range setup -> particle task counts -> task-offset scan
+//   -> task records -> Poisson counts (FP32, then the deferred FP64 draws) ->
+//   hit-offset scan with the tile map -> hit kernel -> FP64 recheck ->
+//   compaction (atomic) or sort + fold (deterministic)
+// between a starting and a finishing kernel.  Batched calls use one range for
+// all events (the grouped simulation of Sec. 4) or waves of events; per-event
+// calls use one range per event, as the paper's per-event GPU path did.  No
+// launch depends on a host-read size except in sync calls, which read the hit
+// count once to size the workspace.  Host-buffer calls with pinned buffers run
+// as two waves on three streams so that the transfers overlap the compute.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -550,8 +552,8 @@ int enqueue_call(const CallArgs& a, bool sync_size, const HitCfg& hc, int key_ta
 
 HitCfg hit_cfg(const fcs_config& c) {
   HitCfg h;
-  h.block = c.block ? c.block : 256;
-  h.hpt = c.hits_per_thread ? c.hits_per_thread : 4;
+  h.block = c.block ? c.block : 128;  // the shape fcs_autotune picks on GB300 for pile-up batches
+  h.hpt = c.hits_per_thread ? c.hits_per_thread : 8;
   h.det = c.mode == FCS_MODE_DETERMINISTIC;
   return h;
 }

@@ -1,8 +1,10 @@
 // fcs_tasks.cu - task build of the hit loop (Listing 1): per particle the
 // parametrisation entry and its layers with a non-zero float layer energy;
 // per task the Poisson hit count (get_number_of_hits) and the float hit
-// energy; task records in (event, particle, layer) order and the tile -> task
-// map.  Flat per-task kernels keep the Poisson draws of a warp together.
+// energy; task records in (event, particle, layer) order.  Flat per-task
+// kernels keep the Poisson draws of a warp together.  (The hit-offset scan
+// writes the tile -> task map; the task finish kernel here writes it again
+// when a call grew the map after that scan.)
 #include <algorithm>
 
 #include "fcs_internal.cuh"
