@@ -718,6 +718,13 @@ int host_two_waves(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
     if (e == cudaSuccess) rc = enqueue_two_waves(a, type, E, eta, phi, event_offsets, W, p_mid, key_task_bits);
     cudaError_t e2 = cudaStreamEndCapture(cs, &g);
     cudaStreamDestroy(cs);
+    if (e != cudaSuccess || rc != FCS_OK || e2 != cudaSuccess) {
+      // the forked streams took part in a failed capture: start them afresh
+      (void)cudaGetLastError();
+      cudaStreamDestroy(ws->s_in);
+      cudaStreamDestroy(ws->s_out);
+      ws->s_in = ws->s_out = nullptr;
+    }
     if (e != cudaSuccess) return set_err(FCS_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
     if (rc != FCS_OK) {
       if (g) cudaGraphDestroy(g);
