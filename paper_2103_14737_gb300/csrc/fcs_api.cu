@@ -240,7 +240,8 @@ struct fcs_workspace {
   }
 
   ScanTmp scan_tmp() const {
-    return ScanTmp{scan_state, ss_cap - 2, d_sizes ? &d_sizes->flags : nullptr, num_sms * 2};
+    // three 256-thread CTAs per SM: the scans' 76 registers and 35 KB of tile buffer allow it
+    return ScanTmp{scan_state, ss_cap - 2, d_sizes ? &d_sizes->flags : nullptr, num_sms * 3};
   }
 };
 
@@ -320,11 +321,19 @@ __global__ void k_call_begin(Sizes* s) {
   *s = z;
 }
 
-__global__ void k_range_begin(Sizes* s, const int64_t* __restrict__ off, int32_t ev_lo, int32_t ev_hi,
-                              int64_t n_particles, int64_t pcap) {
+// One block of kRangeThreads: the range's offsets are checked in parallel
+// (non-decreasing, within [0, n_particles] and the particle capacity), then
+// thread 0 resets the range's counters.
+constexpr int kRangeThreads = 256;
+__global__ void __launch_bounds__(kRangeThreads) k_range_begin(Sizes* s, const int64_t* __restrict__ off,
+                                                               int32_t ev_lo, int32_t ev_hi, int64_t n_particles,
+                                                               int64_t pcap) {
+  bool bad = false;
+  for (int32_t e = ev_lo + (int32_t)threadIdx.x; e < ev_hi; e += kRangeThreads) bad |= off[e + 1] < off[e];
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x != 0) return;
   const int64_t a = off[ev_lo], b = off[ev_hi];
-  bool bad = a < 0 || b < a || b > n_particles || (b - a) > pcap;
-  for (int32_t e = ev_lo; e < ev_hi && !bad; ++e) bad = off[e + 1] < off[e];
+  bad = bad || a < 0 || b < a || b > n_particles || (b - a) > pcap;
   s->n_part = bad ? 0 : (b - a);
   if (bad) s->flags |= FCS_FLAG_BAD_OFFSETS;
   s->n_tasks = 0;
@@ -440,7 +449,8 @@ int enqueue_range_hits(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, int32_t 
   const int det = a.cfg.mode == FCS_MODE_DETERMINISTIC;
   cudaEvent_t* tev = a.cfg.timing ? &ws->tev[(size_t)range * 5] : nullptr;
   if (tev) FCS_CUDA(record_stage(tev[0], a.s));
-  k_range_begin<<<1, 1, 0, a.s>>>(ws->d_sizes, a.parts.event_offsets, ev_lo, ev_hi, a.n_particles, ws->pcap);
+  k_range_begin<<<1, kRangeThreads, 0, a.s>>>(ws->d_sizes, a.parts.event_offsets, ev_lo, ev_hi, a.n_particles,
+                                              ws->pcap);
   const uint32_t k0 = (uint32_t)(a.seed & 0xFFFFFFFFu), k1 = (uint32_t)(a.seed >> 32);
   const ScanTmp tmp = ws->scan_tmp();
   auto view = [&]() {
@@ -595,7 +605,7 @@ int enqueue_two_waves(const CallArgs& a, const int32_t* type, const float* E, co
   fcs_workspace* ws = a.ws;
   const cudaStream_t cs = a.s, s_in = ws->s_in, s_out = ws->s_out;
   const HitCfg hc = hit_cfg(a.cfg);
-  const ScanTmp tmp2{ws->scan_state2, ws->ss2_cap - 2, &ws->d_sizes->flags, ws->num_sms * 2};
+  const ScanTmp tmp2{ws->scan_state2, ws->ss2_cap - 2, &ws->d_sizes->flags, ws->num_sms * 3};
   const fcs_particles& d = a.parts;
   auto copy_in = [&](int64_t lo, int64_t hi) -> cudaError_t {
     if (hi <= lo) return cudaSuccess;
@@ -1405,7 +1415,8 @@ int fcs_simulate_backward(const fcs_geo* geo, const fcs_params* prm, fcs_workspa
   k_call_begin<<<1, 1, 0, s>>>(ws->d_sizes);
   for (int32_t lo = 0; lo < n_events; lo += rows) {
     const int32_t hi = std::min(n_events, lo + rows);
-    k_range_begin<<<1, 1, 0, s>>>(ws->d_sizes, particles->event_offsets, lo, hi, n_particles, ws->pcap);
+    k_range_begin<<<1, kRangeThreads, 0, s>>>(ws->d_sizes, particles->event_offsets, lo, hi, n_particles,
+                                              ws->pcap);
     WsDev w = ws->view();
     FCS_CUDA(launch_task_counts(geo->d, prm->d, *particles, lo, hi, k0, k1, first_event, w, tmp, n_particles,
                                 cfg.energy_interp, L));

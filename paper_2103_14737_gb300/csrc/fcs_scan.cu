@@ -157,22 +157,32 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const In* in, int64_t* ou
     int64_t run = s_excl + thread_excl;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-      if constexpr (GMAP) {
-        const int64_t i = t0 + threadIdx.x * kScanItems + k;  // task i: hits [run, run + v[k])
-        if (i < n) {
-          for (int64_t g = (run + kGranule - 1) / kGranule; g * kGranule < run + v[k] && g < gmap_cap; ++g)
-            gmap[g] = (int32_t)i;
-        }
-      }
       s_tile[threadIdx.x * (kScanItems + 1) + k] = run;
       run += v[k];
     }
     __syncthreads();
+    if constexpr (GMAP) {
+#pragma unroll 1
+      for (int k = 0; k < kScanItems; ++k) {
+        const int j = k * kScanThreads + threadIdx.x;
+        const int64_t i = t0 + j;
+        if (i < n) {
+          const int64_t b = s_tile[j + j / kScanItems];
+          out[i] = b;
+          // task i holds hits [b, e): e is the next task's first hit (the
+          // tile's end for its last task)
+          const int jn = j + 1;
+          const int64_t e = (jn < kScanTile && i + 1 < n) ? s_tile[jn + jn / kScanItems] : s_excl + tile_total;
+          for (int64_t g = (b + kGranule - 1) / kGranule; g * kGranule < e && g < gmap_cap; ++g) gmap[g] = (int32_t)i;
+        }
+      }
+    } else {
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-      const int j = k * kScanThreads + threadIdx.x;
-      const int64_t i = t0 + j;
-      if (i < n) out[i] = s_tile[j + j / kScanItems];
+      for (int k = 0; k < kScanItems; ++k) {
+        const int j = k * kScanThreads + threadIdx.x;
+        const int64_t i = t0 + j;
+        if (i < n) out[i] = s_tile[j + j / kScanItems];
+      }
     }
     __syncthreads();  // the tile buffer and s_ticket are reused
   }
