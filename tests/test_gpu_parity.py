@@ -399,6 +399,37 @@ def test_host_entry_point_two_waves(sim):
             assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 2 * 13
 
 
+@pytest.mark.parametrize("layout", ["two_events", "empty_first_wave"])
+def test_host_entry_point_two_waves_edges(sim, layout):
+    """Two-wave host calls at their edges: two events (a wave each), and a first
+    wave whose events have no particles (all particles in the last quarter)."""
+    src = synth.pileup(seed=18, n_events=2, mu_pu=10)
+    if layout == "two_events":
+        parts = src
+    else:
+        # eight events: six empty, then the two events above
+        parts = synth.Particles(src.type, src.E, src.eta, src.phi,
+                                np.concatenate([np.zeros(6, np.int64), src.event_offsets]).astype(np.int64))
+    ne = len(parts.event_offsets) - 1
+    ref = sim.simulate(sim.to_device(parts), 8, mode=fcs.MODE_DETERMINISTIC)
+    nnz = ref["stats"]["n_nonzero"]
+    pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(parts, k))).pin_memory()
+           for k in ("type", "E", "eta", "phi", "event_offsets")}
+    ids = torch.full((nnz + 8,), -1, dtype=torch.int32).pin_memory()
+    E = torch.zeros(nnz + 8, dtype=torch.float32).pin_memory()
+    off = torch.zeros(ne + 1, dtype=torch.int64).pin_memory()
+    for _ in range(2):
+        rc, st = fcs.fcs_simulate_events_host(sim.geo, sim.prm, sim.ws, pin["type"].numpy(), pin["E"].numpy(),
+                                              pin["eta"].numpy(), pin["phi"].numpy(), pin["event_offsets"].numpy(),
+                                              8, 0, fcs.make_config(), ids.numpy(), E.numpy(), off.numpy())
+        assert rc == 0 and st.n_nonzero == nnz and st.n_hits == ref["stats"]["n_hits"]
+        assert np.array_equal(off.numpy(), ref["event_offsets"].cpu().numpy())
+        assert np.array_equal(ids.numpy()[:nnz], ref["cell_ids"][:nnz].cpu().numpy())
+        want = ref["cell_E"][:nnz].cpu().numpy().astype(np.float64)
+        assert (np.abs(E.numpy()[:nnz] - want) <= RTOL * np.abs(want) + ATOL).all()
+    assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 2 * 13
+
+
 def test_sync_call_outgrows_workspace(geo, prm, ogeo, oprm):
     """A fresh workspace is sized by its first call; a larger later call
     overflows it, grows it and runs again with the same results."""
