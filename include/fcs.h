@@ -221,6 +221,15 @@ int fcs_workspace_status(fcs_workspace* ws, fcs_stats* stats, cudaStream_t s);
  * graph. */
 int fcs_workspace_graph_kernels(const fcs_workspace* ws, int64_t* n_kernels);
 
+/* Self-test of the bounded device waits (the single-pass scans' look-back):
+ * runs a three-tile scan, in buffers of its own, in which one tile never
+ * publishes its status, so that the next tile's wait gives up after its poll
+ * limit (2^20 polls, about 0.2 s) and sets FCS_FLAG_WAIT_TIMEOUT.  Returns
+ * FCS_E_TIMEOUT, the status a call returns when one of its waits gives up;
+ * the device stays usable.  FCS_E_DEVICE_CHECK if the wait did not report
+ * giving up.  ms: host, written: the kernel's time.  Synchronous. */
+int fcs_selftest_wait_timeout(float* ms, cudaStream_t s);
+
 /* Stage times of the last call on ws that ran with config->timing != 0, in
  * milliseconds, summed over its event ranges (CUDA events on the call's
  * stream; waits for them): ms[FCS_STAGE_TASKS] particle tasks, scans, task

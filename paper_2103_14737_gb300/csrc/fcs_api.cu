@@ -1073,6 +1073,16 @@ int fcs_workspace_graph_kernels(const fcs_workspace* ws, int64_t* n_kernels) {
   return ok();
 }
 
+int fcs_selftest_wait_timeout(float* ms, cudaStream_t s) {
+  if (!ms) return set_err(FCS_E_ARG, "ms is NULL");
+  *ms = 0.0f;
+  uint32_t flags = 0;
+  FCS_CUDA(scan_wait_selftest(&flags, ms, s));
+  if (!(flags & FCS_FLAG_WAIT_TIMEOUT))
+    return set_err(FCS_E_DEVICE_CHECK, "the self-test's wait did not report giving up (flags 0x%x)", flags);
+  return set_err(FCS_E_TIMEOUT, "a bounded device wait gave up after %.0f ms (self-test)", *ms);
+}
+
 int fcs_workspace_timings(fcs_workspace* ws, float* ms) {
   if (!ws || !ms) return set_err(FCS_E_ARG, "NULL argument");
   if (ws->timed_ranges <= 0) return set_err(FCS_E_ARG, "no timed call on this workspace");

@@ -207,6 +207,9 @@ int64_t scan_state_words(int64_t max_elements);
 cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, const int64_t* n_dev, int64_t n_host,
                             int64_t* total_dst, int64_t total_add_base_from_dst, ScanTmp tmp,
                             cudaStream_t s);
+// Self-test of the scan's bounded wait (a tile that never publishes): the
+// device flag word and the kernel's time in ms.
+cudaError_t scan_wait_selftest(uint32_t* flags_out, float* ms, cudaStream_t s);
 // Exclusive scan of n uint32 values into int64 (no base, no total).
 cudaError_t launch_scan_u32(const uint32_t* in, int64_t* out, int64_t n, ScanTmp tmp, cudaStream_t s);
 // The hit offsets th (exclusive scan of the tasks' hit counts tn, *n_tasks of

@@ -29,7 +29,7 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr uint64_t kFlagAgg = 1ull << 62;
 constexpr uint64_t kFlagPrefix = 2ull << 62;
 constexpr uint64_t kValueMask = (1ull << 62) - 1;
-constexpr uint32_t kSpinLimit = 1u << 24;  // status polls before a wait gives up (seconds)
+constexpr uint32_t kSpinLimit = 1u << 20;  // status polls before a wait gives up (about 0.2 s on GB300)
 
 __device__ __forceinline__ int64_t load_n(const int64_t* n_dev, int64_t n_host) {
   return n_dev ? *n_dev : n_host;
@@ -101,7 +101,7 @@ template <typename In, bool GMAP>
 __global__ void __launch_bounds__(kScanThreads) k_scan(const In* in, int64_t* out, const int64_t* n_dev, int64_t n_host,
                                                      int64_t* total_dst, int base_from_dst, uint64_t* state,
                                                      int64_t cap_tiles, uint32_t* flags, int32_t* gmap,
-                                                     int64_t gmap_cap) {
+                                                     int64_t gmap_cap, int64_t mute_tile) {
   __shared__ int64_t s_tile[kScanTile + kScanTile / kScanItems];  // element j at j + j / kScanItems
   __shared__ int64_t s_warp[kScanThreads / 32];
   __shared__ int64_t s_excl;
@@ -144,11 +144,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const In* in, int64_t* ou
       if (t == 0) {
         excl = base_from_dst ? *total_dst : 0;
       } else {
-        if (lane == 0) atomicExch(reinterpret_cast<unsigned long long*>(status + t), kFlagAgg | (uint64_t)tile_total);
+        if (lane == 0 && t != mute_tile)
+          atomicExch(reinterpret_cast<unsigned long long*>(status + t), kFlagAgg | (uint64_t)tile_total);
         excl = look_back(status, t, flags);
       }
-      if (lane == 0) {
+      if (lane == 0 && t != mute_tile) {
         atomicExch(reinterpret_cast<unsigned long long*>(status + t), kFlagPrefix | (uint64_t)(excl + tile_total));
+      }
+      if (lane == 0) {
         s_excl = excl;
         if (t == n_tiles - 1 && total_dst) *total_dst = excl + tile_total;
       }
@@ -219,7 +222,7 @@ static cudaError_t launch_scan(const In* in, int64_t* out, const int64_t* n_dev,
                                int64_t* total_dst, int64_t base_from_dst, ScanTmp tmp, cudaStream_t s,
                                int32_t* gmap = nullptr, int64_t gmap_cap = 0) {
   k_scan<In, GMAP><<<tmp.grid, kScanThreads, 0, s>>>(in, out, n_dev, n_host, total_dst, base_from_dst ? 1 : 0,
-                                                     tmp.state, tmp.cap_tiles, tmp.flags, gmap, gmap_cap);
+                                                     tmp.state, tmp.cap_tiles, tmp.flags, gmap, gmap_cap, -1);
   return cudaGetLastError();
 }
 
@@ -230,6 +233,36 @@ cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, const int64_t* n_de
 
 cudaError_t launch_scan_u32(const uint32_t* in, int64_t* out, int64_t n, ScanTmp tmp, cudaStream_t s) {
   return launch_scan(in, out, nullptr, n, nullptr, 0, tmp, s);
+}
+
+// Self-test of the bounded wait: a scan of three tiles on four CTAs, in its
+// own zeroed buffers, in which tile 1 never publishes its status, so that the
+// look-back of tile 2 gives up after kSpinLimit polls and sets
+// FCS_FLAG_WAIT_TIMEOUT.  Writes the device flag word and the kernel's time.
+cudaError_t scan_wait_selftest(uint32_t* flags_out, float* ms, cudaStream_t s) {
+  constexpr int64_t n_tiles = 3, n = n_tiles * kScanTile;
+  const size_t bytes = (size_t)(2 * n + 2 + n_tiles + 1) * 8;
+  unsigned char* buf = nullptr;
+  cudaError_t e = cudaMalloc((void**)&buf, bytes);
+  if (e != cudaSuccess) return e;
+  int64_t* in = reinterpret_cast<int64_t*>(buf);
+  int64_t* out = in + n;
+  uint64_t* state = reinterpret_cast<uint64_t*>(out + n);
+  uint32_t* flags = reinterpret_cast<uint32_t*>(state + 2 + n_tiles);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if ((e = cudaEventCreate(&e0)) == cudaSuccess && (e = cudaEventCreate(&e1)) == cudaSuccess &&
+      (e = cudaMemsetAsync(buf, 0, bytes, s)) == cudaSuccess && (e = cudaEventRecord(e0, s)) == cudaSuccess) {
+    k_scan<int64_t, false><<<4, kScanThreads, 0, s>>>(in, out, nullptr, n, nullptr, 0, state, n_tiles, flags, nullptr,
+                                                      0, 1);
+    if ((e = cudaGetLastError()) == cudaSuccess && (e = cudaEventRecord(e1, s)) == cudaSuccess &&
+        (e = cudaMemcpyAsync(flags_out, flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) == cudaSuccess &&
+        (e = cudaStreamSynchronize(s)) == cudaSuccess)
+      e = cudaEventElapsedTime(ms, e0, e1);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(buf);
+  return e;
 }
 
 cudaError_t launch_scan_hits(const int64_t* tn, int64_t* th, const int64_t* n_tasks, int64_t* n_hits, int32_t* gmap,

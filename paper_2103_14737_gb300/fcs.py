@@ -30,6 +30,7 @@ MODE_ATOMIC, MODE_DETERMINISTIC = 0, 1
 EXPORTED = ("fcs_version", "fcs_last_error", "fcs_load_geometry", "fcs_geometry_info", "fcs_free_geometry",
             "fcs_load_params", "fcs_free_params", "fcs_workspace_create", "fcs_workspace_reserve",
             "fcs_workspace_status", "fcs_workspace_timings", "fcs_workspace_graph_kernels", "fcs_workspace_free",
+            "fcs_selftest_wait_timeout",
             "fcs_simulate_events", "fcs_simulate_events_host",
             "fcs_simulate_events_static", "fcs_autotune", "fcs_microbench", "fcs_simulate_backward",
             "fcs_update_params")
@@ -100,6 +101,7 @@ def load_library(build_if_missing: bool = True):
         L.fcs_workspace_status.argtypes = [vp, vp, vp]
         L.fcs_workspace_timings.argtypes = [vp, vp]
         L.fcs_workspace_graph_kernels.argtypes = [vp, vp]
+        L.fcs_selftest_wait_timeout.argtypes = [vp, vp]
         L.fcs_workspace_free.argtypes = [vp]
         L.fcs_workspace_free.restype = None
         L.fcs_simulate_events.argtypes = [vp, vp, vp, vp, i64, i32, u64, i64, vp, vp, vp, vp, vp, i64, vp, vp, vp]
@@ -218,6 +220,14 @@ def fcs_workspace_graph_kernels(ws):
     n = C.c_int64()
     _check(load_library().fcs_workspace_graph_kernels(ws, C.byref(n)))
     return n.value
+
+
+def fcs_selftest_wait_timeout():
+    """Runs the bounded-wait self-test; returns (status, kernel ms).  The
+    expected status is FCS_E_TIMEOUT."""
+    ms = C.c_float()
+    rc = load_library().fcs_selftest_wait_timeout(C.byref(ms), _stream())
+    return rc, ms.value
 
 
 def fcs_workspace_free(ws):

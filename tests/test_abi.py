@@ -90,3 +90,5 @@ def test_params_and_simulate_validation(lib):
     assert lib.fcs_simulate_backward(None, None, None, None, 0, 0, 0, 0, None, None, None, None,
                                      None, None) == fcs.FCS_E_ARG
     assert lib.fcs_update_params(None, None, None, None, None) == fcs.FCS_E_ARG
+    assert lib.fcs_selftest_wait_timeout(None, None) == fcs.FCS_E_ARG
+    assert lib.fcs_workspace_reserve(None, None, 0, 1, 0, 0) == fcs.FCS_E_ARG

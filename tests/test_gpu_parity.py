@@ -430,6 +430,37 @@ def test_host_entry_point_two_waves_edges(sim, layout):
     assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 2 * 13
 
 
+def test_bounded_wait_gives_up(sim):
+    """A device wait that nothing ends (a scan tile that never publishes its
+    status) gives up after its poll limit; the call reports FCS_E_TIMEOUT and the
+    device stays usable: a simulation call right after it succeeds."""
+    rc, ms = fcs.fcs_selftest_wait_timeout()
+    assert rc == fcs.FCS_E_TIMEOUT, rc
+    assert 0.0 < ms < 20000.0, ms
+    parts = synth.pileup(seed=19, n_events=1, mu_pu=5)
+    r = sim.simulate(sim.to_device(parts), 3)
+    assert r["status"] == 0 and r["stats"]["n_hits"] > 0
+
+
+def test_allocation_failure_is_reported(geo, prm, sim):
+    """A workspace request larger than the device (2^46 hits: a tile map of
+    2 TiB) is refused by cudaMalloc and reported as FCS_E_OOM; the workspace
+    stays usable and its next call gives the same deterministic cells as a
+    workspace that never failed."""
+    s = fcs.Simulator(geo, prm)
+    try:
+        with pytest.raises(fcs.FcsError) as ei:
+            fcs.fcs_workspace_reserve(s.ws, s.geo, 0, 1, 1 << 46)
+        assert ei.value.code == fcs.FCS_E_OOM
+        parts = synth.pileup(seed=23, n_events=2, mu_pu=5)
+        a = s.simulate(s.to_device(parts), 5, mode=fcs.MODE_DETERMINISTIC, dense=True)
+        b = sim.simulate(sim.to_device(parts), 5, mode=fcs.MODE_DETERMINISTIC, dense=True)
+        assert a["status"] == 0 and b["status"] == 0
+        assert torch.equal(a["cells"].view(torch.int32), b["cells"].view(torch.int32))
+    finally:
+        s.close()
+
+
 def test_sync_call_outgrows_workspace(geo, prm, ogeo, oprm):
     """A fresh workspace is sized by its first call; a larger later call
     overflows it, grows it and runs again with the same results."""
