@@ -100,10 +100,15 @@ __device__ __noinline__ int64_t poisson_draw(double mu, uint32_t layer, uint32_t
 // the iteration (PTRS) or the whole inversion is redone in FP64.  Bounds:
 //   inversion: expf <= 2 ulp, each of the k multiply/reciprocal steps adds
 //     <= 3 roundings (2^-24 each) to p_k, each partial sum one more, so
-//     |F32_k - F_k| <= 2^-22 + (4k + 1) 2^-24 (F <= 1); used: 2^-21 (k + 2);
-//     the 53-bit uniform rounded to FP32 is off by <= 2^-24.
-//   PTRS constants: sqrtf / logf / IEEE divisions and the FP32 images of the
-//     decimal constants, a few roundings each: relative error <= 2^-20.
+//     |F32_k - F_k| <= 2^-22 + (4k + 1) 2^-24 (F <= 1); the 53-bit uniform
+//     rounded to FP32 is off by <= 2^-24 and the difference u - F rounds once
+//     more (<= 2^-25): (4k + 6.5) 2^-24 in all; used: 2^-21 (k + 2).
+//   PTRS constants: sqrtf / logf, the FP32 images of the decimal constants
+//     and __fdividef (<= 2 ulp for divisors in [2^-126, 2^126], as documented;
+//     every divisor here is): a few roundings each, so b, a and 1/alpha are
+//     within 2^-20 relative and v_r within 2^-21 absolute.  The quotients
+//     2a/us and a/us^2 of an iteration are likewise within 2^-21 relative;
+//     the bounds they feed allow 2^-18.
 //   uniforms: exact integers rounded once to FP32 (relative 2^-24).
 constexpr float kPtrsFastMaxMu = 4096.0f;  // larger means go to FP64 (counts of ~1e4 lose FP32 headroom)
 
@@ -121,8 +126,8 @@ __device__ __forceinline__ PtrsConst32 ptrs_const32(float mu, const float* lfact
   c.loglam = logf(mu);
   c.b = fmaf(2.53f, slam, 0.931f);
   c.a = fmaf(0.02483f, c.b, -0.059f);
-  c.invalpha = 1.1239f + 1.1328f / (c.b - 3.4f);
-  c.vr = 0.9277f - 3.6224f / (c.b - 2.0f);
+  c.invalpha = 1.1239f + __fdividef(1.1328f, c.b - 3.4f);
+  c.vr = 0.9277f - __fdividef(3.6224f, c.b - 2.0f);
   c.two_a = 2.0f * c.a;
   return c;
 }
@@ -157,7 +162,7 @@ __device__ __forceinline__ int64_t ptrs_iter32(float mu, const PtrsConst32& c, u
   const float usf = u53f_edge(w.x, w.y);
   const float Vf = u53f(w.z, w.w);
   // k = floor((2a/us + b) U + mu + 0.43)
-  const float t1 = c.two_a / usf;
+  const float t1 = __fdividef(c.two_a, usf);
   const float x = ((t1 + c.b) * Uf + mu) + 0.43f;
   const float bx = (fabsf(t1 * Uf) + fabsf(c.b * Uf)) * 0x1p-18f + (fabsf(x) + 1.0f) * 0x1p-22f;
   const float kf = floorf(x);
@@ -179,7 +184,7 @@ __device__ __forceinline__ int64_t ptrs_iter32(float mu, const PtrsConst32& c, u
   if (!(us_ge_0013 || v_le_us)) return -2;
   // full test: log V + log invalpha - log(a / us^2 + b) <= -mu + k log mu - lgamma(k + 1)
   if (!k_sure) return -2;
-  const float l1 = logf(Vf), l2 = logf(c.invalpha), l3 = logf(c.a / (usf * usf) + c.b);
+  const float l1 = logf(Vf), l2 = logf(c.invalpha), l3 = logf(__fdividef(c.a, usf * usf) + c.b);
   const int32_t ki = (int32_t)kf;
   const float kl = kf * c.loglam, lg = (ki < c.n_lfact) ? __ldg(c.lfact + ki) : lgammaf(kf + 1.0f);
   const float d = (l1 + l2 - l3) - ((-mu + kl) - lg);
@@ -202,16 +207,19 @@ __device__ __forceinline__ int32_t poisson_inv_fp32(float mu32, uint32_t layer, 
   const float uf = u53f(x.x, x.y);
   float p = expf(-mu32);
   float F = p;
+  float e = 0x1p-20f;  // (k + 2) 2^-21, exact in FP32 for k <= kInvMax
+  float d = uf - F;
   int k = 0;
-  while (true) {
-    const float e = (float)(k + 2) * 0x1p-21f;
-    if (uf < F - e) return k;          // u < F_k: stop at k
-    if (!(uf > F + e)) return -1;      // uncertain
-    if (k == kInvMax) return k;        // the definition stops here too
+  while (d > e && k < kInvMax) {  // u > F_k for certain: the search goes on
     k += 1;
+    e += 0x1p-21f;
     p = (p * mu32) * rcp[k];
     F = F + p;
+    d = uf - F;
   }
+  if (d < -e) return k;  // u < F_k for certain: stop at k
+  if (d > e) return k;   // k == kInvMax: the definition stops here too
+  return -1;             // uncertain
 }
 
 // PTRS (mu >= 10), iteration i alone: the accepted count, -1 when it rejects
