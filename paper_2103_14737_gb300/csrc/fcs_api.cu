@@ -131,6 +131,16 @@ int current_device(int* dev) {
 }
 }  // namespace
 
+// Host-buffer calls run in waves of events (host_two_waves).  The shares, in
+// eighths of the call's events: the first wave's results (three quarters of
+// the output) move over the link while the second wave computes, and only the
+// second wave's results move after the last kernel.  Measured on 64 pile-up
+// events: 1.54 ms per call against 1.62-1.64 ms for splits of 2/3, 5/6 and
+// 7/8, and 1.68 ms on one stream.
+constexpr int kHostWaveEighths[] = {6, 2};
+constexpr int kMaxHostWaves = 4;
+static_assert(sizeof(kHostWaveEighths) / sizeof(int) <= kMaxHostWaves, "wave table");
+
 struct fcs_workspace {
   int device = -1;
   int num_sms = 0;
@@ -186,10 +196,10 @@ struct fcs_workspace {
   // events so that a captured call gets event-record nodes in its graph
   std::vector<cudaEvent_t> tev;
   int timed_ranges = 0;
-  // host-buffer calls in two waves: the copy-in and output streams, their
+  // host-buffer calls in waves: the copy-in and output streams, their
   // fork/join events, the output stream's scan state and the cached graph
   cudaStream_t s_in = nullptr, s_out = nullptr;
-  cudaEvent_t pev[6] = {};
+  cudaEvent_t pev[2 * kMaxHostWaves + 2] = {};
   uint64_t* scan_state2 = nullptr;
   int64_t ss2_cap = 0;
   cudaGraphExec_t pgraph = nullptr;
@@ -595,13 +605,32 @@ void* mapped_host(const void* p) {
   return (at.type == cudaMemoryTypeHost && at.devicePointer) ? at.devicePointer : nullptr;
 }
 
-// Host-buffer call in two waves of events on three streams, captured as one
-// CUDA graph: the second wave's particles are copied in while the first wave
-// computes, and the first wave's cells are compacted into the mapped output
-// buffers (over the CPU-GPU link) while the second wave computes.  Each wave
-// has its own accumulation rows; the output stream has its own scan state.
+// Wave boundaries of a host-buffer call: the events bnd[i] .. bnd[i + 1] - 1
+// form wave i.  The shares come from kHostWaveEighths; empty waves are
+// dropped, and a call of two or more events gets at least two waves.
+int host_wave_bounds(int32_t n, int32_t* bnd) {
+  int nw = 0, cum = 0;
+  bnd[0] = 0;
+  for (int share : kHostWaveEighths) {
+    cum += share;
+    const int32_t b = (int32_t)std::min<int64_t>(n, ((int64_t)n * cum + 7) / 8);
+    if (b > bnd[nw]) bnd[++nw] = b;
+  }
+  if (nw == 1 && n >= 2) {
+    bnd[1] = (n + 1) / 2;
+    bnd[2] = n;
+    nw = 2;
+  }
+  return nw;
+}
+
+// Host-buffer call in waves of events on three streams, captured as one CUDA
+// graph: each later wave's particles are copied in while the waves before it
+// compute, and each wave's cells are compacted into the mapped output buffers
+// (over the CPU-GPU link) while the next wave computes.  Each wave has its own
+// accumulation rows; the output stream has its own scan state.
 int enqueue_two_waves(const CallArgs& a, const int32_t* type, const float* E, const float* eta, const float* phi,
-                      const int64_t* event_offsets, int32_t W, int64_t p_mid, int key_task_bits) {
+                      const int64_t* event_offsets, const int32_t* bnd, int nw, int key_task_bits) {
   fcs_workspace* ws = a.ws;
   const cudaStream_t cs = a.s, s_in = ws->s_in, s_out = ws->s_out;
   const HitCfg hc = hit_cfg(a.cfg);
@@ -622,25 +651,24 @@ int enqueue_two_waves(const CallArgs& a, const int32_t* type, const float* E, co
   FCS_CUDA(cudaStreamWaitEvent(s_out, ws->pev[0], 0));
   FCS_CUDA(cudaMemcpyAsync((void*)d.event_offsets, event_offsets, (size_t)(a.n_events + 1) * 8,
                            cudaMemcpyHostToDevice, s_in));
-  FCS_CUDA(copy_in(0, p_mid));
-  FCS_CUDA(cudaEventRecord(ws->pev[1], s_in));
-  FCS_CUDA(copy_in(p_mid, a.n_particles));
-  FCS_CUDA(cudaEventRecord(ws->pev[2], s_in));
-  const int32_t lo[2] = {0, W}, hi[2] = {W, a.n_events};
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < nw; ++k) {
+    FCS_CUDA(copy_in(event_offsets[bnd[k]], event_offsets[bnd[k + 1]]));
+    FCS_CUDA(cudaEventRecord(ws->pev[1 + k], s_in));
+  }
+  for (int k = 0; k < nw; ++k) {
     FCS_CUDA(cudaStreamWaitEvent(cs, ws->pev[1 + k], 0));
     WsDev w{};
-    FCS_TRY(enqueue_range_hits(a, lo[k], hi[k], k, false, hc, key_task_bits, lo[k], &w));
+    FCS_TRY(enqueue_range_hits(a, bnd[k], bnd[k + 1], k, false, hc, key_task_bits, bnd[k], &w));
     k_range_end<<<1, 1, 0, cs>>>(ws->d_sizes);
-    FCS_CUDA(cudaEventRecord(ws->pev[3 + k], cs));
-    FCS_CUDA(cudaStreamWaitEvent(s_out, ws->pev[3 + k], 0));
+    FCS_CUDA(cudaEventRecord(ws->pev[1 + nw + k], cs));
+    FCS_CUDA(cudaStreamWaitEvent(s_out, ws->pev[1 + nw + k], 0));
     // the compaction runs beside the next wave on half the SMs: its stores
     // over the CPU-GPU link need few CTAs to keep the link busy
-    FCS_TRY(enqueue_range_reduce(a, w, lo[k], hi[k] - lo[k], key_task_bits, tmp2, s_out, ws->num_sms / 2));
+    FCS_TRY(enqueue_range_reduce(a, w, bnd[k], bnd[k + 1] - bnd[k], key_task_bits, tmp2, s_out, ws->num_sms / 2));
   }
   k_call_end<<<1, 1, 0, s_out>>>(ws->d_sizes, a.event_offsets_out, a.n_events, a.capacity, a.cell_ids ? 1 : 0);
-  FCS_CUDA(cudaEventRecord(ws->pev[5], s_out));
-  FCS_CUDA(cudaStreamWaitEvent(cs, ws->pev[5], 0));
+  FCS_CUDA(cudaEventRecord(ws->pev[1 + 2 * nw], s_out));
+  FCS_CUDA(cudaStreamWaitEvent(cs, ws->pev[1 + 2 * nw], 0));
   FCS_CUDA(cudaGetLastError());
   return FCS_OK;
 }
@@ -663,13 +691,8 @@ int host_two_waves(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
   if (event_offsets[0] != 0 || event_offsets[n_events] != n_particles) return FCS_E_UNSUPPORTED;
   for (int32_t e = 0; e < n_events; ++e)
     if (event_offsets[e + 1] < event_offsets[e]) return FCS_E_UNSUPPORTED;
-  // the first wave takes three quarters of the events: its results (three
-  // quarters of the output) move over the link while the second wave computes,
-  // and only the second wave's results move after the last kernel (measured
-  // on 64 pile-up events: 1.54 ms per call against 1.62-1.64 ms for splits of
-  // 2/3, 5/6 and 7/8, and 1.68 ms on one stream)
-  const int32_t W = n_events > 3 ? (3 * n_events + 3) / 4 : (n_events + 1) / 2;
-  const int64_t p_mid = event_offsets[W];
+  int32_t bnd[kMaxHostWaves + 1];
+  const int nw = host_wave_bounds(n_events, bnd);
   if ((int64_t)n_events * geo->d.acc_stride >= (int64_t(1) << 32)) return FCS_E_UNSUPPORTED;
   FCS_TRY(ws_reserve_static(ws, geo, n_particles, n_events, cfg.mode));
   if (ws->ss2_cap < ws->ss_cap) {
@@ -696,7 +719,7 @@ int host_two_waves(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
   put(hp, sizeof(hp));
   put(&n_particles, sizeof(n_particles));
   put(&n_events, sizeof(n_events));
-  put(&p_mid, sizeof(p_mid));
+  put(bnd, sizeof(int32_t) * (nw + 1));
   put(&seed, sizeof(seed));
   put(&first_event, sizeof(first_event));
   put(&cfg, sizeof(cfg));
@@ -725,7 +748,7 @@ int host_two_waves(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     int rc = FCS_OK;
-    if (e == cudaSuccess) rc = enqueue_two_waves(a, type, E, eta, phi, event_offsets, W, p_mid, key_task_bits);
+    if (e == cudaSuccess) rc = enqueue_two_waves(a, type, E, eta, phi, event_offsets, bnd, nw, key_task_bits);
     cudaError_t e2 = cudaStreamEndCapture(cs, &g);
     cudaStreamDestroy(cs);
     if (e != cudaSuccess || rc != FCS_OK || e2 != cudaSuccess) {

@@ -578,10 +578,36 @@ __global__ void __launch_bounds__(32 * kPoisWarps) k_task_poisson(WsDev w, Philo
   }
 }
 
-// The deferred draws in FP64 (the definition itself): the inversion list
-// (front of pdefer), then the PTRS list (back of pdefer), 32 per warp, so
-// that a warp runs one method except at the seam.
-__global__ void __launch_bounds__(128) k_task_poisson64(WsDev w, uint32_t k0, uint32_t k1, uint32_t first_event_lo,
+// A deferred PTRS draw from its uncertain iteration i0 on: iteration i0 in
+// FP64 (the definition), each later one in FP32 where its decisions are
+// certain (they are then the FP64 ones) and in FP64 where they are not.  A
+// warp's time is its longest chain of FP64 iterations, and most draws that
+// reject at i0 are decided in FP32 after it.
+__device__ __noinline__ int64_t ptrs_resume(float mu32, uint32_t layer, uint32_t particle, uint32_t event,
+                                            uint32_t k0, uint32_t k1, const PhiloxRoundKeys& rk,
+                                            const float* lfact, const double* lfact64, int32_t n_lfact, uint32_t i0) {
+  const double mu = (double)mu32;
+  const PtrsConst64 c = ptrs_const64(mu);
+  for (uint32_t i = i0; i < kPtrsMaxIter; ++i) {
+    if (i != i0) {
+      const int32_t k32 = ptrs_step_fp32(mu32, layer, particle, event, rk, lfact, n_lfact, i);
+      if (k32 >= 0) return k32;
+      if (k32 == -1) continue;
+    }
+    double u, V;
+    draw_pair(i, layer, particle, event, k0, k1, &u, &V);
+    const int64_t k = ptrs_iter64(mu, c, u, V, lfact64, n_lfact);
+    if (k >= 0) return k;
+  }
+  return (int64_t)floor(mu);
+}
+
+// The deferred draws: the inversion list (front of pdefer) by the FP64
+// definition, then the PTRS list (back of pdefer) resumed at the iteration
+// the FP32 path could not decide; 32 per warp, so that a warp runs one method
+// except at the seam.
+__global__ void __launch_bounds__(128) k_task_poisson64(WsDev w, uint32_t k0, uint32_t k1, PhiloxRoundKeys rk,
+                                                         uint32_t first_event_lo, const float* lfact,
                                                          const double* lfact64, int32_t n_lfact) {
   const int64_t n_inv = w.sizes->n_pdefer, n_ptrs = w.sizes->n_pdefer_ptrs;
   const int64_t n = n_inv + n_ptrs;
@@ -590,9 +616,11 @@ __global__ void __launch_bounds__(128) k_task_poisson64(WsDev w, uint32_t k0, ui
     const bool inv = q < n_inv;
     const int32_t t = w.pdefer[inv ? q : w.pdefer_cap - 1 - (q - n_inv)];
     const TaskRec& r = w.tasks[t];
-    const uint32_t i0 = inv ? 0u : (uint32_t)w.tn[t];
-    int64_t k = poisson_draw((double)w.tmu[t], (uint32_t)r.layer(), (uint32_t)r.particle,
-                             first_event_lo + (uint32_t)r.event(), k0, k1, lfact64, n_lfact, i0);
+    const uint32_t layer = (uint32_t)r.layer(), particle = (uint32_t)r.particle;
+    const uint32_t event = first_event_lo + (uint32_t)r.event();
+    int64_t k = inv ? poisson_draw((double)w.tmu[t], layer, particle, event, k0, k1, lfact64, n_lfact, 0u)
+                    : ptrs_resume(w.tmu[t], layer, particle, event, k0, k1, rk, lfact, lfact64, n_lfact,
+                                  (uint32_t)w.tn[t]);
     if (k < 1) k = 1;
     if (k > 0x7FFFFFFF) k = 0x7FFFFFFF;
     w.tn[t] = k;
@@ -657,7 +685,8 @@ cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_par
                                                      p.n_lfact);
   // the FP64 pipe is narrow: one warp per block spreads the few deferred draws
   // over every SM
-  k_task_poisson64<<<L.num_sms * 8, 32, 0, L.s>>>(w, k0, k1, (uint32_t)first_event, p.lfact64, p.n_lfact);
+  k_task_poisson64<<<L.num_sms * 8, 32, 0, L.s>>>(w, k0, k1, philox_round_keys(k0, k1), (uint32_t)first_event,
+                                                   p.lfact, p.lfact64, p.n_lfact);
   // the scan counts the tasks actually written (n_tasks <= task_cap by construction)
   return launch_scan_hits(w.tn, w.th, &w.sizes->n_tasks, &w.sizes->n_hits, w.gmap, w.gmap_cap, tmp, L.s);
 }
