@@ -666,6 +666,18 @@ int grid_for(int64_t n, const Launch& L) {
   return (int)std::min<int64_t>(b, (int64_t)L.num_sms * 16);
 }
 
+// Blocks of `block` threads of `kernel` that one SM holds at once (its
+// registers and shared memory decide).  Grid-stride kernels launched with
+// more blocks than that run the surplus as a second, mostly empty wave.
+int resident_blocks(const void* kernel, int block) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, 0) != cudaSuccess) {
+    (void)cudaGetLastError();
+    n = 1;
+  }
+  return std::max(n, 1);
+}
+
 }  // namespace
 
 cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_particles& parts, int32_t ev_lo,
@@ -677,10 +689,13 @@ cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_par
   k_particle_count<<<gp, 128, 0, L.s>>>(p, parts, ev_lo, ev_hi, w, energy_interp, k0, k1, (uint32_t)first_event);
   cudaError_t e = launch_scan_i64(w.pcount, w.poff, &w.sizes->n_part, 0, &w.sizes->n_tasks, 0, tmp, L.s);
   if (e != cudaSuccess) return e;
-  k_task_init<<<gp, 128, 0, L.s>>>(g, p, parts, ev_lo, w);
+  // the task kernels loop grid-stride: one wave of resident blocks
+  static const int occ_init = resident_blocks((const void*)k_task_init, 128);
+  static const int occ_pois = resident_blocks((const void*)k_task_poisson, 32 * kPoisWarps);
+  k_task_init<<<std::min(gp, L.num_sms * occ_init), 128, 0, L.s>>>(g, p, parts, ev_lo, w);
   const int gpois = (int)std::min<int64_t>(
       (std::max<int64_t>(n_part_max * p.NL, 1) + kPoisWarps * kPoisWin - 1) / (kPoisWarps * kPoisWin),
-      (int64_t)L.num_sms * 16);
+      (int64_t)L.num_sms * occ_pois);
   k_task_poisson<<<gpois, 32 * kPoisWarps, 0, L.s>>>(w, philox_round_keys(k0, k1), (uint32_t)first_event, p.lfact,
                                                      p.n_lfact);
   // the FP64 pipe is narrow: one warp per block spreads the few deferred draws
