@@ -557,8 +557,55 @@ def main():
             nnz = st.n_nonzero
         h2d = parts.n * 16 + (n_ev + 1) * 8
         d2h = nnz * 8 + (n_ev + 1) * 8
-        e2e = {"value": H / float(np.mean(tt)), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * float(np.mean(tt))}
+        single = {"value": H / float(np.mean(tt)), "ms_per_step": 1e3 * float(np.mean(tt))}
+
+        # A serving loop: two workspaces on two streams, each call enqueued without
+        # waiting (config sync = 0).  Before a workspace is used again, its previous
+        # call is waited for and its status and counts are read.  Every step still
+        # copies its inputs in and writes its results into mapped host buffers inside
+        # the timed region; one call's copies and results overlap the other's compute.
+        ws2 = fcs.fcs_workspace_create()
+        slots = []
+        for ws_k in (sim.ws, ws2):
+            slots.append((ws_k, torch.cuda.Stream(), torch.empty(cap, dtype=torch.int32).pin_memory().numpy(),
+                          torch.empty(cap, dtype=torch.float32).pin_memory().numpy(),
+                          torch.empty(n_ev + 1, dtype=torch.int64).pin_memory().numpy()))
+        acfg = fcs.make_config(hits_per_thread=args.hpt, block=args.block, sync=0)
+
+        def enqueue(sl):
+            with torch.cuda.stream(sl[1]):
+                fcs.fcs_simulate_events_host(sim.geo, sim.prm, sl[0], pin["type"], pin["E"], pin["eta"], pin["phi"],
+                                             pin["event_offsets"], SEED, first_event, acfg, sl[2], sl[3], sl[4])
+
+        def wait(sl):
+            with torch.cuda.stream(sl[1]):
+                rc, st = fcs.fcs_workspace_status(sl[0])
+            if rc != fcs.FCS_OK or st.n_nonzero != nnz:
+                raise RuntimeError(f"pipelined host call: status {rc}, {st.n_nonzero} cells (expected {nnz})")
+
+        for _ in range(2):  # sizes the second workspace, captures both graphs
+            for sl in slots:
+                enqueue(sl)
+                wait(sl)
+        torch.cuda.synchronize()
+        Kp = max(4, args.steps)
+        t0 = time.perf_counter()
+        for i in range(Kp):
+            if i >= 2:
+                wait(slots[i % 2])
+            enqueue(slots[i % 2])
+        for i in range(max(0, Kp - 2), Kp):
+            wait(slots[i % 2])
+        tp = (time.perf_counter() - t0) / Kp
+        if not np.array_equal(slots[0][4], off) or not np.array_equal(slots[1][2][:nnz], ids[:nnz]):
+            raise RuntimeError("pipelined host calls returned other cells than the synchronous call")
+        fcs.fcs_workspace_free(ws2)
+        e2e = {"value": H / tp, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": 1e3 * tp, "steps": Kp,
+               "mode": "serving loop: two workspaces on two streams, asynchronous host-buffer calls, "
+                       "a workspace's previous call waited for and its status read before reuse; "
+                       "no L2 flush (the other workspace's step streams over 300 MB through L2)",
+               "single_call": single}
 
     # unit throughputs on this GPU (roofline denominators), measured after the timed region
     pipes = None

@@ -277,10 +277,11 @@ int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace
  * particle arrays (host SoA, same layout as fcs_particles, event_offsets on
  * the host) are copied to the device, simulated, and the compacted result
  * copied back into host cell_ids / cell_E / event_offsets_out (capacity
- * entries).  Always synchronous.  When every output array is mapped pinned
- * host memory (cudaMallocHost, cudaHostAlloc(Mapped) or a registered range;
- * the device address is taken with cudaPointerGetAttributes), the compaction
- * kernel writes the results there directly and no device-to-host copy runs.
+ * entries).  Synchronous, except as config->sync == 0 allows (below).  When
+ * every output array is mapped pinned host memory (cudaMallocHost,
+ * cudaHostAlloc(Mapped) or a registered range; the device address is taken
+ * with cudaPointerGetAttributes), the compaction kernel writes the results
+ * there directly and no device-to-host copy runs.
  * When the particle arrays are pinned too, the call is in atomic mode in one
  * launch sequence (wave_events 0), has at least two events and offsets from
  * 0 to n_particles, and the workspace has been sized by an earlier call, it
@@ -289,7 +290,16 @@ int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace
  * in while the first wave computes, and the first wave's results (the first
  * three quarters of the events) move to the host while the second computes.
  * Each wave has its own accumulation rows.
- * Pageable memory works through device staging and copies. */
+ * Pageable memory works through device staging and copies.
+ * config->sync == 0 asks for a call that does not wait: when the call runs
+ * as the two-wave graph above, it returns FCS_OK once the graph is enqueued
+ * on s, with *stats zeroed, and fcs_workspace_status(ws, stats, s) waits for
+ * it and returns its status and statistics (FCS_E_RANGE when the workspace
+ * held fewer hits than the call produced: repeat the call synchronously).
+ * Until then the call's host buffers and ws stay in use.  A serving loop
+ * alternates two workspaces on two streams, so that one call's copies and
+ * results overlap the other's compute.  Any other call runs synchronously
+ * whatever config->sync says. */
 int fcs_simulate_events_host(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
                              const int32_t* type, const float* E, const float* eta,
                              const float* phi, const int64_t* event_offsets,

@@ -1314,6 +1314,9 @@ int fcs_simulate_events_host(const fcs_geo* geo, const fcs_params* prm, fcs_work
   fcs_config cfg{};
   cfg.batched = 1;
   if (config) cfg = *config;
+  // sync == 0: a call that runs as the cached two-wave graph returns once it
+  // is enqueued; every other call runs synchronously
+  const bool enqueue_only = config && config->sync == 0;
   cfg.sync = 1;
   cfg.use_graph = 0;
   // staging: particles, offsets, outputs (16-byte aligned slices)
@@ -1353,6 +1356,11 @@ int fcs_simulate_events_host(const fcs_geo* geo, const fcs_params* prm, fcs_work
     // results overlap (pinned inputs; see host_two_waves)
     const int rc2 = host_two_waves(geo, prm, ws, type, E, eta, phi, event_offsets, n_particles, n_events, seed,
                                    first_event, cfg, parts, m_ids, m_cE, m_oout, capacity, s);
+    if (rc2 == FCS_OK && enqueue_only) {
+      // fcs_workspace_status waits for the call and reports it
+      if (stats) std::memset(stats, 0, sizeof(*stats));
+      return ok();
+    }
     if (rc2 == FCS_OK) {
       FCS_CUDA(cudaMemcpyAsync(ws->h_sizes, ws->d_sizes, sizeof(Sizes), cudaMemcpyDeviceToHost, s));
       FCS_CUDA(cudaStreamSynchronize(s));

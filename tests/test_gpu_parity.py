@@ -430,6 +430,52 @@ def test_host_entry_point_two_waves_edges(sim, layout):
     assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 2 * 13
 
 
+def test_host_entry_point_async_two_workspaces(sim):
+    """config sync = 0: host calls on two fresh workspaces and two streams,
+    enqueued without waiting and interleaved, return the synchronous call's
+    cells (ids and offsets exactly, energies to the atomic tolerance); each
+    status comes from fcs_workspace_status.  A fresh workspace's first call
+    sizes it synchronously."""
+    parts = synth.pileup(seed=21, n_events=6, mu_pu=30)
+    pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(parts, k))).pin_memory().numpy()
+           for k in ("type", "E", "eta", "phi", "event_offsets")}
+    cap = 6 * sim.n_cells
+
+    def bufs():
+        return (torch.full((cap,), -1, dtype=torch.int32).pin_memory().numpy(),
+                torch.zeros(cap, dtype=torch.float32).pin_memory().numpy(),
+                torch.zeros(7, dtype=torch.int64).pin_memory().numpy())
+
+    ref = bufs()
+    rc, st = fcs.fcs_simulate_events_host(sim.geo, sim.prm, sim.ws, pin["type"], pin["E"], pin["eta"], pin["phi"],
+                                          pin["event_offsets"], 4, 1, fcs.make_config(), *ref)
+    assert rc == 0
+    nnz = st.n_nonzero
+    acfg = fcs.make_config(sync=0)
+    slots = [(fcs.fcs_workspace_create(), torch.cuda.Stream(), bufs()) for _ in range(2)]
+    try:
+        for rep in range(3):
+            for ws, stream, out in slots:
+                out[0].fill(-1)
+                with torch.cuda.stream(stream):
+                    rc, _ = fcs.fcs_simulate_events_host(sim.geo, sim.prm, ws, pin["type"], pin["E"], pin["eta"],
+                                                         pin["phi"], pin["event_offsets"], 4, 1, acfg, *out)
+                assert rc == 0
+            for ws, stream, out in slots:
+                with torch.cuda.stream(stream):
+                    rc, st = fcs.fcs_workspace_status(ws)
+                assert rc == 0 and st.n_nonzero == nnz
+                assert np.array_equal(out[2], ref[2]) and np.array_equal(out[0][:nnz], ref[0][:nnz])
+                want = ref[1][:nnz].astype(np.float64)
+                assert (np.abs(out[1][:nnz] - want) <= RTOL * np.abs(want) + ATOL).all()
+                assert (out[0][nnz:] == -1).all()
+        assert fcs.fcs_workspace_graph_kernels(slots[0][0]) == 2 + 2 * 13
+    finally:
+        torch.cuda.synchronize()
+        for ws, _, _ in slots:
+            fcs.fcs_workspace_free(ws)
+
+
 def test_bounded_wait_gives_up(sim):
     """A device wait that nothing ends (a scan tile that never publishes its
     status) gives up after its poll limit; the call reports FCS_E_TIMEOUT and the
