@@ -131,7 +131,7 @@ int current_device(int* dev) {
 }
 }  // namespace
 
-// Host-buffer calls run in waves of events (host_two_waves).  The shares, in
+// Host-buffer calls run in waves of events (host_waves).  The shares, in
 // eighths of the call's events: the first wave's results (three quarters of
 // the output) move over the link while the second wave computes, and only the
 // second wave's results move after the last kernel.  Measured on 64 pile-up
@@ -629,7 +629,7 @@ int host_wave_bounds(int32_t n, int32_t* bnd) {
 // compute, and each wave's cells are compacted into the mapped output buffers
 // (over the CPU-GPU link) while the next wave computes.  Each wave has its own
 // accumulation rows; the output stream has its own scan state.
-int enqueue_two_waves(const CallArgs& a, const int32_t* type, const float* E, const float* eta, const float* phi,
+int enqueue_waves(const CallArgs& a, const int32_t* type, const float* E, const float* eta, const float* phi,
                       const int64_t* event_offsets, const int32_t* bnd, int nw, int key_task_bits) {
   fcs_workspace* ws = a.ws;
   const cudaStream_t cs = a.s, s_in = ws->s_in, s_out = ws->s_out;
@@ -677,7 +677,7 @@ int enqueue_two_waves(const CallArgs& a, const int32_t* type, const float* E, co
 // of a host-buffer call on stream s.  FCS_E_UNSUPPORTED when the call does not
 // qualify: atomic mode in one launch sequence, at least two events, pinned
 // inputs, offsets from 0 to n_particles, a workspace sized for the hits.
-int host_two_waves(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws, const int32_t* type, const float* E,
+int host_waves(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws, const int32_t* type, const float* E,
                    const float* eta, const float* phi, const int64_t* event_offsets, int64_t n_particles,
                    int32_t n_events, uint64_t seed, int64_t first_event, const fcs_config& cfg,
                    const fcs_particles& dparts, int32_t* m_ids, float* m_cE, int64_t* m_oout, int64_t capacity,
@@ -748,7 +748,7 @@ int host_two_waves(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     int rc = FCS_OK;
-    if (e == cudaSuccess) rc = enqueue_two_waves(a, type, E, eta, phi, event_offsets, bnd, nw, key_task_bits);
+    if (e == cudaSuccess) rc = enqueue_waves(a, type, E, eta, phi, event_offsets, bnd, nw, key_task_bits);
     cudaError_t e2 = cudaStreamEndCapture(cs, &g);
     cudaStreamDestroy(cs);
     if (e != cudaSuccess || rc != FCS_OK || e2 != cudaSuccess) {
@@ -1353,8 +1353,8 @@ int fcs_simulate_events_host(const fcs_geo* geo, const fcs_params* prm, fcs_work
   const bool direct = m_oout && (!cell_ids || (m_ids && m_cE));
   if (direct && cfg.batched == 1 && ws->gmap_cap > 0) {
     // two waves on three streams: copies in, compute and the transfer of
-    // results overlap (pinned inputs; see host_two_waves)
-    const int rc2 = host_two_waves(geo, prm, ws, type, E, eta, phi, event_offsets, n_particles, n_events, seed,
+    // results overlap (pinned inputs; see host_waves)
+    const int rc2 = host_waves(geo, prm, ws, type, E, eta, phi, event_offsets, n_particles, n_events, seed,
                                    first_event, cfg, parts, m_ids, m_cE, m_oout, capacity, s);
     if (rc2 == FCS_OK && enqueue_only) {
       // fcs_workspace_status waits for the call and reports it

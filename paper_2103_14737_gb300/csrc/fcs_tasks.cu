@@ -7,6 +7,8 @@
 // when a call grew the map after that scan.)
 #include <algorithm>
 
+#include <atomic>
+
 #include "fcs_internal.cuh"
 
 namespace fcs {
@@ -678,6 +680,13 @@ int resident_blocks(const void* kernel, int block) {
   return std::max(n, 1);
 }
 
+// The same, cached per device for the two task kernels (the stores are
+// ordered so that a non-zero `init` implies `pois` is set).
+constexpr int kMaxDevices = 64;
+struct TaskOccupancy {
+  std::atomic<int> init{0}, pois{0};
+};
+
 }  // namespace
 
 cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_particles& parts, int32_t ev_lo,
@@ -690,8 +699,19 @@ cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_par
   cudaError_t e = launch_scan_i64(w.pcount, w.poff, &w.sizes->n_part, 0, &w.sizes->n_tasks, 0, tmp, L.s);
   if (e != cudaSuccess) return e;
   // the task kernels loop grid-stride: one wave of resident blocks
-  static const int occ_init = resident_blocks((const void*)k_task_init, 128);
-  static const int occ_pois = resident_blocks((const void*)k_task_poisson, 32 * kPoisWarps);
+  static TaskOccupancy occ_by_device[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = kMaxDevices - 1;
+  TaskOccupancy& occ = occ_by_device[dev];
+  int occ_init = occ.init.load(std::memory_order_acquire), occ_pois;
+  if (occ_init) {
+    occ_pois = occ.pois.load(std::memory_order_relaxed);
+  } else {
+    occ_pois = resident_blocks((const void*)k_task_poisson, 32 * kPoisWarps);
+    occ_init = resident_blocks((const void*)k_task_init, 128);
+    occ.pois.store(occ_pois, std::memory_order_relaxed);
+    occ.init.store(occ_init, std::memory_order_release);
+  }
   k_task_init<<<std::min(gp, L.num_sms * occ_init), 128, 0, L.s>>>(g, p, parts, ev_lo, w);
   const int gpois = (int)std::min<int64_t>(
       (std::max<int64_t>(n_part_max * p.NL, 1) + kPoisWarps * kPoisWin - 1) / (kPoisWarps * kPoisWin),
