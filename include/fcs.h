@@ -211,7 +211,11 @@ void fcs_free_params(fcs_params* prm);
 int fcs_workspace_create(fcs_workspace** out);
 int fcs_workspace_reserve(fcs_workspace* ws, const fcs_geo* geo, int64_t n_particles,
                           int32_t n_events, int64_t n_hits, int32_t mode);
-/* Reads the device status of the last call on ws (waits for stream s). */
+/* Reads the device status of the last call on ws: waits for stream s, then
+ * fills *stats (may be NULL) and returns the call's status, as a synchronous
+ * call would.  This completes a call made with config->sync == 0, on the
+ * device (fcs_simulate_events) or from host buffers (fcs_simulate_events_host).
+ * s: the stream of that call. */
 int fcs_workspace_status(fcs_workspace* ws, fcs_stats* stats, cudaStream_t s);
 
 /* Kernel launches of one replay of the CUDA graph the workspace launched
