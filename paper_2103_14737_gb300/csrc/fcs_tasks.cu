@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(128) k_task_init(const GeoDev g, const ParamDe
   }
 }
 
-// n = max(1, Poisson(mu)) in FP32.  Each warp takes windows of 128
+// n = max(1, Poisson(mu)) in FP32.  Each warp takes windows of 256
 // consecutive tasks, lists the window's inversion tasks (mu < 10) from the
 // front and its PTRS tasks from the back of a per-warp shared array, and
 // draws them 32 at a time, inversion rounds first: a round runs one method,
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(128) k_task_init(const GeoDev g, const ParamDe
 // Draws the FP32 path cannot certify are queued for k_task_poisson64, so that
 // FP64 work runs in full warps instead of stalling a warp for one lane.
 constexpr int kPoisWarps = 4;
-constexpr int kPoisWin = 128;
+constexpr int kPoisWin = 256;
 
 // Appends the tasks of the lanes with `push` set to a list: warp-aggregated
 // counter increment, entry q at list[q] (front) or list[cap - 1 - q] (back).
