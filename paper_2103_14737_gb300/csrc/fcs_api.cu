@@ -136,7 +136,9 @@ int current_device(int* dev) {
 // the output) move over the link while the second wave computes, and only the
 // second wave's results move after the last kernel.  Measured on 64 pile-up
 // events: 1.54 ms per call against 1.62-1.64 ms for splits of 2/3, 5/6 and
-// 7/8, and 1.68 ms on one stream.
+// 7/8, and 1.68 ms on one stream.  Three or four waves (5/8 2/8 1/8, 4/8 3/8
+// 1/8, 4/8 2/8 1/8 1/8) took 1.70-1.81 ms: each wave repeats about 0.12 ms of
+// latency-bound kernels.
 constexpr int kHostWaveEighths[] = {6, 2};
 constexpr int kMaxHostWaves = 4;
 static_assert(sizeof(kHostWaveEighths) / sizeof(int) <= kMaxHostWaves, "wave table");
