@@ -105,6 +105,46 @@ static void draw_pair(const uint32_t key[2], uint32_t i, uint32_t layer, uint32_
 #define POISSON_INV_MAX 200
 #define PTRS_MAX_ITER 64
 
+/* PTRS constants of a mean mu >= 10 (Hoermann 1993, Table 2 of the        */
+/* transformed-rejection paper: b, a, the hat's 1/alpha and the squeeze v_r). */
+typedef struct ptrs_c {
+  double mu, loglam, b, a, invalpha, vr;
+} ptrs_c;
+
+static ptrs_c ptrs_constants(double mu) {
+  ptrs_c c;
+  const double slam = sqrt(mu);
+  c.mu = mu;
+  c.loglam = log(mu);
+  c.b = 0.931 + 2.53 * slam;
+  c.a = -0.059 + 0.02483 * c.b;
+  c.invalpha = 1.1239 + 1.1328 / (c.b - 3.4);
+  c.vr = 0.9277 - 3.6224 / (c.b - 2.0);
+  return c;
+}
+
+/* One PTRS iteration from its uniforms u, V in [0, 1): the accepted count,  */
+/* or -1 when the iteration rejects.  k = floor((2a/us + b) U + mu + 0.43)    */
+/* with U = u - 1/2, us = 1/2 - |U|; quick acceptance (squeeze) when us >=   */
+/* 0.07 and V <= v_r; rejection when k < 0 or (us < 0.013 and V > us); else  */
+/* acceptance when log V + log(1/alpha) - log(a/us^2 + b) <= log p_mu(k).     */
+static int64_t ptrs_iter(const ptrs_c* c, double u, double V) {
+  const double U = u - 0.5;
+  const double us = 0.5 - fabs(U);
+  if (us <= 0.0) return -1; /* u == 0 exactly */
+  const double kd = floor((2.0 * c->a / us + c->b) * U + c->mu + 0.43);
+  if (us >= 0.07 && V <= c->vr) return (int64_t)kd;
+  if (kd < 0.0 || (us < 0.013 && V > us)) return -1;
+  const double lhs = log(V) + log(c->invalpha) - log(c->a / (us * us) + c->b);
+  const double rhs = -c->mu + kd * c->loglam - lgamma(kd + 1.0);
+  return (lhs <= rhs) ? (int64_t)kd : -1;
+}
+
+void orc_ptrs_iter_n(int64_t n, double mu, const double* u, const double* V, int64_t* out) {
+  const ptrs_c c = ptrs_constants(mu);
+  for (int64_t i = 0; i < n; ++i) out[i] = ptrs_iter(&c, u[i], V[i]);
+}
+
 int64_t orc_poisson(double mu, const uint32_t key[2], uint32_t layer, uint32_t particle,
                     uint32_t event) {
   if (!(mu > 0.0)) return 0;
@@ -122,24 +162,12 @@ int64_t orc_poisson(double mu, const uint32_t key[2], uint32_t layer, uint32_t p
     }
     return k;
   }
-  const double slam = sqrt(mu);
-  const double loglam = log(mu);
-  const double b = 0.931 + 2.53 * slam;
-  const double a = -0.059 + 0.02483 * b;
-  const double invalpha = 1.1239 + 1.1328 / (b - 3.4);
-  const double vr = 0.9277 - 3.6224 / (b - 2.0);
+  const ptrs_c c = ptrs_constants(mu);
   for (uint32_t i = 0; i < PTRS_MAX_ITER; ++i) {
     double u, V;
     draw_pair(key, i, layer, particle, event, &u, &V);
-    const double U = u - 0.5;
-    const double us = 0.5 - fabs(U);
-    if (us <= 0.0) continue; /* u == 0 exactly */
-    const double kd = floor((2.0 * a / us + b) * U + mu + 0.43);
-    if (us >= 0.07 && V <= vr) return (int64_t)kd;
-    if (kd < 0.0 || (us < 0.013 && V > us)) continue;
-    const double lhs = log(V) + log(invalpha) - log(a / (us * us) + b);
-    const double rhs = -mu + kd * loglam - lgamma(kd + 1.0);
-    if (lhs <= rhs) return (int64_t)kd;
+    const int64_t k = ptrs_iter(&c, u, V);
+    if (k >= 0) return k;
   }
   return (int64_t)floor(mu);
 }

@@ -63,6 +63,9 @@ int64_t orc_poisson(double mu, const uint32_t key[2], uint32_t layer, uint32_t p
                     uint32_t event);
 void orc_poisson_n(int64_t n, const double* mu, const uint32_t key[2], const uint32_t* layer,
                    const uint32_t* particle, const uint32_t* event, int64_t* out);
+/* One iteration of the PTRS draw (mu >= 10) from given uniforms u[i], V[i]:
+ * the accepted count, or -1 where the iteration rejects. */
+void orc_ptrs_iter_n(int64_t n, double mu, const double* u, const double* V, int64_t* out);
 
 /* Parametrisation entry (without the layer index) for a particle. */
 int32_t orc_param_entry(const orc_params* P, int32_t type, float E, float eta);

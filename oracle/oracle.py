@@ -85,6 +85,7 @@ def lib():
             L.orc_version.restype = C.c_char_p
             L.orc_philox_n.argtypes = [C.c_int64, vp, vp, vp]
             L.orc_poisson_n.argtypes = [C.c_int64, vp, vp, vp, vp, vp, vp]
+            L.orc_ptrs_iter_n.argtypes = [C.c_int64, C.c_double, vp, vp, vp]
             L.orc_param_entry.argtypes = [vp, C.c_int32, C.c_float, C.c_float]
             L.orc_param_entry.restype = C.c_int32
             L.orc_thresholds.argtypes = [vp, C.c_int32, vp, vp]
@@ -171,6 +172,15 @@ def poisson(mu, seed: int, layer, particle, event) -> np.ndarray:
     out = np.empty(n, dtype=np.int64)
     k = key_of(seed)
     lib().orc_poisson_n(n, _p(mu), _p(k), _p(lay), _p(par), _p(ev), _p(out))
+    return out
+
+
+def ptrs_iter(mu: float, u, V) -> np.ndarray:
+    """One PTRS iteration per (u, V) pair: the accepted count or -1."""
+    u = np.ascontiguousarray(u, dtype=np.float64).ravel()
+    V = np.ascontiguousarray(np.broadcast_to(V, u.shape), dtype=np.float64)
+    out = np.empty(len(u), dtype=np.int64)
+    lib().orc_ptrs_iter_n(len(u), float(mu), _p(u), _p(V), _p(out))
     return out
 
 

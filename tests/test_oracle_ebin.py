@@ -62,6 +62,16 @@ def test_fraction_and_edges(oprm, oprm_i, prm):
     top = O.param_entry(oprm, 2, Etop, 2.0)
     assert _bins(prm, top) == NE - 1
     assert all(O.param_entry_rng(oprm_i, 2, Etop, 2.0, 3, p, 0) == top for p in range(200))
+    # below the table: the points 2^k and 2^(k+1) of E = 1.75 2^k with k + 1 <= ebin_log2_min both
+    # clamp to bin 0, so the particle never moves; from 2^ebin_log2_min on it moves to bin 1
+    for k in (prm.ebin_log2_min - 3, prm.ebin_log2_min - 1):
+        Elow = float(1.75 * 2.0 ** k)
+        low = O.param_entry(oprm, 0, Elow, 0.4)
+        assert _bins(prm, low) == 0
+        assert all(O.param_entry_rng(oprm_i, 0, Elow, 0.4, 3, p, 1) == low for p in range(300))
+    E0 = float(1.75 * 2.0 ** prm.ebin_log2_min)
+    moved = {_bins(prm, O.param_entry_rng(oprm_i, 0, E0, 0.4, 3, p, 1)) for p in range(300)}
+    assert moved == {0, 1}
 
 
 def test_simulation_uses_interpolated_entries(ogeo, oprm, oprm_i, prm):
