@@ -2,8 +2,13 @@
 
 Events are independent: event e of a batch uses random-stream event number
 first_event + e, so a batch split into contiguous event ranges, one per rank,
-gives exactly the cells of the unsplit batch.  No data-path collective is
-needed; ranks only agree on timing (the maximum over ranks).
+gives exactly the cells of the unsplit batch.  The forward needs no
+data-path collective; ranks only agree on timing (the maximum over ranks).
+
+The adjoint has one exchange.  A loss summed over events (and over random
+streams, the seeds) has a gradient that is the sum of the per-event (per-seed)
+gradients, so ranks that each ran fcs_simulate_backward on their own events
+or seeds sum d_frac and d_shape_w over the ranks: allreduce_gradients.
 """
 from __future__ import annotations
 
@@ -29,3 +34,21 @@ def max_over_ranks(value: float) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def allreduce_gradients(*grads):
+    """Sums gradient tensors in place over the ranks of the default process
+    group (NCCL for CUDA tensors, gloo for CPU tensors) and returns them.
+
+    Use after each rank's fcs_simulate_backward over its event range or its
+    seeds: every rank then holds the gradient of the whole batch.  None
+    entries are skipped; without a process group, or with one rank, nothing
+    changes.  All ranks must pass tensors of the same shapes in the same
+    order."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return grads
+    for g in grads:
+        if g is not None:
+            dist.all_reduce(g, op=dist.ReduceOp.SUM)
+    return grads
