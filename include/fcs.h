@@ -101,7 +101,8 @@ typedef struct fcs_particles {
 } fcs_particles;
 
 enum fcs_mode {
-  FCS_MODE_ATOMIC = 0,       /* FP32 atomic accumulation, warp-aggregated (Sec. 4: atomicAdd) */
+  FCS_MODE_ATOMIC = 0,       /* warp-aggregated atomics (Sec. 4: atomicAdd) of the float count x Ehit of
+                                each group of hits into FP64 cells, rounded once to float per cell */
   FCS_MODE_DETERMINISTIC = 1 /* sort by (cell, task), fixed-order FP32 fold; bit-reproducible */
 };
 
@@ -118,8 +119,8 @@ typedef struct fcs_config {
                               graph keyed by every argument, replay it on identical calls */
   int32_t timing;          /* != 0: record CUDA events around each stage (fcs_workspace_timings) */
   int32_t wave_events;     /* batched: events per launch sequence (a wave), >= 0; 0 = all events of
-                              the call.  A wave's accumulation rows (4 B x cells per event) stay
-                              in L2 while they fit; the workspace holds one wave's rows */
+                              the call.  A wave's accumulation rows (FP64: 8 B x cells per event)
+                              stay in L2 while they fit; the workspace holds one wave's rows */
   int32_t energy_interp;   /* 1: probabilistic energy-bin interpolation.  A particle of energy
                               E = m 2^k (m in [1, 2)) takes the next energy bin with probability
                               m - 1: when word 0 of Philox block (0, 2 << 16, particle in event,
@@ -334,7 +335,9 @@ int fcs_autotune(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
  * FCS_MB_LOP3 = shift + 3-input XOR + add steps/s; FCS_MB_FFMA = FP32 FMAs/s;
  * FCS_MB_RED = float reductions into global memory at uniformly random
  * addresses of a `size`-float array per second; FCS_MB_MUFU = hardware sines
- * (__sinf)/s; FCS_MB_LDS = 32-bit words/s read by 128-bit shared-memory loads.  A full grid (4 waves of
+ * (__sinf)/s; FCS_MB_LDS = 32-bit words/s read by 128-bit shared-memory loads;
+ * FCS_MB_RED64 = double reductions at uniformly random addresses of a
+ * `size`-double array per second (the accumulation rows' atomics).  A full grid (4 waves of
  * 256-thread blocks) runs `iters` iterations per thread, once to warm up and
  * once timed with CUDA events on stream s; *rate receives operations per
  * second.  Allocates and frees its own device buffer.  Synchronous. */
@@ -345,7 +348,8 @@ enum fcs_microbench_kind {
   FCS_MB_FFMA = 3,
   FCS_MB_RED = 4,
   FCS_MB_MUFU = 5,
-  FCS_MB_LDS = 6
+  FCS_MB_LDS = 6,
+  FCS_MB_RED64 = 7
 };
 int fcs_microbench(int32_t kind, int64_t size, int32_t iters, double* rate, cudaStream_t s);
 
@@ -362,12 +366,13 @@ int fcs_microbench(int32_t kind, int64_t size, int32_t iters, double* rate, cuda
  * entry point has no counterpart in the paper; it only changes where the
  * intermediate buffers live.
  * Inputs and outputs are as for fcs_simulate_events (device pointers; the
- * dense cells_out and the validation dumps are not offered); the task
+ * dense cells_out and the validation dumps are not offered; n_events == 0
+ * writes event_offsets_out[0] = 0, zeroes *stats and returns FCS_OK); the task
  * records, tile map, recheck queue and accumulation rows are carved out of
  * one static device array of FCS_STATIC_SCRATCH_BYTES.  The call is
  * synchronous on stream s and returns the device status like a sync call.
  * Limits: the particle tables (about 76 bytes x layers + 32 bytes per particle) plus the
- * accumulation rows (4 bytes x cells, padded, per event) must fit in the
+ * accumulation rows (8 bytes x cells, padded, per event) must fit in the
  * array, and the hits of the call are bounded by what remains (128 hits per
  * 4 remaining bytes); otherwise FCS_E_RANGE with the sizes in the message.
  * The first call on a device looks up the array's device address

@@ -163,7 +163,7 @@ struct fcs_workspace {
   int64_t gmap_cap = 0;
   uint2* recheck = nullptr;
   int64_t recheck_cap = 0;
-  float* acc = nullptr;
+  double* acc = nullptr;  // FP64 accumulation rows
   int64_t acc_cap = 0, rows_cap = 0;
   int32_t acc_stride = 0;
   int64_t* chunk_counts = nullptr;
@@ -1546,7 +1546,7 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
                                           int64_t capacity, fcs_stats* stats, cudaStream_t s) {
   if (!geo || !prm) return set_err(FCS_E_ARG, "geo and params are required");
   FCS_TRY(check_particles(particles, n_particles));
-  if (n_particles < 0 || n_events < 1 || capacity < 0) return set_err(FCS_E_ARG, "bad size");
+  if (n_particles < 0 || n_events < 0 || capacity < 0) return set_err(FCS_E_ARG, "bad size");
   if (n_events >= kMaxEventsPerCall) return set_err(FCS_E_RANGE, "at most 2^24 - 1 events per call");
   if (!event_offsets_out) return set_err(FCS_E_ARG, "event_offsets_out is required");
   if ((cell_ids == nullptr) != (cell_E == nullptr)) return set_err(FCS_E_ARG, "cell_ids and cell_E go together");
@@ -1555,6 +1555,13 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   FCS_TRY(current_device(&dev));
   if (dev != geo->device || dev != prm->device)
     return set_err(FCS_E_ARG, "geometry and parametrisation must live on the current device");
+  if (n_events == 0) {  // as fcs_simulate_events: an empty output, zeroed statistics
+    k_empty_offsets<<<1, 32, 0, s>>>(event_offsets_out, 0);
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    FCS_CUDA(cudaGetLastError());
+    FCS_CUDA(cudaStreamSynchronize(s));
+    return ok();
+  }
   void* base = nullptr;
   int sms = 0;
   FCS_TRY(static_scratch(dev, &base, &sms));
@@ -1579,7 +1586,7 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   w.pdefer = c.take<int32_t>(P * NL);
   w.pd_cap = P * NL;
   w.task_cap = P * NL;
-  w.acc = c.take<float>((int64_t)n_events * geo->d.acc_stride);
+  w.acc = c.take<double>((int64_t)n_events * geo->d.acc_stride);
   w.rows_cap = n_events;
   w.acc_stride = geo->d.acc_stride;
   const int64_t chunks = compact_chunks(geo->d.n_cells, n_events);
@@ -1629,7 +1636,7 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   // the array keeps the previous call's contents: the accumulation rows and
   // the scan state must start at zero
   int rc = FCS_OK;
-  cudaError_t e = cudaMemsetAsync(w.acc, 0, (size_t)n_events * geo->d.acc_stride * sizeof(float), s);
+  cudaError_t e = cudaMemsetAsync(w.acc, 0, (size_t)n_events * geo->d.acc_stride * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.scan_state, 0, (size_t)w.ss_cap * sizeof(uint64_t), s);
   if (e != cudaSuccess) rc = set_err(FCS_E_CUDA, "clearing the static scratch: %s", cudaGetErrorString(e));
   if (rc == FCS_OK) {

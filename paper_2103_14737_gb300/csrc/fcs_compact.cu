@@ -1,7 +1,9 @@
 // fcs_compact.cu - gathers the hit cells of each event as (cell id, E) pairs
 // for the transfer of results (the paper's sim_ct kernel, Sec. 4) and resets
 // the accumulation rows to zero in the same pass (the paper's separate
-// clean kernel, Sec. 4, is folded in).  Output order: event-major, ascending
+// clean kernel, Sec. 4, is folded in).  The rows are FP64 (fcs_internal.cuh:
+// acc_add); each hit cell is rounded once to the float of the output.
+// Output order: event-major, ascending
 // cell id; offsets come from an exclusive scan of per-chunk counts, so the
 // result is deterministic.
 #include "fcs_internal.cuh"
@@ -10,31 +12,34 @@ namespace fcs {
 namespace {
 
 constexpr int kCThreads = 256;
-constexpr int kCItems = 16;  // four float4 per thread (rows are padded to 64 cells)
-constexpr int kCVec = kCItems / 4;
+constexpr int kCItems = 16;  // eight 16-byte loads of FP64 cells per thread (rows are padded to 64 cells)
+constexpr int kCVec = kCItems / 2;
 constexpr int kChunk = kCThreads * kCItems;
+
+// A row value is a hit cell when it is not +-0 (an integer test, off the FP64 pipe).
+__device__ __forceinline__ bool acc_nonzero(double d) {
+  return ((unsigned long long)__double_as_longlong(d) << 1) != 0ull;
+}
 
 // Both kernels take the chunks (kChunk cells of one row) t = row * cpr + chunk
 // grid-stride, so a capped grid leaves SMs to concurrent work.
-__global__ void __launch_bounds__(kCThreads) k_compact_count(const float* __restrict__ acc, int32_t n_cells,
+__global__ void __launch_bounds__(kCThreads) k_compact_count(const double* __restrict__ acc, int32_t n_cells,
                                                            int32_t stride, int32_t cpr, int64_t n_chunks,
                                                            int64_t* __restrict__ counts) {
   __shared__ int s[kCThreads / 32];
   for (int64_t t = blockIdx.x; t < n_chunks; t += gridDim.x) {
     const int chunk = (int)(t % cpr), row = (int)(t / cpr);
     const int64_t c0 = (int64_t)chunk * kChunk + threadIdx.x * kCItems;
-    const float4* src = reinterpret_cast<const float4*>(acc + (int64_t)row * stride + c0);
+    const double2* src = reinterpret_cast<const double2*>(acc + (int64_t)row * stride + c0);
     int cnt = 0;
     if (c0 < n_cells) {
-      float4 a[kCVec];
+      double2 a[kCVec];
 #pragma unroll
       for (int q = 0; q < kCVec; ++q) a[q] = src[q];
 #pragma unroll
       for (int q = 0; q < kCVec; ++q) {
-        cnt += (c0 + 4 * q < n_cells) && (a[q].x != 0.0f);
-        cnt += (c0 + 4 * q + 1 < n_cells) && (a[q].y != 0.0f);
-        cnt += (c0 + 4 * q + 2 < n_cells) && (a[q].z != 0.0f);
-        cnt += (c0 + 4 * q + 3 < n_cells) && (a[q].w != 0.0f);
+        cnt += (c0 + 2 * q < n_cells) && acc_nonzero(a[q].x);
+        cnt += (c0 + 2 * q + 1 < n_cells) && acc_nonzero(a[q].y);
       }
     }
     cnt = __reduce_add_sync(0xffffffffu, cnt);
@@ -50,7 +55,7 @@ __global__ void __launch_bounds__(kCThreads) k_compact_count(const float* __rest
 }
 
 __global__ void __launch_bounds__(kCThreads) k_compact_write(
-    float* __restrict__ acc, int32_t n_cells, int32_t stride, int32_t cpr, int64_t n_chunks, int32_t ev_lo,
+    double* __restrict__ acc, int32_t n_cells, int32_t stride, int32_t cpr, int64_t n_chunks, int32_t ev_lo,
     const int64_t* __restrict__ offsets, float* __restrict__ cells_out, int32_t* __restrict__ cell_ids,
     float* __restrict__ cell_E, int64_t* __restrict__ event_offsets_out, int64_t capacity) {
   __shared__ int s_w[kCThreads / 32];
@@ -60,28 +65,29 @@ __global__ void __launch_bounds__(kCThreads) k_compact_write(
   for (int64_t t = blockIdx.x; t < n_chunks; t += gridDim.x) {
     const int chunk = (int)(t % cpr), row = (int)(t / cpr);
     const int64_t c0 = (int64_t)chunk * kChunk + threadIdx.x * kCItems;
-    float4* src = reinterpret_cast<float4*>(acc + (int64_t)row * stride + c0);
+    double2* src = reinterpret_cast<double2*>(acc + (int64_t)row * stride + c0);
     float v[kCItems];
+    unsigned mask = 0;
 #pragma unroll
     for (int k = 0; k < kCItems; ++k) v[k] = 0.0f;
     if (c0 < n_cells) {
-      float4 a[kCVec];
+      double2 a[kCVec];
 #pragma unroll
       for (int q = 0; q < kCVec; ++q) a[q] = src[q];
-      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      const double2 z = make_double2(0.0, 0.0);
 #pragma unroll
       for (int q = 0; q < kCVec; ++q) {
-        v[4 * q] = a[q].x;
-        v[4 * q + 1] = a[q].y;
-        v[4 * q + 2] = a[q].z;
-        v[4 * q + 3] = a[q].w;
+        if (c0 + 2 * q < n_cells && acc_nonzero(a[q].x)) {
+          mask |= 1u << (2 * q);
+          v[2 * q] = acc_to_f32(a[q].x);
+        }
+        if (c0 + 2 * q + 1 < n_cells && acc_nonzero(a[q].y)) {
+          mask |= 1u << (2 * q + 1);
+          v[2 * q + 1] = acc_to_f32(a[q].y);
+        }
         src[q] = z;
       }
     }
-    unsigned mask = 0;
-#pragma unroll
-    for (int k = 0; k < kCItems; ++k)
-      if (c0 + k < n_cells && v[k] != 0.0f) mask |= 1u << k;
     const int cnt = __popc(mask);
     // block exclusive scan of cnt
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -121,7 +127,7 @@ __global__ void __launch_bounds__(kCThreads) k_compact_write(
       float* dst = cells_out + (int64_t)(ev_lo + row) * n_cells + c0;
       if (c0 + kCItems <= n_cells && (n_cells & 3) == 0) {
 #pragma unroll
-        for (int q = 0; q < kCVec; ++q)
+        for (int q = 0; q < kCItems / 4; ++q)
           reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       } else {
 #pragma unroll

@@ -15,9 +15,10 @@
 // eta or phi lies within the bound of a cell or region edge is queued and
 // decided by the FP64 recheck kernel, which repeats the oracle's FP64 steps
 // (the paper's two FP32 cell mismatches in 62M hits were removed with FP64,
-// Sec. 6).  Certified hits are deposited with warp-aggregated float atomics
-// (Sec. 4 chose atomicAdd) or, in deterministic mode, emitted as
-// (cell, task, count) records for the sort-by-cell reduction.
+// Sec. 6).  Certified hits are deposited with warp-aggregated atomics (Sec. 4
+// chose atomicAdd) of the float count x Ehit into FP64 cells or, in
+// deterministic mode, emitted as (cell, task, count) records for the
+// sort-by-cell reduction.
 #pragma once
 
 #include <type_traits>
@@ -318,7 +319,7 @@ __device__ __forceinline__ void deposit_single(const HitKParams& kp, int32_t eve
                                                int32_t cell, int mode, int32_t entry, int bin, int64_t slot) {
   const int64_t row = event - kp.ev_lo;
   if (mode == kModeAtomic) {
-    atomicAdd(kp.w.acc + row * kp.g.acc_stride + cell, Ehit);
+    acc_add(kp.w.acc + row * kp.g.acc_stride + cell, Ehit);
   } else if (mode == kModeGrad) {
     const float v = __fmul_rn(Ehit, __ldg(kp.grad_in + row * kp.g.n_cells + cell));
     atomicAdd(kp.grad_acc + ((int64_t)entry << 7) + bin, (double)v);
@@ -464,7 +465,7 @@ __global__ void __launch_bounds__(BLOCK, MODE == kModeAtomic ? 1280 / BLOCK : 0)
                                             : __match_any_sync(m, ((unsigned long long)(uint32_t)tl << 32) |
                                                                       (uint32_t)f.cell);
             if (lane == __ffs(peers) - 1)
-              atomicAdd(w.acc + T.row_off + f.cell, __fmul_rn((float)__popc(peers), T.Ehit));
+              acc_add(w.acc + T.row_off + f.cell, __fmul_rn((float)__popc(peers), T.Ehit));
           }
         } else {
           const uint32_t cg = T.row_off + (uint32_t)f.cell;

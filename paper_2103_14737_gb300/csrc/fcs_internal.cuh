@@ -123,7 +123,7 @@ struct WsDev {
                        // front, PTRS draws from the back (their resume iteration waits in tn)
   int32_t* gmap;       // [gmap_cap] granule -> task
   uint2* recheck;      // [recheck_cap] (task, hit in task)
-  float* acc;          // [rows][acc_stride] zero-maintained accumulation rows
+  double* acc;         // [rows][acc_stride] zero-maintained accumulation rows (FP64: see acc_add)
   int64_t task_cap, gmap_cap, recheck_cap, rows_cap, pdefer_cap;
   uint64_t* keys;      // deterministic mode record slots, one per hit [rec_cap]
   uint64_t* keys_alt;  // ping-pong buffer [rec_cap]
@@ -183,6 +183,38 @@ __device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
 }
 __device__ __forceinline__ double u24d(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
 __device__ __forceinline__ float u24f(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+
+// ---- accumulation rows ------------------------------------------------------
+// Cells accumulate in FP64.  A deposit is the float count x Ehit of a group
+// of hits (one rounding, relative 2^-24); FP64 sums of such terms carry no
+// order-dependent error that reaches the float result, which the compaction
+// rounds once.  (In FP32 a cell that collects thousands of equal group
+// deposits drifts by the same rounding every time, and red.add.f32 flushes
+// subnormal operands and results to zero.)  The widening is integer bit
+// manipulation, off the narrow FP64 pipe; zero, subnormal and non-finite
+// floats take the conversion instruction.
+__device__ __forceinline__ double f32_to_f64_bits(float v) {
+  const uint32_t u = __float_as_uint(v);
+  const uint32_t ex = u & 0x7F800000u;
+  if (ex == 0u || ex == 0x7F800000u) return (double)v;
+  const uint32_t hi = (u & 0x80000000u) | (((u & 0x7FFFFFFFu) >> 3) + (896u << 20));
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+__device__ __forceinline__ void acc_add(double* cell, float v) { atomicAdd(cell, f32_to_f64_bits(v)); }
+
+// Round-to-nearest-even of an FP64 row value to float, with integer
+// operations where the result is a normal float; zero, subnormal, overflowing
+// and non-finite values take the conversion instruction.
+__device__ __forceinline__ float acc_to_f32(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  const uint32_t e = (hi >> 20) & 0x7FFu;
+  if (e < 897u || e > 1150u) return __double2float_rn(d);
+  uint32_t r = ((e - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const uint32_t dropped = lo & 0x1FFFFFFFu;
+  r += (dropped > 0x10000000u || (dropped == 0x10000000u && (r & 1u))) ? 1u : 0u;  // a carry rounds the exponent up
+  return __uint_as_float(r | (hi & 0x80000000u));
+}
 
 // ---- launchers (host) -------------------------------------------------------
 struct Launch {

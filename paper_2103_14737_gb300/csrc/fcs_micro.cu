@@ -126,6 +126,18 @@ __global__ void __launch_bounds__(kMbThreads) k_mb_red(float* arr, int64_t n, in
   }
 }
 
+// FP64 reductions at pseudo-random addresses of an n-double array (the
+// accumulation rows' atomics).
+__global__ void __launch_bounds__(kMbThreads) k_mb_red64(double* arr, int64_t n, int iters, uint32_t seed) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t s = tid * 2654435761u ^ seed;
+  for (int i = 0; i < iters; ++i) {
+    s = s * 1664525u + 1013904223u;  // LCG address stream
+    const uint64_t idx = ((uint64_t)s * (uint64_t)n) >> 32;
+    atomicAdd(arr + idx, 1.0);
+  }
+}
+
 }  // namespace
 }  // namespace fcs
 
@@ -140,9 +152,14 @@ extern "C" int fcs_microbench(int32_t kind, int64_t size, int32_t iters, double*
   const int blocks = sms * (2048 / kMbThreads) * 4;  // four full waves of 256-thread blocks
   const int64_t threads = (int64_t)blocks * kMbThreads;
   void* buf = nullptr;
-  const int64_t arr_n = (kind == FCS_MB_RED) ? size : 0;
-  if (arr_n < 0 || (kind == FCS_MB_RED && arr_n < 1)) return FCS_E_ARG;
-  if (cudaMalloc(&buf, (size_t)(threads + arr_n) * 4) != cudaSuccess) return FCS_E_OOM;
+  const bool red = kind == FCS_MB_RED || kind == FCS_MB_RED64;
+  const int64_t arr_n = red ? size : 0;
+  if (arr_n < 0 || (red && arr_n < 1)) return FCS_E_ARG;
+  const size_t elem = kind == FCS_MB_RED64 ? 8 : 4;
+  // per-thread outputs (4 bytes), then the reduction array (8-byte aligned)
+  const size_t arr_off = ((size_t)threads * 4 + 255) / 256 * 256;
+  if (cudaMalloc(&buf, arr_off + (size_t)arr_n * elem) != cudaSuccess) return FCS_E_OOM;
+  void* arr = (unsigned char*)buf + arr_off;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -152,17 +169,18 @@ extern "C" int fcs_microbench(int32_t kind, int64_t size, int32_t iters, double*
       case FCS_MB_MULWIDE: k_mb_mulwide<<<blocks, kMbThreads, 0, s>>>((uint32_t*)buf, it, 3u); break;
       case FCS_MB_LOP3: k_mb_lop3<<<blocks, kMbThreads, 0, s>>>((uint32_t*)buf, it, 5u); break;
       case FCS_MB_FFMA: k_mb_ffma<<<blocks, kMbThreads, 0, s>>>((float*)buf, it, 0.5f); break;
-      case FCS_MB_RED: k_mb_red<<<blocks, kMbThreads, 0, s>>>((float*)buf + threads, arr_n, it, 9u); break;
+      case FCS_MB_RED: k_mb_red<<<blocks, kMbThreads, 0, s>>>((float*)arr, arr_n, it, 9u); break;
+      case FCS_MB_RED64: k_mb_red64<<<blocks, kMbThreads, 0, s>>>((double*)arr, arr_n, it, 9u); break;
       case FCS_MB_MUFU: k_mb_mufu<<<blocks, kMbThreads, 0, s>>>((float*)buf, it, 0.3f); break;
       case FCS_MB_LDS: k_mb_lds<<<blocks, kMbThreads, 0, s>>>((uint32_t*)buf, it, 13u); break;
       default: break;
     }
   };
   int rc = FCS_OK;
-  if (kind < FCS_MB_PHILOX || kind > FCS_MB_LDS) rc = FCS_E_ARG;
+  if (kind < FCS_MB_PHILOX || kind > FCS_MB_RED64) rc = FCS_E_ARG;
   float ms = 0.0f;
   if (rc == FCS_OK) {
-    if (kind == FCS_MB_RED) cudaMemsetAsync((float*)buf + threads, 0, (size_t)arr_n * 4, s);
+    if (red) cudaMemsetAsync(arr, 0, (size_t)arr_n * elem, s);
     launch(iters);  // warm-up
     cudaEventRecord(e0, s);
     launch(iters);
@@ -173,7 +191,7 @@ extern "C" int fcs_microbench(int32_t kind, int64_t size, int32_t iters, double*
   }
   if (rc == FCS_OK && ms > 0.0f) {
     // operations per thread per iteration of each kernel
-    const double per = (kind == FCS_MB_PHILOX) ? 1.0 : (kind == FCS_MB_RED) ? 1.0 : (kind == FCS_MB_LDS) ? 32.0 : 8.0;
+    const double per = (kind == FCS_MB_PHILOX || red) ? 1.0 : (kind == FCS_MB_LDS) ? 32.0 : 8.0;
     *rate = (double)threads * iters * per / (ms * 1e-3);
   }
   cudaEventDestroy(e0);

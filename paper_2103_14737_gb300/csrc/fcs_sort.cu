@@ -20,8 +20,8 @@
 //      (insertion, up to 32 records), merges the records of a task (their
 //      counts add exactly) and folds; a warp per longer segment sorts it in
 //      shared memory (bitonic) before its first lane folds.  The float result
-//      goes to the accumulation row, where the compaction of the atomic mode
-//      picks it up and re-zeroes it.
+//      goes to the (FP64) accumulation row, where the compaction of the atomic
+//      mode picks it up, rounds it back to the same float and re-zeroes it.
 // Only the order of places inside a segment depends on scheduling, and the
 // sort removes it, so the cells are bit-reproducible.
 #include "fcs_internal.cuh"
@@ -118,7 +118,7 @@ struct Fold {
 // place by insertion and folded; longer ones are listed for k_det_fold_big.
 __global__ void __launch_bounds__(256) k_det_fold(uint64_t* __restrict__ recs, const int64_t* __restrict__ cell_off,
                                                   int64_t n_cells_all, Sizes* sz, int64_t cap, uint64_t task_mask,
-                                                  const float* __restrict__ task_ehit, float* __restrict__ acc,
+                                                  const float* __restrict__ task_ehit, double* __restrict__ acc,
                                                   int64_t* __restrict__ big) {
   if (sz->flags & FCS_FLAG_HIT_CAPACITY) return;
   const int64_t total = min(sz->n_records, cap);
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(32 * kBigWarps) k_det_fold_big(uint64_t* __res
                                                                  const int64_t* __restrict__ cell_off,
                                                                  int64_t n_cells_all, const Sizes* sz, int64_t cap,
                                                                  uint64_t task_mask, const float* __restrict__ task_ehit,
-                                                                 float* __restrict__ acc,
+                                                                 double* __restrict__ acc,
                                                                  const int64_t* __restrict__ big) {
   __shared__ uint64_t s_rec[kBigWarps][kBigMax];
   if (sz->flags & FCS_FLAG_HIT_CAPACITY) return;

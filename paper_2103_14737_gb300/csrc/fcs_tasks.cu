@@ -238,8 +238,9 @@ __device__ __forceinline__ int32_t ptrs_step_fp32(float mu32, uint32_t layer, ui
 }
 
 // Parametrisation entry of a particle (without the layer index).  Energy bin
-// from the float's exponent field (= floor(log2 E) for normal E; subnormal E
-// clamps to bin 0).  |eta| bin: for an integer scale S < 256, |eta| S =
+// from floor(log2 E): the float's exponent field for normal E, and for a
+// subnormal E = m 2^-149 the position of m's leading bit.  |eta| bin: for an
+// integer scale S < 256, |eta| S =
 // m S 2^(e - 150) with m the 24-bit significand, so its floor is an exact
 // integer shift; other scales take the FP64 product, which is exact too.
 __device__ __forceinline__ int32_t eta_bin(const ParamDev& p, float eta) {
@@ -264,8 +265,10 @@ __device__ __forceinline__ int32_t eta_bin(const ParamDev& p, float eta) {
 }
 
 __device__ __forceinline__ int32_t param_entry(const ParamDev& p, int32_t type, float E, float eta) {
-  const int32_t ef = (int32_t)((__float_as_uint(E) >> 23) & 0xFFu);  // E > 0
-  int32_t eb = (ef - 127) - p.ebin_min;
+  const uint32_t bits = __float_as_uint(E);  // E > 0
+  const int32_t ef = (int32_t)((bits >> 23) & 0xFFu);
+  const int32_t lg2 = ef ? ef - 127 : -118 - __clz(bits & 0x7FFFFFu);  // subnormal: -149 + (31 - clz(m))
+  int32_t eb = lg2 - p.ebin_min;
   eb = max(0, min(eb, p.NE - 1));
   return (type * p.NE + eb) * p.NH + eta_bin(p, eta);
 }
@@ -309,18 +312,19 @@ __device__ __forceinline__ uint32_t layer_mask(const ParamDev& p, int64_t row, f
   return mask;
 }
 
-// Energy-bin interpolation: E = m 2^k (m in [1, 2)) takes the next energy
-// bin (clamped to the last) with probability m - 1, decided exactly in
-// integers: word 0 of Philox block (0, 2 << 16, particle in event, event)
-// below the 23 mantissa bits of E shifted left by 9.
+// Energy-bin interpolation: E = m 2^k (m in [1, 2)) takes the bin of the
+// next point 2^(k+1), clamp(k + 1 - ebin_min, 0, NE - 1), with probability
+// m - 1, decided exactly in integers: word 0 of Philox block (0, 2 << 16,
+// particle in event, event) below the 23 mantissa bits of E shifted left by
+// 9.  (Below the table's first point both points clamp to bin 0.)
 __device__ __forceinline__ int32_t interp_entry(const ParamDev& p, int32_t entry, float E, uint32_t pin,
                                                 uint32_t event, uint32_t k0, uint32_t k1) {
   const uint32_t x0 = philox4x32_10(make_uint4(0u, kPurposeEnergyBin << 16, pin, event), k0, k1).x;
   const uint32_t bits = __float_as_uint(E);
   if ((bits >> 23) == 0 || x0 >= ((bits & 0x7FFFFFu) << 9)) return entry;  // subnormal E: m < 1
-  const int32_t hb = entry % p.NH, teb = entry / p.NH;
-  const int32_t eb = teb % p.NE, t = teb / p.NE;
-  return (t * p.NE + min(eb + 1, p.NE - 1)) * p.NH + hb;
+  const int32_t hb = entry % p.NH, t = entry / (p.NH * p.NE);
+  const int32_t eb = max(0, min((int32_t)((bits >> 23) & 0xFFu) - 127 + 1 - p.ebin_min, p.NE - 1));
+  return (t * p.NE + eb) * p.NH + hb;
 }
 
 // Per particle: its checks, parametrisation entry, event and layer mask; the

@@ -279,7 +279,7 @@ def fcs_simulate_events_host(geo, prm, ws, type_, E, eta, phi, event_offsets, se
     return rc, st
 
 
-MB_PHILOX, MB_MULWIDE, MB_LOP3, MB_FFMA, MB_RED, MB_MUFU, MB_LDS = range(7)
+MB_PHILOX, MB_MULWIDE, MB_LOP3, MB_FFMA, MB_RED, MB_MUFU, MB_LDS, MB_RED64 = range(8)
 
 
 def fcs_microbench(kind, size=0, iters=256):

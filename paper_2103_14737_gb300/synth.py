@@ -344,3 +344,222 @@ def workload(name: str, seed: int = 1, n_events: int | None = None) -> Particles
     if w["kind"] == "ttbar":
         return ttbar_like(seed, ne)
     return pileup(seed, ne)
+
+
+# ---------------------------------------------------------------------------
+# Edge inputs: seeded geometries, parametrisations and particles that reach
+# the corners of the method (the same loaders and the same rules as above;
+# still input data only)
+# ---------------------------------------------------------------------------
+def random_geometry(seed: int, n_layers: int = 8, regions_per_layer=(1, 4), n_regions_total: int | None = None,
+                    n_eta_range=(1, 40), n_phi_choices=(1, 2, 7, 32, 64, 100, 256)) -> Geometry:
+    """A seeded geometry without the mirror symmetry of ``geometry()``.
+
+    Per layer: barrel or end-cap at a random radius / |z|, 1 to 4 regions (or
+    ``n_regions_total`` regions spread over the layers, up to 256) laid out
+    from a random eta start in ascending eta_lo with unequal gaps between
+    them: none (adjacent), 1e-4, a wide gap, or an overlap of 5e-10 (the
+    loaders accept overlaps below 1e-9).  Granularities from a set that
+    includes a non-dyadic 0.0371; phi grids start at -pi, 0 or a random angle,
+    mostly with n_phi d_phi = 2 pi and sometimes covering less of the circle
+    (the grid index wraps modulo n_phi either way).
+    """
+    rng = np.random.default_rng(seed)
+    if n_regions_total is None:
+        counts = rng.integers(regions_per_layer[0], regions_per_layer[1] + 1, size=n_layers)
+    else:
+        assert n_layers <= n_regions_total
+        counts = np.ones(n_layers, dtype=np.int64)
+        extra = rng.multinomial(n_regions_total - n_layers, rng.dirichlet(np.full(n_layers, 0.7)))
+        counts += extra
+    detas = (0.003125, 0.00625, 0.0125, 0.025, 0.05, 0.1, 0.0371, 0.2)
+    recs, lrb = [], [0]
+    n_gap = 0  # gap kinds cycle, so that every kind occurs
+    lay = np.zeros(n_layers, dtype=LAYER_DTYPE)
+    cell = 0
+    for li in range(n_layers):
+        barrel = bool(rng.random() < 0.5)
+        lay[li]["rz"] = rng.uniform(1200.0, 6000.0)
+        lay[li]["barrel"] = 1 if barrel else 0
+        eta = rng.uniform(-2.2, 0.3) if barrel else rng.uniform(-4.6, 1.5)
+        if counts[li] > 8:  # many regions: narrow ones, so that the layer stays within |eta| < 6
+            eta = rng.uniform(-5.5, -3.0)
+        for j in range(int(counts[li])):
+            if j > 0:
+                kind = n_gap % 4
+                n_gap += 1
+                eta += (0.0, 1e-4, rng.uniform(0.01, 0.5 if counts[li] <= 8 else 0.05), -5e-10)[kind]
+            de = float(rng.choice(detas if counts[li] <= 8 else detas[:6]))
+            ne = int(rng.integers(n_eta_range[0], n_eta_range[1] + 1))
+            if counts[li] > 8:
+                ne = max(1, min(ne, int(0.25 / de)))
+            nphi = int(rng.choice(n_phi_choices))
+            phi_lo = float(rng.choice([-math.pi, 0.0, rng.uniform(-math.pi, math.pi)]))
+            dphi = 2.0 * math.pi / nphi
+            if rng.random() < 0.15:
+                dphi *= rng.uniform(0.5, 1.0)
+            recs.append((eta, de, phi_lo, dphi, ne, nphi, cell, li))
+            cell += ne * nphi
+            eta = eta + ne * de
+        lrb.append(len(recs))
+    return Geometry(regions=np.array(recs, dtype=REGION_DTYPE), layer_region_begin=np.array(lrb, dtype=np.int32),
+                    layers=lay, n_cells=cell, names=tuple(f"L{i}" for i in range(n_layers)))
+
+
+# histogram kinds of edge_params
+SHAPE_KINDS = ("falling", "interior_zeros", "trailing_zeros", "single_bin", "steep", "first_only", "last_only",
+               "wide_range", "tiny_scale")
+
+
+def edge_params(geo: Geometry, seed: int, n_types: int = 2, n_ebins: int = 7, n_etabins: int = 40,
+                eta_bin_scale: float = 12.5, ebin_log2_min: int = 8, mean_hit_range=(1.0, 100.0),
+                r_edge_kind: str = "random", a_edge_kind: str = "random", subnormal_frac: bool = True) -> Params:
+    """A seeded parametrisation whose entries reach the edge cases of the method.
+
+    * layer fractions: Dirichlet(1) over a random subset of the layers, a
+      single layer, no layer at all, or (``subnormal_frac``) one subnormal
+      fraction (a float layer energy that rounds to 0, no task, or to a
+      subnormal value);
+    * mean hit energy: log-uniform on ``mean_hit_range`` MeV, or 3e38 MeV for
+      5 % of the entries (a Poisson mean near 0: every such task gets its one
+      hit);
+    * shape weights, one kind per entry (``SHAPE_KINDS``): falling with
+      radius; the same with half the bins zero; the same with every bin after
+      a random last bin K in [0, 126] zero; a single non-zero bin; one bin
+      holding 99 % of the weight and the 127 others sharing 1 % (guide cells
+      that span tens of bins); only bin 0; only bin 127; weights spread over
+      24 decades; falling weights scaled by 1e-30;
+    * radial edges: random increasing values from 0 or 0.5 mm; angular edges:
+      random increasing values within [0, 2 pi] (or 8 equal bins).
+    """
+    rng = np.random.default_rng(seed)
+    nl = geo.n_layers
+    shape = (n_types, n_ebins, n_etabins, nl)
+    frac = np.zeros(shape, dtype=np.float64)
+    for t in range(n_types):
+        for e in range(n_ebins):
+            for h in range(n_etabins):
+                kind = rng.integers(0, 10)
+                if kind == 0:
+                    continue  # no layer: the particle makes no task
+                if kind == 1:
+                    frac[t, e, h, rng.integers(0, nl)] = 1.0
+                    continue
+                k = int(rng.integers(1, nl + 1))
+                lays = rng.choice(nl, size=k, replace=False)
+                frac[t, e, h, lays] = rng.dirichlet(np.ones(k))
+                if kind == 2 and subnormal_frac:
+                    frac[t, e, h, lays[0]] = 1e-42  # subnormal in float32
+    lo, hi = mean_hit_range
+    mhe = np.exp(rng.uniform(math.log(lo), math.log(hi), size=shape))
+    mhe[rng.random(size=shape) < 0.05] = 3.0e38
+    if r_edge_kind == "random":
+        r0 = float(rng.choice([0.0, 0.5]))
+        re = np.concatenate([[r0], r0 + np.cumsum(rng.uniform(0.5, 60.0, size=N_RBINS))])
+    else:
+        re = r_edges().astype(np.float64)
+    if a_edge_kind == "random":
+        ae = np.sort(rng.uniform(0.0, 2.0 * math.pi, size=N_ABINS + 1))
+        ae[0] = float(rng.choice([0.0, ae[0]]))
+        ae[-1] = float(rng.choice([np.float32(2.0 * math.pi).astype(np.float64) - 1e-6, ae[-1]]))
+    else:
+        ae = a_edges().astype(np.float64)
+    r_mid = 0.5 * (re[:-1] + re[1:])
+    nb = N_RBINS * N_ABINS
+    w = np.empty(shape + (nb,), dtype=np.float64)
+    kinds = rng.integers(0, len(SHAPE_KINDS), size=shape)
+    for idx in np.ndindex(*shape):
+        lam = rng.uniform(10.0, 100.0)
+        base = (np.exp(-r_mid[:, None] / lam) * (1.0 + 0.2 * rng.uniform(-1.0, 1.0, size=(N_RBINS, N_ABINS)))).ravel()
+        name = SHAPE_KINDS[kinds[idx]]
+        if name == "falling":
+            v = base
+        elif name == "interior_zeros":
+            v = base * (rng.random(nb) < 0.5)
+            if not v.any():
+                v[rng.integers(0, nb)] = 1.0
+        elif name == "trailing_zeros":
+            K = int(rng.integers(0, nb - 1))
+            v = base.copy()
+            v[K + 1:] = 0.0
+        elif name == "single_bin":
+            v = np.zeros(nb)
+            v[rng.integers(0, nb)] = rng.uniform(0.1, 10.0)
+        elif name == "steep":
+            v = rng.uniform(0.5, 1.5, size=nb)
+            v *= 0.01 / v.sum()
+            v[rng.integers(0, nb)] = 0.99
+        elif name == "first_only":
+            v = np.zeros(nb)
+            v[0] = 1.0
+        elif name == "last_only":
+            v = np.zeros(nb)
+            v[-1] = 2.0
+        elif name == "wide_range":
+            v = 10.0 ** rng.uniform(-12.0, 12.0, size=nb)
+        else:  # tiny_scale
+            v = base * 1e-30
+        w[idx] = v
+    return Params(frac=frac.astype(np.float32), mean_hit_E=mhe.astype(np.float32),
+                  shape_w=w.reshape(shape + (N_RBINS, N_ABINS)).astype(np.float32),
+                  r_edges=re.astype(np.float32), a_edges=ae.astype(np.float32),
+                  eta_bin_scale=float(eta_bin_scale), ebin_log2_min=int(ebin_log2_min))
+
+
+def _f32_neighbours(x: float) -> list:
+    """x rounded to float32 and the float32 values one ulp below and above."""
+    f = np.float32(x)
+    return [np.nextafter(f, np.float32(-np.inf)), f, np.nextafter(f, np.float32(np.inf))]
+
+
+def edge_particles(seed: int, geo: Geometry, prm: Params, n_events: int = 4, n_random: int = 150,
+                   extreme_eta=(7.5, -7.5, 6.0, -6.0)) -> Particles:
+    """Particles at the edges of the parametrisation lookup and the geometry.
+
+    Each event mixes: |eta| exactly on |eta|-bin edges k / scale and one float
+    ulp either side, with both signs; energies exactly on the power-of-two
+    energy-bin edges (below, inside and above the table's range) and one ulp
+    either side; eta on region boundaries (eta_lo of each region and the
+    midpoints between regions) and one ulp either side; phi at +-pi rounded
+    to float, one ulp inside, and beyond the circle (7.5 and -40 rad); eta
+    far outside every region (``extreme_eta``) and +-0; a subnormal and a
+    tiny energy; plus ``n_random`` particles spread over the geometry.  Event
+    1 (of 3 or more) is empty.  Types cycle over the table's types.
+    """
+    rng = np.random.default_rng(seed)
+    NT, NE, NH = prm.frac.shape[:3]
+    s = prm.eta_bin_scale
+    etas = []
+    for k in rng.choice(NH + 1, size=min(NH + 1, 12), replace=False):
+        for v in _f32_neighbours(k / s):
+            etas += [v, -v]
+    reg = geo.regions
+    for r in range(len(reg)):
+        etas += _f32_neighbours(reg["eta_lo"][r])
+        etas += _f32_neighbours(reg["eta_lo"][r] + reg["n_eta"][r] * reg["deta"][r])
+    etas += [np.float32(v) for v in extreme_eta + (0.0, -0.0)]
+    energies = []
+    for j in range(-2, NE + 2):
+        energies += _f32_neighbours(2.0 ** (prm.ebin_log2_min + j))
+    energies += [np.float32(1e-40), np.float32(1e-3)]
+    phis = _f32_neighbours(math.pi) + _f32_neighbours(-math.pi) + [np.float32(7.5), np.float32(-40.0), np.float32(0.0)]
+    lo_eta = float(reg["eta_lo"].min()) - 0.3
+    hi_eta = float((reg["eta_lo"] + reg["n_eta"] * reg["deta"]).max()) + 0.3
+    parts = []
+    for ev in range(n_events):
+        if ev == 1 and n_events >= 3:
+            z = np.zeros(0)
+            parts.append((z.astype(np.int32), z, z, z))
+            continue
+        eta = np.array(etas + list(rng.uniform(lo_eta, hi_eta, size=n_random)), dtype=np.float32)
+        n = len(eta)
+        rng.shuffle(eta)
+        E = np.array(energies, dtype=np.float32)[rng.integers(0, len(energies), size=n)]
+        rand_E = rng.random(n) < 0.5
+        E[rand_E] = (2.0 ** rng.uniform(prm.ebin_log2_min - 1, prm.ebin_log2_min + NE + 1, size=rand_E.sum()))
+        phi = rng.uniform(-math.pi, math.pi, size=n).astype(np.float32)
+        pick = rng.random(n) < 0.3
+        phi[pick] = np.array(phis, dtype=np.float32)[rng.integers(0, len(phis), size=pick.sum())]
+        t = (np.arange(n) % NT).astype(np.int32)
+        parts.append((t, E.astype(np.float32), eta, phi))
+    return _concat(parts)

@@ -18,9 +18,7 @@ pytestmark = pytest.mark.gpu
 from oracle import oracle as O  # noqa: E402
 from paper_2103_14737_gb300 import fcs, synth  # noqa: E402
 from paper_2103_14737_gb300.autograd import simulate_cells  # noqa: E402
-
-TOL = 1e-5
-
+from parity import check_grad, grad_scales  # noqa: E402
 
 @pytest.fixture(scope="module")
 def sim(geo, prm):
@@ -29,31 +27,6 @@ def sim(geo, prm):
     s = fcs.Simulator(geo, prm)
     yield s
     s.close()
-
-
-def grad_scales(ogeo, oprm, prm, parts, seed, g, first_event=0):
-    """Per-component sums of absolute terms of the oracle's gradient."""
-    fa, wa = O.backward(ogeo, oprm, parts, seed, np.abs(g), first_event=first_event)
-    f = prm.frac.reshape(-1).astype(np.float64)
-    w = prm.shape_w.reshape(-1, 128).astype(np.float64)
-    S_abs = f * fa
-    W = w.sum(axis=1)
-    with np.errstate(divide="ignore", invalid="ignore"):
-        sw = np.where(W > 0, S_abs / W, 0.0)
-    return fa, wa + 2 * sw[:, None]
-
-
-def check_grad(got_f, got_w, ref_f, ref_w, sc_f, sc_w):
-    gf = got_f.cpu().numpy().astype(np.float64)
-    gw = got_w.cpu().numpy().astype(np.float64).reshape(ref_w.shape)
-    ef = np.abs(gf - ref_f)
-    bad = ef > TOL * sc_f + 1e-6 * np.abs(ref_f) + 1e-30
-    assert not bad.any(), f"{bad.sum()} d_frac out of tolerance, worst rel {(ef / (sc_f + 1e-300)).max()}"
-    ew = np.abs(gw - ref_w)
-    bad = ew > TOL * sc_w + 1e-6 * np.abs(ref_w) + 1e-30
-    assert not bad.any(), f"{bad.sum()} d_shape_w out of tolerance, worst rel {(ew / (sc_w + 1e-300)).max()}"
-    # untouched entries stay exactly zero
-    assert np.array_equal(gf == 0, ref_f == 0)
 
 
 @pytest.mark.parametrize("case", ["electron", "ttbar", "ttbar_perevent"])

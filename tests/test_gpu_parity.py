@@ -16,9 +16,8 @@ pytestmark = pytest.mark.gpu
 
 from oracle import oracle as O  # noqa: E402
 from paper_2103_14737_gb300 import fcs, synth  # noqa: E402
-
-RTOL, ATOL = 1e-5, 1e-3
-
+from parity import (ATOL, RTOL, check_cells_atomic, check_compacted, check_tasks_hits,  # noqa: E402
+                    run_both)
 
 @pytest.fixture(scope="module")
 def sim(geo, prm):
@@ -27,54 +26,6 @@ def sim(geo, prm):
     s = fcs.Simulator(geo, prm)
     yield s
     s.close()
-
-
-def run_both(sim, ogeo, oprm, parts, seed, first_event=0, mode=fcs.MODE_ATOMIC, batched=1, hpt=0, block=0,
-             hits=True):
-    d = sim.to_device(parts)
-    ref = O.simulate(ogeo, oprm, parts, seed=seed, first_event=first_event,
-                     hit_cap=(10**7 if hits else 0))
-    n_t = ref.n_tasks
-    got = sim.simulate(d, seed, first_event=first_event, mode=mode, batched=batched, hits_per_thread=hpt,
-                       block=block, dense=True, debug_tasks=max(n_t, 1), debug_hits=(max(ref.n_hits, 1) if hits else 0))
-    torch.cuda.synchronize()
-    return ref, got
-
-
-def check_tasks_hits(ref, got):
-    st = got["stats"]
-    assert st["n_tasks"] == ref.n_tasks
-    assert st["n_hits"] == ref.n_hits
-    for k in ("task_event", "task_particle", "task_layer", "task_n"):
-        assert np.array_equal(got[k].cpu().numpy(), getattr(ref, k)), k
-    assert np.array_equal(got["task_Ehit"].cpu().numpy().view(np.uint32), ref.task_Ehit.view(np.uint32))
-    if "hit_cell" in got and ref.hit_cell is not None:
-        hc = got["hit_cell"].cpu().numpy()
-        mism = np.nonzero(hc != ref.hit_cell)[0]
-        assert len(mism) == 0, f"{len(mism)} hit-cell mismatches, first {mism[:5]}"
-        assert np.array_equal(got["hit_bin"].cpu().numpy(), ref.hit_bin)
-
-
-def check_cells_atomic(ref, got, n_events):
-    cells = got["cells"].cpu().numpy().astype(np.float64)
-    want = ref.cells64
-    err = np.abs(cells - want)
-    bad = err > RTOL * np.abs(want) + ATOL
-    assert not bad.any(), f"{bad.sum()} cells out of tolerance, worst {err.max()}"
-    assert np.array_equal(cells != 0, want != 0)
-    check_compacted(got, cells, n_events)
-
-
-def check_compacted(got, dense, n_events):
-    off = got["event_offsets"].cpu().numpy()
-    ids = got["cell_ids"].cpu().numpy()
-    E = got["cell_E"].cpu().numpy()
-    assert off[0] == 0 and off[-1] == got["stats"]["n_nonzero"]
-    for e in range(n_events):
-        nz = np.nonzero(dense[e])[0]
-        a, b = off[e], off[e + 1]
-        assert np.array_equal(ids[a:b], nz)
-        assert np.array_equal(E[a:b].astype(np.float64), dense[e][nz])
 
 
 @pytest.mark.parametrize("batched", [1, 0])
@@ -546,5 +497,6 @@ def test_unit_microbenchmarks(sim):
         r = fcs.fcs_microbench(kind, 0, 64)
         assert 0 < r < lim * per_clk, (kind, r)
     assert fcs.fcs_microbench(fcs.MB_RED, 1 << 20, 16) > 0
+    assert fcs.fcs_microbench(fcs.MB_RED64, 1 << 20, 16) > 0
     with pytest.raises(fcs.FcsError):
         fcs.fcs_microbench(99, 0, 1)
