@@ -1,13 +1,17 @@
 #!/usr/bin/env python
 """Benchmark of the calorimeter hit path on GB300.
 
-One step = one fcs_simulate_events call over a batch of 64 pile-up events
-(hard scatter + Poisson(200) minimum-bias collisions of Poisson(60) particles),
-i.e. every step of the hot path: parametrisation lookup and Poisson hit counts,
-task records, the hit kernel (Philox, inverse-CDF shape sampling, (r, alpha)
--> (eta, phi), cell lookup, warp-aggregated deposit), the FP64 recheck and the
-compaction of non-zero cells.  Inputs are resident in HBM; the call is replayed
-as a CUDA graph; L2 is flushed (256 MB write) between timed steps.
+One step = one fcs_simulate_events call over a batch of 1024 pile-up events
+(hard scatter + Poisson(200) minimum-bias collisions of Poisson(60) particles,
+about 12.7M particles and 1.37e9 hits), i.e. every step of the hot path:
+parametrisation lookup and Poisson hit counts, task records, the hit kernel
+(Philox, inverse-CDF shape sampling, (r, alpha) -> (eta, phi), cell lookup,
+warp-aggregated deposit), the FP64 recheck and the compaction of non-zero
+cells.  Inputs are resident in HBM; the call is replayed as a CUDA graph; L2
+is flushed (256 MB write) between timed steps.  The same JSON line carries
+the paper's comparison (Sec. 4, GPU vs GPU_g): the same events as one launch
+sequence per event (graph-replayed and eagerly launched) and, on a two-event
+subset, one hit-kernel launch per task.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
 bounded sample of the same workload instead.
@@ -30,8 +34,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "simulated hits/s at 1 GB300 (batched; events/s and per-event launches alongside)"
 UNIT = "hits/s"
-WORKLOAD = "pileup64"
-N_EVENTS = 64
+WORKLOAD = "pileup1024"
+N_EVENTS = 1024
+PER_TASK_EVENTS = 2  # events 0 .. 1 of the batch: the per-task launch comparison (one launch per task)
 SEED = 1
 # ALU roofline of the hit kernel (the hit path's bound, per pipe):
 #   time per hit = sum over pipes of (algorithmic ops per hit / pipe peak),
@@ -162,7 +167,7 @@ def cpu_baseline(geo, prm, parts, seconds=10.0):
         evN += cores
     dtN = time.perf_counter() - t0
     return {"value": hitsN / dtN, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{evN} whole events of {WORKLOAD} ({hitsN} hits, {dtN:.1f} s) event-parallel on {cores} "
+            "sample": f"{evN} whole events of pileup{parts.n_events} ({hitsN} hits, {dtN:.1f} s) event-parallel on {cores} "
                       f"threads",
             "events_per_s": evN / dtN,
             "single_thread": {"value": hits1 / dt1, "unit": UNIT, "cores": 1,
@@ -178,9 +183,10 @@ def run_reference(args, rank, world):
         return
     geo = synth.geometry()
     prm = synth.params(geo)
-    parts = synth.workload(WORKLOAD, seed=SEED)
-    og, op = O.OracleGeometry(geo), O.OracleParams(prm)
     cores = os.cpu_count() or 1
+    # the batch's leading events (event k of a pile-up batch does not depend on the batch size)
+    parts = synth.pileup(seed=SEED, n_events=min(args.events, (args.warmup + args.steps) * cores))
+    og, op = O.OracleGeometry(geo), O.OracleParams(prm)
     hits = 0
     times = []
     for k in range(args.warmup + args.steps):
@@ -193,12 +199,13 @@ def run_reference(args, rank, world):
             hits += h
     tot = sum(times)
     v = hits / tot
-    sample = f"{cores} whole events of {WORKLOAD} per step, event-parallel on {cores} threads"
+    workload = f"pileup{args.events}"
+    sample = f"{cores} whole events of {workload} per step, event-parallel on {cores} threads"
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": sample},
+            "config": {"workload": workload, "sample": sample},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -353,6 +360,79 @@ def run_sweep(args):
     sim.close()
 
 
+def per_event_and_per_task(sim, d, parts, first_event, H, ms_batched, shape, flush, steps):
+    """The paper's comparison on GB300 (Sec. 4: the GPU path launched per
+    particle and layer, GPU_g grouping many tasks per launch), timed like the
+    headline: the same events as one launch sequence per event, replayed as
+    a CUDA graph and launched eagerly from the host; and one hit-kernel launch
+    per task on the first PER_TASK_EVENTS events, against the batched call on
+    the same events.  Each mode gives the same cells (parity tests)."""
+    import torch
+    from paper_2103_14737_gb300 import fcs
+    out = {}
+    n_ev = parts.n_events
+    K = max(3, min(10, steps // 10))
+    kw = dict(first_event=first_event, outputs=dict(cells=None), **shape)
+
+    def device_time(W, **extra):
+        sizing = {k: v for k, v in extra.items() if k != "use_graph"}
+        r = sim.simulate(d, SEED, **kw, **sizing)  # sizes the workspace (not timed)
+        assert r["status"] == 0 and r["stats"]["n_hits"] == H
+        for _ in range(W):
+            sim.simulate(d, SEED, sync=0, **kw, **extra)
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        for k in range(K):
+            flush.zero_()
+            st[k].record()
+            sim.simulate(d, SEED, sync=0, **kw, **extra)
+            en[k].record()
+        torch.cuda.synchronize()
+        rc, stt = fcs.fcs_workspace_status(sim.ws)
+        assert rc == 0, (rc, stt.as_dict())
+        return float(np.mean([a.elapsed_time(b) for a, b in zip(st, en)]))
+
+    ms_g = device_time(2, batched=0, use_graph=1)
+    launches = fcs.fcs_workspace_graph_kernels(sim.ws)
+    out["per_event_graph"] = {"events": n_ev, "ms_per_step": ms_g, "hits_per_s": H / (ms_g * 1e-3),
+                              "launches_per_step": launches, "batched_speedup": ms_g / ms_batched,
+                              "mode": "one launch sequence per event (batched = 0), the call replayed as a CUDA graph"}
+    ms_e = device_time(1, batched=0, use_graph=0)
+    out["per_event_eager"] = {"events": n_ev, "ms_per_step": ms_e, "hits_per_s": H / (ms_e * 1e-3),
+                              "batched_speedup": ms_e / ms_batched,
+                              "mode": "one launch sequence per event (batched = 0), kernels launched from the host "
+                                      "as the paper's per-event GPU path"}
+    # one hit-kernel launch per task: synchronous calls (the call reads each event's
+    # task list back), timed on the host like the batched call on the same events
+    sub = sim.to_device(parts.events(0, PER_TASK_EVENTS))
+
+    def host_time(reps, **extra):
+        kw2 = {**shape, **extra}
+        r = sim.simulate(sub, SEED, first_event=first_event, outputs=dict(cells=None), **kw2)
+        assert r["status"] == 0
+        torch.cuda.synchronize()
+        tt = []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim.simulate(sub, SEED, first_event=first_event, outputs=dict(cells=None), **kw2)
+            torch.cuda.synchronize()
+            tt.append(time.perf_counter() - t0)
+        return 1e3 * float(np.median(tt)), r["stats"]
+
+    ms_b, st_b = host_time(max(5, K))
+    ms_t, st_t = host_time(3, batched=2, block=128, hits_per_thread=1)
+    assert st_t["n_hits"] == st_b["n_hits"] and st_t["n_nonzero"] == st_b["n_nonzero"]
+    out["per_task"] = {"events": PER_TASK_EVENTS, "subset": f"events 0-{PER_TASK_EVENTS - 1} of the batch",
+                       "tasks": st_t["n_tasks"], "hits": st_t["n_hits"], "ms_per_call": ms_t,
+                       "hits_per_s": st_t["n_hits"] / (ms_t * 1e-3), "batched_ms_per_call": ms_b,
+                       "batched_hits_per_s": st_b["n_hits"] / (ms_b * 1e-3), "batched_speedup": ms_t / ms_b,
+                       "mode": "one hit-kernel launch per task (batched = 2, 128 x 1), the paper's non-grouped GPU "
+                               "mode; both calls synchronous, host wall time, median"}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -366,6 +446,7 @@ def main():
     ap.add_argument("--extra", action="store_true", help="also time deterministic mode and per-event launches")
     ap.add_argument("--events", type=int, default=N_EVENTS, help="events per step (smaller cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ab", action="store_true", help="skip the per-event and per-task launch comparison")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--sweep", action="store_true", help="the 1024-event sweep and launch latency table instead")
     ap.add_argument("--sweep-events", type=int, default=1024)
@@ -392,7 +473,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     geo = synth.geometry()
     prm = synth.params(geo)
-    # weak scaling: the job is world x 64 events; rank r simulates its contiguous
+    # weak scaling: the job is world x n_ev events; rank r simulates its contiguous
     # share (random-stream events first_event ...), with no data-path collective
     n_ev = args.events
     first_event, n_mine = shard_events(n_ev * world, rank, world)
@@ -409,8 +490,13 @@ def main():
     # size the workspace and the outputs with one synchronous call
     ref = sim.simulate(d, SEED, first_event=first_event, hits_per_thread=args.hpt, block=args.block)
     H = ref["stats"]["n_hits"]
-    outs = {k: ref[k] for k in ("cell_ids", "cell_E", "event_offsets")}
-    outs["cells"] = None
+    nnz_ref = ref["stats"]["n_nonzero"]
+    cap = nnz_ref + nnz_ref // 20 + 4096  # room for the other simulation seeds of --extra
+    outs = dict(cell_ids=torch.empty(cap, dtype=torch.int32, device="cuda"),
+                cell_E=torch.empty(cap, dtype=torch.float32, device="cuda"),
+                event_offsets=torch.empty(n_ev + 1, dtype=torch.int64, device="cuda"), cells=None)
+    ref_stats = ref["stats"]
+    del ref
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def timed(K, W, seed=SEED, **kw):
@@ -464,15 +550,18 @@ def main():
                 "kernel_ms": hit_ms, "ops_per_hit": OPS_PER_HIT, "lanes_per_sm_clk": LANES_PER_SM_CLK,
                 "peak_note": "derived: sum over pipes of ops/hit / (lanes x 152 SMs x 2070 MHz)"}
 
+    # the paper's comparison: per-event and per-task launches of the same events
+    ab = None
+    if rank == 0 and not args.no_ab:
+        ab = per_event_and_per_task(sim, d, parts, first_event, H, ms, dict(hits_per_thread=args.hpt,
+                                                                            block=args.block), flush, args.steps)
+
     extra = {}
     if args.extra and rank == 0:
         ts, tst = timed(max(5, args.steps // 2), 2, mode=fcs.MODE_DETERMINISTIC, hits_per_thread=args.hpt,
                         block=args.block)
         extra["deterministic"] = {"hits_per_s": H / (np.mean(ts) * 1e-3), "ms_per_step": float(np.mean(ts)),
                                   "stages_ms": {k: float(np.mean([s[k] for s in tst])) for k in fcs.STAGES}}
-        ts, tst = timed(max(5, args.steps // 2), 2, batched=0, hits_per_thread=args.hpt, block=args.block)
-        extra["per_event_launches"] = {"hits_per_s": H / (np.mean(ts) * 1e-3), "ms_per_step": float(np.mean(ts)),
-                                       "batched_speedup": float(np.mean(ts)) / ms}
         # the adjoint (gradients of the layer fractions and shape weights) over the
         # same events, for a fixed dL/dE_cell (dense float32 rows, 48 MB)
         gcell = torch.randn((n_ev, geo.n_cells), generator=torch.Generator("cuda").manual_seed(3), device="cuda")
@@ -535,7 +624,6 @@ def main():
     if rank == 0 and not args.no_e2e:
         pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(parts, k))).pin_memory().numpy()
                for k in ("type", "E", "eta", "phi", "event_offsets")}
-        cap = outs["cell_ids"].numel()
         ids = torch.empty(cap, dtype=torch.int32).pin_memory().numpy()
         cE = torch.empty(cap, dtype=torch.float32).pin_memory().numpy()
         off = torch.empty(n_ev + 1, dtype=torch.int64).pin_memory().numpy()
@@ -618,6 +706,7 @@ def main():
                  "mufu_sin_per_s": fcs.fcs_microbench(fcs.MB_MUFU, 0, 1024),
                  "lds_words_per_s": fcs.fcs_microbench(fcs.MB_LDS, 0, 1024),
                  "red_f32_random_per_s": fcs.fcs_microbench(fcs.MB_RED, acc_cells, 64),
+                 "red_f64_random_per_s": fcs.fcs_microbench(fcs.MB_RED64, acc_cells, 64),
                  "red_array_floats": acc_cells}
         # lanes per SM per clock the microbenchmarks reach at the sampled clock
         mhz = (clocks or {}).get("sm_mhz") or SM_MAX_MHZ
@@ -635,18 +724,19 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD if n_ev == N_EVENTS else f"pileup{n_ev}",
+                "config": {"workload": f"pileup{n_ev}",
                            "events_per_step": n_ev, "particles_per_step": parts.n,
-                           "hits_per_step": H, "tasks_per_step": ref["stats"]["n_tasks"],
-                           "nonzero_cells_per_step": ref["stats"]["n_nonzero"],
-                           "recheck_hits_per_step": ref["stats"]["n_recheck"],
-                           "poisson_fp64_per_step": ref["stats"]["n_poisson_fp64"], "mode": "atomic",
-                           "hit_kernel_shape": f"{args.block or 256}x{args.hpt or 4}",
+                           "hits_per_step": H, "tasks_per_step": ref_stats["n_tasks"],
+                           "nonzero_cells_per_step": ref_stats["n_nonzero"],
+                           "recheck_hits_per_step": ref_stats["n_recheck"],
+                           "poisson_fp64_per_step": ref_stats["n_poisson_fp64"], "mode": "atomic",
+                           "hit_kernel_shape": f"{args.block or 128}x{args.hpt or 8}",
                            "launch": "batched, CUDA graph", "l2": "flushed between steps (256 MB write)",
                            "parallelism": f"replicas x{world} (events sharded, no collective)"},
                 "events_per_s": n_ev * world / (ms * 1e-3),
                 "autotune": tune,
                 "stages_ms": stage_ms,
+                "batched_vs_per_event": ab,
                 "roofline": roofline, "pipes": pipes, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches_per_step * args.steps, "wall_s": wall}
         line.update(extra)
