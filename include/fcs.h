@@ -166,7 +166,8 @@ int fcs_last_error(char* buf, size_t len);
  * eta_lo within a layer, non-overlapping, n_eta, n_phi >= 1, deta, dphi > 0,
  * cell ids contiguous (layer-major, region, i_eta, i_phi); layer_region_begin:
  * host [n_layers + 1]; layers: host [n_layers].  Limits: n_layers <= 32,
- * n_regions <= 256, cells < 2^31.  FCS_E_ARG if the table breaks a rule.
+ * n_regions <= 256, n_eta <= 2^22 per region, cells < 2^31.  FCS_E_ARG if
+ * the table breaks a rule.
  * Copies everything to the device on stream s and waits for it. */
 int fcs_load_geometry(fcs_geo** out, const fcs_region* regions, int32_t n_regions,
                       const int32_t* layer_region_begin, int32_t n_layers,

@@ -809,6 +809,7 @@ int fcs_load_geometry(fcs_geo** out, const fcs_region* regions, int32_t n_region
   if (lrb[0] != 0 || lrb[n_layers] != n_regions) return set_err(FCS_E_ARG, "layer_region_begin must span [0, n_regions]");
   int64_t cells = 0;
   std::vector<RegionF> rf(n_regions);
+  std::vector<float> split32(n_regions);
   std::vector<double> eta_lo(n_regions), deta(n_regions), phi_lo(n_regions), dphi(n_regions), split(n_regions);
   std::vector<int32_t> ne(n_regions), np(n_regions), co(n_regions);
   for (int l = 0; l < n_layers; ++l) {
@@ -820,6 +821,7 @@ int fcs_load_geometry(fcs_geo** out, const fcs_region* regions, int32_t n_region
       const fcs_region& g = regions[r];
       if (g.layer != l) return set_err(FCS_E_ARG, "region %d: layer %d != %d", r, g.layer, l);
       if (g.n_eta < 1 || g.n_phi < 1) return set_err(FCS_E_ARG, "region %d: empty grid", r);
+      if (g.n_eta > (1 << 22)) return set_err(FCS_E_ARG, "region %d: more than 2^22 eta cells", r);
       if (!(g.deta > 0.0) || !(g.dphi > 0.0) || !std::isfinite(g.deta) || !std::isfinite(g.dphi) ||
           !std::isfinite(g.eta_lo) || !std::isfinite(g.phi_lo))
         return set_err(FCS_E_ARG, "region %d: bad bounds", r);
@@ -842,12 +844,16 @@ int fcs_load_geometry(fcs_geo** out, const fcs_region* regions, int32_t n_region
         split[r] = 0.5 * (top + g.eta_lo);
       }
       RegionF& f = rf[r];
-      f.eta_lo = (float)g.eta_lo;
+      f = RegionF{};
+      f.ek = (float)(-g.eta_lo / g.deta);
       f.inv_deta = (float)(1.0 / g.deta);
-      f.phi_lo = (float)g.phi_lo;
+      f.pk = (float)(-g.phi_lo / g.dphi);
       f.inv_dphi = (float)(1.0 / g.dphi);
-      f.split = (float)split[r];
-      f.n_eta = g.n_eta;
+      split32[r] = (float)split[r];
+      f.n_eta_hf = (float)g.n_eta - 0.5f;
+      // bounds of the FP32 index beyond the position's error (fcs_hits.cuh: fast_cell), rounded up
+      f.ce = (float)(std::fabs((double)f.ek) * 0x1p-23 + 0x1p-22) * 1.0001f;
+      f.cp = (float)(std::fabs((double)f.pk) * 0x1p-23 + 0x1p-22) * 1.0001f;
       f.n_phi = g.n_phi;
       f.cell_off = g.cell_offset;
     }
@@ -861,7 +867,7 @@ int fcs_load_geometry(fcs_geo** out, const fcs_region* regions, int32_t n_region
   if ((rc = current_device(&geo->device)) != FCS_OK) return fail(rc);
   RegionF* d_rf;
   double *d_el, *d_de, *d_pl, *d_dp, *d_sp, *d_rz;
-  float* d_rz32;
+  float *d_rz32, *d_sp32;
   int32_t *d_ne, *d_np, *d_co, *d_lrb, *d_bar;
   if ((rc = dev_alloc(&d_rf, n_regions, &geo->allocs)) || (rc = dev_alloc(&d_el, n_regions, &geo->allocs)) ||
       (rc = dev_alloc(&d_de, n_regions, &geo->allocs)) || (rc = dev_alloc(&d_pl, n_regions, &geo->allocs)) ||
@@ -869,7 +875,7 @@ int fcs_load_geometry(fcs_geo** out, const fcs_region* regions, int32_t n_region
       (rc = dev_alloc(&d_ne, n_regions, &geo->allocs)) || (rc = dev_alloc(&d_np, n_regions, &geo->allocs)) ||
       (rc = dev_alloc(&d_co, n_regions, &geo->allocs)) || (rc = dev_alloc(&d_lrb, n_layers + 1, &geo->allocs)) ||
       (rc = dev_alloc(&d_rz, n_layers, &geo->allocs)) || (rc = dev_alloc(&d_bar, n_layers, &geo->allocs)) ||
-      (rc = dev_alloc(&d_rz32, n_layers, &geo->allocs)))
+      (rc = dev_alloc(&d_rz32, n_layers, &geo->allocs)) || (rc = dev_alloc(&d_sp32, n_regions, &geo->allocs)))
     return fail(rc);
   std::vector<double> rz(n_layers);
   std::vector<float> rz32(n_layers);
@@ -889,7 +895,7 @@ int fcs_load_geometry(fcs_geo** out, const fcs_region* regions, int32_t n_region
                 {d_ne, ne.data(), n_regions * sizeof(int32_t)},   {d_np, np.data(), n_regions * sizeof(int32_t)},
                 {d_co, co.data(), n_regions * sizeof(int32_t)},   {d_lrb, lrb, (n_layers + 1) * sizeof(int32_t)},
                 {d_rz, rz.data(), n_layers * sizeof(double)},     {d_bar, bar.data(), n_layers * sizeof(int32_t)},
-                {d_rz32, rz32.data(), n_layers * sizeof(float)}};
+                {d_rz32, rz32.data(), n_layers * sizeof(float)},  {d_sp32, split32.data(), n_regions * sizeof(float)}};
   for (const auto& c : copies) {
     cudaError_t e = cudaMemcpyAsync(c.d, c.h, c.n, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail(set_err(FCS_E_CUDA, "geometry copy: %s", cudaGetErrorString(e)));
@@ -907,6 +913,7 @@ int fcs_load_geometry(fcs_geo** out, const fcs_region* regions, int32_t n_region
   d.phi_lo = d_pl;
   d.dphi = d_dp;
   d.split = d_sp;
+  d.split32 = d_sp32;
   d.n_eta = d_ne;
   d.n_phi = d_np;
   d.cell_off = d_co;

@@ -54,19 +54,31 @@ struct HitKParams {
 };
 
 // ---- shape bin: inverse CDF by guide table and binary search --------------
-__device__ __forceinline__ int sample_bin(const ParamDev& p, int32_t entry, uint32_t x0) {
-  const uint2 gg = __ldg(p.guide + (size_t)entry * kGuideCells + (x0 >> 25));
-  int lo = gg.y & 0xFF, hi = (gg.y >> 8) & 0xFF;
-  if (lo == hi) return lo;
-  if (x0 < gg.x) return lo;  // the first candidate's threshold comes with the guide cell
-  lo += 1;
-  const uint32_t* T = p.thr + (size_t)entry * kNBins;
+// Binary search for the first k in [lo, hi) with x0 < T[k], else hi.
+static __device__ __noinline__ int bin_search(const uint32_t* T, int lo, int hi, uint32_t x0) {
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
     if (x0 < __ldg(T + mid)) hi = mid;
     else lo = mid + 1;
   }
   return lo;
+}
+
+// The bin of word x0: the packed guide cell of x0's top 7 bits gives lo and
+// the first two thresholds of the cell as offsets (fcs_params.cu); two
+// comparisons decide unless the cell spans three or more bins and x0 lies
+// past the second threshold (a few percent of the words), which finishes with
+// a binary search over the thresholds.
+__device__ __forceinline__ int sample_bin(const ParamDev& p, int32_t entry, uint32_t x0) {
+  const uint2 gg = __ldg(p.guide + ((uint32_t)entry * kGuideCells + (x0 >> 25)));
+  const uint32_t xo = x0 & 0x1FFFFFFu;
+  const uint32_t t0 = gg.x & 0x1FFFFFFu;
+  const uint32_t t1 = __funnelshift_r(gg.x, gg.y, 25) & 0x1FFFFFFu;
+  const int lo = (int)((gg.y >> 18) & 0x7Fu);
+  const int bin = lo + (xo > t0 ? 1 : 0) + (xo > t1 ? 1 : 0);
+  const int span = (int)(gg.y >> 25);
+  if (span > 2 && xo > t1) return bin_search(p.thr + (uint32_t)entry * kNBins, lo + 2, lo + span, x0);
+  return bin;
 }
 
 // ---- FP64 path: the oracle's steps, each rounding once ----------------------
@@ -125,17 +137,21 @@ static __device__ __noinline__ int32_t cell_fp64(const GeoDev& g, const ParamDev
 // ---- shared tables of a CTA ---------------------------------------------------
 struct HitSmemTables {
   RegionF reg[kMaxRegions];
+  float split[kMaxRegions];  // lower ownership boundary of each region (FP32)
   int32_t lrb[kMaxLayers + 1];
-  float4 rb[kNR];  // r bin: lo, width, hi
+  float4 rb[kNR];  // r bin: lo, width, hi, hi 2^-17 (the bin's term of the error bound)
   float2 ab[kNA];  // alpha bin: lo - pi, width
 };
 
 __device__ __forceinline__ void load_tables(HitSmemTables& t, const GeoDev& g, const ParamDev& p) {
-  for (int i = threadIdx.x; i < g.n_regions; i += blockDim.x) t.reg[i] = g.regf[i];
+  for (int i = threadIdx.x; i < g.n_regions; i += blockDim.x) {
+    t.reg[i] = g.regf[i];
+    t.split[i] = g.split32[i];
+  }
   for (int i = threadIdx.x; i <= g.n_layers; i += blockDim.x) t.lrb[i] = g.lrb[i];
   if (threadIdx.x < kNR) {
     const float lo = p.r_edges[threadIdx.x], hi = p.r_edges[threadIdx.x + 1];
-    t.rb[threadIdx.x] = make_float4(lo, hi - lo, hi, 0.0f);
+    t.rb[threadIdx.x] = make_float4(lo, hi - lo, hi, hi * 0x1p-17f);
   }
   if (threadIdx.x < kNA) {
     const double lo = p.a_edges[threadIdx.x], hi = p.a_edges[threadIdx.x + 1];
@@ -152,9 +168,15 @@ __device__ __forceinline__ void load_tables(HitSmemTables& t, const GeoDev& g, c
 //     relative; the two products 2 * 2^-24 relative:
 //   => |deta32 - deta| <= r_hi |s_eta| 2^-19.5; bound used: r_hi |s| 2^-17;
 //   the final add rounds by |eta| 2^-24; bound used: |eta| 2^-21.
+// Scaled index te = fl(eta32 inv + ek) with inv = fl(1/deta), ek =
+// fl(-eta_lo/deta): |te - te*| <= be inv + (|eta| inv) 2^-24 + |ek| 2^-24 +
+// |te| 2^-24 (the reciprocal, the constant and the FMA's rounding), and
+// |eta| inv <= |te| + |ek|; bound used: be inv + |ek| 2^-23 + |te| 2^-21 +
+// 2^-22; |ek| 2^-23 + 2^-22 is the region's constant ce (and likewise cp for
+// phi).
 // A decision is certified when the FP32 value is farther than the bound
-// (plus the FP32 rounding of the boundary and of the scaled index) from the
-// boundary it is compared with.
+// (plus the FP32 rounding of the boundary) from the boundary it is compared
+// with.
 struct FastHit {
   int32_t cell;
   bool sure;
@@ -174,7 +196,7 @@ __device__ __forceinline__ uint32_t task_lay(const HitSmemTables& tb, int layer,
   const float L = eta_c - D, U = eta_c + D;
   int a = rb, b = re;
   for (int q = rb + 1; q < re; ++q) {
-    const float sp = tb.reg[q].split;
+    const float sp = tb.split[q];
     if (fmaf(fabsf(sp), 0x1p-22f, sp) <= L) a = q;
     if (b == re && fmaf(-fabsf(sp), 0x1p-22f, sp) > U) b = q;
   }
@@ -232,28 +254,37 @@ __device__ __forceinline__ FastHit fast_cell(const HitSmemTables& tb, const TT& 
   const float dp = (r * -sn) * T.s_phi;
   const float eta = T.eta_c + de;
   const float phi = T.phi_c + dp;
-  const float rh = rbin.z;
-  const float be = fmaf(rh * fabsf(T.s_eta), 0x1p-17f, fabsf(eta) * 0x1p-21f);
-  const float bp = fmaf(rh * fabsf(T.s_phi), 0x1p-17f, fabsf(phi) * 0x1p-21f);
-  bool sure = (fabsf(eta) < 1.0e30f) && (fabsf(phi) < 1.0e30f);
+  // the bounds r_hi |s| 2^-17 + |x| 2^-21 of the FP32 eta and phi
+  const float be = fmaf(rbin.w, fabsf(T.s_eta), fabsf(eta) * 0x1p-21f);
+  const float bp = fmaf(rbin.w, fabsf(T.s_phi), fabsf(phi) * 0x1p-21f);
+  bool sure = fabsf(eta) < 1.0e30f;  // false for NaN or huge eta (a NaN phi fails its own test below)
+  // region: the last of the task's reachable regions [rb, re) whose split lies
+  // at or below eta.  Most tasks reach one region or two (one split, tested
+  // without a branch); a loop takes the further splits.
   const int rb = (T.lay >> 8) & 0xFFF, re = T.lay >> 20;
-  int rr = rb;
-  for (int q = rb + 1; q < re; ++q) {
-    const float sp = tb.reg[q].split;
-    if (eta >= sp) rr = q;
-    sure &= fabsf(eta - sp) > fmaf(fabsf(sp), 0x1p-23f, be);
+  const bool two = re > rb + 1;
+  const float sp1 = tb.split[min(rb + 1, kMaxRegions - 1)];  // read by every lane, used where two
+  int rr = (two && eta >= sp1) ? rb + 1 : rb;
+  sure &= !two || fabsf(eta - sp1) > fmaf(fabsf(sp1), 0x1p-23f, be);
+  if (re > rb + 2) {
+    for (int q = rb + 2; q < re; ++q) {
+      const float sp = tb.split[q];
+      if (eta >= sp) rr = q;
+      sure &= fabsf(eta - sp) > fmaf(fabsf(sp), 0x1p-23f, be);
+    }
   }
   const RegionF R = tb.reg[rr];
-  const float te = (eta - R.eta_lo) * R.inv_deta;
+  // eta index, clamped to [1/2, n_eta - 1/2]: outside it the cell is the first
+  // or the last whichever side of the region's edge the hit lies, and at the
+  // clamp the distance to the nearest integer is 1/2, so only interior cell
+  // edges are certified
+  const float te = fminf(fmaxf(fmaf(eta, R.inv_deta, R.ek), 0.5f), R.n_eta_hf);
   const float ke = rintf(te);
-  const float ee = fmaf(fmaf(fabsf(R.eta_lo), 0x1p-23f, be), R.inv_deta, fmaf(fabsf(te), 0x1p-21f, 0x1p-22f));
-  if (ke >= 1.0f && ke <= (float)(R.n_eta - 1)) sure &= fabsf(te - ke) > ee;
-  int ie = (int)floorf(te);
-  ie = min(max(ie, 0), R.n_eta - 1);
-  const float tp = (phi - R.phi_lo) * R.inv_dphi;
+  sure &= fabsf(te - ke) > fmaf(te, 0x1p-21f, fmaf(be, R.inv_deta, R.ce));
+  const int ie = (int)te;  // te >= 1/2: truncation is the floor
+  const float tp = fmaf(phi, R.inv_dphi, R.pk);
   const float kp = rintf(tp);
-  const float ep = fmaf(fmaf(fabsf(R.phi_lo), 0x1p-23f, bp), R.inv_dphi, fmaf(fabsf(tp), 0x1p-21f, 0x1p-22f));
-  sure &= fabsf(tp - kp) > ep;
+  sure &= fabsf(tp - kp) > fmaf(fabsf(tp), 0x1p-21f, fmaf(bp, R.inv_dphi, R.cp));
   int ip = (int)floorf(tp);
   if (ip < 0) ip += R.n_phi;
   else if (ip >= R.n_phi) ip -= R.n_phi;
@@ -365,10 +396,41 @@ __device__ __forceinline__ void owner_scan(int16_t* s_owner, int* s_wmax) {
   for (int k = 0; k < HPT; ++k) s_owner[tid * HPT + k] = (int16_t)max(v[k], excl);
 }
 
+// The uncertain hits of a warp step (need set, m = their ballot, non-zero):
+// queued for the FP64 recheck kernel as (task, hit in task); when the queue is
+// full the hit's cell is decided here in FP64, as the recheck kernel would.
+// Called by the whole warp; out of line, as it runs for well under one warp
+// step in a hundred.
+template <int MODE, bool DBG>
+static __device__ __noinline__ void queue_uncertain(const HitKParams& kp, bool need, unsigned m, int64_t task,
+                                                    uint32_t hit, int32_t layer, float eta_c, float phi_c, uint4 x,
+                                                    int bin, int32_t ev, float Ehit, int32_t entry, int64_t slot,
+                                                    int64_t dbg_h) {
+  const WsDev& w = kp.w;
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  const int l0 = __ffs(m) - 1;
+  if (lane == l0) base = atomicAdd((unsigned long long*)&w.sizes->n_recheck, (unsigned long long)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, l0);
+  if (!need) return;
+  const unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
+  if (pos < (unsigned long long)w.recheck_cap) {
+    w.recheck[pos] = make_uint2((uint32_t)task, hit);
+    return;
+  }
+  const int32_t c = cell_fp64(kp.g, kp.p, layer, eta_c, phi_c, x, bin);
+  deposit_single(kp, ev, Ehit, task, c, MODE, entry, bin, slot);
+  atomicAdd((unsigned long long*)&w.sizes->n_inline, 1ull);
+  atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_RECHECK_SPILL);
+  if (DBG && kp.dbg_hit_cell && dbg_h < kp.dbg_hit_cap) kp.dbg_hit_cell[dbg_h] = c;
+}
+
 // Atomic mode asks for 10 CTAs of 128 threads per SM (48 registers): the
 // extra warps hide the guide-table loads; the other modes keep the
-// compiler's choice (a minimum of 0 CTAs is no constraint).
-template <int BLOCK, int HPT, int MODE>
+// compiler's choice (a minimum of 0 CTAs is no constraint).  DBG: the
+// validation dumps of fcs_debug (a separate instantiation, so that the
+// production kernel carries none of their code).
+template <int BLOCK, int HPT, int MODE, bool DBG>
 __global__ void __launch_bounds__(BLOCK, MODE == kModeAtomic ? 1280 / BLOCK : 0) k_hits(const __grid_constant__ HitKParams kp) {
   constexpr bool DET = MODE == kModeDet;
   constexpr int TILE = BLOCK * HPT;
@@ -378,7 +440,7 @@ __global__ void __launch_bounds__(BLOCK, MODE == kModeAtomic ? 1280 / BLOCK : 0)
   __shared__ __align__(16) TileTask s_task[kSmemTasks];
   __shared__ int16_t s_owner[TILE];
   __shared__ int s_wmax[BLOCK / 32];
-  __shared__ unsigned long long s_tile;
+  __shared__ uint32_t s_tile;
   __shared__ float s_gv[MODE == kModeGrad ? BLOCK : 1];
   __shared__ unsigned long long s_recs;  // deterministic mode: records of this CTA
   load_tables(tb, kp.g, kp.p);
@@ -391,21 +453,22 @@ __global__ void __launch_bounds__(BLOCK, MODE == kModeAtomic ? 1280 / BLOCK : 0)
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_HIT_CAPACITY);
     return;
   }
-  const unsigned long long n_tiles = (unsigned long long)((H - hbase + TILE - 1) / TILE);
+  const uint32_t n_tiles = (uint32_t)((H - hbase + TILE - 1) / TILE);  // < 2^32: hits < 2^39
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t hit_dbg_base = kp.dbg_hit_cell || kp.dbg_hit_bin ? w.sizes->hit_base : 0;
+  const unsigned lanes_below = (1u << lane) - 1u;
+  const int64_t hit_dbg_base = DBG ? w.sizes->hit_base : 0;
   // accumulation rows (atomic, deterministic) or dL/dE_cell rows (gradient)
   const uint32_t row_stride = MODE == kModeGrad ? (uint32_t)kp.g.n_cells : (uint32_t)kp.g.acc_stride;
   if (threadIdx.x == 0) {
-    s_tile = kp.static_tiles ? blockIdx.x : atomicAdd(&w.sizes->queue, 1ull);
+    s_tile = kp.static_tiles ? blockIdx.x : (uint32_t)atomicAdd(&w.sizes->queue, 1ull);
     s_recs = 0;
   }
   __syncthreads();
-  unsigned long long tile = s_tile;
+  uint32_t tile = s_tile;
   unsigned long long recs = 0;  // deterministic mode: this warp's records
   while (tile < n_tiles) {
     __syncthreads();  // everyone has read s_tile; s_owner is zero again
-    if (threadIdx.x == 0) s_tile = kp.static_tiles ? n_tiles : atomicAdd(&w.sizes->queue, 1ull);
+    if (threadIdx.x == 0) s_tile = kp.static_tiles ? n_tiles : (uint32_t)atomicAdd(&w.sizes->queue, 1ull);
     const int64_t h0 = hbase + (int64_t)tile * TILE;
     const int hn = (int)min((int64_t)TILE, H - h0);  // hits in this tile
     const int32_t t0 = kp.static_tiles ? kp.t_last : w.gmap[h0 / kGranule];
@@ -464,7 +527,7 @@ __global__ void __launch_bounds__(BLOCK, MODE == kModeAtomic ? 1280 / BLOCK : 0)
             const unsigned peers = kp.key32 ? __match_any_sync(m, ((uint32_t)f.cell << 13) | (uint32_t)tl)
                                             : __match_any_sync(m, ((unsigned long long)(uint32_t)tl << 32) |
                                                                       (uint32_t)f.cell);
-            if (lane == __ffs(peers) - 1)
+            if ((peers & lanes_below) == 0u)  // the group's first lane deposits
               acc_add(w.acc + T.row_off + f.cell, __fmul_rn((float)__popc(peers), T.Ehit));
           }
         } else {
@@ -474,26 +537,11 @@ __global__ void __launch_bounds__(BLOCK, MODE == kModeAtomic ? 1280 / BLOCK : 0)
         }
         // queue the uncertain hits for the FP64 recheck
         const unsigned m = __ballot_sync(0xffffffffu, need);
-        if (m) {
-          unsigned long long base = 0;
-          const int l0 = __ffs(m) - 1;
-          if (lane == l0) base = atomicAdd((unsigned long long*)&w.sizes->n_recheck, (unsigned long long)__popc(m));
-          base = __shfl_sync(0xffffffffu, base, l0);
-          if (need) {
-            const unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
-            if (pos < (unsigned long long)w.recheck_cap) {
-              w.recheck[pos] = make_uint2((uint32_t)(t0 + tl), hit);
-            } else {
-              const int32_t ev = (int32_t)(T.ctr_w - kp.first_event_lo);
-              const int32_t c = cell_fp64(kp.g, kp.p, (int32_t)(T.lay & 0xFF), T.eta_c, T.phi_c, x, bin);
-              deposit_single(kp, ev, T.Ehit, t0 + tl, c, MODE, T.entry, bin, h0 + i);
-              atomicAdd((unsigned long long*)&w.sizes->n_inline, 1ull);
-              atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_RECHECK_SPILL);
-              if (kp.dbg_hit_cell && hit_dbg_base + h0 + i < kp.dbg_hit_cap) kp.dbg_hit_cell[hit_dbg_base + h0 + i] = c;
-            }
-          }
-        }
-        if (kp.dbg_hit_cell || kp.dbg_hit_bin) {
+        if (m)
+          queue_uncertain<MODE, DBG>(kp, need, m, t0 + tl, hit, (int32_t)(T.lay & 0xFF), T.eta_c, T.phi_c, x, bin,
+                                     (int32_t)(T.ctr_w - kp.first_event_lo), T.Ehit, T.entry, h0 + i,
+                                     hit_dbg_base + h0 + i);
+        if constexpr (DBG) {
           const int64_t h = hit_dbg_base + h0 + i;
           if (valid && h < kp.dbg_hit_cap) {
             if (kp.dbg_hit_cell && f.sure) kp.dbg_hit_cell[h] = f.cell;

@@ -27,12 +27,12 @@ static inline HitKParams make_hit_params(const GeoDev& g, const ParamDev& p, WsD
   return kp;
 }
 
-template <int BLOCK, int HPT, int MODE>
-static cudaError_t launch_hits_shape(const HitKParams& kp, const Launch& L) {
+template <int BLOCK, int HPT, int MODE, bool DBG>
+static cudaError_t launch_hits_kernel(const HitKParams& kp, const Launch& L) {
   static int occ = -1;  // resident CTAs per SM of this instantiation
   if (occ < 0) {
     int o = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_hits<BLOCK, HPT, MODE>, BLOCK, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_hits<BLOCK, HPT, MODE, DBG>, BLOCK, 0);
     if (e != cudaSuccess) return e;
     occ = o < 1 ? 1 : o;
   }
@@ -42,8 +42,17 @@ static cudaError_t launch_hits_shape(const HitKParams& kp, const Launch& L) {
     grid = (kp.h_hi - kp.h_lo + TILE - 1) / TILE;
     if (grid <= 0) return cudaSuccess;
   }
-  k_hits<BLOCK, HPT, MODE><<<(unsigned)grid, BLOCK, 0, L.s>>>(kp);
+  k_hits<BLOCK, HPT, MODE, DBG><<<(unsigned)grid, BLOCK, 0, L.s>>>(kp);
   return cudaGetLastError();
+}
+
+// The validation dumps run in their own instantiation (no gradient-mode dumps).
+template <int BLOCK, int HPT, int MODE>
+static cudaError_t launch_hits_shape(const HitKParams& kp, const Launch& L) {
+  if constexpr (MODE != kModeGrad) {
+    if (kp.dbg_hit_cell || kp.dbg_hit_bin) return launch_hits_kernel<BLOCK, HPT, MODE, true>(kp, L);
+  }
+  return launch_hits_kernel<BLOCK, HPT, MODE, false>(kp, L);
 }
 
 template <int MODE>

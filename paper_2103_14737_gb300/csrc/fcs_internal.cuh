@@ -40,13 +40,19 @@ struct __align__(16) TaskRec {
 static_assert(sizeof(TaskRec) == 32, "TaskRec layout");
 constexpr int32_t kMaxEventsPerCall = 1 << 24;  // batch-local events fit the record's 24 bits
 
-// FP32 view of a region for the fast path (shared-memory staged).
-struct RegionF {
-  float eta_lo, inv_deta, phi_lo, inv_dphi;
-  float split;  // lower ownership boundary (FP32 of the FP64 midpoint); -inf for a layer's first
-  int32_t n_eta, n_phi, cell_off;
+// FP32 view of a region for the fast path (shared-memory staged): the scaled
+// indices are te = eta inv_deta + ek and tp = phi inv_dphi + pk, one FMA each,
+// and the constant parts of their error bounds come with the region.
+struct __align__(16) RegionF {
+  float ek, inv_deta;  // -eta_lo / deta (FP32 of the FP64 quotient), 1 / deta
+  float pk, inv_dphi;  // -phi_lo / dphi, 1 / dphi
+  float n_eta_hf;      // n_eta - 1/2: the scaled eta index is clamped to [1/2, n_eta - 1/2]
+  float ce;            // |ek| 2^-23 + 2^-22: eta-index bound beyond the position's and |te| 2^-21
+  float cp;            // |pk| 2^-23 + 2^-22: phi-index bound beyond the position's and |tp| 2^-21
+  int32_t n_phi, cell_off;
+  int32_t pad[3];
 };
-static_assert(sizeof(RegionF) == 32, "RegionF layout");
+static_assert(sizeof(RegionF) == 48, "RegionF layout");
 
 // Device geometry (all pointers device memory owned by fcs_geo).
 struct GeoDev {
@@ -57,6 +63,7 @@ struct GeoDev {
   const double* phi_lo;
   const double* dphi;
   const double* split;   // split[r] for r > layer's first region
+  const float* split32;  // [n_regions] FP32 of split (the lower ownership boundary); -inf for a layer's first
   const int32_t* n_eta;
   const int32_t* n_phi;
   const int32_t* cell_off;
@@ -80,7 +87,8 @@ struct ParamDev {
   const float* shape_w;  // [n_entries][128] shape weights (the gradient's likelihood ratios)
   const float* mhe;      // [n_entries]
   const uint32_t* thr;   // [n_entries][128] inverse-CDF thresholds
-  const uint2* guide;    // [n_entries][128]: (T[lo], lo | hi << 8) per guide cell
+  const uint2* guide;    // [n_entries][128] packed guide cells (fcs_params.cu: thresholds T[lo], T[lo + 1]
+                         // as offsets within the cell, lo, hi - lo)
   const float* r_edges;  // [17]
   const float* a_edges;  // [9]
 };
@@ -191,14 +199,23 @@ __device__ __forceinline__ float u24f(uint32_t x) { return (float)(x >> 8) * (1.
 // rounds once.  (In FP32 a cell that collects thousands of equal group
 // deposits drifts by the same rounding every time, and red.add.f32 flushes
 // subnormal operands and results to zero.)  The widening is integer bit
-// manipulation, off the narrow FP64 pipe; zero, subnormal and non-finite
-// floats take the conversion instruction.
+// manipulation, off the narrow FP64 pipe, for finite floats (deposits are
+// finite): a normal float's exponent is rebiased by 1023 - 127; a subnormal
+// m 2^-149 (and zero) is normalised by the position of m's leading bit.
 __device__ __forceinline__ double f32_to_f64_bits(float v) {
   const uint32_t u = __float_as_uint(v);
-  const uint32_t ex = u & 0x7F800000u;
-  if (ex == 0u || ex == 0x7F800000u) return (double)v;
-  const uint32_t hi = (u & 0x80000000u) | (((u & 0x7FFFFFFFu) >> 3) + (896u << 20));
-  return __hiloint2double((int)hi, (int)(u << 29));
+  const uint32_t a = u & 0x7FFFFFFFu;
+  uint32_t hi, lo;
+  if (a >= 0x00800000u) {
+    hi = (a >> 3) + (896u << 20);
+    lo = u << 29;
+  } else {
+    const int lz = __clz(a);                     // 9 .. 31 for a subnormal, 32 for zero
+    const uint32_t m = (a << (lz - 8)) & 0x7FFFFFu;  // the bits below the leading one
+    hi = a ? ((uint32_t)(905 - lz) << 20) | (m >> 3) : 0u;  // exponent (31 - lz) - 149 + 1023
+    lo = m << 29;
+  }
+  return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)lo);
 }
 __device__ __forceinline__ void acc_add(double* cell, float v) { atomicAdd(cell, f32_to_f64_bits(v)); }
 
