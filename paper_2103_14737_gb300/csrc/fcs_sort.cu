@@ -16,10 +16,11 @@
 //      record array;
 //   2. scatter: every record takes a place in its cell's segment; the
 //      counter, counted down, hands out the places and ends at zero;
-//   3. fold: one thread per cell sorts its segment by (task, count) in place
-//      (insertion, up to 32 records), merges the records of a task (their
-//      counts add exactly) and folds; a warp per longer segment sorts it in
-//      shared memory (bitonic) before its first lane folds.  The float result
+//   3. fold: one thread per cell sorts its segment by (task, count) - a copy
+//      in registers with a sorting network up to 8 records, in place by
+//      insertion up to 32 - merges the records of a task (their counts add
+//      exactly) and folds; a warp per longer segment sorts it in shared
+//      memory (bitonic) before its first lane folds.  The float result
 //      goes to the (FP64) accumulation row, where the compaction of the atomic
 //      mode picks it up, rounds it back to the same float and re-zeroes it.
 // Only the order of places inside a segment depends on scheduling, and the
@@ -114,8 +115,27 @@ struct Fold {
   }
 };
 
-// One thread per cell: segments of up to kInsertionMax records are sorted in
-// place by insertion and folded; longer ones are listed for k_det_fold_big.
+// Ascending sort of 8 keys in registers: Batcher's odd-even merge network
+// (19 compare-exchanges); absent records are all ones and sort last.
+constexpr int kRegSortMax = 8;
+__device__ __forceinline__ void cmpx(uint64_t& x, uint64_t& y) {
+  const uint64_t lo = x < y ? x : y, hi = x < y ? y : x;
+  x = lo;
+  y = hi;
+}
+__device__ __forceinline__ void sort8(uint64_t (&r)[8]) {
+  cmpx(r[0], r[1]); cmpx(r[2], r[3]); cmpx(r[4], r[5]); cmpx(r[6], r[7]);
+  cmpx(r[0], r[2]); cmpx(r[1], r[3]); cmpx(r[4], r[6]); cmpx(r[5], r[7]);
+  cmpx(r[1], r[2]); cmpx(r[5], r[6]);
+  cmpx(r[0], r[4]); cmpx(r[1], r[5]); cmpx(r[2], r[6]); cmpx(r[3], r[7]);
+  cmpx(r[2], r[4]); cmpx(r[3], r[5]);
+  cmpx(r[1], r[2]); cmpx(r[3], r[4]); cmpx(r[5], r[6]);
+}
+
+// One thread per cell: segments of up to 8 records are sorted as a copy in
+// registers (92 % of the hit cells of pile-up events; nothing is written back),
+// up to kInsertionMax in place by insertion, and folded; longer ones are
+// listed for k_det_fold_big.
 __global__ void __launch_bounds__(256) k_det_fold(uint64_t* __restrict__ recs, const int64_t* __restrict__ cell_off,
                                                   int64_t n_cells_all, Sizes* sz, int64_t cap, uint64_t task_mask,
                                                   const float* __restrict__ task_ehit, double* __restrict__ acc,
@@ -129,6 +149,18 @@ __global__ void __launch_bounds__(256) k_det_fold(uint64_t* __restrict__ recs, c
     const int64_t n = b - a;
     if (n > kInsertionMax) {
       big[atomicAdd((unsigned long long*)&sz->n_big, 1ull)] = c;
+      continue;
+    }
+    if (n <= kRegSortMax) {
+      uint64_t r[kRegSortMax];
+#pragma unroll
+      for (int j = 0; j < kRegSortMax; ++j) r[j] = j < n ? recs[a + j] : ~0ull;
+      sort8(r);
+      Fold f;
+#pragma unroll
+      for (int j = 0; j < kRegSortMax; ++j)
+        if (j < n) f.add(r[j], task_mask, task_ehit);
+      acc[c] = f.result(task_ehit);
       continue;
     }
     uint64_t* seg = recs + a;
