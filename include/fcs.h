@@ -354,6 +354,24 @@ enum fcs_microbench_kind {
 };
 int fcs_microbench(int32_t kind, int64_t size, int32_t iters, double* rate, cudaStream_t s);
 
+/* Audit of the Poisson hit counts (Listing 1, get_number_of_hits: n = Poisson(mu),
+ * by inversion for mu < 10 and by PTRS above).  The library draws each count in
+ * FP32 where every comparison is certified by an error bound, and in FP64 (the
+ * definition) where one is not; this call runs both for n draws so that a test
+ * can check the certified FP32 decisions against the FP64 ones on many more
+ * draws than a CPU reference can.  Draw i has mean mu[i] and the Philox
+ * counter fields of a task with layer i & 0xFF, particle i >> 8 and event 0,
+ * under key `seed`.  Outputs (device, n entries each):
+ *   n_fp32[i]: the FP32 count; -1 where an inversion decision was uncertain,
+ *     -2 - i0 where PTRS iteration i0 was (the library then draws in FP64);
+ *   n_fp64[i]: the FP64 definition's count (before max(1, n), clamped to
+ *     2^31 - 1).
+ * mu: device, n positive finite means (callers' responsibility; others give
+ * counts without meaning).  prm must live on the current device.
+ * Synchronous on stream s.  Errors: FCS_E_ARG, FCS_E_CUDA. */
+int fcs_poisson_audit(const fcs_params* prm, const float* mu, int64_t n, uint64_t seed,
+                      int32_t* n_fp32, int32_t* n_fp64, cudaStream_t s);
+
 /* Size of the library's static device scratch used by
  * fcs_simulate_events_static (16 MiB, held on every GPU that loads the
  * library until the process exits). */

@@ -154,11 +154,11 @@ struct fcs_workspace {
   uint4* pinfo = nullptr;
   int64_t pc_cap = 0, po_cap = 0, pi_cap = 0, pcap = 0;
   TaskRec* tasks = nullptr;
-  float* tmu = nullptr;
-  int64_t* tn = nullptr;
+  float* tehit = nullptr;
+  int32_t* tn = nullptr;
   int64_t* th = nullptr;
   int32_t* pdefer = nullptr;
-  int64_t task_cap = 0, tmu_cap = 0, tn_cap = 0, th_cap = 0, tl_cap = 0, pd_cap = 0;
+  int64_t task_cap = 0, tehit_cap = 0, tn_cap = 0, th_cap = 0, tl_cap = 0, pd_cap = 0;
   int32_t* gmap = nullptr;
   int64_t gmap_cap = 0;
   uint2* recheck = nullptr;
@@ -217,7 +217,7 @@ struct fcs_workspace {
     if (s_in) cudaStreamDestroy(s_in);
     if (s_out) cudaStreamDestroy(s_out);
     if (scan_state2) cudaFree(scan_state2);
-    void* ps[] = {d_sizes, pcount, poff, pinfo, tasks, tmu, tn, th, pdefer, gmap, recheck, acc, chunk_counts, chunk_offsets,
+    void* ps[] = {d_sizes, pcount, poff, pinfo, tasks, tehit, tn, th, pdefer, gmap, recheck, acc, chunk_counts, chunk_offsets,
                   scan_state, keys, keys_alt, cell_off, stage, grad_acc, grad_touched};
     for (void* p : ps)
       if (p) cudaFree(p);
@@ -233,7 +233,7 @@ struct fcs_workspace {
     w.pinfo = pinfo;
     w.pcap = pcap;
     w.tasks = tasks;
-    w.tmu = tmu;
+    w.tehit = tehit;
     w.tn = tn;
     w.th = th;
     w.pdefer = pdefer;
@@ -279,7 +279,7 @@ int ws_reserve_static(fcs_workspace* ws, const fcs_geo* geo, int64_t P, int32_t 
     ws->pcap = Pc;
   }
   FCS_TRY(grow(&ws->tasks, &ws->task_cap, Pc * NL));
-  FCS_TRY(grow(&ws->tmu, &ws->tmu_cap, Pc * NL));
+  FCS_TRY(grow(&ws->tehit, &ws->tehit_cap, Pc * NL));
   FCS_TRY(grow(&ws->tn, &ws->tn_cap, Pc * NL));
   FCS_TRY(grow(&ws->th, &ws->th_cap, Pc * NL));
   FCS_TRY(grow(&ws->pdefer, &ws->pd_cap, Pc * NL));
@@ -495,13 +495,13 @@ int enqueue_range_hits(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, int32_t 
     }
     if (nt > 0) {
       FCS_CUDA(cudaMemcpyAsync(ws->h_tasks, ws->th, (size_t)nt * sizeof(int64_t), cudaMemcpyDeviceToHost, a.s));
-      FCS_CUDA(cudaMemcpyAsync(ws->h_tasks + nt, ws->tn, (size_t)nt * sizeof(int64_t), cudaMemcpyDeviceToHost, a.s));
+      FCS_CUDA(cudaMemcpyAsync(ws->h_tasks + nt, ws->tn, (size_t)nt * sizeof(int32_t), cudaMemcpyDeviceToHost, a.s));
       FCS_CUDA(cudaStreamSynchronize(a.s));
     }
     for (int64_t t = 0; t < nt; ++t) {
       const int64_t hb = ws->h_tasks[t];
       FCS_CUDA(launch_hits_task(a.geo->d, a.prm->d, w, ev_lo, k0, k1, a.first_event, hc, key_task_bits, a.dbg, hb,
-                                hb + ws->h_tasks[nt + t], (int32_t)t, L));
+                                hb + reinterpret_cast<const int32_t*>(ws->h_tasks + nt)[t], (int32_t)t, L));
     }
   } else {
     FCS_CUDA(launch_hits(a.geo->d, a.prm->d, w, ev_lo, k0, k1, a.first_event, hc, key_task_bits, a.dbg, L));
@@ -1115,6 +1115,20 @@ int fcs_selftest_wait_timeout(float* ms, cudaStream_t s) {
   return set_err(FCS_E_TIMEOUT, "a bounded device wait gave up after %.0f ms (self-test)", *ms);
 }
 
+int fcs_poisson_audit(const fcs_params* prm, const float* mu, int64_t n, uint64_t seed, int32_t* n_fp32,
+                      int32_t* n_fp64, cudaStream_t s) {
+  if (!prm || n < 0 || (n > 0 && (!mu || !n_fp32 || !n_fp64))) return set_err(FCS_E_ARG, "bad argument");
+  int dev = 0, sms = 0;
+  FCS_TRY(current_device(&dev));
+  if (dev != prm->device) return set_err(FCS_E_ARG, "the parametrisation must live on the current device");
+  FCS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const Launch L{s, sms};
+  FCS_CUDA(launch_poisson_audit(prm->d, mu, n, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), n_fp32, n_fp64,
+                                L));
+  FCS_CUDA(cudaStreamSynchronize(s));
+  return ok();
+}
+
 int fcs_workspace_timings(fcs_workspace* ws, float* ms) {
   if (!ws || !ms) return set_err(FCS_E_ARG, "NULL argument");
   if (ws->timed_ranges <= 0) return set_err(FCS_E_ARG, "no timed call on this workspace");
@@ -1587,8 +1601,8 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   w.pinfo = c.take<uint4>(P);
   w.pcap = P;
   w.tasks = c.take<TaskRec>(P * NL);
-  w.tmu = c.take<float>(P * NL);
-  w.tn = c.take<int64_t>(P * NL);
+  w.tehit = c.take<float>(P * NL);
+  w.tn = c.take<int32_t>(P * NL);
   w.th = c.take<int64_t>(P * NL);
   w.pdefer = c.take<int32_t>(P * NL);
   w.pd_cap = P * NL;
@@ -1603,7 +1617,7 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   w.scan_state = c.take<uint64_t>(w.ss_cap);
   w.recheck = c.take<uint2>(recheck_cap);
   w.recheck_cap = recheck_cap;
-  const bool fits = w.d_sizes && w.pcount && w.poff && w.pinfo && w.tasks && w.tmu && w.tn && w.th && w.pdefer &&
+  const bool fits = w.d_sizes && w.pcount && w.poff && w.pinfo && w.tasks && w.tehit && w.tn && w.th && w.pdefer &&
                     w.acc &&
                     w.chunk_counts &&
                     w.chunk_offsets && w.scan_state && w.recheck && c.cap - c.off >= 4096;
@@ -1618,7 +1632,7 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
     w.poff = nullptr;
     w.pinfo = nullptr;
     w.tasks = nullptr;
-    w.tmu = nullptr;
+    w.tehit = nullptr;
     w.tn = nullptr;
     w.th = nullptr;
     w.pdefer = nullptr;

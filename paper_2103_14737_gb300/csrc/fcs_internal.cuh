@@ -123,9 +123,9 @@ struct WsDev {
   uint4* pinfo;        // [pcap] per particle: entry (without layer), event, layer mask, 0
   int64_t pcap;        // particle capacity
   TaskRec* tasks;      // [task_cap]
-  float* tmu;          // [task_cap] Poisson mean of each task; its hit energy after the task
-                       // finish in deterministic mode (a compact copy for the fold)
-  int64_t* tn;         // [task_cap] hits of each task
+  float* tehit;        // [task_cap] deterministic mode: each task's hit energy, written by the
+                       // task finish (a compact copy for the fold)
+  int32_t* tn;         // [task_cap] hits of each task
   int64_t* th;         // [task_cap] first hit of each task (exclusive scan of tn)
   int32_t* pdefer;     // [pdefer_cap] tasks whose draw is redone in FP64: inversion draws from the
                        // front, PTRS draws from the back (their resume iteration waits in tn)
@@ -264,7 +264,7 @@ cudaError_t launch_scan_u32(const uint32_t* in, int64_t* out, int64_t n, ScanTmp
 // The hit offsets th (exclusive scan of the tasks' hit counts tn, *n_tasks of
 // them; total to *n_hits) and the tile map gmap[g] = the task holding hit
 // g * kGranule, for g < gmap_cap.
-cudaError_t launch_scan_hits(const int64_t* tn, int64_t* th, const int64_t* n_tasks, int64_t* n_hits, int32_t* gmap,
+cudaError_t launch_scan_hits(const int32_t* tn, int64_t* th, const int64_t* n_tasks, int64_t* n_hits, int32_t* gmap,
                              int64_t gmap_cap, ScanTmp tmp, cudaStream_t s);
 
 // fcs_tasks.cu: tasks, Poisson counts and the two scans (task and hit offsets);
@@ -276,6 +276,11 @@ cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_par
                                int energy_interp, const Launch& L);
 cudaError_t launch_task_finish(WsDev w, const fcs_debug* dbg, int det, int fill_map, int64_t n_task_max,
                                const Launch& L);
+
+// Draws i = 0..n-1 with means mu (device) by the FP32 path and by the FP64
+// definition (fcs_poisson_audit).
+cudaError_t launch_poisson_audit(const ParamDev& p, const float* mu, int64_t n, uint32_t k0, uint32_t k1,
+                                 int32_t* n32, int32_t* n64, const Launch& L);
 
 // fcs_hits.cu: what the hit kernel does with a certified hit
 enum HitMode : int {

@@ -265,9 +265,9 @@ cudaError_t scan_wait_selftest(uint32_t* flags_out, float* ms, cudaStream_t s) {
   return e;
 }
 
-cudaError_t launch_scan_hits(const int64_t* tn, int64_t* th, const int64_t* n_tasks, int64_t* n_hits, int32_t* gmap,
+cudaError_t launch_scan_hits(const int32_t* tn, int64_t* th, const int64_t* n_tasks, int64_t* n_hits, int32_t* gmap,
                              int64_t gmap_cap, ScanTmp tmp, cudaStream_t s) {
-  return launch_scan<int64_t, true>(tn, th, n_tasks, 0, n_hits, 0, tmp, s, gmap, gmap_cap);
+  return launch_scan<int32_t, true>(tn, th, n_tasks, 0, n_hits, 0, tmp, s, gmap, gmap_cap);
 }
 
 }  // namespace fcs

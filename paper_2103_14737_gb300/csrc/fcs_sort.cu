@@ -253,10 +253,10 @@ cudaError_t launch_det_reduce(const GeoDev& g, WsDev w, int32_t rows, int key_ta
                                                 n_cells_all, w.keys_alt);
   // the slot array is free after the scatter: it lists the long segments
   int64_t* big = reinterpret_cast<int64_t*>(w.keys);
-  k_det_fold<<<L.num_sms * 8, 256, 0, L.s>>>(w.keys_alt, cell_off, n_cells_all, w.sizes, w.rec_cap, task_mask, w.tmu,
+  k_det_fold<<<L.num_sms * 8, 256, 0, L.s>>>(w.keys_alt, cell_off, n_cells_all, w.sizes, w.rec_cap, task_mask, w.tehit,
                                              w.acc, big);
   k_det_fold_big<<<L.num_sms * 4, 32 * kBigWarps, 0, L.s>>>(w.keys_alt, cell_off, n_cells_all, w.sizes, w.rec_cap,
-                                                            task_mask, w.tmu, w.acc, big);
+                                                            task_mask, w.tehit, w.acc, big);
   return cudaGetLastError();
 }
 

@@ -1,10 +1,11 @@
 // fcs_tasks.cu - task build of the hit loop (Listing 1): per particle the
 // parametrisation entry and its layers with a non-zero float layer energy;
 // per task the Poisson hit count (get_number_of_hits) and the float hit
-// energy; task records in (event, particle, layer) order.  Flat per-task
-// kernels keep the Poisson draws of a warp together.  (The hit-offset scan
-// writes the tile -> task map; the task finish kernel here writes it again
-// when a call grew the map after that scan.)
+// energy; task records in (event, particle, layer) order.  One kernel writes
+// the records and draws their counts, keeping the Poisson draws of a warp
+// together in per-method queues.  (The hit-offset scan writes the tile -> task
+// map; the task finish kernel here writes it again when a call grew the map
+// after that scan.)
 #include <algorithm>
 
 #include <atomic>
@@ -99,18 +100,26 @@ __device__ __noinline__ int64_t poisson_draw(double mu, uint32_t layer, uint32_t
 // bound on |FP32 value - exact value| (the FP64 values of the definition are
 // within a few 2^-53 of exact, covered by the slack).  When the two sides are
 // farther apart than the bound the FP32 decision is the FP64 one; otherwise
-// the iteration (PTRS) or the whole inversion is redone in FP64.  Bounds:
-//   inversion: expf <= 2 ulp, each of the k multiply/reciprocal steps adds
-//     <= 3 roundings (2^-24 each) to p_k, each partial sum one more, so
-//     |F32_k - F_k| <= 2^-22 + (4k + 1) 2^-24 (F <= 1); the 53-bit uniform
-//     rounded to FP32 is off by <= 2^-24 and the difference u - F rounds once
-//     more (<= 2^-25): (4k + 6.5) 2^-24 in all; used: 2^-21 (k + 2).
-//   PTRS constants: sqrtf / logf, the FP32 images of the decimal constants
-//     and __fdividef (<= 2 ulp for divisors in [2^-126, 2^126], as documented;
-//     every divisor here is): a few roundings each, so b, a and 1/alpha are
-//     within 2^-20 relative and v_r within 2^-21 absolute.  The quotients
-//     2a/us and a/us^2 of an iteration are likewise within 2^-21 relative;
-//     the bounds they feed allow 2^-18.
+// the iteration (PTRS) or the whole inversion is redone in FP64.  Rounding to
+// nearest costs at most 2^-24 relative; expf and logf are within 2 and 1 ulp
+// (2^-22 and 2^-23 relative), __fdividef within 2 ulp for divisors in
+// [2^-126, 2^126] (every divisor here is), as documented.  Bounds:
+//   inversion: p_0 = expf(-mu) is within 2^-22 relative; each step's two
+//     products by mu and by the rounded 1/k add 3 2^-24, so p_k is within
+//     (4 + 3k) 2^-24 relative and, with one rounding per partial sum (F <= 1),
+//     |F32_k - F_k| <= (4 + 4k) 2^-24; the 53-bit uniform rounded to FP32 is
+//     off by <= 2^-24, so u - F is known to (4k + 5) 2^-24 = (k + 1.25) 2^-22.
+//     Used: (k + 2) 2^-22.
+//   PTRS constants: sqrtf, the FP32 images of the decimal constants and one
+//     rounding per operation put b within 2^-22 relative, a within 2^-21,
+//     1/alpha within 2^-22 and v_r within 2^-21 absolute.  The quotients
+//     2a/us and a/us^2 of an iteration are within 2^-20 relative.
+//   PTRS acceptance test, d = (log V + log 1/alpha - log(a/us^2 + b))
+//     - (-mu + k log mu - log k!): the left side is known to
+//     1.875 2^-20 + 2^-22 (|l1| + |l2| + |l3|), the right side (log mu within
+//     1 ulp, log k! a correctly rounded table entry, two sums) to
+//     2^-23 (2.5 |k log mu| + |log k!| + mu).  Used: 2^-18 + 2^-20 times the sum
+//     of all six magnitudes (at least twice each term of the two).
 //   uniforms: exact integers rounded once to FP32 (relative 2^-24).
 constexpr float kPtrsFastMaxMu = 4096.0f;  // larger means go to FP64 (counts of ~1e4 lose FP32 headroom)
 
@@ -190,7 +199,9 @@ __device__ __forceinline__ int64_t ptrs_iter32(float mu, const PtrsConst32& c, u
   const int32_t ki = (int32_t)kf;
   const float kl = kf * c.loglam, lg = (ki < c.n_lfact) ? __ldg(c.lfact + ki) : lgammaf(kf + 1.0f);
   const float d = (l1 + l2 - l3) - ((-mu + kl) - lg);
-  const float bd = (fabsf(l1) + fabsf(l2) + fabsf(l3) + fabsf(kl) + fabsf(lg) + mu + 1.0f) * 0x1p-18f;
+  // (k below the table for every mu <= kPtrsFastMaxMu; lgammaf's larger
+  // error past it is covered by the 2^-18 term only for small k)
+  const float bd = fmaf(fabsf(l1) + fabsf(l2) + fabsf(l3) + fabsf(kl) + fabsf(lg) + mu, 0x1p-20f, 0x1p-18f);
   if (d < -bd) return (int64_t)ki;
   if (d > bd) return -1;
   return -2;
@@ -209,12 +220,12 @@ __device__ __forceinline__ int32_t poisson_inv_fp32(float mu32, uint32_t layer, 
   const float uf = u53f(x.x, x.y);
   float p = expf(-mu32);
   float F = p;
-  float e = 0x1p-20f;  // (k + 2) 2^-21, exact in FP32 for k <= kInvMax
+  float e = 0x1p-21f;  // (k + 2) 2^-22, exact in FP32 for k <= kInvMax
   float d = uf - F;
   int k = 0;
   while (d > e && k < kInvMax) {  // u > F_k for certain: the search goes on
     k += 1;
-    e += 0x1p-21f;
+    e += 0x1p-22f;
     p = (p * mu32) * rcp[k];
     F = F + p;
     d = uf - F;
@@ -235,6 +246,30 @@ __device__ __forceinline__ int32_t ptrs_step_fp32(float mu32, uint32_t layer, ui
   const PtrsConst32 c = ptrs_const32(mu32, lfact, n_lfact);
   const uint4 x = philox4x32_10_rk(make_uint4(i, layer | (kPurposePoisson << 16), particle, event), rk);
   return (int32_t)ptrs_iter32(mu32, c, x);
+}
+
+// A deferred PTRS draw from its uncertain iteration i0 on: iteration i0 in
+// FP64 (the definition), each later one in FP32 where its decisions are
+// certain (they are then the FP64 ones) and in FP64 where they are not.  A
+// warp's time is its longest chain of FP64 iterations, and most draws that
+// reject at i0 are decided in FP32 after it.
+__device__ __noinline__ int64_t ptrs_resume(float mu32, uint32_t layer, uint32_t particle, uint32_t event,
+                                            uint32_t k0, uint32_t k1, const PhiloxRoundKeys& rk,
+                                            const float* lfact, const double* lfact64, int32_t n_lfact, uint32_t i0) {
+  const double mu = (double)mu32;
+  const PtrsConst64 c = ptrs_const64(mu);
+  for (uint32_t i = i0; i < kPtrsMaxIter; ++i) {
+    if (i != i0) {
+      const int32_t k32 = ptrs_step_fp32(mu32, layer, particle, event, rk, lfact, n_lfact, i);
+      if (k32 >= 0) return k32;
+      if (k32 == -1) continue;
+    }
+    double u, V;
+    draw_pair(i, layer, particle, event, k0, k1, &u, &V);
+    const int64_t k = ptrs_iter64(mu, c, u, V, lfact64, n_lfact);
+    if (k >= 0) return k;
+  }
+  return (int64_t)floor(mu);
 }
 
 // Parametrisation entry of a particle (without the layer index).  Energy bin
@@ -354,19 +389,135 @@ __global__ void __launch_bounds__(128) k_particle_count(const ParamDev p, const 
   }
 }
 
-// Task records in (event, particle, layer) order and their Poisson means.
-// A warp takes 32 consecutive particles, whose tasks are consecutive too
-// (poff), and fills them 32 at a time: lane s of a round builds the task in
+// Task records in (event, particle, layer) order and their FP32 Poisson hit
+// counts, n = max(1, Poisson(mu)), in one pass: a task's draw runs while its
+// record is still at hand, so the records are written once and not read back.
+//
+// Building: a warp takes 32 consecutive particles, whose tasks are consecutive
+// too (poff), and fills them 32 at a time: lane s of a round builds the task in
 // slot s of the warp's range, so each round writes 32 consecutive 32-byte
 // records.  The owner of a slot is found by a binary search over the lanes'
 // inclusive task counts (shuffles); its data comes by shuffle from the lane
 // that loaded the particle.
-__global__ void __launch_bounds__(128) k_task_init(const GeoDev g, const ParamDev p, const fcs_particles parts,
-                                                   int32_t ev_lo, WsDev w) {
+//
+// Drawing: each new task joins one of two per-warp queues in shared memory,
+// inversion (mu < 10) or PTRS, with its Philox counter fields.  Whenever a
+// queue holds 32 draws the warp runs one round of that method on 32 of them,
+// so a round runs one method in full lanes and warps never wait for one
+// another.  A PTRS round runs one iteration per lane (most draws accept at
+// their first); a draw that rejects goes back into the queue with its next
+// iteration, so one long draw does not hold 31 idle lanes.  Draws the FP32 path
+// cannot certify (a few in 1e4) are listed for k_task_poisson64, which runs
+// them in full warps: an FP64 instruction holds the narrow FP64 pipe as long
+// for one lane as for 32.  A warp drains its queues after its last particles.
+constexpr int kBuildWarps = 4;
+constexpr int kDrawQ = 64;  // < 32 left after the rounds + 32 new (or 32 retried)
+
+struct DrawEnt {
+  float mu;
+  int32_t t;          // task
+  uint32_t particle;  // particle in its event
+  uint32_t evl;       // event in the range << 8 | layer
+};
+
+// Per-warp queues in shared memory: entries [0, n) of each, n warp-uniform.
+struct WarpQueue {
+  DrawEnt* e;
+  uint8_t* it;  // PTRS queue: the entry's next iteration
+  int n;
+};
+
+// Appends the draws of the lanes with `push` set to a queue (n + 32 <= kDrawQ).
+__device__ __forceinline__ void queue_push(WarpQueue& q, bool push, const DrawEnt& d, uint8_t it) {
+  const int lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(0xffffffffu, push);
+  if (push) {
+    const int j = q.n + __popc(m & ((1u << lane) - 1u));
+    q.e[j] = d;
+    q.it[j] = it;
+  }
+  q.n += __popc(m);
+  __syncwarp();
+}
+
+// Takes the last min(n, 32) entries of a queue, one per lane; false for the
+// lanes past them.
+__device__ __forceinline__ bool queue_take(WarpQueue& q, DrawEnt* d, uint32_t* it) {
+  const int lane = threadIdx.x & 31;
+  const int cnt = min(q.n, 32);
+  const bool valid = lane < cnt;
+  if (valid) {
+    *d = q.e[q.n - cnt + lane];
+    *it = q.it[q.n - cnt + lane];
+  }
+  q.n -= cnt;
+  __syncwarp();  // read before the queue grows again
+  return valid;
+}
+
+// Appends the tasks of the lanes with `push` set to a global list:
+// warp-aggregated counter increment, entry q at list[q] (front) or
+// list[cap - 1 - q] (back).  Deferred draws are listed by method (inversion at
+// the front of pdefer, PTRS at its back) so that the FP64 warps run one method.
+__device__ __forceinline__ void warp_push(bool push, int32_t task, unsigned long long* counter, int32_t* list,
+                                          bool back, int64_t cap) {
+  const int lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(0xffffffffu, push);
+  if (!m) return;
+  unsigned long long b = 0;
+  const int l0 = __ffs(m) - 1;
+  if (lane == l0) b = atomicAdd(counter, (unsigned long long)__popc(m));
+  b = __shfl_sync(0xffffffffu, b, l0);
+  const int64_t q = (int64_t)b + __popc(m & ((1u << lane) - 1u));
+  if (push) list[back ? cap - 1 - q : q] = task;
+}
+
+// One inversion round; uncertain draws are listed for k_task_poisson64.
+__device__ __forceinline__ void inversion_round(WarpQueue& q, const WsDev& w, const PhiloxRoundKeys& rk,
+                                                uint32_t first_event_lo, const float* rcp) {
+  DrawEnt d{};
+  uint32_t it = 0;
+  const bool valid = queue_take(q, &d, &it);
+  int32_t k = 0;
+  if (valid) {
+    k = poisson_inv_fp32(d.mu, d.evl & 0xFFu, d.particle, first_event_lo + (d.evl >> 8), rk, rcp);
+    if (k >= 0) w.tn[d.t] = k < 1 ? 1 : k;
+  }
+  warp_push(valid && k < 0, d.t, (unsigned long long*)&w.sizes->n_pdefer, w.pdefer, false, w.pdefer_cap);
+}
+
+// One PTRS round: iteration it of each of up to 32 draws; the draws that
+// reject for certain go back into the queue with it + 1, the uncertain ones
+// are listed for k_task_poisson64 (tn holds the iteration to resume at).
+__device__ __forceinline__ void ptrs_round(WarpQueue& q, const WsDev& w, const PhiloxRoundKeys& rk,
+                                           uint32_t first_event_lo, const float* lfact, int32_t n_lfact) {
+  DrawEnt d{};
+  uint32_t it = 0;
+  const bool valid = queue_take(q, &d, &it);
+  int32_t k = 0;
+  if (valid) {
+    k = ptrs_step_fp32(d.mu, d.evl & 0xFFu, d.particle, first_event_lo + (d.evl >> 8), rk, lfact, n_lfact, it);
+    if (k == -1 && it + 1 >= kPtrsMaxIter) k = (int32_t)floorf(d.mu);  // every iteration rejected
+    if (k >= 0) w.tn[d.t] = k < 1 ? 1 : k;
+    else if (k == -2) w.tn[d.t] = (int32_t)it;
+  }
+  queue_push(q, valid && k == -1, d, (uint8_t)(it + 1));
+  warp_push(valid && k == -2, d.t, (unsigned long long*)&w.sizes->n_pdefer_ptrs, w.pdefer, true, w.pdefer_cap);
+}
+
+__global__ void __launch_bounds__(32 * kBuildWarps) k_task_build(const GeoDev g, const ParamDev p,
+                                                                 const fcs_particles parts, int32_t ev_lo, WsDev w,
+                                                                 PhiloxRoundKeys rk, uint32_t first_event_lo) {
+  __shared__ DrawEnt s_e[2][kBuildWarps][kDrawQ];  // inversion and PTRS queues
+  __shared__ uint8_t s_it[2][kBuildWarps][kDrawQ];
+  __shared__ float s_rcp[kInvMax + 1];  // 1 / k, correctly rounded
+  for (int k = threadIdx.x; k <= kInvMax; k += blockDim.x) s_rcp[k] = __frcp_rn((float)k);
+  __syncthreads();
   const int64_t pb = parts.event_offsets[ev_lo];
   const int64_t P = w.sizes->n_part;
   const int NL = p.NL;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  WarpQueue qi{s_e[0][wi], s_it[0][wi], 0}, qp{s_e[1][wi], s_it[1][wi], 0};
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t wb = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; wb < P; wb += warps * 32) {
     const int64_t li = wb + lane;
@@ -417,202 +568,51 @@ __global__ void __launch_bounds__(128) k_task_init(const GeoDev g, const ParamDe
       const float oth = __shfl_sync(0xffffffffu, th, o);
       const int32_t opin = __shfl_sync(0xffffffffu, pin, o);
       const int64_t to = tbase + sl;
-      if (sl >= total || to >= w.task_cap) continue;  // the capacity is particles x layers: never
-      const int l = (int)__fns(mask, 0u, j + 1);
-      const int64_t e = (int64_t)entry * NL + l;
-      const float El = __fmul_rn(oE, __ldg(p.frac + e));
-      TaskRec r;
-      r.entry = (int32_t)e;
-      r.El = El;
-      r.eta_c = oeta;
-      r.phi_c = ophi;
-      const float R = g.rz32[l];
-      if (g.barrel[l]) {
-        r.s_phi = 1.0f / R;
-        r.s_eta = 1.0f / (R * och);
-      } else {
-        const float mm = (oth * osh) / R;
-        r.s_phi = osh / R;
-        r.s_eta = (oeta < 0.0f) ? mm : -mm;
-      }
-      r.particle = opin;
-      r.ev_layer = (ev << 8) | (uint32_t)l;
-      w.tasks[to] = r;
-      w.tmu[to] = __fdiv_rn(El, __ldg(p.mhe + e));
-    }
-  }
-}
-
-// n = max(1, Poisson(mu)) in FP32.  Each warp takes windows of 256
-// consecutive tasks, lists the window's inversion tasks (mu < 10) from the
-// front and its PTRS tasks from the back of a per-warp shared array, and
-// draws them 32 at a time, inversion rounds first: a round runs one method,
-// and warps never wait for one another.  A PTRS round runs one iteration per
-// lane (most draws accept at their first); a draw that rejects goes to the
-// warp's retry list with its next iteration, and the list runs as a round
-// whenever it holds 32, so that one long draw does not hold 31 idle lanes.
-// Draws the FP32 path cannot certify are queued for k_task_poisson64, so that
-// FP64 work runs in full warps instead of stalling a warp for one lane.
-constexpr int kPoisWarps = 4;
-constexpr int kPoisWin = 256;
-
-// Appends the tasks of the lanes with `push` set to a list: warp-aggregated
-// counter increment, entry q at list[q] (front) or list[cap - 1 - q] (back).
-// Deferred draws are listed by method (inversion at the front of pdefer, PTRS
-// at its back) so that the FP64 warps run one method.
-__device__ __forceinline__ void warp_push(bool push, int64_t task, unsigned long long* counter, int32_t* list,
-                                          bool back, int64_t cap) {
-  const int lane = threadIdx.x & 31;
-  const unsigned m = __ballot_sync(0xffffffffu, push);
-  if (!m) return;
-  unsigned long long b = 0;
-  const int l0 = __ffs(m) - 1;
-  if (lane == l0) b = atomicAdd(counter, (unsigned long long)__popc(m));
-  b = __shfl_sync(0xffffffffu, b, l0);
-  const int64_t q = (int64_t)b + __popc(m & ((1u << lane) - 1u));
-  if (push) list[back ? cap - 1 - q : q] = (int32_t)task;
-}
-
-__global__ void __launch_bounds__(32 * kPoisWarps) k_task_poisson(WsDev w, PhiloxRoundKeys rk, uint32_t first_event_lo,
-                                                                   const float* lfact, int32_t n_lfact) {
-  __shared__ int s_list[kPoisWarps][kPoisWin];  // inversion tasks from the front, PTRS from the back
-  __shared__ float s_mu[kPoisWarps][kPoisWin];
-  __shared__ float s_rcp[kInvMax + 1];          // 1 / k, correctly rounded
-  __shared__ int32_t s_rt[kPoisWarps][64];      // retry list: task
-  __shared__ uint8_t s_ri[kPoisWarps][64];      //             and its next PTRS iteration
-  for (int k = threadIdx.x; k <= kInvMax; k += blockDim.x) s_rcp[k] = __frcp_rn((float)k);
-  __syncthreads();
-  const int64_t T = min(w.sizes->n_tasks, w.task_cap);
-  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
-  const int64_t nw = (int64_t)gridDim.x * kPoisWarps;
-  unsigned long long* n_inv_defer = (unsigned long long*)&w.sizes->n_pdefer;
-  unsigned long long* n_ptrs_defer = (unsigned long long*)&w.sizes->n_pdefer_ptrs;
-  int n_r = 0;  // retry list length (warp-uniform, < 64)
-  // the loop runs one window past the warp's last to drain the retry list
-  for (int64_t win = ((int64_t)blockIdx.x * kPoisWarps + wi) * kPoisWin;; win += nw * kPoisWin) {
-    const bool have = win < T;
-    int n_i = 0, n_p = 0;
-    if (have) {
-#pragma unroll
-      for (int c = 0; c < kPoisWin / 32; ++c) {
-        const int idx = c * 32 + lane;
-        const int64_t t = win + idx;
-        const float mu = t < T ? w.tmu[t] : 0.0f;
-        const bool inv = t < T && mu < 10.0f, pt = t < T && !(mu < 10.0f);
-        const unsigned bi = __ballot_sync(0xffffffffu, inv), bp = __ballot_sync(0xffffffffu, pt);
-        s_mu[wi][idx] = mu;
-        if (inv) s_list[wi][n_i + __popc(bi & lt)] = idx;
-        if (pt) s_list[wi][kPoisWin - 1 - (n_p + __popc(bp & lt))] = idx;
-        n_i += __popc(bi);
-        n_p += __popc(bp);
-      }
-      __syncwarp();
-      for (int r0 = 0; r0 < n_i; r0 += 32) {
-        const int j = r0 + lane;
-        const bool valid = j < n_i;
-        int32_t k = 0;
-        int64_t t = 0;
-        if (valid) {
-          const int idx = s_list[wi][j];
-          t = win + idx;
-          const TaskRec& r = w.tasks[t];
-          k = poisson_inv_fp32(s_mu[wi][idx], (uint32_t)r.layer(), (uint32_t)r.particle,
-                               first_event_lo + (uint32_t)r.event(), rk, s_rcp);
-          w.tn[t] = k < 1 ? 1 : k;  // provisional for a deferred draw
-        }
-        warp_push(valid && k < 0, t, n_inv_defer, w.pdefer, false, w.pdefer_cap);
-      }
-    }
-    // PTRS rounds: new draws of the window 32 at a time, or 32 retries when
-    // the list holds that many (after the warp's last window: all it holds)
-    int p_next = 0;
-    while (p_next < n_p || n_r >= (have ? 32 : 1)) {
-      const bool from_retry = n_r >= 32 || p_next >= n_p;
-      const int cnt = from_retry ? min(n_r, 32) : min(n_p - p_next, 32);
-      const bool valid = lane < cnt;
-      int64_t t = 0;
-      uint32_t it = 0;
+      // the capacity is particles x layers: `to` never reaches it
+      const bool valid = sl < total && to < w.task_cap;
       float mu = 0.0f;
+      uint32_t evl = 0;
       if (valid) {
-        if (from_retry) {
-          t = s_rt[wi][lane];
-          it = s_ri[wi][lane];
-          mu = w.tmu[t];
+        const int l = (int)__fns(mask, 0u, j + 1);
+        const int64_t e = (int64_t)entry * NL + l;
+        const float El = __fmul_rn(oE, __ldg(p.frac + e));
+        TaskRec r;
+        r.entry = (int32_t)e;
+        r.El = El;
+        r.eta_c = oeta;
+        r.phi_c = ophi;
+        const float R = g.rz32[l];
+        if (g.barrel[l]) {
+          r.s_phi = 1.0f / R;
+          r.s_eta = 1.0f / (R * och);
         } else {
-          const int idx = s_list[wi][kPoisWin - 1 - (p_next + lane)];
-          t = win + idx;
-          mu = s_mu[wi][idx];
+          const float mm = (oth * osh) / R;
+          r.s_phi = osh / R;
+          r.s_eta = (oeta < 0.0f) ? mm : -mm;
         }
+        r.particle = opin;
+        evl = (ev << 8) | (uint32_t)l;
+        r.ev_layer = evl;
+        w.tasks[to] = r;
+        mu = __fdiv_rn(El, __ldg(p.mhe + e));
       }
-      if (from_retry) {  // the entries past the round move to the front
-        const int rest = n_r - cnt;
-        const int32_t mt = lane < rest ? s_rt[wi][cnt + lane] : 0;
-        const uint8_t mi = lane < rest ? s_ri[wi][cnt + lane] : 0;
-        __syncwarp();
-        if (lane < rest) {
-          s_rt[wi][lane] = mt;
-          s_ri[wi][lane] = mi;
-        }
-        __syncwarp();
-        n_r = rest;
-      } else {
-        p_next += cnt;
-      }
-      int32_t k = 0;
-      if (valid) {
-        const TaskRec& r = w.tasks[t];
-        k = ptrs_step_fp32(mu, (uint32_t)r.layer(), (uint32_t)r.particle, first_event_lo + (uint32_t)r.event(), rk,
-                           lfact, n_lfact, it);
-        if (k == -1 && it + 1 >= kPtrsMaxIter) k = (int32_t)floorf(mu);  // every iteration rejected
-        if (k >= 0) w.tn[t] = k < 1 ? 1 : k;
-        else if (k == -2) w.tn[t] = it;  // the FP64 definition resumes here
-      }
-      warp_push(valid && k == -2, t, n_ptrs_defer, w.pdefer, true, w.pdefer_cap);
-      const bool rt = valid && k == -1;
-      const unsigned rm = __ballot_sync(0xffffffffu, rt);
-      if (rt) {
-        const int q = n_r + __popc(rm & lt);
-        s_rt[wi][q] = (int32_t)t;
-        s_ri[wi][q] = (uint8_t)(it + 1);
-      }
-      n_r += __popc(rm);
-      __syncwarp();
+      const DrawEnt d{mu, (int32_t)to, (uint32_t)opin, evl};
+      queue_push(qi, valid && mu < 10.0f, d, 0);
+      queue_push(qp, valid && !(mu < 10.0f), d, 0);
+      if (qi.n >= 32) inversion_round(qi, w, rk, first_event_lo, s_rcp);
+      while (qp.n >= 32) ptrs_round(qp, w, rk, first_event_lo, p.lfact, p.n_lfact);
     }
-    if (!have) break;
-    __syncwarp();  // the window's lists are reused
   }
-}
-
-// A deferred PTRS draw from its uncertain iteration i0 on: iteration i0 in
-// FP64 (the definition), each later one in FP32 where its decisions are
-// certain (they are then the FP64 ones) and in FP64 where they are not.  A
-// warp's time is its longest chain of FP64 iterations, and most draws that
-// reject at i0 are decided in FP32 after it.
-__device__ __noinline__ int64_t ptrs_resume(float mu32, uint32_t layer, uint32_t particle, uint32_t event,
-                                            uint32_t k0, uint32_t k1, const PhiloxRoundKeys& rk,
-                                            const float* lfact, const double* lfact64, int32_t n_lfact, uint32_t i0) {
-  const double mu = (double)mu32;
-  const PtrsConst64 c = ptrs_const64(mu);
-  for (uint32_t i = i0; i < kPtrsMaxIter; ++i) {
-    if (i != i0) {
-      const int32_t k32 = ptrs_step_fp32(mu32, layer, particle, event, rk, lfact, n_lfact, i);
-      if (k32 >= 0) return k32;
-      if (k32 == -1) continue;
-    }
-    double u, V;
-    draw_pair(i, layer, particle, event, k0, k1, &u, &V);
-    const int64_t k = ptrs_iter64(mu, c, u, V, lfact64, n_lfact);
-    if (k >= 0) return k;
-  }
-  return (int64_t)floor(mu);
+  while (qi.n > 0) inversion_round(qi, w, rk, first_event_lo, s_rcp);
+  while (qp.n > 0) ptrs_round(qp, w, rk, first_event_lo, p.lfact, p.n_lfact);
 }
 
 // The deferred draws: the inversion list (front of pdefer) by the FP64
 // definition, then the PTRS list (back of pdefer) resumed at the iteration
 // the FP32 path could not decide; 32 per warp, so that a warp runs one method
-// except at the seam.
-__global__ void __launch_bounds__(128) k_task_poisson64(WsDev w, uint32_t k0, uint32_t k1, PhiloxRoundKeys rk,
+// except at the seam.  A task's mean is recomputed from its record as the
+// build kernel computed it.
+__global__ void __launch_bounds__(128) k_task_poisson64(WsDev w, const float* mhe, PhiloxRoundKeys rk,
                                                          uint32_t first_event_lo, const float* lfact,
                                                          const double* lfact64, int32_t n_lfact) {
   const int64_t n_inv = w.sizes->n_pdefer, n_ptrs = w.sizes->n_pdefer_ptrs;
@@ -624,16 +624,54 @@ __global__ void __launch_bounds__(128) k_task_poisson64(WsDev w, uint32_t k0, ui
     const TaskRec& r = w.tasks[t];
     const uint32_t layer = (uint32_t)r.layer(), particle = (uint32_t)r.particle;
     const uint32_t event = first_event_lo + (uint32_t)r.event();
-    int64_t k = inv ? poisson_draw((double)w.tmu[t], layer, particle, event, k0, k1, lfact64, n_lfact, 0u)
-                    : ptrs_resume(w.tmu[t], layer, particle, event, k0, k1, rk, lfact, lfact64, n_lfact,
+    const float mu = __fdiv_rn(r.El, __ldg(mhe + r.entry));
+    int64_t k = inv ? poisson_draw((double)mu, layer, particle, event, rk.k[0], rk.k[1], lfact64, n_lfact, 0u)
+                    : ptrs_resume(mu, layer, particle, event, rk.k[0], rk.k[1], rk, lfact, lfact64, n_lfact,
                                   (uint32_t)w.tn[t]);
     if (k < 1) k = 1;
     if (k > 0x7FFFFFFF) k = 0x7FFFFFFF;
-    w.tn[t] = k;
+    w.tn[t] = (int32_t)k;
   }
 }
 
-// One thread per task: in deterministic mode the hit energy into tmu (the
+// Audit of the FP32 path against the FP64 definition: draw i with mean mu[i]
+// (Philox counter fields layer i & 0xFF, particle i >> 8, event 0) by the FP32
+// path alone, which stops at its first uncertain decision, and by the FP64
+// definition.  n32[i]: the FP32 count, -1 where an inversion was uncertain,
+// -2 - i0 where PTRS iteration i0 was; n64[i]: the definition's count (both
+// before max(1, .)).
+__global__ void __launch_bounds__(128) k_poisson_audit(const float* mu, int64_t n, uint32_t k0, uint32_t k1,
+                                                        PhiloxRoundKeys rk, const float* lfact,
+                                                        const double* lfact64, int32_t n_lfact, int32_t* n32,
+                                                        int32_t* n64) {
+  __shared__ float s_rcp[kInvMax + 1];
+  for (int k = threadIdx.x; k <= kInvMax; k += blockDim.x) s_rcp[k] = __frcp_rn((float)k);
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float m = mu[i];
+    const uint32_t layer = (uint32_t)(i & 0xFF), particle = (uint32_t)(i >> 8);
+    int32_t r = -1;
+    if (m < 10.0f) {
+      r = poisson_inv_fp32(m, layer, particle, 0u, rk, s_rcp);
+    } else {
+      for (uint32_t it = 0; it < kPtrsMaxIter; ++it) {
+        const int32_t k = ptrs_step_fp32(m, layer, particle, 0u, rk, lfact, n_lfact, it);
+        if (k == -1) {
+          if (it + 1 >= kPtrsMaxIter) r = (int32_t)floorf(m);
+          continue;
+        }
+        r = k >= 0 ? k : -2 - (int32_t)it;
+        break;
+      }
+    }
+    int64_t k64 = poisson_draw((double)m, layer, particle, 0u, k0, k1, lfact64, n_lfact, 0u);
+    if (k64 > 0x7FFFFFFF) k64 = 0x7FFFFFFF;
+    n32[i] = r;
+    n64[i] = (int32_t)k64;
+  }
+}
+
+// One thread per task: in deterministic mode the hit energy into tehit (the
 // fold's compact copy); validation dumps; the tile map (granule -> task
 // holding its first hit) again when the call grew it after the scan that
 // wrote it (fill_map).
@@ -651,7 +689,7 @@ __global__ void k_task_finish(WsDev w, fcs_debug dbg, int has_dbg, int det, int 
     if (det || has_dbg) {
       const TaskRec& r = w.tasks[t];
       const float Ehit = __fdiv_rn(r.El, (float)n);
-      if (det) w.tmu[t] = Ehit;
+      if (det) w.tehit[t] = Ehit;
       if (has_dbg) {
         const int64_t dt = task_base + t;
         if (dt < dbg.task_capacity) {
@@ -684,12 +722,7 @@ int resident_blocks(const void* kernel, int block) {
   return std::max(n, 1);
 }
 
-// The same, cached per device for the two task kernels (the stores are
-// ordered so that a non-zero `init` implies `pois` is set).
 constexpr int kMaxDevices = 64;
-struct TaskOccupancy {
-  std::atomic<int> init{0}, pois{0};
-};
 
 }  // namespace
 
@@ -702,30 +735,23 @@ cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_par
   k_particle_count<<<gp, 128, 0, L.s>>>(p, parts, ev_lo, ev_hi, w, energy_interp, k0, k1, (uint32_t)first_event);
   cudaError_t e = launch_scan_i64(w.pcount, w.poff, &w.sizes->n_part, 0, &w.sizes->n_tasks, 0, tmp, L.s);
   if (e != cudaSuccess) return e;
-  // the task kernels loop grid-stride: one wave of resident blocks
-  static TaskOccupancy occ_by_device[kMaxDevices];
+  // the build kernel loops grid-stride: one wave of resident blocks
+  static std::atomic<int> occ_by_device[kMaxDevices];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = kMaxDevices - 1;
-  TaskOccupancy& occ = occ_by_device[dev];
-  int occ_init = occ.init.load(std::memory_order_acquire), occ_pois;
-  if (occ_init) {
-    occ_pois = occ.pois.load(std::memory_order_relaxed);
-  } else {
-    occ_pois = resident_blocks((const void*)k_task_poisson, 32 * kPoisWarps);
-    occ_init = resident_blocks((const void*)k_task_init, 128);
-    occ.pois.store(occ_pois, std::memory_order_relaxed);
-    occ.init.store(occ_init, std::memory_order_release);
+  int occ = occ_by_device[dev].load(std::memory_order_relaxed);
+  if (!occ) {
+    occ = resident_blocks((const void*)k_task_build, 32 * kBuildWarps);
+    occ_by_device[dev].store(occ, std::memory_order_relaxed);
   }
-  k_task_init<<<std::min(gp, L.num_sms * occ_init), 128, 0, L.s>>>(g, p, parts, ev_lo, w);
-  const int gpois = (int)std::min<int64_t>(
-      (std::max<int64_t>(n_part_max * p.NL, 1) + kPoisWarps * kPoisWin - 1) / (kPoisWarps * kPoisWin),
-      (int64_t)L.num_sms * occ_pois);
-  k_task_poisson<<<gpois, 32 * kPoisWarps, 0, L.s>>>(w, philox_round_keys(k0, k1), (uint32_t)first_event, p.lfact,
-                                                     p.n_lfact);
+  const PhiloxRoundKeys rk = philox_round_keys(k0, k1);
+  const int gb = (int)std::min<int64_t>((std::max<int64_t>(n_part_max, 1) + 32 * kBuildWarps - 1) / (32 * kBuildWarps),
+                                        (int64_t)L.num_sms * occ);
+  k_task_build<<<gb, 32 * kBuildWarps, 0, L.s>>>(g, p, parts, ev_lo, w, rk, (uint32_t)first_event);
   // the FP64 pipe is narrow: one warp per block spreads the few deferred draws
   // over every SM
-  k_task_poisson64<<<L.num_sms * 8, 32, 0, L.s>>>(w, k0, k1, philox_round_keys(k0, k1), (uint32_t)first_event,
-                                                   p.lfact, p.lfact64, p.n_lfact);
+  k_task_poisson64<<<L.num_sms * 8, 32, 0, L.s>>>(w, p.mhe, rk, (uint32_t)first_event, p.lfact, p.lfact64,
+                                                   p.n_lfact);
   // the scan counts the tasks actually written (n_tasks <= task_cap by construction)
   return launch_scan_hits(w.tn, w.th, &w.sizes->n_tasks, &w.sizes->n_hits, w.gmap, w.gmap_cap, tmp, L.s);
 }
@@ -736,6 +762,14 @@ cudaError_t launch_task_finish(WsDev w, const fcs_debug* dbg, int det, int fill_
   fcs_debug d{};
   if (dbg) d = *dbg;
   k_task_finish<<<grid_for(n_task_max, L), 128, 0, L.s>>>(w, d, dbg ? 1 : 0, det, fill_map);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_poisson_audit(const ParamDev& p, const float* mu, int64_t n, uint32_t k0, uint32_t k1,
+                                 int32_t* n32, int32_t* n64, const Launch& L) {
+  if (n <= 0) return cudaSuccess;
+  k_poisson_audit<<<grid_for(n, L), 128, 0, L.s>>>(mu, n, k0, k1, philox_round_keys(k0, k1), p.lfact, p.lfact64,
+                                                   p.n_lfact, n32, n64);
   return cudaGetLastError();
 }
 

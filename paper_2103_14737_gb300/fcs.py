@@ -33,7 +33,7 @@ EXPORTED = ("fcs_version", "fcs_last_error", "fcs_load_geometry", "fcs_geometry_
             "fcs_selftest_wait_timeout",
             "fcs_simulate_events", "fcs_simulate_events_host",
             "fcs_simulate_events_static", "fcs_autotune", "fcs_microbench", "fcs_simulate_backward",
-            "fcs_update_params")
+            "fcs_update_params", "fcs_poisson_audit")
 
 
 class FcsError(RuntimeError):
@@ -112,6 +112,7 @@ def load_library(build_if_missing: bool = True):
         L.fcs_microbench.argtypes = [i32, i64, i32, vp, vp]
         L.fcs_simulate_backward.argtypes = [vp, vp, vp, vp, i64, i32, u64, i64, vp, vp, vp, vp, vp, vp]
         L.fcs_update_params.argtypes = [vp, vp, vp, vp, vp]
+        L.fcs_poisson_audit.argtypes = [vp, vp, i64, u64, vp, vp, vp]
         # every other entry point returns an int status (the ctypes default restype)
         _lib = L
         return L
@@ -287,6 +288,19 @@ def fcs_microbench(kind, size=0, iters=256):
     rate = C.c_double()
     _check(load_library().fcs_microbench(int(kind), int(size), int(iters), C.byref(rate), _stream()))
     return rate.value
+
+
+def fcs_poisson_audit(prm, mu, seed):
+    """FP32-path and FP64-definition Poisson counts of draws i = 0..n-1 with
+    means mu (a CUDA float32 tensor), as two CUDA int32 tensors (see
+    include/fcs.h for the codes of uncertain FP32 draws)."""
+    import torch
+    n = mu.numel()
+    n32 = torch.empty(n, dtype=torch.int32, device=mu.device)
+    n64 = torch.empty(n, dtype=torch.int32, device=mu.device)
+    _check(load_library().fcs_poisson_audit(prm, mu.data_ptr(), n, int(seed) & 0xFFFFFFFFFFFFFFFF, n32.data_ptr(),
+                                            n64.data_ptr(), _stream()))
+    return n32, n64
 
 
 AUTOTUNE_BLOCKS = (128, 256, 512)

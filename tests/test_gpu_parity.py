@@ -19,6 +19,11 @@ from paper_2103_14737_gb300 import fcs, synth  # noqa: E402
 from parity import (ATOL, RTOL, check_cells_atomic, check_compacted, check_tasks_hits,  # noqa: E402
                     run_both)
 
+# kernels of one event range in a replayed graph (begin and end of the call
+# add two more)
+KERNELS_PER_RANGE = 12
+
+
 @pytest.fixture(scope="module")
 def sim(geo, prm):
     if not torch.cuda.is_available():
@@ -271,14 +276,15 @@ def test_async_graph_replay_matches(sim):
     assert rc == 0 and st.n_nonzero == ref["stats"]["n_nonzero"]
     diff = (outs["cells"] - ref["cells"]).abs()
     assert (diff <= RTOL * ref["cells"].abs() + ATOL).all()
-    # the launch sequence of one event range (13 kernels): range begin,
-    # particle counts, the task-offset scan, task records, Poisson FP32 and
-    # FP64 (2), the hit-offset scan with the tile map, hits, recheck,
-    # compaction (count, scan, write), range end; plus call begin and end
-    assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 13
+    # the launch sequence of one event range (12 kernels): range begin,
+    # particle counts, the task-offset scan, task records with their FP32
+    # Poisson draws, the FP64 draws, the hit-offset scan with the tile map,
+    # hits, recheck, compaction (count, scan, write), range end; plus call
+    # begin and end
+    assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + KERNELS_PER_RANGE
     sim.simulate(d, 21, sync=0, use_graph=1, outputs=outs, wave_events=2)
     torch.cuda.synchronize()
-    assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 2 * 13
+    assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 2 * KERNELS_PER_RANGE
 
 
 def test_host_entry_point_matches(sim):
@@ -347,7 +353,7 @@ def test_host_entry_point_two_waves(sim):
         assert (err <= RTOL * np.abs(ref_E) + ATOL).all()
         assert (ids.numpy()[nnz:] == -1).all()
         if call > 0:  # the first call may size the workspace synchronously
-            assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 2 * 13
+            assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 2 * KERNELS_PER_RANGE
 
 
 @pytest.mark.parametrize("layout", ["two_events", "empty_first_wave"])
@@ -378,7 +384,7 @@ def test_host_entry_point_two_waves_edges(sim, layout):
         assert np.array_equal(ids.numpy()[:nnz], ref["cell_ids"][:nnz].cpu().numpy())
         want = ref["cell_E"][:nnz].cpu().numpy().astype(np.float64)
         assert (np.abs(E.numpy()[:nnz] - want) <= RTOL * np.abs(want) + ATOL).all()
-    assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 2 * 13
+    assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 2 * KERNELS_PER_RANGE
 
 
 def test_host_entry_point_async_two_workspaces(sim):
@@ -420,7 +426,7 @@ def test_host_entry_point_async_two_workspaces(sim):
                 want = ref[1][:nnz].astype(np.float64)
                 assert (np.abs(out[1][:nnz] - want) <= RTOL * np.abs(want) + ATOL).all()
                 assert (out[0][nnz:] == -1).all()
-        assert fcs.fcs_workspace_graph_kernels(slots[0][0]) == 2 + 2 * 13
+        assert fcs.fcs_workspace_graph_kernels(slots[0][0]) == 2 + 2 * KERNELS_PER_RANGE
     finally:
         torch.cuda.synchronize()
         for ws, _, _ in slots:
