@@ -867,7 +867,7 @@ int fcs_load_geometry(fcs_geo** out, const fcs_region* regions, int32_t n_region
   if ((rc = current_device(&geo->device)) != FCS_OK) return fail(rc);
   RegionF* d_rf;
   double *d_el, *d_de, *d_pl, *d_dp, *d_sp, *d_rz;
-  float *d_rz32, *d_sp32;
+  float *d_rinv32, *d_sp32;
   int32_t *d_ne, *d_np, *d_co, *d_lrb, *d_bar;
   if ((rc = dev_alloc(&d_rf, n_regions, &geo->allocs)) || (rc = dev_alloc(&d_el, n_regions, &geo->allocs)) ||
       (rc = dev_alloc(&d_de, n_regions, &geo->allocs)) || (rc = dev_alloc(&d_pl, n_regions, &geo->allocs)) ||
@@ -875,14 +875,14 @@ int fcs_load_geometry(fcs_geo** out, const fcs_region* regions, int32_t n_region
       (rc = dev_alloc(&d_ne, n_regions, &geo->allocs)) || (rc = dev_alloc(&d_np, n_regions, &geo->allocs)) ||
       (rc = dev_alloc(&d_co, n_regions, &geo->allocs)) || (rc = dev_alloc(&d_lrb, n_layers + 1, &geo->allocs)) ||
       (rc = dev_alloc(&d_rz, n_layers, &geo->allocs)) || (rc = dev_alloc(&d_bar, n_layers, &geo->allocs)) ||
-      (rc = dev_alloc(&d_rz32, n_layers, &geo->allocs)) || (rc = dev_alloc(&d_sp32, n_regions, &geo->allocs)))
+      (rc = dev_alloc(&d_rinv32, n_layers, &geo->allocs)) || (rc = dev_alloc(&d_sp32, n_regions, &geo->allocs)))
     return fail(rc);
   std::vector<double> rz(n_layers);
-  std::vector<float> rz32(n_layers);
+  std::vector<float> rinv32(n_layers);
   std::vector<int32_t> bar(n_layers);
   for (int l = 0; l < n_layers; ++l) {
     rz[l] = layers[l].rz;
-    rz32[l] = (float)layers[l].rz;
+    rinv32[l] = 1.0f / (float)layers[l].rz;  // correctly rounded, as on the device
     bar[l] = layers[l].barrel;
   }
   const struct {
@@ -895,7 +895,7 @@ int fcs_load_geometry(fcs_geo** out, const fcs_region* regions, int32_t n_region
                 {d_ne, ne.data(), n_regions * sizeof(int32_t)},   {d_np, np.data(), n_regions * sizeof(int32_t)},
                 {d_co, co.data(), n_regions * sizeof(int32_t)},   {d_lrb, lrb, (n_layers + 1) * sizeof(int32_t)},
                 {d_rz, rz.data(), n_layers * sizeof(double)},     {d_bar, bar.data(), n_layers * sizeof(int32_t)},
-                {d_rz32, rz32.data(), n_layers * sizeof(float)},  {d_sp32, split32.data(), n_regions * sizeof(float)}};
+                {d_rinv32, rinv32.data(), n_layers * sizeof(float)},  {d_sp32, split32.data(), n_regions * sizeof(float)}};
   for (const auto& c : copies) {
     cudaError_t e = cudaMemcpyAsync(c.d, c.h, c.n, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail(set_err(FCS_E_CUDA, "geometry copy: %s", cudaGetErrorString(e)));
@@ -919,7 +919,7 @@ int fcs_load_geometry(fcs_geo** out, const fcs_region* regions, int32_t n_region
   d.cell_off = d_co;
   d.lrb = d_lrb;
   d.rz = d_rz;
-  d.rz32 = d_rz32;
+  d.rinv32 = d_rinv32;
   d.barrel = d_bar;
   *out = geo;
   return ok();

@@ -164,9 +164,11 @@ __device__ __forceinline__ void load_tables(HitSmemTables& t, const GeoDev& g, c
 //   cos/sin: |alpha32 - alpha| <= ~2^-21.4 (alpha - pi in [-pi, pi] from an
 //     FMA of FP32 table values) and __sincosf's documented absolute error on
 //     [-pi, pi] (2^-21.19 for cos, 2^-21.41 for sin): <= 2^-20.4 in all;
-//   r32 <= r_hi * 2^-23 off; s32 (coshf/sinhf/tanhf, a few ulp) <= 2^-21
-//     relative; the two products 2 * 2^-24 relative:
-//   => |deta32 - deta| <= r_hi |s_eta| 2^-19.5; bound used: r_hi |s| 2^-17;
+//   r32 <= r_hi * 2^-23 off; s32 (coshf, sinhf and tanhf within 2, 3 and 2
+//     ulp as documented, a correctly rounded 1/R or 1/cosh and up to two
+//     products: <= 8 ulp) <= 2^-20 relative; the two products 2 * 2^-24
+//     relative:
+//   => |deta32 - deta| <= r_hi |s_eta| 2^-19; bound used: r_hi |s| 2^-17;
 //   the final add rounds by |eta| 2^-24; bound used: |eta| 2^-21.
 // Scaled index te = fl(eta32 inv + ek) with inv = fl(1/deta), ek =
 // fl(-eta_lo/deta): |te - te*| <= be inv + (|eta| inv) 2^-24 + |ek| 2^-24 +

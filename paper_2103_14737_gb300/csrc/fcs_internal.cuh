@@ -69,7 +69,7 @@ struct GeoDev {
   const int32_t* cell_off;
   const int32_t* lrb;    // [n_layers + 1]
   const double* rz;      // [n_layers]
-  const float* rz32;     // [n_layers] FP32 copy for the fast path
+  const float* rinv32;   // [n_layers] 1 / fl32(R), correctly rounded, for the fast path
   const int32_t* barrel; // [n_layers]
 };
 

@@ -20,7 +20,7 @@ namespace {
 // PTRS, the transformed rejection with squeeze of Hoermann (1993).  Draw i of
 // a task is Philox block (i, layer | 1 << 16, particle, event); its words give
 // two 53-bit uniforms.  The bounds of both loops match the oracle.
-constexpr int kInvMax = 200;
+constexpr int kInvMax = 200;  // even: the FP32 search takes two steps a trip
 constexpr uint32_t kPtrsMaxIter = 64;
 
 __device__ __forceinline__ void draw_pair(uint32_t i, uint32_t layer, uint32_t particle,
@@ -195,12 +195,11 @@ __device__ __forceinline__ int64_t ptrs_iter32(float mu, const PtrsConst32& c, u
   if (!(us_ge_0013 || v_le_us)) return -2;
   // full test: log V + log invalpha - log(a / us^2 + b) <= -mu + k log mu - lgamma(k + 1)
   if (!k_sure) return -2;
-  const float l1 = logf(Vf), l2 = logf(c.invalpha), l3 = logf(__fdividef(c.a, usf * usf) + c.b);
   const int32_t ki = (int32_t)kf;
-  const float kl = kf * c.loglam, lg = (ki < c.n_lfact) ? __ldg(c.lfact + ki) : lgammaf(kf + 1.0f);
+  if (ki >= c.n_lfact) return -2;  // past the log k! table (never below kPtrsFastMaxMu): FP64
+  const float l1 = logf(Vf), l2 = logf(c.invalpha), l3 = logf(__fdividef(c.a, usf * usf) + c.b);
+  const float kl = kf * c.loglam, lg = __ldg(c.lfact + ki);
   const float d = (l1 + l2 - l3) - ((-mu + kl) - lg);
-  // (k below the table for every mu <= kPtrsFastMaxMu; lgammaf's larger
-  // error past it is covered by the 2^-18 term only for small k)
   const float bd = fmaf(fabsf(l1) + fabsf(l2) + fabsf(l3) + fabsf(kl) + fabsf(lg) + mu, 0x1p-20f, 0x1p-18f);
   if (d < -bd) return (int64_t)ki;
   if (d > bd) return -1;
@@ -215,6 +214,7 @@ __device__ __forceinline__ int64_t ptrs_iter32(float mu, const PtrsConst32& c, u
 // the loop would compute).
 __device__ __forceinline__ int32_t poisson_inv_fp32(float mu32, uint32_t layer, uint32_t particle, uint32_t event,
                                                     const PhiloxRoundKeys& rk, const float* rcp) {
+  static_assert(kInvMax % 2 == 0, "two steps a trip end exactly at kInvMax");
   if (!(mu32 > 0.0f)) return 0;
   const uint4 x = philox4x32_10_rk(make_uint4(0u, layer | (kPurposePoisson << 16), particle, event), rk);
   const float uf = u53f(x.x, x.y);
@@ -223,12 +223,34 @@ __device__ __forceinline__ int32_t poisson_inv_fp32(float mu32, uint32_t layer, 
   float e = 0x1p-21f;  // (k + 2) 2^-22, exact in FP32 for k <= kInvMax
   float d = uf - F;
   int k = 0;
-  while (d > e && k < kInvMax) {  // u > F_k for certain: the search goes on
-    k += 1;
-    e += 0x1p-22f;
-    p = (p * mu32) * rcp[k];
-    F = F + p;
-    d = uf - F;
+  if (d > e) {  // u > F_0 for certain: the search goes on
+    // two steps a trip: F_{k+2} >= F_{k+1} in FP32 too and the bound grows,
+    // so a certain u > F_{k+2} makes u > F_{k+1} certain as well
+    for (;;) {
+      const float p1 = (p * mu32) * rcp[k + 1];
+      const float F1 = F + p1;
+      const float p2 = (p1 * mu32) * rcp[k + 2];
+      const float F2 = F1 + p2;
+      const float d2 = uf - F2, e2 = e + 0x1p-21f;
+      if (d2 > e2 && k + 2 < kInvMax) {
+        k += 2;
+        p = p2;
+        F = F2;
+        e = e2;
+        continue;
+      }
+      const float d1 = uf - F1, e1 = e + 0x1p-22f;
+      if (d1 > e1) {  // the search passes k + 1 and stops at k + 2 (or is uncertain there)
+        k += 2;
+        d = d2;
+        e = e2;
+      } else {
+        k += 1;
+        d = d1;
+        e = e1;
+      }
+      break;
+    }
   }
   if (d < -e) return k;  // u < F_k for certain: stop at k
   if (d > e) return k;   // k == kInvMax: the definition stops here too
@@ -396,9 +418,9 @@ __global__ void __launch_bounds__(128) k_particle_count(const ParamDev p, const 
 // Building: a warp takes 32 consecutive particles, whose tasks are consecutive
 // too (poff), and fills them 32 at a time: lane s of a round builds the task in
 // slot s of the warp's range, so each round writes 32 consecutive 32-byte
-// records.  The owner of a slot is found by a binary search over the lanes'
-// inclusive task counts (shuffles); its data comes by shuffle from the lane
-// that loaded the particle.
+// records.  Each lane first lists its particle's tasks in shared memory (slot
+// -> its lane and the layer of its k-th set mask bit); a slot's builder reads
+// its owner and layer there and the owner's data by shuffle.
 //
 // Drawing: each new task joins one of two per-warp queues in shared memory,
 // inversion (mu < 10) or PTRS, with its Philox counter fields.  Whenever a
@@ -511,6 +533,7 @@ __global__ void __launch_bounds__(32 * kBuildWarps) k_task_build(const GeoDev g,
   __shared__ DrawEnt s_e[2][kBuildWarps][kDrawQ];  // inversion and PTRS queues
   __shared__ uint8_t s_it[2][kBuildWarps][kDrawQ];
   __shared__ float s_rcp[kInvMax + 1];  // 1 / k, correctly rounded
+  __shared__ uint16_t s_slot[kBuildWarps][32 * kMaxLayers];  // owner lane | layer << 8 of the group's tasks
   for (int k = threadIdx.x; k <= kInvMax; k += blockDim.x) s_rcp[k] = __frcp_rn((float)k);
   __syncthreads();
   const int64_t pb = parts.event_offsets[ev_lo];
@@ -533,6 +556,11 @@ __global__ void __launch_bounds__(32 * kBuildWarps) k_task_build(const GeoDev g,
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     if (total == 0) continue;
     const int64_t tbase = __shfl_sync(0xffffffffu, w.poff[have ? li : wb], 0);
+    uint16_t* slot = s_slot[wi];
+    __syncwarp();  // the previous group's rounds have read their slots
+    for (uint32_t m = info.z, k = (uint32_t)(incl - cnt); m; m &= m - 1u, ++k)
+      slot[k] = (uint16_t)(lane | ((__ffs(m) - 1) << 8));
+    __syncwarp();
     // the particle this lane loaded (lanes without tasks load nothing)
     float E = 0.0f, eta = 0.0f, phi = 0.0f, ch = 0.0f, sh = 0.0f, th = 0.0f;
     int32_t pin = 0;
@@ -551,17 +579,11 @@ __global__ void __launch_bounds__(32 * kBuildWarps) k_task_build(const GeoDev g,
     }
     for (int s0 = 0; s0 < total; s0 += 32) {
       const int sl = s0 + lane;
-      int o = 0;  // owner: the first lane whose inclusive count exceeds sl
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int v = __shfl_sync(0xffffffffu, incl, o + step - 1);
-        if (v <= sl) o += step;
-      }
-      o = min(o, 31);
-      const int j = sl - (__shfl_sync(0xffffffffu, incl, o) - __shfl_sync(0xffffffffu, cnt, o));
+      const uint32_t sv = sl < total ? slot[sl] : 0u;
+      const int o = (int)(sv & 31u);  // the particle's lane
+      const int l = (int)(sv >> 8);    // the task's layer
       const uint32_t entry = __shfl_sync(0xffffffffu, info.x, o);
       const uint32_t ev = __shfl_sync(0xffffffffu, info.y, o);
-      const uint32_t mask = __shfl_sync(0xffffffffu, info.z, o);
       const float oE = __shfl_sync(0xffffffffu, E, o), oeta = __shfl_sync(0xffffffffu, eta, o);
       const float ophi = __shfl_sync(0xffffffffu, phi, o);
       const float och = __shfl_sync(0xffffffffu, ch, o), osh = __shfl_sync(0xffffffffu, sh, o);
@@ -573,7 +595,6 @@ __global__ void __launch_bounds__(32 * kBuildWarps) k_task_build(const GeoDev g,
       float mu = 0.0f;
       uint32_t evl = 0;
       if (valid) {
-        const int l = (int)__fns(mask, 0u, j + 1);
         const int64_t e = (int64_t)entry * NL + l;
         const float El = __fmul_rn(oE, __ldg(p.frac + e));
         TaskRec r;
@@ -581,13 +602,16 @@ __global__ void __launch_bounds__(32 * kBuildWarps) k_task_build(const GeoDev g,
         r.El = El;
         r.eta_c = oeta;
         r.phi_c = ophi;
-        const float R = g.rz32[l];
+        // barrel 1/R and 1/(R cosh eta), end cap sinh|eta|/R and
+        // -+tanh|eta| sinh|eta|/R, each a few ulp off (see the hit kernel's
+        // error bound)
+        const float rinv = __ldg(g.rinv32 + l);
         if (g.barrel[l]) {
-          r.s_phi = 1.0f / R;
-          r.s_eta = 1.0f / (R * och);
+          r.s_phi = rinv;
+          r.s_eta = rinv * __frcp_rn(och);
         } else {
-          const float mm = (oth * osh) / R;
-          r.s_phi = osh / R;
+          const float mm = (oth * osh) * rinv;
+          r.s_phi = osh * rinv;
           r.s_eta = (oeta < 0.0f) ? mm : -mm;
         }
         r.particle = opin;
