@@ -313,7 +313,7 @@ int ws_reserve_hits(fcs_workspace* ws, int64_t H, int mode) {
   const int64_t rq = std::max<int64_t>(1 << 16, H / 16);
   if (rq > ws->recheck_cap) FCS_TRY(grow(&ws->recheck, &ws->recheck_cap, rq + rq / 4));
   if (mode == FCS_MODE_DETERMINISTIC) {
-    const int64_t need = std::max<int64_t>(H, 1);
+    const int64_t need = std::max<int64_t>(H, 1) + kRecordSlack;
     if (need > ws->rec_cap) {
       const int64_t cap = need + need / 8;
       int64_t c1 = ws->k_cap, c2 = ws->ka_cap;
@@ -352,7 +352,9 @@ __global__ void __launch_bounds__(kRangeThreads) k_range_begin(Sizes* s, const i
   s->n_hits = 0;
   s->n_recheck = 0;
   s->n_records = 0;
+  s->n_slots = 0;
   s->n_big = 0;
+  s->n_mid = 0;
   s->n_pdefer = 0;
   s->n_pdefer_ptrs = 0;
   s->queue = 0;

@@ -301,31 +301,60 @@ __device__ __forceinline__ FastHit fast_cell(const HitSmemTables& tb, const TT& 
 }
 
 // ---- warp-level deposit / record emission -----------------------------------
-// Deterministic mode: every hit of the range owns the record slot of its hit
-// index.  The first lane of each group of equal (cell, task) keys in the warp
-// writes the group's record (count - 1 in the low bits) to its own slot and
-// counts it in the cell's uint32 counter (the accumulation row); the other
-// valid lanes write the empty record (all ones).  Uncertain hits leave their
-// slot empty for the recheck kernel to fill.  Returns the warp's number of
-// records (the caller counts them per CTA: one counter hit by every warp would
-// serialise).
-__device__ __forceinline__ unsigned emit_slots(bool valid, bool ok, unsigned long long gkey, uint32_t cell,
-                                               int64_t slot, const WsDev& w) {
+// Deterministic mode: the first lane of each group of equal (cell, task) keys
+// in the warp writes the group's record (count - 1 in the low bits) and counts
+// it in the cell's uint32 counter (the accumulation row).  A warp writes its
+// records contiguously into chunks of kRecordChunk slots that it takes from
+// the range's slot counter (a round that does not fit continues in the next
+// chunk) and fills the rest of its last chunk with the empty record (all ones)
+// when it ends, so the slots handed out hold every record and a few empty
+// ones.  Uncertain hits are left to the recheck kernel.  Returns the warp's
+// number of records (the caller counts them per CTA: one counter hit by every
+// warp would serialise).
+struct RecordChunk {
+  int64_t base = 0;
+  int fill = kRecordChunk;  // no chunk yet
+};
+
+__device__ __forceinline__ unsigned emit_records(bool ok, unsigned long long gkey, uint32_t cell, RecordChunk& ch,
+                                                 const WsDev& w) {
   const int lane = threadIdx.x & 31;
   const unsigned m = __ballot_sync(0xffffffffu, ok);
   unsigned peers = 0;
   if (ok) peers = __match_any_sync(m, gkey);
   const bool lead = ok && (lane == __ffs(peers) - 1);
   const unsigned lm = __ballot_sync(0xffffffffu, lead);
-  if (valid) {
+  const int cnt = __popc(lm);
+  if (cnt == 0) return 0u;
+  const bool spill = ch.fill + cnt > kRecordChunk;
+  unsigned long long nbase = 0;
+  if (spill) {
+    if (lane == 0) nbase = atomicAdd((unsigned long long*)&w.sizes->n_slots, (unsigned long long)kRecordChunk);
+    nbase = __shfl_sync(0xffffffffu, nbase, 0);
+  }
+  if (lead) {
+    const int pos = ch.fill + __popc(lm & ((1u << lane) - 1u));
+    const int64_t slot = pos < kRecordChunk ? ch.base + pos : (int64_t)nbase + (pos - kRecordChunk);
     if (slot < w.rec_cap) {
-      w.keys[slot] = lead ? ((gkey << kRecordCountBits) | (unsigned long long)(__popc(peers) - 1)) : ~0ull;
-      if (lead) atomicAdd(reinterpret_cast<uint32_t*>(w.acc) + cell, 1u);
+      w.keys[slot] = (gkey << kRecordCountBits) | (unsigned long long)(__popc(peers) - 1);
+      atomicAdd(reinterpret_cast<uint32_t*>(w.acc) + cell, 1u);
     } else {
       atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_HIT_CAPACITY);
     }
   }
-  return (unsigned)__popc(lm);
+  if (spill) {
+    ch.base = (int64_t)nbase;
+    ch.fill += cnt - kRecordChunk;
+  } else {
+    ch.fill += cnt;
+  }
+  return (unsigned)cnt;
+}
+
+// The empty records after a warp's last one in its chunk.
+__device__ __forceinline__ void close_records(const RecordChunk& ch, const WsDev& w) {
+  for (int j = ch.fill + (threadIdx.x & 31); j < kRecordChunk; j += 32)
+    if (ch.base + j < w.rec_cap) w.keys[ch.base + j] = ~0ull;
 }
 
 // Sum of v over each group of lanes with equal keys, added by the group's
@@ -349,7 +378,7 @@ __device__ __forceinline__ void grad_warp(bool ok, uint32_t key, float v, float*
 }
 
 __device__ __forceinline__ void deposit_single(const HitKParams& kp, int32_t event, float Ehit, int64_t task_rel,
-                                               int32_t cell, int mode, int32_t entry, int bin, int64_t slot) {
+                                               int32_t cell, int mode, int32_t entry, int bin) {
   const int64_t row = event - kp.ev_lo;
   if (mode == kModeAtomic) {
     acc_add(kp.w.acc + row * kp.g.acc_stride + cell, Ehit);
@@ -360,6 +389,7 @@ __device__ __forceinline__ void deposit_single(const HitKParams& kp, int32_t eve
   } else {
     const uint32_t c = (uint32_t)(row * kp.g.acc_stride + cell);
     const unsigned long long gkey = ((unsigned long long)c << kp.key_task_bits) | (unsigned long long)task_rel;
+    const int64_t slot = (int64_t)atomicAdd((unsigned long long*)&kp.w.sizes->n_slots, 1ull);  // a slot of its own
     if (slot < kp.w.rec_cap) {
       atomicAdd((unsigned long long*)&kp.w.sizes->n_records, 1ull);
       kp.w.keys[slot] = gkey << kRecordCountBits;
@@ -406,8 +436,7 @@ __device__ __forceinline__ void owner_scan(int16_t* s_owner, int* s_wmax) {
 template <int MODE, bool DBG>
 static __device__ __noinline__ void queue_uncertain(const HitKParams& kp, bool need, unsigned m, int64_t task,
                                                     uint32_t hit, int32_t layer, float eta_c, float phi_c, uint4 x,
-                                                    int bin, int32_t ev, float Ehit, int32_t entry, int64_t slot,
-                                                    int64_t dbg_h) {
+                                                    int bin, int32_t ev, float Ehit, int32_t entry, int64_t dbg_h) {
   const WsDev& w = kp.w;
   const int lane = threadIdx.x & 31;
   unsigned long long base = 0;
@@ -421,7 +450,7 @@ static __device__ __noinline__ void queue_uncertain(const HitKParams& kp, bool n
     return;
   }
   const int32_t c = cell_fp64(kp.g, kp.p, layer, eta_c, phi_c, x, bin);
-  deposit_single(kp, ev, Ehit, task, c, MODE, entry, bin, slot);
+  deposit_single(kp, ev, Ehit, task, c, MODE, entry, bin);
   atomicAdd((unsigned long long*)&w.sizes->n_inline, 1ull);
   atomicOr(&w.sizes->flags, (uint32_t)FCS_FLAG_RECHECK_SPILL);
   if (DBG && kp.dbg_hit_cell && dbg_h < kp.dbg_hit_cap) kp.dbg_hit_cell[dbg_h] = c;
@@ -468,6 +497,7 @@ __global__ void __launch_bounds__(BLOCK, MODE == kModeAtomic ? 1280 / BLOCK : 0)
   __syncthreads();
   uint32_t tile = s_tile;
   unsigned long long recs = 0;  // deterministic mode: this warp's records
+  RecordChunk chunk;            //   and the slots it writes them to
   while (tile < n_tiles) {
     __syncthreads();  // everyone has read s_tile; s_owner is zero again
     if (threadIdx.x == 0) s_tile = kp.static_tiles ? n_tiles : (uint32_t)atomicAdd(&w.sizes->queue, 1ull);
@@ -535,14 +565,13 @@ __global__ void __launch_bounds__(BLOCK, MODE == kModeAtomic ? 1280 / BLOCK : 0)
         } else {
           const uint32_t cg = T.row_off + (uint32_t)f.cell;
           const unsigned long long gkey = ((unsigned long long)cg << kp.key_task_bits) | (unsigned long long)(t0 + tl);
-          recs += emit_slots(valid, ok, gkey, cg, h0 + i, w);
+          recs += emit_records(ok, gkey, cg, chunk, w);
         }
         // queue the uncertain hits for the FP64 recheck
         const unsigned m = __ballot_sync(0xffffffffu, need);
         if (m)
           queue_uncertain<MODE, DBG>(kp, need, m, t0 + tl, hit, (int32_t)(T.lay & 0xFF), T.eta_c, T.phi_c, x, bin,
-                                     (int32_t)(T.ctr_w - kp.first_event_lo), T.Ehit, T.entry, h0 + i,
-                                     hit_dbg_base + h0 + i);
+                                     (int32_t)(T.ctr_w - kp.first_event_lo), T.Ehit, T.entry, hit_dbg_base + h0 + i);
         if constexpr (DBG) {
           const int64_t h = hit_dbg_base + h0 + i;
           if (valid && h < kp.dbg_hit_cap) {
@@ -559,6 +588,7 @@ __global__ void __launch_bounds__(BLOCK, MODE == kModeAtomic ? 1280 / BLOCK : 0)
     tile = s_tile;
   }
   if constexpr (DET) {
+    close_records(chunk, w);
     if (lane == 0 && recs) atomicAdd(&s_recs, recs);
     __syncthreads();
     if (threadIdx.x == 0 && s_recs) atomicAdd((unsigned long long*)&w.sizes->n_records, s_recs);
@@ -582,7 +612,7 @@ __global__ void __launch_bounds__(128) k_recheck(const __grid_constant__ HitKPar
         kp.k0, kp.k1);
     const int bin = sample_bin(kp.p, T.entry, x.x);
     const int32_t c = cell_fp64(kp.g, kp.p, layer, T.eta_c, T.phi_c, x, bin);
-    deposit_single(kp, event, __fdiv_rn(T.El, (float)w.tn[q.x]), q.x, c, MODE, T.entry, bin, hb + q.y);
+    deposit_single(kp, event, __fdiv_rn(T.El, (float)w.tn[q.x]), q.x, c, MODE, T.entry, bin);
     const int64_t h = hit_dbg_base + hb + q.y;
     if (kp.dbg_hit_cell && h < kp.dbg_hit_cap) kp.dbg_hit_cell[h] = c;
   }

@@ -17,6 +17,8 @@ constexpr int kNBins = 128;      // 16 r-bins x 8 alpha-bins
 constexpr int kNR = 16;
 constexpr int kNA = 8;
 constexpr int kGuideCells = 128; // guide cells per histogram (top 7 bits of word 0)
+constexpr int kRecordChunk = 256;  // deterministic mode: record slots a warp takes at a time
+constexpr int64_t kRecordSlack = 1 << 22;  // slots beyond the hits: the warps' partly filled chunks
 constexpr int kGranule = 128;    // hits per granule of the tile -> task map (divides every tile)
 constexpr int kRecordCountBits = 5;  // deterministic mode: count - 1 in the low 5 bits
 constexpr int kLfactEntries = 8192;  // log k! table for the FP32 Poisson test (k < 8192)
@@ -98,7 +100,8 @@ struct Sizes {
   int64_t n_tasks;
   int64_t n_hits;
   int64_t n_recheck;    // entries appended to the recheck queue (may exceed its capacity)
-  int64_t n_records;    // deterministic mode: non-empty record slots
+  int64_t n_records;    // deterministic mode: records written
+  int64_t n_slots;      // deterministic mode: record slots handed out (chunks of kRecordChunk)
   int64_t nnz;          // non-zero cells of the current event range
   int64_t nnz_total;    // running output size over the call (per-event mode)
   int64_t n_inline;     // recheck hits done inline because the queue was full
@@ -107,6 +110,7 @@ struct Sizes {
   int64_t recheck_total;  // recheck hits over the call
   int64_t n_part;       // particles of the current event range (checked against the capacity)
   int64_t n_big;        // deterministic mode: cells with more records than one thread sorts
+  int64_t n_mid;        // deterministic mode: cells of 9 to 32 records (sorted by their own kernel)
   int64_t n_pdefer;     // inversion draws deferred to FP64 in the current range (front of pdefer)
   int64_t n_pdefer_ptrs;  // PTRS draws deferred to FP64 in the current range (back of pdefer)
   unsigned long long queue;  // hit-kernel work-queue counter (tiles handed out)

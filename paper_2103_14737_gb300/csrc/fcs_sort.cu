@@ -9,20 +9,22 @@
 //
 // Record layout (uint64): [ cell | task | count - 1 (5 bits) ], with cell the
 // index into the accumulation rows (row * acc_stride + cell in row).  The hit
-// kernel writes each record to the slot of one of its hits (the other slots
-// hold the empty record, all ones) and counts the records of every cell in
-// the accumulation rows, used as uint32 counters.  Then:
+// kernel writes the records to slots handed out in chunks (unused slots hold
+// the empty record, all ones) and counts the records of every cell in the
+// accumulation rows, used as uint32 counters.  Then:
 //   1. an exclusive scan of the counters gives each cell its segment of the
 //      record array;
 //   2. scatter: every record takes a place in its cell's segment; the
 //      counter, counted down, hands out the places and ends at zero;
 //   3. fold: one thread per cell sorts its segment by (task, count) - a copy
-//      in registers with a sorting network up to 8 records, in place by
-//      insertion up to 32 - merges the records of a task (their counts add
-//      exactly) and folds; a warp per longer segment sorts it in shared
-//      memory (bitonic) before its first lane folds.  The float result
-//      goes to the (FP64) accumulation row, where the compaction of the atomic
-//      mode picks it up, rounds it back to the same float and re-zeroes it.
+//      in registers with a sorting network up to 16 records, a thread-local
+//      copy by insertion up to 32, the three classes in kernels of their
+//      own - merges the
+//      records of a task (their counts add exactly) and folds; a warp per
+//      longer segment sorts it in shared memory (bitonic) before its first
+//      lane folds.  The float result goes to the (FP64) accumulation row,
+//      where the compaction of the atomic mode picks it up, rounds it back to
+//      the same float and re-zeroes it.
 // Only the order of places inside a segment depends on scheduling, and the
 // sort removes it, so the cells are bit-reproducible.
 #include "fcs_internal.cuh"
@@ -31,7 +33,7 @@ namespace fcs {
 namespace {
 
 constexpr uint64_t kEmpty = ~0ull;
-constexpr int kInsertionMax = 32;  // segments sorted in place by insertion up to here, heapsort beyond
+constexpr int kInsertionMax = 32;  // segments sorted by insertion up to here, heapsort beyond
 
 // A range that outgrew the workspace (FCS_FLAG_HIT_CAPACITY) has slots the
 // hit kernel did not write: the scatter and the fold then do nothing (the
@@ -41,7 +43,7 @@ __global__ void __launch_bounds__(256) k_det_scatter(const uint64_t* __restrict_
                                                      const int64_t* __restrict__ cell_off, int64_t n_cells_all,
                                                      uint64_t* __restrict__ out) {
   if (sz->flags & FCS_FLAG_HIT_CAPACITY) return;
-  const int64_t n = min(sz->n_hits, cap);
+  const int64_t n = min(sz->n_slots, cap);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
     uint64_t k[4];
@@ -115,31 +117,67 @@ struct Fold {
   }
 };
 
-// Ascending sort of 8 keys in registers: Batcher's odd-even merge network
-// (19 compare-exchanges); absent records are all ones and sort last.
-constexpr int kRegSortMax = 8;
+// Ascending sort of N keys in registers (N a power of two): Batcher's
+// odd-even merge sort (Batcher 1968; 19 compare-exchanges for 8 keys, 63 for
+// 16), every index a compile-time constant; absent records are all ones and
+// sort last.
 __device__ __forceinline__ void cmpx(uint64_t& x, uint64_t& y) {
   const uint64_t lo = x < y ? x : y, hi = x < y ? y : x;
   x = lo;
   y = hi;
 }
-__device__ __forceinline__ void sort8(uint64_t (&r)[8]) {
-  cmpx(r[0], r[1]); cmpx(r[2], r[3]); cmpx(r[4], r[5]); cmpx(r[6], r[7]);
-  cmpx(r[0], r[2]); cmpx(r[1], r[3]); cmpx(r[4], r[6]); cmpx(r[5], r[7]);
-  cmpx(r[1], r[2]); cmpx(r[5], r[6]);
-  cmpx(r[0], r[4]); cmpx(r[1], r[5]); cmpx(r[2], r[6]); cmpx(r[3], r[7]);
-  cmpx(r[2], r[4]); cmpx(r[3], r[5]);
-  cmpx(r[1], r[2]); cmpx(r[3], r[4]); cmpx(r[5], r[6]);
+// Merge of the sorted halves of r[LO, LO + N) taken with stride R: the odd
+// and even subsequences recursively, then neighbours R apart.
+template <int LO, int N, int R, int M>
+__device__ __forceinline__ void oe_merge(uint64_t (&r)[M]) {
+  constexpr int S = 2 * R;
+  if constexpr (S < N) {
+    oe_merge<LO, N, S>(r);
+    oe_merge<LO + R, N, S>(r);
+#pragma unroll
+    for (int i = LO + R; i + R < LO + N; i += S) cmpx(r[i], r[i + R]);
+  } else {
+    cmpx(r[LO], r[LO + R]);
+  }
+}
+template <int LO, int N, int M>
+__device__ __forceinline__ void oe_sort(uint64_t (&r)[M]) {
+  if constexpr (N > 1) {
+    oe_sort<LO, N / 2>(r);
+    oe_sort<LO + N / 2, N / 2>(r);
+    oe_merge<LO, N, 1>(r);
+  }
+}
+template <int N>
+__device__ __forceinline__ void merge_sort_net(uint64_t (&r)[N]) {
+  oe_sort<0, N>(r);
 }
 
-// One thread per cell: segments of up to 8 records are sorted as a copy in
-// registers (92 % of the hit cells of pile-up events; nothing is written back),
-// up to kInsertionMax in place by insertion, and folded; longer ones are
-// listed for k_det_fold_big.
-__global__ void __launch_bounds__(256) k_det_fold(uint64_t* __restrict__ recs, const int64_t* __restrict__ cell_off,
-                                                  int64_t n_cells_all, Sizes* sz, int64_t cap, uint64_t task_mask,
-                                                  const float* __restrict__ task_ehit, double* __restrict__ acc,
-                                                  int64_t* __restrict__ big) {
+// Sort and fold of a segment of n <= N records (a register copy).
+template <int N>
+__device__ __forceinline__ float fold_small(const uint64_t* __restrict__ recs, int64_t a, int n, uint64_t task_mask,
+                                            const float* __restrict__ task_ehit) {
+  uint64_t r[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) r[j] = j < n ? recs[a + j] : ~0ull;
+  merge_sort_net<N>(r);
+  Fold f;
+#pragma unroll
+  for (int j = 0; j < N; ++j)
+    if (j < n) f.add(r[j], task_mask, task_ehit);
+  return f.result(task_ehit);
+}
+
+// One thread per cell: segments of up to 8 records (92 % of the hit cells of
+// pile-up events) are sorted as a copy in registers, with nothing written
+// back, and folded; segments of 9 to kInsertionMax records are listed for
+// k_det_fold_mid (from the back of the list array) and longer ones for
+// k_det_fold_big (from its front), so that the warps of each kernel run one
+// path.
+__global__ void __launch_bounds__(256) k_det_fold(const uint64_t* __restrict__ recs,
+                                                  const int64_t* __restrict__ cell_off, int64_t n_cells_all, Sizes* sz,
+                                                  int64_t cap, uint64_t task_mask, const float* __restrict__ task_ehit,
+                                                  double* __restrict__ acc, int64_t* __restrict__ lists) {
   if (sz->flags & FCS_FLAG_HIT_CAPACITY) return;
   const int64_t total = min(sz->n_records, cap);
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells_all;
@@ -147,26 +185,39 @@ __global__ void __launch_bounds__(256) k_det_fold(uint64_t* __restrict__ recs, c
     const int64_t a = cell_off[c], b = min((c + 1 < n_cells_all) ? cell_off[c + 1] : total, cap);
     if (a >= b) continue;
     const int64_t n = b - a;
-    if (n > kInsertionMax) {
-      big[atomicAdd((unsigned long long*)&sz->n_big, 1ull)] = c;
+    if (n > 8) {
+      if (n > kInsertionMax) lists[atomicAdd((unsigned long long*)&sz->n_big, 1ull)] = c;
+      else lists[cap - 1 - (int64_t)atomicAdd((unsigned long long*)&sz->n_mid, 1ull)] = c;
       continue;
     }
-    if (n <= kRegSortMax) {
-      uint64_t r[kRegSortMax];
-#pragma unroll
-      for (int j = 0; j < kRegSortMax; ++j) r[j] = j < n ? recs[a + j] : ~0ull;
-      sort8(r);
-      Fold f;
-#pragma unroll
-      for (int j = 0; j < kRegSortMax; ++j)
-        if (j < n) f.add(r[j], task_mask, task_ehit);
-      acc[c] = f.result(task_ehit);
+    acc[c] = fold_small<8>(recs, a, (int)n, task_mask, task_ehit);
+  }
+}
+
+// One thread per listed cell of 9 to kInsertionMax records: up to 16 sorted
+// as a copy in registers, longer ones as a thread-local copy by insertion
+// (its dependent steps hit L1, not L2); then folded.
+__global__ void __launch_bounds__(256) k_det_fold_mid(const uint64_t* __restrict__ recs,
+                                                      const int64_t* __restrict__ cell_off, int64_t n_cells_all,
+                                                      const Sizes* sz, int64_t cap, uint64_t task_mask,
+                                                      const float* __restrict__ task_ehit, double* __restrict__ acc,
+                                                      const int64_t* __restrict__ lists) {
+  if (sz->flags & FCS_FLAG_HIT_CAPACITY) return;
+  const int64_t total = min(sz->n_records, cap);
+  const int64_t n_mid = sz->n_mid;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_mid; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = lists[cap - 1 - q];
+    const int64_t a = cell_off[c], b = min((c + 1 < n_cells_all) ? cell_off[c + 1] : total, cap);
+    const int n = (int)(b - a);
+    if (n <= 16) {
+      acc[c] = fold_small<16>(recs, a, n, task_mask, task_ehit);
       continue;
     }
-    uint64_t* seg = recs + a;
-    for (int64_t i = 1; i < n; ++i) {
+    uint64_t seg[kInsertionMax];
+    for (int i = 0; i < n; ++i) seg[i] = recs[a + i];
+    for (int i = 1; i < n; ++i) {
       const uint64_t v = seg[i];
-      int64_t j = i - 1;
+      int j = i - 1;
       while (j >= 0 && seg[j] > v) {
         seg[j + 1] = seg[j];
         --j;
@@ -174,7 +225,7 @@ __global__ void __launch_bounds__(256) k_det_fold(uint64_t* __restrict__ recs, c
       seg[j + 1] = v;
     }
     Fold f;
-    for (int64_t j = 0; j < n; ++j) f.add(seg[j], task_mask, task_ehit);
+    for (int j = 0; j < n; ++j) f.add(seg[j], task_mask, task_ehit);
     acc[c] = f.result(task_ehit);
   }
 }
@@ -251,12 +302,15 @@ cudaError_t launch_det_reduce(const GeoDev& g, WsDev w, int32_t rows, int key_ta
   const uint64_t task_mask = (key_task_bits >= 64) ? ~0ull : ((1ull << key_task_bits) - 1ull);
   k_det_scatter<<<L.num_sms * 8, 256, 0, L.s>>>(w.keys, w.sizes, w.rec_cap, cell_shift, counters, cell_off,
                                                 n_cells_all, w.keys_alt);
-  // the slot array is free after the scatter: it lists the long segments
-  int64_t* big = reinterpret_cast<int64_t*>(w.keys);
+  // the slot array is free after the scatter: it lists the segments of more
+  // than 8 records
+  int64_t* lists = reinterpret_cast<int64_t*>(w.keys);
   k_det_fold<<<L.num_sms * 8, 256, 0, L.s>>>(w.keys_alt, cell_off, n_cells_all, w.sizes, w.rec_cap, task_mask, w.tehit,
-                                             w.acc, big);
+                                             w.acc, lists);
+  k_det_fold_mid<<<L.num_sms * 8, 256, 0, L.s>>>(w.keys_alt, cell_off, n_cells_all, w.sizes, w.rec_cap, task_mask,
+                                                 w.tehit, w.acc, lists);
   k_det_fold_big<<<L.num_sms * 4, 32 * kBigWarps, 0, L.s>>>(w.keys_alt, cell_off, n_cells_all, w.sizes, w.rec_cap,
-                                                            task_mask, w.tehit, w.acc, big);
+                                                            task_mask, w.tehit, w.acc, lists);
   return cudaGetLastError();
 }
 
