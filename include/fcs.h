@@ -390,7 +390,7 @@ int fcs_poisson_audit(const fcs_params* prm, const float* mu, int64_t n, uint64_
  * records, tile map, recheck queue and accumulation rows are carved out of
  * one static device array of FCS_STATIC_SCRATCH_BYTES.  The call is
  * synchronous on stream s and returns the device status like a sync call.
- * Limits: the particle tables (about 76 bytes x layers + 32 bytes per particle) plus the
+ * Limits: the particle tables (about 52 bytes x layers + 32 bytes per particle) plus the
  * accumulation rows (8 bytes x cells, padded, per event) must fit in the
  * array, and the hits of the call are bounded by what remains (128 hits per
  * 4 remaining bytes); otherwise FCS_E_RANGE with the sizes in the message.

@@ -85,7 +85,9 @@ __global__ void __launch_bounds__(kCThreads) k_compact_write(
           mask |= 1u << (2 * q + 1);
           v[2 * q + 1] = acc_to_f32(a[q].y);
         }
-        src[q] = z;
+        // re-zero only what is not zero (the padding past n_cells stays zero):
+        // rows are mostly zero, and a store of zeros would still dirty the line
+        if (acc_nonzero(a[q].x) || acc_nonzero(a[q].y)) src[q] = z;
       }
     }
     const int cnt = __popc(mask);

@@ -97,14 +97,16 @@ __device__ __noinline__ void sort_segment(uint64_t* a, int64_t n) {
 }
 
 // One step of the fold of a cell's records in ascending order: per task the
-// summed count times the task's hit energy, added in task order.
+// summed count times the task's hit energy, added in task order.  The count
+// is 32-bit (a task's hits fit in 31 bits) and converted as such: conversions
+// from 64-bit integers, like float-to-double ones, run on the narrow FP64 pipe.
 struct Fold {
   float E = 0.0f;
   int64_t prev_task = -1;
-  int64_t cnt = 0;
+  uint32_t cnt = 0;
   __device__ __forceinline__ void add(uint64_t k, uint64_t task_mask, const float* __restrict__ task_ehit) {
     const int64_t task = (int64_t)((k >> kRecordCountBits) & task_mask);
-    const int64_t c = (int64_t)(k & ((1u << kRecordCountBits) - 1u)) + 1;
+    const uint32_t c = (uint32_t)(k & ((1u << kRecordCountBits) - 1u)) + 1u;
     if (task != prev_task) {
       if (prev_task >= 0) E = __fadd_rn(E, __fmul_rn((float)cnt, task_ehit[prev_task]));
       prev_task = task;
@@ -112,8 +114,10 @@ struct Fold {
     }
     cnt += c;
   }
-  __device__ __forceinline__ float result(const float* __restrict__ task_ehit) const {
-    return __fadd_rn(E, __fmul_rn((float)cnt, task_ehit[prev_task]));
+  // the folded float, as the FP64 row value the compaction reads (an exact
+  // widening done with integer operations)
+  __device__ __forceinline__ double result(const float* __restrict__ task_ehit) const {
+    return f32_to_f64_bits(__fadd_rn(E, __fmul_rn((float)cnt, task_ehit[prev_task])));
   }
 };
 
@@ -126,6 +130,7 @@ __device__ __forceinline__ void cmpx(uint64_t& x, uint64_t& y) {
   x = lo;
   y = hi;
 }
+
 // Merge of the sorted halves of r[LO, LO + N) taken with stride R: the odd
 // and even subsequences recursively, then neighbours R apart.
 template <int LO, int N, int R, int M>
@@ -155,7 +160,7 @@ __device__ __forceinline__ void merge_sort_net(uint64_t (&r)[N]) {
 
 // Sort and fold of a segment of n <= N records (a register copy).
 template <int N>
-__device__ __forceinline__ float fold_small(const uint64_t* __restrict__ recs, int64_t a, int n, uint64_t task_mask,
+__device__ __forceinline__ double fold_small(const uint64_t* __restrict__ recs, int64_t a, int n, uint64_t task_mask,
                                             const float* __restrict__ task_ehit) {
   uint64_t r[N];
 #pragma unroll
