@@ -222,7 +222,7 @@ int fcs_workspace_status(fcs_workspace* ws, fcs_stats* stats, cudaStream_t s);
 
 /* Kernel launches of one replay of the CUDA graph the workspace launched
  * last: a call with config->use_graph != 0, or a host-buffer call replayed in
- * two waves (fcs_simulate_events_host).  The kernel nodes of the captured
+ * waves (fcs_simulate_events_host).  The kernel nodes of the captured
  * graph.  n_kernels: host, written.  FCS_E_ARG when no call on ws has run as a
  * graph. */
 int fcs_workspace_graph_kernels(const fcs_workspace* ws, int64_t* n_kernels);
@@ -291,14 +291,14 @@ int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace
  * When the particle arrays are pinned too, the call is in atomic mode in one
  * launch sequence (wave_events 0), has at least two events and offsets from
  * 0 to n_particles, and the workspace has been sized by an earlier call, it
- * runs as two waves of events on three streams (one CUDA graph, replayed
- * while the arguments stay the same): the second wave's particles are copied
- * in while the first wave computes, and the first wave's results (the first
- * three quarters of the events) move to the host while the second computes.
- * Each wave has its own accumulation rows.
+ * runs as waves of events on three streams (one CUDA graph, replayed while
+ * the arguments stay the same): a wave's particles are copied in while the
+ * wave before it computes, and a wave's results move to the host while the
+ * next computes.  Two waves (3/4 and 1/4 of the events) below 512 events,
+ * three (1/2, 1/4, 1/4) from 512 on.  Each wave has its own accumulation rows.
  * Pageable memory works through device staging and copies.
  * config->sync == 0 asks for a call that does not wait: when the call runs
- * as the two-wave graph above, it returns FCS_OK once the graph is enqueued
+ * as the wave graph above, it returns FCS_OK once the graph is enqueued
  * on s, with *stats zeroed, and fcs_workspace_status(ws, stats, s) waits for
  * it and returns its status and statistics (FCS_E_RANGE when the workspace
  * held fewer hits than the call produced: repeat the call synchronously).

@@ -132,16 +132,22 @@ int current_device(int* dev) {
 }  // namespace
 
 // Host-buffer calls run in waves of events (host_waves).  The shares, in
-// eighths of the call's events: the first wave's results (three quarters of
-// the output) move over the link while the second wave computes, and only the
-// second wave's results move after the last kernel.  Measured on 64 pile-up
-// events: 1.54 ms per call against 1.62-1.64 ms for splits of 2/3, 5/6 and
-// 7/8, and 1.68 ms on one stream.  Three or four waves (5/8 2/8 1/8, 4/8 3/8
-// 1/8, 4/8 2/8 1/8 1/8) took 1.70-1.81 ms: each wave repeats about 0.12 ms of
-// latency-bound kernels.
+// eighths of the call's events: the first waves' results move over the link
+// while the later waves compute, and only the last wave's results move after
+// the last kernel.  Each wave repeats about 0.12 ms of latency-bound kernels,
+// so small calls take two waves and large ones three.  Measured on 64
+// pile-up events (one call at a time): 6/8 2/8 took 1.54 ms per call against
+// 1.62-1.64 ms for splits of 2/3, 5/6 and 7/8, 1.68 ms on one stream, and
+// 1.70-1.81 ms for three or four waves.  On 1024 events (the serving loop of
+// two workspaces): 4/8 2/8 2/8 took 18.4 ms per call against 19.0-19.6 ms for
+// 6/8 2/8, 18.5 ms for 3/8 3/8 2/8 and 18.6 ms for 4/8 4/8.
 constexpr int kHostWaveEighths[] = {6, 2};
+constexpr int kHostWaveEighthsLarge[] = {4, 2, 2};
+constexpr int32_t kHostLargeEvents = 512;  // calls of this many events or more take the large table
 constexpr int kMaxHostWaves = 4;
-static_assert(sizeof(kHostWaveEighths) / sizeof(int) <= kMaxHostWaves, "wave table");
+static_assert(sizeof(kHostWaveEighths) / sizeof(int) <= kMaxHostWaves &&
+                  sizeof(kHostWaveEighthsLarge) / sizeof(int) <= kMaxHostWaves,
+              "wave tables");
 
 struct fcs_workspace {
   int device = -1;
@@ -615,11 +621,15 @@ void* mapped_host(const void* p) {
 int host_wave_bounds(int32_t n, int32_t* bnd) {
   int nw = 0, cum = 0;
   bnd[0] = 0;
-  for (int share : kHostWaveEighths) {
-    cum += share;
-    const int32_t b = (int32_t)std::min<int64_t>(n, ((int64_t)n * cum + 7) / 8);
-    if (b > bnd[nw]) bnd[++nw] = b;
-  }
+  auto take = [&](const int* shares, int count) {
+    for (int q = 0; q < count; ++q) {
+      cum += shares[q];
+      const int32_t b = (int32_t)std::min<int64_t>(n, ((int64_t)n * cum + 7) / 8);
+      if (b > bnd[nw]) bnd[++nw] = b;
+    }
+  };
+  if (n >= kHostLargeEvents) take(kHostWaveEighthsLarge, (int)(sizeof(kHostWaveEighthsLarge) / sizeof(int)));
+  else take(kHostWaveEighths, (int)(sizeof(kHostWaveEighths) / sizeof(int)));
   if (nw == 1 && n >= 2) {
     bnd[1] = (n + 1) / 2;
     bnd[2] = n;

@@ -4,28 +4,36 @@
 // The element count may live in device memory, so the launch needs no host
 // synchronisation.
 //
-// Persistent CTAs take tiles of kScanTile elements in increasing order from
+// Persistent CTAs take tiles of 256 threads x 16 elements (32 for the hit
+// offsets, whose tile map work makes fewer, larger tiles pay) in increasing order from
 // an atomic ticket.  A tile publishes its aggregate, then (after looking back
 // over its predecessors) its inclusive prefix, each as one 64-bit status word
 // [flag:2 | value:62].  A tile waits only on tiles with smaller tickets, which
 // CTAs that are already running hold, so the waits end; each wait is bounded
 // all the same and sets FCS_FLAG_WAIT_TIMEOUT when it gives up.  Input and
 // output move through shared memory (coalesced), each thread scanning
-// kScanItems consecutive elements.  The last CTA to finish resets the ticket
+// its consecutive elements.  The last CTA to finish resets the ticket
 // and the status words it used, so the state is zero again for the next scan.
 //
 // The scan of the tasks' hit counts also writes the tile map: granule g (hits
 // [g kGranule, (g + 1) kGranule)) -> the task holding hit g kGranule, from
 // each task's first hit and count while the tile is at hand (granules below
 // the map's capacity; the hit kernel reports a map too small for the hits).
+#include <atomic>
+
 #include "fcs_internal.cuh"
 
 namespace fcs {
 namespace {
 
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 16;
-constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kScanItems = 16;  // elements per thread: 16, or 32 for the hit offsets
+constexpr int kScanTile = kScanThreads * kScanItems;  // the smallest tile (sizes the status words)
+constexpr int kHitScanItems = 32;
+
+// Dynamic shared memory of a scan with `items` elements per thread: its tile,
+// element j at j + j / items.
+constexpr size_t scan_smem_bytes(int items) { return (size_t)kScanThreads * (items + 1) * sizeof(int64_t); }
 constexpr uint64_t kFlagAgg = 1ull << 62;
 constexpr uint64_t kFlagPrefix = 2ull << 62;
 constexpr uint64_t kValueMask = (1ull << 62) - 1;
@@ -97,12 +105,13 @@ __device__ __forceinline__ int64_t look_back(const uint64_t* status, int64_t t, 
   }
 }
 
-template <typename In, bool GMAP>
+template <typename In, bool GMAP, int ITEMS>
 __global__ void __launch_bounds__(kScanThreads) k_scan(const In* in, int64_t* out, const int64_t* n_dev, int64_t n_host,
                                                      int64_t* total_dst, int base_from_dst, uint64_t* state,
                                                      int64_t cap_tiles, uint32_t* flags, int32_t* gmap,
                                                      int64_t gmap_cap, int64_t mute_tile) {
-  __shared__ int64_t s_tile[kScanTile + kScanTile / kScanItems];  // element j at j + j / kScanItems
+  constexpr int TILE = kScanThreads * ITEMS;
+  extern __shared__ int64_t s_tile[];  // scan_smem_bytes(ITEMS): element j at j + j / ITEMS
   __shared__ int64_t s_warp[kScanThreads / 32];
   __shared__ int64_t s_excl;
   __shared__ unsigned long long s_ticket;
@@ -111,7 +120,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const In* in, int64_t* ou
   unsigned long long* done = ticket + 1;
   uint64_t* status = state + 2;
   const int64_t n = load_n(n_dev, n_host);
-  int64_t n_tiles = (n + kScanTile - 1) / kScanTile;
+  int64_t n_tiles = (n + TILE - 1) / TILE;
   if (n_tiles > cap_tiles) {  // the workspace sizes the state for its arrays: never
     if (threadIdx.x == 0) atomicOr(flags, (uint32_t)FCS_FLAG_WAIT_TIMEOUT);
     n_tiles = 0;
@@ -122,21 +131,17 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const In* in, int64_t* ou
     __syncthreads();
     const int64_t t = (int64_t)s_ticket;
     if (t >= n_tiles) break;
-    const int64_t t0 = t * kScanTile;
+    const int64_t t0 = t * TILE;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
       const int j = k * kScanThreads + threadIdx.x;
       const int64_t i = t0 + j;
-      s_tile[j + j / kScanItems] = i < n ? (int64_t)in[i] : 0;
+      s_tile[j + j / ITEMS] = i < n ? (int64_t)in[i] : 0;
     }
     __syncthreads();
-    int64_t v[kScanItems];
     int64_t sum = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-      v[k] = s_tile[threadIdx.x * (kScanItems + 1) + k];
-      sum += v[k];
-    }
+    for (int k = 0; k < ITEMS; ++k) sum += s_tile[threadIdx.x * (ITEMS + 1) + k];
     int64_t tile_total;
     const int64_t thread_excl = block_excl_scan(sum, s_warp, &tile_total);  // synchronises the block
     if (warp == 0) {
@@ -159,32 +164,33 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const In* in, int64_t* ou
     __syncthreads();
     int64_t run = s_excl + thread_excl;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-      s_tile[threadIdx.x * (kScanItems + 1) + k] = run;
-      run += v[k];
+    for (int k = 0; k < ITEMS; ++k) {  // the thread's inputs, still in the tile buffer
+      const int64_t x = s_tile[threadIdx.x * (ITEMS + 1) + k];
+      s_tile[threadIdx.x * (ITEMS + 1) + k] = run;
+      run += x;
     }
     __syncthreads();
     if constexpr (GMAP) {
 #pragma unroll 1
-      for (int k = 0; k < kScanItems; ++k) {
+      for (int k = 0; k < ITEMS; ++k) {
         const int j = k * kScanThreads + threadIdx.x;
         const int64_t i = t0 + j;
         if (i < n) {
-          const int64_t b = s_tile[j + j / kScanItems];
+          const int64_t b = s_tile[j + j / ITEMS];
           out[i] = b;
           // task i holds hits [b, e): e is the next task's first hit (the
           // tile's end for its last task)
           const int jn = j + 1;
-          const int64_t e = (jn < kScanTile && i + 1 < n) ? s_tile[jn + jn / kScanItems] : s_excl + tile_total;
+          const int64_t e = (jn < TILE && i + 1 < n) ? s_tile[jn + jn / ITEMS] : s_excl + tile_total;
           for (int64_t g = (b + kGranule - 1) / kGranule; g * kGranule < e && g < gmap_cap; ++g) gmap[g] = (int32_t)i;
         }
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < kScanItems; ++k) {
+      for (int k = 0; k < ITEMS; ++k) {
         const int j = k * kScanThreads + threadIdx.x;
         const int64_t i = t0 + j;
-        if (i < n) out[i] = s_tile[j + j / kScanItems];
+        if (i < n) out[i] = s_tile[j + j / ITEMS];
       }
     }
     __syncthreads();  // the tile buffer and s_ticket are reused
@@ -217,12 +223,27 @@ int64_t scan_state_words(int64_t max_elements) {
 // (a running total in device memory) else 0.  Writes base + sum to
 // *total_dst when total_dst is non-NULL.  in and out may alias (a tile is
 // read whole before it is written).
-template <typename In, bool GMAP = false>
+template <typename In, bool GMAP = false, int ITEMS = kScanItems>
 static cudaError_t launch_scan(const In* in, int64_t* out, const int64_t* n_dev, int64_t n_host,
                                int64_t* total_dst, int64_t base_from_dst, ScanTmp tmp, cudaStream_t s,
                                int32_t* gmap = nullptr, int64_t gmap_cap = 0) {
-  k_scan<In, GMAP><<<tmp.grid, kScanThreads, 0, s>>>(in, out, n_dev, n_host, total_dst, base_from_dst ? 1 : 0,
-                                                     tmp.state, tmp.cap_tiles, tmp.flags, gmap, gmap_cap, -1);
+  constexpr size_t smem = scan_smem_bytes(ITEMS);
+  if constexpr (smem > 48 * 1024) {  // above the default limit: opt in, once per device
+    constexpr int kMaxDevices = 64;
+    static std::atomic<bool> opted[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = -1;
+    if (dev < 0 || !opted[dev].load(std::memory_order_acquire)) {
+      const cudaError_t e = cudaFuncSetAttribute(k_scan<In, GMAP, ITEMS>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      if (dev >= 0) opted[dev].store(true, std::memory_order_release);
+    }
+  }
+  // the status words are sized for kScanTile-element tiles; larger tiles need fewer
+  k_scan<In, GMAP, ITEMS><<<tmp.grid, kScanThreads, smem, s>>>(in, out, n_dev, n_host, total_dst,
+                                                              base_from_dst ? 1 : 0, tmp.state, tmp.cap_tiles,
+                                                              tmp.flags, gmap, gmap_cap, -1);
   return cudaGetLastError();
 }
 
@@ -252,8 +273,8 @@ cudaError_t scan_wait_selftest(uint32_t* flags_out, float* ms, cudaStream_t s) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if ((e = cudaEventCreate(&e0)) == cudaSuccess && (e = cudaEventCreate(&e1)) == cudaSuccess &&
       (e = cudaMemsetAsync(buf, 0, bytes, s)) == cudaSuccess && (e = cudaEventRecord(e0, s)) == cudaSuccess) {
-    k_scan<int64_t, false><<<4, kScanThreads, 0, s>>>(in, out, nullptr, n, nullptr, 0, state, n_tiles, flags, nullptr,
-                                                      0, 1);
+    k_scan<int64_t, false, kScanItems><<<4, kScanThreads, scan_smem_bytes(kScanItems), s>>>(
+        in, out, nullptr, n, nullptr, 0, state, n_tiles, flags, nullptr, 0, 1);
     if ((e = cudaGetLastError()) == cudaSuccess && (e = cudaEventRecord(e1, s)) == cudaSuccess &&
         (e = cudaMemcpyAsync(flags_out, flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) == cudaSuccess &&
         (e = cudaStreamSynchronize(s)) == cudaSuccess)
@@ -267,7 +288,7 @@ cudaError_t scan_wait_selftest(uint32_t* flags_out, float* ms, cudaStream_t s) {
 
 cudaError_t launch_scan_hits(const int32_t* tn, int64_t* th, const int64_t* n_tasks, int64_t* n_hits, int32_t* gmap,
                              int64_t gmap_cap, ScanTmp tmp, cudaStream_t s) {
-  return launch_scan<int32_t, true>(tn, th, n_tasks, 0, n_hits, 0, tmp, s, gmap, gmap_cap);
+  return launch_scan<int32_t, true, kHitScanItems>(tn, th, n_tasks, 0, n_hits, 0, tmp, s, gmap, gmap_cap);
 }
 
 }  // namespace fcs

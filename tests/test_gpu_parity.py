@@ -325,7 +325,7 @@ def test_host_entry_point_pinned_outputs(sim):
 def test_host_entry_point_two_waves(sim):
     """Pinned inputs and outputs: after a sizing call the host entry runs as two
     waves on three streams (copies in, compute and results out overlapped),
-    one graph of 2 + 2 x 13 kernels; its cells match the deterministic
+    one graph of 2 + 2 x KERNELS_PER_RANGE kernels; its cells match the deterministic
     device call (atomic tolerance) and its ids and offsets match exactly, for
     an odd event count and over repeated calls."""
     parts = synth.pileup(seed=17, n_events=5, mu_pu=30)
@@ -354,6 +354,39 @@ def test_host_entry_point_two_waves(sim):
         assert (ids.numpy()[nnz:] == -1).all()
         if call > 0:  # the first call may size the workspace synchronously
             assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 2 * KERNELS_PER_RANGE
+
+
+def test_host_entry_point_three_waves(sim):
+    """A host-buffer call of 512 events or more runs as three waves (4/8, 2/8
+    and 2/8 of the events): one graph of 2 + 3 x KERNELS_PER_RANGE kernels,
+    whose ids and offsets equal the deterministic device call's and whose
+    cells lie within the atomic tolerance, over repeated calls."""
+    n_ev = 512
+    parts = synth.pileup(seed=23, n_events=n_ev, mu_pu=1, per_collision=6, hs_particles=6)
+    ref = sim.simulate(sim.to_device(parts), 8, first_event=5, mode=fcs.MODE_DETERMINISTIC)
+    nnz = ref["stats"]["n_nonzero"]
+    cap = nnz + 16
+    pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(parts, k))).pin_memory()
+           for k in ("type", "E", "eta", "phi", "event_offsets")}
+    ids = torch.full((cap,), -1, dtype=torch.int32).pin_memory()
+    E = torch.zeros(cap, dtype=torch.float32).pin_memory()
+    off = torch.zeros(n_ev + 1, dtype=torch.int64).pin_memory()
+    cfg = fcs.make_config()
+    ref_ids = ref["cell_ids"][:nnz].cpu().numpy()
+    ref_E = ref["cell_E"][:nnz].cpu().numpy().astype(np.float64)
+    for call in range(3):
+        ids.fill_(-1)
+        E.zero_()
+        rc, st = fcs.fcs_simulate_events_host(sim.geo, sim.prm, sim.ws, pin["type"].numpy(), pin["E"].numpy(),
+                                              pin["eta"].numpy(), pin["phi"].numpy(), pin["event_offsets"].numpy(),
+                                              8, 5, cfg, ids.numpy(), E.numpy(), off.numpy())
+        assert rc == 0 and st.n_nonzero == nnz and st.n_hits == ref["stats"]["n_hits"]
+        assert np.array_equal(off.numpy(), ref["event_offsets"].cpu().numpy())
+        assert np.array_equal(ids.numpy()[:nnz], ref_ids)
+        err = np.abs(E.numpy()[:nnz].astype(np.float64) - ref_E)
+        assert (err <= RTOL * np.abs(ref_E) + ATOL).all()
+        if call > 0:  # the first call may size the workspace synchronously
+            assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 3 * KERNELS_PER_RANGE
 
 
 @pytest.mark.parametrize("layout", ["two_events", "empty_first_wave"])
