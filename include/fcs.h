@@ -295,7 +295,7 @@ int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace
  * the arguments stay the same): a wave's particles are copied in while the
  * wave before it computes, and a wave's results move to the host while the
  * next computes.  Two waves (3/4 and 1/4 of the events) below 512 events,
- * three (1/2, 1/4, 1/4) from 512 on.  Each wave has its own accumulation rows.
+ * four (1/4 each) from 512 on.  Each wave has its own accumulation rows.
  * Pageable memory works through device staging and copies.
  * config->sync == 0 asks for a call that does not wait: when the call runs
  * as the wave graph above, it returns FCS_OK once the graph is enqueued

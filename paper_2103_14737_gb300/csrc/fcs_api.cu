@@ -135,14 +135,15 @@ int current_device(int* dev) {
 // eighths of the call's events: the first waves' results move over the link
 // while the later waves compute, and only the last wave's results move after
 // the last kernel.  Each wave repeats about 0.12 ms of latency-bound kernels,
-// so small calls take two waves and large ones three.  Measured on 64
+// so small calls take two waves and large ones four.  Measured on 64
 // pile-up events (one call at a time): 6/8 2/8 took 1.54 ms per call against
 // 1.62-1.64 ms for splits of 2/3, 5/6 and 7/8, 1.68 ms on one stream, and
 // 1.70-1.81 ms for three or four waves.  On 1024 events (the serving loop of
-// two workspaces): 4/8 2/8 2/8 took 18.4 ms per call against 19.0-19.6 ms for
-// 6/8 2/8, 18.5 ms for 3/8 3/8 2/8 and 18.6 ms for 4/8 4/8.
+// two workspaces, the compaction on a third of the SMs): four waves of 2/8
+// took 17.7 ms per call against 18.4 ms for 4/8 2/8 2/8, 19.0-19.6 ms for
+// 6/8 2/8 and 18.2-18.8 ms for eight waves of 1/8.
 constexpr int kHostWaveEighths[] = {6, 2};
-constexpr int kHostWaveEighthsLarge[] = {4, 2, 2};
+constexpr int kHostWaveEighthsLarge[] = {2, 2, 2, 2};
 constexpr int32_t kHostLargeEvents = 512;  // calls of this many events or more take the large table
 constexpr int kMaxHostWaves = 4;
 static_assert(sizeof(kHostWaveEighths) / sizeof(int) <= kMaxHostWaves &&
@@ -676,9 +677,11 @@ int enqueue_waves(const CallArgs& a, const int32_t* type, const float* E, const 
     k_range_end<<<1, 1, 0, cs>>>(ws->d_sizes);
     FCS_CUDA(cudaEventRecord(ws->pev[1 + nw + k], cs));
     FCS_CUDA(cudaStreamWaitEvent(s_out, ws->pev[1 + nw + k], 0));
-    // the compaction runs beside the next wave on half the SMs: its stores
-    // over the CPU-GPU link need few CTAs to keep the link busy
-    FCS_TRY(enqueue_range_reduce(a, w, bnd[k], bnd[k + 1] - bnd[k], key_task_bits, tmp2, s_out, ws->num_sms / 2));
+    // the compaction runs beside the next wave on a third of the SMs: its
+    // stores over the CPU-GPU link need few CTAs to keep the link busy, and
+    // the next wave's kernels keep the rest (a quarter starved the link on
+    // small calls; half slowed the next wave on large ones)
+    FCS_TRY(enqueue_range_reduce(a, w, bnd[k], bnd[k + 1] - bnd[k], key_task_bits, tmp2, s_out, ws->num_sms / 3));
   }
   k_call_end<<<1, 1, 0, s_out>>>(ws->d_sizes, a.event_offsets_out, a.n_events, a.capacity, a.cell_ids ? 1 : 0);
   FCS_CUDA(cudaEventRecord(ws->pev[1 + 2 * nw], s_out));

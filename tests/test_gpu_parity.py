@@ -356,9 +356,9 @@ def test_host_entry_point_two_waves(sim):
             assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 2 * KERNELS_PER_RANGE
 
 
-def test_host_entry_point_three_waves(sim):
-    """A host-buffer call of 512 events or more runs as three waves (4/8, 2/8
-    and 2/8 of the events): one graph of 2 + 3 x KERNELS_PER_RANGE kernels,
+def test_host_entry_point_four_waves(sim):
+    """A host-buffer call of 512 events or more runs as four waves (2/8 of the
+    events each): one graph of 2 + 4 x KERNELS_PER_RANGE kernels,
     whose ids and offsets equal the deterministic device call's and whose
     cells lie within the atomic tolerance, over repeated calls."""
     n_ev = 512
@@ -386,7 +386,7 @@ def test_host_entry_point_three_waves(sim):
         err = np.abs(E.numpy()[:nnz].astype(np.float64) - ref_E)
         assert (err <= RTOL * np.abs(ref_E) + ATOL).all()
         if call > 0:  # the first call may size the workspace synchronously
-            assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 3 * KERNELS_PER_RANGE
+            assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 4 * KERNELS_PER_RANGE
 
 
 @pytest.mark.parametrize("layout", ["two_events", "empty_first_wave"])
