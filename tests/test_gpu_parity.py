@@ -210,27 +210,6 @@ def test_pileup_events_parity(sim, ogeo, oprm):
     assert got["stats"]["n_poisson_fp64"] < 0.01 * ref.n_tasks
 
 
-def test_full_batch_sampled(sim, ogeo, oprm):
-    """The benchmark batch (64 pile-up events, one batched launch sequence);
-    sampled events checked against the oracle, every event's energy sum
-    checked against its tasks."""
-    parts = synth.workload("pileup64", seed=1)
-    d = sim.to_device(parts)
-    got = sim.simulate(d, 1, dense=True, debug_tasks=parts.n * 24)
-    torch.cuda.synchronize()
-    cells = got["cells"].cpu().numpy().astype(np.float64)
-    tev = got["task_event"].cpu().numpy()
-    n = got["task_n"].cpu().numpy().astype(np.float64)
-    eh = got["task_Ehit"].cpu().numpy().astype(np.float64)
-    k = got["stats"]["n_tasks"]
-    per_event = np.bincount(tev[:k], weights=n[:k] * eh[:k], minlength=64)
-    assert np.allclose(cells.sum(1), per_event, rtol=1e-5)
-    for e in (0, 37, 63):
-        ref = O.simulate(ogeo, oprm, parts.event(e), seed=1, first_event=e, tasks=False)
-        err = np.abs(cells[e] - ref.cells64[0])
-        assert not (err > RTOL * np.abs(ref.cells64[0]) + ATOL).any()
-
-
 def test_empty_events_and_zero_events(sim, ogeo, oprm):
     p = synth.ttbar_like(seed=2, n_events=3, n=50)
     # make event 1 empty
