@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(kCThreads) k_compact_write(
           v[2 * q + 1] = acc_to_f32(a[q].y);
         }
         // re-zero only what is not zero (the padding past n_cells stays zero):
-        // rows are mostly zero, and a store of zeros would still dirty the line
+        // many row cells are never hit, and a store of zeros would still dirty
+        // the line
         if (acc_nonzero(a[q].x) || acc_nonzero(a[q].y)) src[q] = z;
       }
     }
