@@ -115,11 +115,13 @@ __device__ __noinline__ int64_t poisson_draw(double mu, uint32_t layer, uint32_t
 //     1/alpha within 2^-22 and v_r within 2^-21 absolute.  The quotients
 //     2a/us and a/us^2 of an iteration are within 2^-20 relative.
 //   PTRS acceptance test, d = (log V + log 1/alpha - log(a/us^2 + b))
-//     - (-mu + k log mu - log k!): the left side is known to
-//     1.875 2^-20 + 2^-22 (|l1| + |l2| + |l3|), the right side (log mu within
-//     1 ulp, log k! a correctly rounded table entry, two sums) to
-//     2^-23 (2.5 |k log mu| + |log k!| + mu).  Used: 2^-18 + 2^-20 times the sum
-//     of all six magnitudes (at least twice each term of the two).
+//     - (-mu + k log mu - log k!): its three logs take __logf, within
+//     2^-21.41 absolute on [1/2, 2] and 3 ulp (3 2^-23 relative) elsewhere,
+//     as documented, so the left side is known to
+//     3.0 2^-20 + 1.25 2^-20 (|l1| + |l2| + |l3|); the right side (log mu
+//     within 1 ulp, log k! a correctly rounded table entry, two sums) to
+//     2^-23 (2.5 |k log mu| + |log k!| + mu).  Used: 2^-18 + 2^-19 (|l1| + |l2|
+//     + |l3|) + 2^-20 (|k log mu| + |log k!| + mu), above each term.
 //   uniforms: exact integers rounded once to FP32 (relative 2^-24).
 constexpr float kPtrsFastMaxMu = 4096.0f;  // larger means go to FP64 (counts of ~1e4 lose FP32 headroom)
 
@@ -197,10 +199,11 @@ __device__ __forceinline__ int64_t ptrs_iter32(float mu, const PtrsConst32& c, u
   if (!k_sure) return -2;
   const int32_t ki = (int32_t)kf;
   if (ki >= c.n_lfact) return -2;  // past the log k! table (never below kPtrsFastMaxMu): FP64
-  const float l1 = logf(Vf), l2 = logf(c.invalpha), l3 = logf(__fdividef(c.a, usf * usf) + c.b);
+  const float l1 = __logf(Vf), l2 = __logf(c.invalpha), l3 = __logf(__fdividef(c.a, usf * usf) + c.b);
   const float kl = kf * c.loglam, lg = __ldg(c.lfact + ki);
   const float d = (l1 + l2 - l3) - ((-mu + kl) - lg);
-  const float bd = fmaf(fabsf(l1) + fabsf(l2) + fabsf(l3) + fabsf(kl) + fabsf(lg) + mu, 0x1p-20f, 0x1p-18f);
+  const float bd = fmaf(fabsf(l1) + fabsf(l2) + fabsf(l3), 0x1p-19f,
+                        fmaf(fabsf(kl) + fabsf(lg) + mu, 0x1p-20f, 0x1p-18f));
   if (d < -bd) return (int64_t)ki;
   if (d > bd) return -1;
   return -2;
