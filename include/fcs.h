@@ -61,7 +61,8 @@ enum fcs_device_flag {
   FCS_FLAG_BAD_PARTICLE = 1u << 0,  /* type out of range, E <= 0 or non-finite, eta/phi non-finite */
   FCS_FLAG_HIT_CAPACITY = 1u << 1,  /* more hits than the workspace was sized for (sync == 0) */
   FCS_FLAG_OUT_CAPACITY = 1u << 2,  /* more non-zero cells than `capacity` */
-  FCS_FLAG_KEY_BITS = 1u << 3,      /* deterministic mode: (cell, task) keys need > 63 bits */
+  FCS_FLAG_KEY_BITS = 1u << 3,      /* deterministic mode: (cell, task) keys need > 63 bits, or an
+                                       event holds 2^27 tasks or more */
   FCS_FLAG_RECHECK_SPILL = 1u << 4, /* informational: FP64 recheck queue full, done inline */
   FCS_FLAG_BAD_OFFSETS = 1u << 5,   /* event_offsets not within [0, n_particles] or decreasing */
   FCS_FLAG_WAIT_TIMEOUT = 1u << 6   /* a bounded device wait gave up: the call's results are invalid */

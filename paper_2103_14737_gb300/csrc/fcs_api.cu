@@ -309,7 +309,7 @@ int ws_reserve_static(fcs_workspace* ws, const fcs_geo* geo, int64_t P, int32_t 
   FCS_TRY(grow(&ws->scan_state, &ws->ss_cap,
                scan_state_words(std::max({Pc * NL, (int64_t)std::max(rows, 1) * stride, chunks})), true));
   if (mode == FCS_MODE_DETERMINISTIC)
-    FCS_TRY(grow(&ws->cell_off, &ws->co_cells_cap, (int64_t)std::max(rows, 1) * stride));
+    FCS_TRY(grow(&ws->cell_off, &ws->co_cells_cap, (int64_t)std::max(rows, 1) * (stride + 1)));
   return FCS_OK;
 }
 
@@ -401,7 +401,8 @@ int status_from(const Sizes& s, fcs_stats* st) {
   if (s.flags & FCS_FLAG_HIT_CAPACITY)
     return set_err(FCS_E_RANGE, "the workspace holds fewer hits than the call produced (%lld); reserve more",
                    (long long)s.hit_base);
-  if (s.flags & FCS_FLAG_KEY_BITS) return set_err(FCS_E_RANGE, "deterministic keys exceed 63 bits");
+  if (s.flags & FCS_FLAG_KEY_BITS)
+    return set_err(FCS_E_RANGE, "deterministic mode: keys exceed 63 bits, or an event holds 2^27 tasks or more");
   if (s.flags & FCS_FLAG_OUT_CAPACITY)
     return set_err(FCS_E_RANGE, "output capacity too small: %lld non-zero cells", (long long)s.nnz_total);
   return ok();
@@ -488,7 +489,7 @@ int enqueue_range_hits(const CallArgs& a, int32_t ev_lo, int32_t ev_hi, int32_t 
     FCS_TRY(ws_reserve_hits(ws, ws->h_sizes->n_hits, a.cfg.mode));
     w = view();
   }
-  FCS_CUDA(launch_task_finish(w, a.dbg, det, (sync_size || a.cfg.batched == 2) ? 1 : 0,
+  FCS_CUDA(launch_task_finish(w, a.dbg, (sync_size || a.cfg.batched == 2) ? 1 : 0,
                               a.n_particles * a.geo->d.n_layers, L));
   if (tev) FCS_CUDA(record_stage(tev[1], a.s));
   if (a.cfg.batched == 2) {
@@ -529,7 +530,7 @@ int enqueue_range_reduce(const CallArgs& a, WsDev w, int32_t ev_lo, int32_t rows
   fcs_workspace* ws = a.ws;
   const Launch L{s, ws->num_sms};
   if (a.cfg.mode == FCS_MODE_DETERMINISTIC)
-    FCS_CUDA(launch_det_reduce(a.geo->d, w, rows, key_task_bits, ws->cell_off, tmp, L));
+    FCS_CUDA(launch_det_reduce(a.geo->d, w, rows, key_task_bits, ws->cell_off, a.parts.event_offsets, ev_lo, tmp, L));
   FCS_CUDA(launch_compact(a.geo->d, w, rows, ev_lo, ws->chunk_counts, ws->chunk_offsets, tmp, a.cells_out,
                           a.cell_ids, a.cell_E, a.event_offsets_out, a.capacity, max_ctas, L));
   return FCS_OK;
@@ -1505,7 +1506,7 @@ int fcs_simulate_backward(const fcs_geo* geo, const fcs_params* prm, fcs_workspa
       FCS_TRY(ws_reserve_hits(ws, ws->h_sizes->n_hits, FCS_MODE_ATOMIC));
       w = ws->view();
     }
-    FCS_CUDA(launch_task_finish(w, nullptr, 0, cfg.sync ? 1 : 0, n_particles * geo->d.n_layers, L));
+    FCS_CUDA(launch_task_finish(w, nullptr, cfg.sync ? 1 : 0, n_particles * geo->d.n_layers, L));
     const float* g = dL_dcells + (int64_t)lo * geo->d.n_cells;
     FCS_CUDA(launch_hits_grad(geo->d, prm->d, w, lo, k0, k1, first_event, hc, g, ws->grad_acc, ws->grad_touched, L));
     FCS_CUDA(launch_recheck_grad(geo->d, prm->d, w, lo, k0, k1, first_event, g, ws->grad_acc, ws->grad_touched, L));

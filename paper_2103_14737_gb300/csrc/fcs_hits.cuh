@@ -506,6 +506,8 @@ __global__ void __launch_bounds__(BLOCK, MODE == kModeAtomic ? 1280 / BLOCK : 0)
     const int32_t t0 = kp.static_tiles ? kp.t_last : w.gmap[h0 / kGranule];
     const int32_t t1 = (h0 + TILE < H && !kp.static_tiles) ? w.gmap[(h0 + TILE) / kGranule] : (int32_t)T_last;
     const int nt = t1 - t0 + 1;
+    // (deterministic mode: the tile that holds a task's first hit writes the
+    // task's hit energy for the fold)
     if (nt <= kSmemTasks) {
       // stage the tile's tasks and mark where each starts
       for (int j = threadIdx.x; j < nt; j += BLOCK) {
@@ -513,11 +515,17 @@ __global__ void __launch_bounds__(BLOCK, MODE == kModeAtomic ? 1280 / BLOCK : 0)
         const int64_t s = q.rel;
         s_task[j] = q;
         if (j > 0 && s < TILE) s_owner[s] = (int16_t)j;
+        if constexpr (DET) {
+          if (s >= 0 && s < TILE) w.tehit[t0 + j] = q.Ehit;
+        }
       }
     } else {
-      for (int j = threadIdx.x + 1; j < nt; j += BLOCK) {
+      for (int j = threadIdx.x; j < nt; j += BLOCK) {
         const int64_t s = w.th[t0 + j] - h0;
-        if (s < TILE) s_owner[s] = (int16_t)j;
+        if (j > 0 && s < TILE) s_owner[s] = (int16_t)j;
+        if constexpr (DET) {
+          if (s >= 0 && s < TILE) w.tehit[t0 + j] = __fdiv_rn(w.tasks[t0 + j].El, (float)w.tn[t0 + j]);
+        }
       }
     }
     __syncthreads();

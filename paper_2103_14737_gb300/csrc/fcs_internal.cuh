@@ -128,7 +128,8 @@ struct WsDev {
   int64_t pcap;        // particle capacity
   TaskRec* tasks;      // [task_cap]
   float* tehit;        // [task_cap] deterministic mode: each task's hit energy, written by the
-                       // task finish (a compact copy for the fold)
+                       // hit kernel's tile that holds the task's first hit (a compact copy
+                       // for the fold)
   int32_t* tn;         // [task_cap] hits of each task
   int64_t* th;         // [task_cap] first hit of each task (exclusive scan of tn)
   int32_t* pdefer;     // [pdefer_cap] tasks whose draw is redone in FP64: inversion draws from the
@@ -281,7 +282,7 @@ cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_par
                                int32_t ev_lo, int32_t ev_hi, uint32_t k0, uint32_t k1,
                                int64_t first_event, WsDev w, ScanTmp tmp, int64_t n_part_max,
                                int energy_interp, const Launch& L);
-cudaError_t launch_task_finish(WsDev w, const fcs_debug* dbg, int det, int fill_map, int64_t n_task_max,
+cudaError_t launch_task_finish(WsDev w, const fcs_debug* dbg, int fill_map, int64_t n_task_max,
                                const Launch& L);
 
 // Draws i = 0..n-1 with means mu (device) by the FP32 path and by the FP64
@@ -339,9 +340,10 @@ cudaError_t launch_compact(const GeoDev& g, WsDev w, int32_t rows, int32_t ev_lo
 int64_t compact_chunks(int32_t n_cells, int32_t rows);
 // Deterministic mode: the records of the range (hit slots) grouped by cell
 // and folded into the accumulation rows, whose uint32 record counters the
-// hit kernel filled.  cell_off: [rows * acc_stride] scratch.  The compaction
-// then runs as in atomic mode.
+// hit kernel filled.  cell_off: [rows * (acc_stride + 1)] scratch (the cells'
+// segments, then each event's first task); event_offsets and ev_lo: the
+// range's events.  The compaction then runs as in atomic mode.
 cudaError_t launch_det_reduce(const GeoDev& g, WsDev w, int32_t rows, int key_task_bits, int64_t* cell_off,
-                              ScanTmp tmp, const Launch& L);
+                              const int64_t* event_offsets, int32_t ev_lo, ScanTmp tmp, const Launch& L);
 
 }  // namespace fcs

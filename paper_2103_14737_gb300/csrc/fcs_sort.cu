@@ -15,7 +15,11 @@
 //   1. an exclusive scan of the counters gives each cell its segment of the
 //      record array;
 //   2. scatter: every record takes a place in its cell's segment; the
-//      counter, counted down, hands out the places and ends at zero;
+//      counter, counted down, hands out the places and ends at zero.  In the
+//      segment the cell is implied and a record shrinks to 32 bits:
+//      [ task - first task of the cell's event (27 bits) | count - 1 ]
+//      (a row holds one event, and its tasks are consecutive), so the
+//      segments take half the bytes and sort as 32-bit keys;
 //   3. fold: one thread per cell sorts its segment by (task, count) - a copy
 //      in registers with a sorting network up to 16 records, a thread-local
 //      copy by insertion up to 32, the three classes in kernels of their
@@ -34,14 +38,32 @@ namespace {
 
 constexpr uint64_t kEmpty = ~0ull;
 constexpr int kInsertionMax = 32;  // segments sorted by insertion up to here, heapsort beyond
+constexpr int kRelTaskBits = 32 - kRecordCountBits;  // a segment record's task, relative to its event's first
+constexpr uint32_t kCountMask = (1u << kRecordCountBits) - 1u;
+
+// The first task of each event (row) of the range, from the per-particle task
+// offsets: base[r] = poff[first particle of event ev_lo + r].
+__global__ void k_det_bases(const int64_t* __restrict__ event_offsets, int32_t ev_lo, int32_t rows,
+                            const int64_t* __restrict__ poff, const Sizes* sz, int64_t* __restrict__ base) {
+  const int64_t n_part = sz->n_part, n_tasks = sz->n_tasks;
+  const int64_t p0 = event_offsets[ev_lo];
+  for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+    const int64_t li = event_offsets[ev_lo + r] - p0;
+    base[r] = (li >= 0 && li < n_part) ? poff[li] : n_tasks;  // events without particles take no records
+  }
+}
 
 // A range that outgrew the workspace (FCS_FLAG_HIT_CAPACITY) has slots the
 // hit kernel did not write: the scatter and the fold then do nothing (the
 // call reports the overflow; the compaction still re-zeroes the rows).
-__global__ void __launch_bounds__(256) k_det_scatter(const uint64_t* __restrict__ slots, const Sizes* sz, int64_t cap,
-                                                     int cell_shift, uint32_t* __restrict__ counters,
+// A record whose task lies 2^27 or more past its event's first sets
+// FCS_FLAG_KEY_BITS and is dropped (the call then fails).
+__global__ void __launch_bounds__(256) k_det_scatter(const uint64_t* __restrict__ slots, Sizes* sz, int64_t cap,
+                                                     int cell_shift, uint64_t task_mask,
+                                                     uint32_t* __restrict__ counters,
                                                      const int64_t* __restrict__ cell_off, int64_t n_cells_all,
-                                                     uint64_t* __restrict__ out) {
+                                                     uint32_t acc_stride, const int64_t* __restrict__ base,
+                                                     uint32_t* __restrict__ out) {
   if (sz->flags & FCS_FLAG_HIT_CAPACITY) return;
   const int64_t n = min(sz->n_slots, cap);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -54,19 +76,24 @@ __global__ void __launch_bounds__(256) k_det_scatter(const uint64_t* __restrict_
       if (k[j] == kEmpty) continue;
       const uint64_t c = k[j] >> cell_shift;
       if (c >= (uint64_t)n_cells_all) continue;  // cannot happen for records of this range
+      const int64_t rel = (int64_t)((k[j] >> kRecordCountBits) & task_mask) - base[(uint32_t)c / acc_stride];
       const int64_t pos = cell_off[c] + (int64_t)atomicSub(counters + c, 1u) - 1;
-      if (pos >= 0 && pos < cap) out[pos] = k[j];
+      if (rel < 0 || rel >= ((int64_t)1 << kRelTaskBits)) {
+        atomicOr(&sz->flags, (uint32_t)FCS_FLAG_KEY_BITS);
+        continue;
+      }
+      if (pos >= 0 && pos < cap) out[pos] = ((uint32_t)rel << kRecordCountBits) | ((uint32_t)k[j] & kCountMask);
     }
   }
 }
 
-__device__ __forceinline__ void sift_down(uint64_t* a, int64_t root, int64_t n) {
+__device__ __forceinline__ void sift_down(uint32_t* a, int64_t root, int64_t n) {
   while (true) {
     int64_t child = 2 * root + 1;
     if (child >= n) return;
     if (child + 1 < n && a[child + 1] > a[child]) ++child;
     if (a[root] >= a[child]) return;
-    const uint64_t t = a[root];
+    const uint32_t t = a[root];
     a[root] = a[child];
     a[child] = t;
     root = child;
@@ -74,10 +101,10 @@ __device__ __forceinline__ void sift_down(uint64_t* a, int64_t root, int64_t n) 
 }
 
 // Ascending sort of a[0, n) in place.
-__device__ __noinline__ void sort_segment(uint64_t* a, int64_t n) {
+__device__ __noinline__ void sort_segment(uint32_t* a, int64_t n) {
   if (n <= kInsertionMax) {
     for (int64_t i = 1; i < n; ++i) {
-      const uint64_t v = a[i];
+      const uint32_t v = a[i];
       int64_t j = i - 1;
       while (j >= 0 && a[j] > v) {
         a[j + 1] = a[j];
@@ -89,7 +116,7 @@ __device__ __noinline__ void sort_segment(uint64_t* a, int64_t n) {
   }
   for (int64_t r = n / 2 - 1; r >= 0; --r) sift_down(a, r, n);
   for (int64_t e = n - 1; e > 0; --e) {
-    const uint64_t t = a[0];
+    const uint32_t t = a[0];
     a[0] = a[e];
     a[e] = t;
     sift_down(a, 0, e);
@@ -102,31 +129,45 @@ __device__ __noinline__ void sort_segment(uint64_t* a, int64_t n) {
 // from 64-bit integers, like float-to-double ones, run on the narrow FP64 pipe.
 struct Fold {
   float E = 0.0f;
-  int64_t prev_task = -1;
+  float e = 0.0f;  // hit energy of prev_task
+  int64_t prev_task = -1;  // relative to the event's first task
   uint32_t cnt = 0;
-  __device__ __forceinline__ void add(uint64_t k, uint64_t task_mask, const float* __restrict__ task_ehit) {
-    const int64_t task = (int64_t)((k >> kRecordCountBits) & task_mask);
-    const uint32_t c = (uint32_t)(k & ((1u << kRecordCountBits) - 1u)) + 1u;
+  // segment record k, whose task's hit energy is ek (loaded ahead by the caller)
+  __device__ __forceinline__ void add(uint32_t k, float ek) {
+    const int64_t task = (int64_t)(k >> kRecordCountBits);
+    const uint32_t c = (k & kCountMask) + 1u;
     if (task != prev_task) {
-      if (prev_task >= 0) E = __fadd_rn(E, __fmul_rn((float)cnt, task_ehit[prev_task]));
+      if (prev_task >= 0) E = __fadd_rn(E, __fmul_rn((float)cnt, e));
       prev_task = task;
+      e = ek;
+      cnt = 0;
+    }
+    cnt += c;
+  }
+  // segment record k, the task's hit energy read from the event's part of
+  // the table when the task changes
+  __device__ __forceinline__ void add(uint32_t k, const float* __restrict__ ev_ehit) {
+    const int64_t task = (int64_t)(k >> kRecordCountBits);
+    const uint32_t c = (k & kCountMask) + 1u;
+    if (task != prev_task) {
+      if (prev_task >= 0) E = __fadd_rn(E, __fmul_rn((float)cnt, e));
+      prev_task = task;
+      e = ev_ehit[task];
       cnt = 0;
     }
     cnt += c;
   }
   // the folded float, as the FP64 row value the compaction reads (an exact
   // widening done with integer operations)
-  __device__ __forceinline__ double result(const float* __restrict__ task_ehit) const {
-    return f32_to_f64_bits(__fadd_rn(E, __fmul_rn((float)cnt, task_ehit[prev_task])));
-  }
+  __device__ __forceinline__ double result() const { return f32_to_f64_bits(__fadd_rn(E, __fmul_rn((float)cnt, e))); }
 };
 
 // Ascending sort of N keys in registers (N a power of two): Batcher's
 // odd-even merge sort (Batcher 1968; 19 compare-exchanges for 8 keys, 63 for
 // 16), every index a compile-time constant; absent records are all ones and
 // sort last.
-__device__ __forceinline__ void cmpx(uint64_t& x, uint64_t& y) {
-  const uint64_t lo = x < y ? x : y, hi = x < y ? y : x;
+__device__ __forceinline__ void cmpx(uint32_t& x, uint32_t& y) {
+  const uint32_t lo = min(x, y), hi = max(x, y);
   x = lo;
   y = hi;
 }
@@ -134,7 +175,7 @@ __device__ __forceinline__ void cmpx(uint64_t& x, uint64_t& y) {
 // Merge of the sorted halves of r[LO, LO + N) taken with stride R: the odd
 // and even subsequences recursively, then neighbours R apart.
 template <int LO, int N, int R, int M>
-__device__ __forceinline__ void oe_merge(uint64_t (&r)[M]) {
+__device__ __forceinline__ void oe_merge(uint32_t (&r)[M]) {
   constexpr int S = 2 * R;
   if constexpr (S < N) {
     oe_merge<LO, N, S>(r);
@@ -146,7 +187,7 @@ __device__ __forceinline__ void oe_merge(uint64_t (&r)[M]) {
   }
 }
 template <int LO, int N, int M>
-__device__ __forceinline__ void oe_sort(uint64_t (&r)[M]) {
+__device__ __forceinline__ void oe_sort(uint32_t (&r)[M]) {
   if constexpr (N > 1) {
     oe_sort<LO, N / 2>(r);
     oe_sort<LO + N / 2, N / 2>(r);
@@ -154,23 +195,34 @@ __device__ __forceinline__ void oe_sort(uint64_t (&r)[M]) {
   }
 }
 template <int N>
-__device__ __forceinline__ void merge_sort_net(uint64_t (&r)[N]) {
+__device__ __forceinline__ void merge_sort_net(uint32_t (&r)[N]) {
   oe_sort<0, N>(r);
 }
 
-// Sort and fold of a segment of n <= N records (a register copy).
+// Sort and fold of a segment of n <= N records (a register copy).  The hit
+// energies of the sorted records' tasks are loaded all at once, ahead of the
+// fold, so that the cell waits for one load latency, not one per task.
 template <int N>
-__device__ __forceinline__ double fold_small(const uint64_t* __restrict__ recs, int64_t a, int n, uint64_t task_mask,
-                                            const float* __restrict__ task_ehit) {
-  uint64_t r[N];
+__device__ __forceinline__ double fold_small(const uint32_t* __restrict__ recs, int64_t a, int n,
+                                            const float* __restrict__ ev_ehit) {
+  uint32_t r[N];
 #pragma unroll
-  for (int j = 0; j < N; ++j) r[j] = j < n ? recs[a + j] : ~0ull;
+  for (int j = 0; j < N; ++j) r[j] = j < n ? recs[a + j] : ~0u;
   merge_sort_net<N>(r);
+  float e[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) e[j] = j < n ? ev_ehit[r[j] >> kRecordCountBits] : 0.0f;
   Fold f;
 #pragma unroll
   for (int j = 0; j < N; ++j)
-    if (j < n) f.add(r[j], task_mask, task_ehit);
-  return f.result(task_ehit);
+    if (j < n) f.add(r[j], e[j]);
+  return f.result();
+}
+
+// The hit energies of the tasks of cell c's event.
+__device__ __forceinline__ const float* event_ehit(const float* __restrict__ task_ehit,
+                                                  const int64_t* __restrict__ base, int64_t c, uint32_t acc_stride) {
+  return task_ehit + base[(uint32_t)c / acc_stride];
 }
 
 // One thread per cell: segments of up to 8 records (92 % of the hit cells of
@@ -179,49 +231,66 @@ __device__ __forceinline__ double fold_small(const uint64_t* __restrict__ recs, 
 // k_det_fold_mid (from the back of the list array) and longer ones for
 // k_det_fold_big (from its front), so that the warps of each kernel run one
 // path.
-__global__ void __launch_bounds__(256) k_det_fold(const uint64_t* __restrict__ recs,
+__global__ void __launch_bounds__(256) k_det_fold(const uint32_t* __restrict__ recs,
                                                   const int64_t* __restrict__ cell_off, int64_t n_cells_all, Sizes* sz,
-                                                  int64_t cap, uint64_t task_mask, const float* __restrict__ task_ehit,
-                                                  double* __restrict__ acc, int64_t* __restrict__ lists) {
-  if (sz->flags & FCS_FLAG_HIT_CAPACITY) return;
+                                                  int64_t cap, uint32_t acc_stride, const int64_t* __restrict__ base,
+                                                  const float* __restrict__ task_ehit, double* __restrict__ acc,
+                                                  int64_t* __restrict__ lists) {
+  if (sz->flags & (FCS_FLAG_HIT_CAPACITY | FCS_FLAG_KEY_BITS)) return;
   const int64_t total = min(sz->n_records, cap);
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells_all;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t a = cell_off[c], b = min((c + 1 < n_cells_all) ? cell_off[c + 1] : total, cap);
-    if (a >= b) continue;
-    const int64_t n = b - a;
-    if (n > 8) {
-      if (n > kInsertionMax) lists[atomicAdd((unsigned long long*)&sz->n_big, 1ull)] = c;
-      else lists[cap - 1 - (int64_t)atomicAdd((unsigned long long*)&sz->n_mid, 1ull)] = c;
-      continue;
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  // warp-uniform trips, so that the lists take one counter update per warp
+  for (int64_t c0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); c0 < n_cells_all;
+       c0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = c0 + lane;
+    int64_t a = 0, n = 0;
+    if (c < n_cells_all) {
+      a = cell_off[c];
+      n = min((c + 1 < n_cells_all) ? cell_off[c + 1] : total, cap) - a;
     }
-    acc[c] = fold_small<8>(recs, a, (int)n, task_mask, task_ehit);
+    const unsigned mb = __ballot_sync(0xffffffffu, n > kInsertionMax);
+    const unsigned mm = __ballot_sync(0xffffffffu, n > 8 && n <= kInsertionMax);
+    if (mb | mm) {
+      unsigned long long bb = 0, bm = 0;
+      if (lane == 0) {
+        if (mb) bb = atomicAdd((unsigned long long*)&sz->n_big, (unsigned long long)__popc(mb));
+        if (mm) bm = atomicAdd((unsigned long long*)&sz->n_mid, (unsigned long long)__popc(mm));
+      }
+      bb = __shfl_sync(0xffffffffu, bb, 0);
+      bm = __shfl_sync(0xffffffffu, bm, 0);
+      if ((mb >> lane) & 1u) lists[bb + __popc(mb & below)] = c;
+      if ((mm >> lane) & 1u) lists[cap - 1 - (int64_t)(bm + __popc(mm & below))] = c;
+    }
+    if (n > 0 && n <= 8) acc[c] = fold_small<8>(recs, a, (int)n, event_ehit(task_ehit, base, c, acc_stride));
   }
 }
 
 // One thread per listed cell of 9 to kInsertionMax records: up to 16 sorted
 // as a copy in registers, longer ones as a thread-local copy by insertion
 // (its dependent steps hit L1, not L2); then folded.
-__global__ void __launch_bounds__(256) k_det_fold_mid(const uint64_t* __restrict__ recs,
+__global__ void __launch_bounds__(256) k_det_fold_mid(const uint32_t* __restrict__ recs,
                                                       const int64_t* __restrict__ cell_off, int64_t n_cells_all,
-                                                      const Sizes* sz, int64_t cap, uint64_t task_mask,
+                                                      const Sizes* sz, int64_t cap, uint32_t acc_stride,
+                                                      const int64_t* __restrict__ base,
                                                       const float* __restrict__ task_ehit, double* __restrict__ acc,
                                                       const int64_t* __restrict__ lists) {
-  if (sz->flags & FCS_FLAG_HIT_CAPACITY) return;
+  if (sz->flags & (FCS_FLAG_HIT_CAPACITY | FCS_FLAG_KEY_BITS)) return;
   const int64_t total = min(sz->n_records, cap);
   const int64_t n_mid = sz->n_mid;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_mid; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = lists[cap - 1 - q];
     const int64_t a = cell_off[c], b = min((c + 1 < n_cells_all) ? cell_off[c + 1] : total, cap);
     const int n = (int)(b - a);
+    const float* ev_ehit = event_ehit(task_ehit, base, c, acc_stride);
     if (n <= 16) {
-      acc[c] = fold_small<16>(recs, a, n, task_mask, task_ehit);
+      acc[c] = fold_small<16>(recs, a, n, ev_ehit);
       continue;
     }
-    uint64_t seg[kInsertionMax];
+    uint32_t seg[kInsertionMax];
     for (int i = 0; i < n; ++i) seg[i] = recs[a + i];
     for (int i = 1; i < n; ++i) {
-      const uint64_t v = seg[i];
+      const uint32_t v = seg[i];
       int j = i - 1;
       while (j >= 0 && seg[j] > v) {
         seg[j + 1] = seg[j];
@@ -230,8 +299,8 @@ __global__ void __launch_bounds__(256) k_det_fold_mid(const uint64_t* __restrict
       seg[j + 1] = v;
     }
     Fold f;
-    for (int j = 0; j < n; ++j) f.add(seg[j], task_mask, task_ehit);
-    acc[c] = f.result(task_ehit);
+    for (int j = 0; j < n; ++j) f.add(seg[j], ev_ehit);
+    acc[c] = f.result();
   }
 }
 
@@ -239,43 +308,45 @@ __global__ void __launch_bounds__(256) k_det_fold_mid(const uint64_t* __restrict
 // to kBigMax records; longer ones take heapsort in place), then lane 0 folds.
 constexpr int kBigWarps = 4;
 constexpr int kBigMax = 1024;
-__global__ void __launch_bounds__(32 * kBigWarps) k_det_fold_big(uint64_t* __restrict__ recs,
+__global__ void __launch_bounds__(32 * kBigWarps) k_det_fold_big(uint32_t* __restrict__ recs,
                                                                  const int64_t* __restrict__ cell_off,
                                                                  int64_t n_cells_all, const Sizes* sz, int64_t cap,
-                                                                 uint64_t task_mask, const float* __restrict__ task_ehit,
+                                                                 uint32_t acc_stride, const int64_t* __restrict__ base,
+                                                                 const float* __restrict__ task_ehit,
                                                                  double* __restrict__ acc,
                                                                  const int64_t* __restrict__ big) {
-  __shared__ uint64_t s_rec[kBigWarps][kBigMax];
-  if (sz->flags & FCS_FLAG_HIT_CAPACITY) return;
+  __shared__ uint32_t s_rec[kBigWarps][kBigMax];
+  if (sz->flags & (FCS_FLAG_HIT_CAPACITY | FCS_FLAG_KEY_BITS)) return;
   const int64_t total = min(sz->n_records, cap);
   const int64_t n_big = sz->n_big;
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-  uint64_t* s = s_rec[wi];
+  uint32_t* s = s_rec[wi];
   for (int64_t q = (int64_t)blockIdx.x * kBigWarps + wi; q < n_big; q += (int64_t)gridDim.x * kBigWarps) {
     const int64_t c = big[q];
     const int64_t a = cell_off[c], b = min((c + 1 < n_cells_all) ? cell_off[c + 1] : total, cap);
     const int64_t n = b - a;
-    uint64_t* seg = recs + a;
+    uint32_t* seg = recs + a;
+    const float* ev_ehit = event_ehit(task_ehit, base, c, acc_stride);
     if (n > kBigMax) {
       if (lane == 0) {
         sort_segment(seg, n);
         Fold f;
-        for (int64_t j = 0; j < n; ++j) f.add(seg[j], task_mask, task_ehit);
-        acc[c] = f.result(task_ehit);
+        for (int64_t j = 0; j < n; ++j) f.add(seg[j], ev_ehit);
+        acc[c] = f.result();
       }
       __syncwarp();
       continue;
     }
     int m = 1;
     while (m < n) m <<= 1;
-    for (int j = lane; j < m; j += 32) s[j] = j < n ? seg[j] : ~0ull;
+    for (int j = lane; j < m; j += 32) s[j] = j < n ? seg[j] : ~0u;
     __syncwarp();
     for (int k = 2; k <= m; k <<= 1) {
       for (int jj = k >> 1; jj > 0; jj >>= 1) {
         for (int i = lane; i < m; i += 32) {
           const int l = i ^ jj;
           if (l > i) {
-            const uint64_t x = s[i], y = s[l];
+            const uint32_t x = s[i], y = s[l];
             const bool up = (i & k) == 0;
             if ((x > y) == up) {
               s[i] = y;
@@ -288,8 +359,8 @@ __global__ void __launch_bounds__(32 * kBigWarps) k_det_fold_big(uint64_t* __res
     }
     if (lane == 0) {
       Fold f;
-      for (int64_t j = 0; j < n; ++j) f.add(s[j], task_mask, task_ehit);
-      acc[c] = f.result(task_ehit);
+      for (int64_t j = 0; j < n; ++j) f.add(s[j], ev_ehit);
+      acc[c] = f.result();
     }
     __syncwarp();
   }
@@ -298,24 +369,28 @@ __global__ void __launch_bounds__(32 * kBigWarps) k_det_fold_big(uint64_t* __res
 }  // namespace
 
 cudaError_t launch_det_reduce(const GeoDev& g, WsDev w, int32_t rows, int key_task_bits, int64_t* cell_off,
-                              ScanTmp tmp, const Launch& L) {
+                              const int64_t* event_offsets, int32_t ev_lo, ScanTmp tmp, const Launch& L) {
   const int64_t n_cells_all = (int64_t)rows * g.acc_stride;
   uint32_t* counters = reinterpret_cast<uint32_t*>(w.acc);
+  int64_t* base = cell_off + n_cells_all;  // [rows] first task of each event
+  const uint32_t stride = (uint32_t)g.acc_stride;
+  k_det_bases<<<(rows + 255) / 256, 256, 0, L.s>>>(event_offsets, ev_lo, rows, w.poff, w.sizes, base);
   cudaError_t e = launch_scan_u32(counters, cell_off, n_cells_all, tmp, L.s);
   if (e != cudaSuccess) return e;
   const int cell_shift = kRecordCountBits + key_task_bits;
   const uint64_t task_mask = (key_task_bits >= 64) ? ~0ull : ((1ull << key_task_bits) - 1ull);
-  k_det_scatter<<<L.num_sms * 8, 256, 0, L.s>>>(w.keys, w.sizes, w.rec_cap, cell_shift, counters, cell_off,
-                                                n_cells_all, w.keys_alt);
+  uint32_t* segs = reinterpret_cast<uint32_t*>(w.keys_alt);
+  k_det_scatter<<<L.num_sms * 8, 256, 0, L.s>>>(w.keys, w.sizes, w.rec_cap, cell_shift, task_mask, counters, cell_off,
+                                                n_cells_all, stride, base, segs);
   // the slot array is free after the scatter: it lists the segments of more
   // than 8 records
   int64_t* lists = reinterpret_cast<int64_t*>(w.keys);
-  k_det_fold<<<L.num_sms * 8, 256, 0, L.s>>>(w.keys_alt, cell_off, n_cells_all, w.sizes, w.rec_cap, task_mask, w.tehit,
+  k_det_fold<<<L.num_sms * 8, 256, 0, L.s>>>(segs, cell_off, n_cells_all, w.sizes, w.rec_cap, stride, base, w.tehit,
                                              w.acc, lists);
-  k_det_fold_mid<<<L.num_sms * 8, 256, 0, L.s>>>(w.keys_alt, cell_off, n_cells_all, w.sizes, w.rec_cap, task_mask,
+  k_det_fold_mid<<<L.num_sms * 8, 256, 0, L.s>>>(segs, cell_off, n_cells_all, w.sizes, w.rec_cap, stride, base,
                                                  w.tehit, w.acc, lists);
-  k_det_fold_big<<<L.num_sms * 4, 32 * kBigWarps, 0, L.s>>>(w.keys_alt, cell_off, n_cells_all, w.sizes, w.rec_cap,
-                                                            task_mask, w.tehit, w.acc, lists);
+  k_det_fold_big<<<L.num_sms * 4, 32 * kBigWarps, 0, L.s>>>(segs, cell_off, n_cells_all, w.sizes, w.rec_cap, stride,
+                                                            base, w.tehit, w.acc, lists);
   return cudaGetLastError();
 }
 

@@ -698,11 +698,10 @@ __global__ void __launch_bounds__(128) k_poisson_audit(const float* mu, int64_t 
   }
 }
 
-// One thread per task: in deterministic mode the hit energy into tehit (the
-// fold's compact copy); validation dumps; the tile map (granule -> task
+// One thread per task: validation dumps; the tile map (granule -> task
 // holding its first hit) again when the call grew it after the scan that
 // wrote it (fill_map).
-__global__ void k_task_finish(WsDev w, fcs_debug dbg, int has_dbg, int det, int fill_map) {
+__global__ void k_task_finish(WsDev w, fcs_debug dbg, int has_dbg, int fill_map) {
   const int64_t T = min(w.sizes->n_tasks, w.task_cap);
   const int64_t H = w.sizes->n_hits;
   const bool map_ok = fill_map && H <= w.gmap_cap * (int64_t)kGranule;
@@ -713,19 +712,16 @@ __global__ void k_task_finish(WsDev w, fcs_debug dbg, int has_dbg, int det, int 
       const int64_t b = w.th[t];
       for (int64_t gi = (b + kGranule - 1) / kGranule; gi * kGranule < b + n; ++gi) w.gmap[gi] = (int32_t)t;
     }
-    if (det || has_dbg) {
+    if (has_dbg) {
       const TaskRec& r = w.tasks[t];
       const float Ehit = __fdiv_rn(r.El, (float)n);
-      if (det) w.tehit[t] = Ehit;
-      if (has_dbg) {
-        const int64_t dt = task_base + t;
-        if (dt < dbg.task_capacity) {
-          if (dbg.task_event) dbg.task_event[dt] = r.event();
-          if (dbg.task_particle) dbg.task_particle[dt] = r.particle;
-          if (dbg.task_layer) dbg.task_layer[dt] = r.layer();
-          if (dbg.task_n) dbg.task_n[dt] = (int32_t)n;
-          if (dbg.task_Ehit) dbg.task_Ehit[dt] = Ehit;
-        }
+      const int64_t dt = task_base + t;
+      if (dt < dbg.task_capacity) {
+        if (dbg.task_event) dbg.task_event[dt] = r.event();
+        if (dbg.task_particle) dbg.task_particle[dt] = r.particle;
+        if (dbg.task_layer) dbg.task_layer[dt] = r.layer();
+        if (dbg.task_n) dbg.task_n[dt] = (int32_t)n;
+        if (dbg.task_Ehit) dbg.task_Ehit[dt] = Ehit;
       }
     }
   }
@@ -783,12 +779,11 @@ cudaError_t launch_task_counts(const GeoDev& g, const ParamDev& p, const fcs_par
   return launch_scan_hits(w.tn, w.th, &w.sizes->n_tasks, &w.sizes->n_hits, w.gmap, w.gmap_cap, tmp, L.s);
 }
 
-cudaError_t launch_task_finish(WsDev w, const fcs_debug* dbg, int det, int fill_map, int64_t n_task_max,
-                               const Launch& L) {
-  if (!dbg && !det && !fill_map) return cudaSuccess;  // the scan wrote the tile map
+cudaError_t launch_task_finish(WsDev w, const fcs_debug* dbg, int fill_map, int64_t n_task_max, const Launch& L) {
+  if (!dbg && !fill_map) return cudaSuccess;  // the scan wrote the tile map
   fcs_debug d{};
   if (dbg) d = *dbg;
-  k_task_finish<<<grid_for(n_task_max, L), 128, 0, L.s>>>(w, d, dbg ? 1 : 0, det, fill_map);
+  k_task_finish<<<grid_for(n_task_max, L), 128, 0, L.s>>>(w, d, dbg ? 1 : 0, fill_map);
   return cudaGetLastError();
 }
 
