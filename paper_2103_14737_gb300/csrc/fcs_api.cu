@@ -320,9 +320,14 @@ int ws_reserve_hits(fcs_workspace* ws, int64_t H, int mode) {
   const int64_t rq = std::max<int64_t>(1 << 16, H / 16);
   if (rq > ws->recheck_cap) FCS_TRY(grow(&ws->recheck, &ws->recheck_cap, rq + rq / 4));
   if (mode == FCS_MODE_DETERMINISTIC) {
+    // the cells' segment offsets are int32: at most 2^31 - 1 record slots
+    const int64_t kMaxSlots = INT32_MAX;
     const int64_t need = std::max<int64_t>(H, 1) + kRecordSlack;
+    if (need > kMaxSlots)
+      return set_err(FCS_E_RANGE, "deterministic mode: %lld hits in one event range exceed 2^31 record slots; use "
+                     "smaller waves", (long long)H);
     if (need > ws->rec_cap) {
-      const int64_t cap = need + need / 8;
+      const int64_t cap = std::min(need + need / 8, kMaxSlots);
       int64_t c1 = ws->k_cap, c2 = ws->ka_cap;
       FCS_TRY(grow(&ws->keys, &c1, cap));
       FCS_TRY(grow(&ws->keys_alt, &c2, cap));
@@ -362,6 +367,7 @@ __global__ void __launch_bounds__(kRangeThreads) k_range_begin(Sizes* s, const i
   s->n_slots = 0;
   s->n_big = 0;
   s->n_mid = 0;
+  s->n_mid32 = 0;
   s->n_pdefer = 0;
   s->n_pdefer_ptrs = 0;
   s->queue = 0;

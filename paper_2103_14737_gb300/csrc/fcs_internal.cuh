@@ -110,7 +110,8 @@ struct Sizes {
   int64_t recheck_total;  // recheck hits over the call
   int64_t n_part;       // particles of the current event range (checked against the capacity)
   int64_t n_big;        // deterministic mode: cells with more records than one thread sorts
-  int64_t n_mid;        // deterministic mode: cells of 9 to 32 records (sorted by their own kernel)
+  int64_t n_mid;        // deterministic mode: cells of 9 to 16 records (sorted by their own kernel)
+  int64_t n_mid32;      //   and of 17 to 32 records
   int64_t n_pdefer;     // inversion draws deferred to FP64 in the current range (front of pdefer)
   int64_t n_pdefer_ptrs;  // PTRS draws deferred to FP64 in the current range (back of pdefer)
   unsigned long long queue;  // hit-kernel work-queue counter (tiles handed out)
@@ -267,8 +268,9 @@ cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, const int64_t* n_de
 // Self-test of the scan's bounded wait (a tile that never publishes): the
 // device flag word and the kernel's time in ms.
 cudaError_t scan_wait_selftest(uint32_t* flags_out, float* ms, cudaStream_t s);
-// Exclusive scan of n uint32 values into int64 (no base, no total).
-cudaError_t launch_scan_u32(const uint32_t* in, int64_t* out, int64_t n, ScanTmp tmp, cudaStream_t s);
+// Exclusive scan of n uint32 values into int32 (no base, no total); zeroes
+// the inputs as it reads them.
+cudaError_t launch_scan_u32_zero(uint32_t* in, int32_t* out, int64_t n, ScanTmp tmp, cudaStream_t s);
 // The hit offsets th (exclusive scan of the tasks' hit counts tn, *n_tasks of
 // them; total to *n_hits) and the tile map gmap[g] = the task holding hit
 // g * kGranule, for g < gmap_cap.
@@ -340,10 +342,10 @@ cudaError_t launch_compact(const GeoDev& g, WsDev w, int32_t rows, int32_t ev_lo
 int64_t compact_chunks(int32_t n_cells, int32_t rows);
 // Deterministic mode: the records of the range (hit slots) grouped by cell
 // and folded into the accumulation rows, whose uint32 record counters the
-// hit kernel filled.  cell_off: [rows * (acc_stride + 1)] scratch (the cells'
-// segments, then each event's first task); event_offsets and ev_lo: the
-// range's events.  The compaction then runs as in atomic mode.
-cudaError_t launch_det_reduce(const GeoDev& g, WsDev w, int32_t rows, int key_task_bits, int64_t* cell_off,
+// hit kernel filled.  scratch: [rows * (acc_stride + 1)] int64 (each event's
+// first task, then the cells' int32 segment offsets); event_offsets and
+// ev_lo: the range's events.  The compaction then runs as in atomic mode.
+cudaError_t launch_det_reduce(const GeoDev& g, WsDev w, int32_t rows, int key_task_bits, int64_t* scratch,
                               const int64_t* event_offsets, int32_t ev_lo, ScanTmp tmp, const Launch& L);
 
 }  // namespace fcs

@@ -105,8 +105,10 @@ __device__ __forceinline__ int64_t look_back(const uint64_t* status, int64_t t, 
   }
 }
 
-template <typename In, bool GMAP, int ITEMS>
-__global__ void __launch_bounds__(kScanThreads) k_scan(const In* in, int64_t* out, const int64_t* n_dev, int64_t n_host,
+// Out: the offsets' type (int64, or int32 for the deterministic mode's cell
+// offsets, which also zero their uint32 inputs as they read them: ZERO_IN).
+template <typename In, bool GMAP, int ITEMS, typename Out = int64_t, bool ZERO_IN = false>
+__global__ void __launch_bounds__(kScanThreads) k_scan(const In* in, Out* out, const int64_t* n_dev, int64_t n_host,
                                                      int64_t* total_dst, int base_from_dst, uint64_t* state,
                                                      int64_t cap_tiles, uint32_t* flags, int32_t* gmap,
                                                      int64_t gmap_cap, int64_t mute_tile) {
@@ -190,7 +192,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const In* in, int64_t* ou
       for (int k = 0; k < ITEMS; ++k) {
         const int j = k * kScanThreads + threadIdx.x;
         const int64_t i = t0 + j;
-        if (i < n) out[i] = s_tile[j + j / ITEMS];
+        if (i < n) {
+          out[i] = (Out)s_tile[j + j / ITEMS];
+          if constexpr (ZERO_IN) const_cast<In*>(in)[i] = 0;  // read whole before the scan
+        }
       }
     }
     __syncthreads();  // the tile buffer and s_ticket are reused
@@ -223,8 +228,8 @@ int64_t scan_state_words(int64_t max_elements) {
 // (a running total in device memory) else 0.  Writes base + sum to
 // *total_dst when total_dst is non-NULL.  in and out may alias (a tile is
 // read whole before it is written).
-template <typename In, bool GMAP = false, int ITEMS = kScanItems>
-static cudaError_t launch_scan(const In* in, int64_t* out, const int64_t* n_dev, int64_t n_host,
+template <typename In, bool GMAP = false, int ITEMS = kScanItems, typename Out = int64_t, bool ZERO_IN = false>
+static cudaError_t launch_scan(const In* in, Out* out, const int64_t* n_dev, int64_t n_host,
                                int64_t* total_dst, int64_t base_from_dst, ScanTmp tmp, cudaStream_t s,
                                int32_t* gmap = nullptr, int64_t gmap_cap = 0) {
   constexpr size_t smem = scan_smem_bytes(ITEMS);
@@ -234,16 +239,17 @@ static cudaError_t launch_scan(const In* in, int64_t* out, const int64_t* n_dev,
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = -1;
     if (dev < 0 || !opted[dev].load(std::memory_order_acquire)) {
-      const cudaError_t e = cudaFuncSetAttribute(k_scan<In, GMAP, ITEMS>,
+      const cudaError_t e = cudaFuncSetAttribute(k_scan<In, GMAP, ITEMS, Out, ZERO_IN>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
       if (dev >= 0) opted[dev].store(true, std::memory_order_release);
     }
   }
   // the status words are sized for kScanTile-element tiles; larger tiles need fewer
-  k_scan<In, GMAP, ITEMS><<<tmp.grid, kScanThreads, smem, s>>>(in, out, n_dev, n_host, total_dst,
-                                                              base_from_dst ? 1 : 0, tmp.state, tmp.cap_tiles,
-                                                              tmp.flags, gmap, gmap_cap, -1);
+  k_scan<In, GMAP, ITEMS, Out, ZERO_IN><<<tmp.grid, kScanThreads, smem, s>>>(in, out, n_dev, n_host, total_dst,
+                                                                            base_from_dst ? 1 : 0, tmp.state,
+                                                                            tmp.cap_tiles, tmp.flags, gmap, gmap_cap,
+                                                                            -1);
   return cudaGetLastError();
 }
 
@@ -252,8 +258,8 @@ cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, const int64_t* n_de
   return launch_scan(in, out, n_dev, n_host, total_dst, base_from_dst, tmp, s);
 }
 
-cudaError_t launch_scan_u32(const uint32_t* in, int64_t* out, int64_t n, ScanTmp tmp, cudaStream_t s) {
-  return launch_scan(in, out, nullptr, n, nullptr, 0, tmp, s);
+cudaError_t launch_scan_u32_zero(uint32_t* in, int32_t* out, int64_t n, ScanTmp tmp, cudaStream_t s) {
+  return launch_scan<uint32_t, false, kScanItems, int32_t, true>(in, out, nullptr, n, nullptr, 0, tmp, s);
 }
 
 // Self-test of the bounded wait: a scan of three tiles on four CTAs, in its

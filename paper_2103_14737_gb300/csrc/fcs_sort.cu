@@ -12,21 +12,20 @@
 // kernel writes the records to slots handed out in chunks (unused slots hold
 // the empty record, all ones) and counts the records of every cell in the
 // accumulation rows, used as uint32 counters.  Then:
-//   1. an exclusive scan of the counters gives each cell its segment of the
-//      record array;
-//   2. scatter: every record takes a place in its cell's segment; the
-//      counter, counted down, hands out the places and ends at zero.  In the
+//   1. an exclusive scan of the counters gives each cell the start of its
+//      segment of the record array (int32) and zeroes the counters;
+//   2. scatter: every record takes a place in its cell's segment from the
+//      cell's offset, counted up, which ends at the segment's end (the next
+//      cell's start), so that one array bounds every segment.  In the
 //      segment the cell is implied and a record shrinks to 32 bits:
 //      [ task - first task of the cell's event (27 bits) | count - 1 ]
 //      (a row holds one event, and its tasks are consecutive), so the
 //      segments take half the bytes and sort as 32-bit keys;
 //   3. fold: one thread per cell sorts its segment by (task, count) - a copy
-//      in registers with a sorting network up to 16 records, a thread-local
-//      copy by insertion up to 32, the three classes in kernels of their
-//      own - merges the
-//      records of a task (their counts add exactly) and folds; a warp per
-//      longer segment sorts it in shared memory (bitonic) before its first
-//      lane folds.  The float result goes to the (FP64) accumulation row,
+//      in registers with a sorting network of 8, 16 or 32 records, each class
+//      in a kernel of its own - merges the records of a task (their counts
+//      add exactly) and folds; a warp per longer segment sorts it in shared
+//      memory (bitonic) before its first lane folds.  The float result goes to the (FP64) accumulation row,
 //      where the compaction of the atomic mode picks it up, rounds it back to
 //      the same float and re-zeroes it.
 // Only the order of places inside a segment depends on scheduling, and the
@@ -37,7 +36,7 @@ namespace fcs {
 namespace {
 
 constexpr uint64_t kEmpty = ~0ull;
-constexpr int kInsertionMax = 32;  // segments sorted by insertion up to here, heapsort beyond
+constexpr int kThreadSortMax = 32;  // segments sorted by one thread (in registers) up to here
 constexpr int kRelTaskBits = 32 - kRecordCountBits;  // a segment record's task, relative to its event's first
 constexpr uint32_t kCountMask = (1u << kRecordCountBits) - 1u;
 
@@ -59,11 +58,9 @@ __global__ void k_det_bases(const int64_t* __restrict__ event_offsets, int32_t e
 // A record whose task lies 2^27 or more past its event's first sets
 // FCS_FLAG_KEY_BITS and is dropped (the call then fails).
 __global__ void __launch_bounds__(256) k_det_scatter(const uint64_t* __restrict__ slots, Sizes* sz, int64_t cap,
-                                                     int cell_shift, uint64_t task_mask,
-                                                     uint32_t* __restrict__ counters,
-                                                     const int64_t* __restrict__ cell_off, int64_t n_cells_all,
-                                                     uint32_t acc_stride, const int64_t* __restrict__ base,
-                                                     uint32_t* __restrict__ out) {
+                                                     int cell_shift, uint64_t task_mask, int32_t* __restrict__ cell_off,
+                                                     int64_t n_cells_all, uint32_t acc_stride,
+                                                     const int64_t* __restrict__ base, uint32_t* __restrict__ out) {
   if (sz->flags & FCS_FLAG_HIT_CAPACITY) return;
   const int64_t n = min(sz->n_slots, cap);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -77,7 +74,7 @@ __global__ void __launch_bounds__(256) k_det_scatter(const uint64_t* __restrict_
       const uint64_t c = k[j] >> cell_shift;
       if (c >= (uint64_t)n_cells_all) continue;  // cannot happen for records of this range
       const int64_t rel = (int64_t)((k[j] >> kRecordCountBits) & task_mask) - base[(uint32_t)c / acc_stride];
-      const int64_t pos = cell_off[c] + (int64_t)atomicSub(counters + c, 1u) - 1;
+      const int64_t pos = atomicAdd(cell_off + c, 1);
       if (rel < 0 || rel >= ((int64_t)1 << kRelTaskBits)) {
         atomicOr(&sz->flags, (uint32_t)FCS_FLAG_KEY_BITS);
         continue;
@@ -100,20 +97,8 @@ __device__ __forceinline__ void sift_down(uint32_t* a, int64_t root, int64_t n) 
   }
 }
 
-// Ascending sort of a[0, n) in place.
+// Ascending sort of a[0, n) in place (heapsort).
 __device__ __noinline__ void sort_segment(uint32_t* a, int64_t n) {
-  if (n <= kInsertionMax) {
-    for (int64_t i = 1; i < n; ++i) {
-      const uint32_t v = a[i];
-      int64_t j = i - 1;
-      while (j >= 0 && a[j] > v) {
-        a[j + 1] = a[j];
-        --j;
-      }
-      a[j + 1] = v;
-    }
-    return;
-  }
   for (int64_t r = n / 2 - 1; r >= 0; --r) sift_down(a, r, n);
   for (int64_t e = n - 1; e > 0; --e) {
     const uint32_t t = a[0];
@@ -219,6 +204,14 @@ __device__ __forceinline__ double fold_small(const uint32_t* __restrict__ recs, 
   return f.result();
 }
 
+// Cell c's segment [a, b) after the scatter: cell_off[c] holds its end, which
+// is the next cell's start.
+__device__ __forceinline__ void segment(const int32_t* __restrict__ cell_off, int64_t c, int64_t cap, int64_t& a,
+                                        int64_t& b) {
+  a = c > 0 ? cell_off[c - 1] : 0;
+  b = min((int64_t)cell_off[c], cap);
+}
+
 // The hit energies of the tasks of cell c's event.
 __device__ __forceinline__ const float* event_ehit(const float* __restrict__ task_ehit,
                                                   const int64_t* __restrict__ base, int64_t c, uint32_t acc_stride) {
@@ -227,80 +220,69 @@ __device__ __forceinline__ const float* event_ehit(const float* __restrict__ tas
 
 // One thread per cell: segments of up to 8 records (92 % of the hit cells of
 // pile-up events) are sorted as a copy in registers, with nothing written
-// back, and folded; segments of 9 to kInsertionMax records are listed for
-// k_det_fold_mid (from the back of the list array) and longer ones for
-// k_det_fold_big (from its front), so that the warps of each kernel run one
-// path.
+// back, and folded; segments of 9 to 16 and of 17 to kThreadSortMax records
+// are listed for the two k_det_fold_mid kernels and longer ones for
+// k_det_fold_big, so that the warps of each kernel run one path.  The list
+// array holds three lists, from its start, a third in and two thirds in: a
+// listed cell has at least 9 records, so each list fits its third.
 __global__ void __launch_bounds__(256) k_det_fold(const uint32_t* __restrict__ recs,
-                                                  const int64_t* __restrict__ cell_off, int64_t n_cells_all, Sizes* sz,
+                                                  const int32_t* __restrict__ cell_off, int64_t n_cells_all, Sizes* sz,
                                                   int64_t cap, uint32_t acc_stride, const int64_t* __restrict__ base,
                                                   const float* __restrict__ task_ehit, double* __restrict__ acc,
                                                   int64_t* __restrict__ lists) {
   if (sz->flags & (FCS_FLAG_HIT_CAPACITY | FCS_FLAG_KEY_BITS)) return;
-  const int64_t total = min(sz->n_records, cap);
   const int lane = threadIdx.x & 31;
   const unsigned below = (1u << lane) - 1u;
   // warp-uniform trips, so that the lists take one counter update per warp
   for (int64_t c0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); c0 < n_cells_all;
        c0 += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = c0 + lane;
-    int64_t a = 0, n = 0;
-    if (c < n_cells_all) {
-      a = cell_off[c];
-      n = min((c + 1 < n_cells_all) ? cell_off[c + 1] : total, cap) - a;
-    }
-    const unsigned mb = __ballot_sync(0xffffffffu, n > kInsertionMax);
-    const unsigned mm = __ballot_sync(0xffffffffu, n > 8 && n <= kInsertionMax);
-    if (mb | mm) {
-      unsigned long long bb = 0, bm = 0;
+    // the segment ends (int32, as is the record count): each lane's, and the
+    // one before the warp's first cell
+    const int32_t b = c < n_cells_all ? cell_off[c] : 0;
+    const int32_t b0 = (lane == 0 && c0 > 0) ? cell_off[c0 - 1] : 0;
+    const int32_t bp = __shfl_up_sync(0xffffffffu, b, 1);
+    const int32_t a = lane ? bp : b0;
+    const int32_t n = c < n_cells_all ? min((int64_t)b, cap) - a : 0;
+    const unsigned mb = __ballot_sync(0xffffffffu, n > kThreadSortMax);
+    const unsigned m16 = __ballot_sync(0xffffffffu, n > 8 && n <= 16);
+    const unsigned m32 = __ballot_sync(0xffffffffu, n > 16 && n <= kThreadSortMax);
+    if (mb | m16 | m32) {
+      unsigned long long bb = 0, b16 = 0, b32 = 0;
       if (lane == 0) {
         if (mb) bb = atomicAdd((unsigned long long*)&sz->n_big, (unsigned long long)__popc(mb));
-        if (mm) bm = atomicAdd((unsigned long long*)&sz->n_mid, (unsigned long long)__popc(mm));
+        if (m16) b16 = atomicAdd((unsigned long long*)&sz->n_mid, (unsigned long long)__popc(m16));
+        if (m32) b32 = atomicAdd((unsigned long long*)&sz->n_mid32, (unsigned long long)__popc(m32));
       }
       bb = __shfl_sync(0xffffffffu, bb, 0);
-      bm = __shfl_sync(0xffffffffu, bm, 0);
+      b16 = __shfl_sync(0xffffffffu, b16, 0);
+      b32 = __shfl_sync(0xffffffffu, b32, 0);
       if ((mb >> lane) & 1u) lists[bb + __popc(mb & below)] = c;
-      if ((mm >> lane) & 1u) lists[cap - 1 - (int64_t)(bm + __popc(mm & below))] = c;
+      if ((m16 >> lane) & 1u) lists[cap / 3 + (int64_t)(b16 + __popc(m16 & below))] = c;
+      if ((m32 >> lane) & 1u) lists[2 * (cap / 3) + (int64_t)(b32 + __popc(m32 & below))] = c;
     }
     if (n > 0 && n <= 8) acc[c] = fold_small<8>(recs, a, (int)n, event_ehit(task_ehit, base, c, acc_stride));
   }
 }
 
-// One thread per listed cell of 9 to kInsertionMax records: up to 16 sorted
-// as a copy in registers, longer ones as a thread-local copy by insertion
-// (its dependent steps hit L1, not L2); then folded.
+// One thread per listed cell of 9 to 16 (N = 16) or 17 to 32 records
+// (N = 32): sorted as a copy in registers, then folded.
+template <int N>
 __global__ void __launch_bounds__(256) k_det_fold_mid(const uint32_t* __restrict__ recs,
-                                                      const int64_t* __restrict__ cell_off, int64_t n_cells_all,
+                                                      const int32_t* __restrict__ cell_off, int64_t n_cells_all,
                                                       const Sizes* sz, int64_t cap, uint32_t acc_stride,
                                                       const int64_t* __restrict__ base,
                                                       const float* __restrict__ task_ehit, double* __restrict__ acc,
                                                       const int64_t* __restrict__ lists) {
+  static_assert(N == 16 || N == kThreadSortMax, "two mid classes");
   if (sz->flags & (FCS_FLAG_HIT_CAPACITY | FCS_FLAG_KEY_BITS)) return;
-  const int64_t total = min(sz->n_records, cap);
-  const int64_t n_mid = sz->n_mid;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_mid; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = lists[cap - 1 - q];
-    const int64_t a = cell_off[c], b = min((c + 1 < n_cells_all) ? cell_off[c + 1] : total, cap);
-    const int n = (int)(b - a);
-    const float* ev_ehit = event_ehit(task_ehit, base, c, acc_stride);
-    if (n <= 16) {
-      acc[c] = fold_small<16>(recs, a, n, ev_ehit);
-      continue;
-    }
-    uint32_t seg[kInsertionMax];
-    for (int i = 0; i < n; ++i) seg[i] = recs[a + i];
-    for (int i = 1; i < n; ++i) {
-      const uint32_t v = seg[i];
-      int j = i - 1;
-      while (j >= 0 && seg[j] > v) {
-        seg[j + 1] = seg[j];
-        --j;
-      }
-      seg[j + 1] = v;
-    }
-    Fold f;
-    for (int j = 0; j < n; ++j) f.add(seg[j], ev_ehit);
-    acc[c] = f.result();
+  const int64_t n_list = N == 16 ? sz->n_mid : sz->n_mid32;
+  const int64_t* list = lists + (N == 16 ? cap / 3 : 2 * (cap / 3));
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_list; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = list[q];
+    int64_t a, b;
+    segment(cell_off, c, cap, a, b);
+    acc[c] = fold_small<N>(recs, a, (int)(b - a), event_ehit(task_ehit, base, c, acc_stride));
   }
 }
 
@@ -309,7 +291,7 @@ __global__ void __launch_bounds__(256) k_det_fold_mid(const uint32_t* __restrict
 constexpr int kBigWarps = 4;
 constexpr int kBigMax = 1024;
 __global__ void __launch_bounds__(32 * kBigWarps) k_det_fold_big(uint32_t* __restrict__ recs,
-                                                                 const int64_t* __restrict__ cell_off,
+                                                                 const int32_t* __restrict__ cell_off,
                                                                  int64_t n_cells_all, const Sizes* sz, int64_t cap,
                                                                  uint32_t acc_stride, const int64_t* __restrict__ base,
                                                                  const float* __restrict__ task_ehit,
@@ -317,13 +299,13 @@ __global__ void __launch_bounds__(32 * kBigWarps) k_det_fold_big(uint32_t* __res
                                                                  const int64_t* __restrict__ big) {
   __shared__ uint32_t s_rec[kBigWarps][kBigMax];
   if (sz->flags & (FCS_FLAG_HIT_CAPACITY | FCS_FLAG_KEY_BITS)) return;
-  const int64_t total = min(sz->n_records, cap);
   const int64_t n_big = sz->n_big;
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   uint32_t* s = s_rec[wi];
   for (int64_t q = (int64_t)blockIdx.x * kBigWarps + wi; q < n_big; q += (int64_t)gridDim.x * kBigWarps) {
     const int64_t c = big[q];
-    const int64_t a = cell_off[c], b = min((c + 1 < n_cells_all) ? cell_off[c + 1] : total, cap);
+    int64_t a, b;
+    segment(cell_off, c, cap, a, b);
     const int64_t n = b - a;
     uint32_t* seg = recs + a;
     const float* ev_ehit = event_ehit(task_ehit, base, c, acc_stride);
@@ -368,27 +350,30 @@ __global__ void __launch_bounds__(32 * kBigWarps) k_det_fold_big(uint32_t* __res
 
 }  // namespace
 
-cudaError_t launch_det_reduce(const GeoDev& g, WsDev w, int32_t rows, int key_task_bits, int64_t* cell_off,
+cudaError_t launch_det_reduce(const GeoDev& g, WsDev w, int32_t rows, int key_task_bits, int64_t* scratch,
                               const int64_t* event_offsets, int32_t ev_lo, ScanTmp tmp, const Launch& L) {
   const int64_t n_cells_all = (int64_t)rows * g.acc_stride;
   uint32_t* counters = reinterpret_cast<uint32_t*>(w.acc);
-  int64_t* base = cell_off + n_cells_all;  // [rows] first task of each event
+  int64_t* base = scratch;                                       // [rows] first task of each event
+  int32_t* cell_off = reinterpret_cast<int32_t*>(scratch + rows);  // [n_cells_all] segment starts, then ends
   const uint32_t stride = (uint32_t)g.acc_stride;
   k_det_bases<<<(rows + 255) / 256, 256, 0, L.s>>>(event_offsets, ev_lo, rows, w.poff, w.sizes, base);
-  cudaError_t e = launch_scan_u32(counters, cell_off, n_cells_all, tmp, L.s);
+  cudaError_t e = launch_scan_u32_zero(counters, cell_off, n_cells_all, tmp, L.s);
   if (e != cudaSuccess) return e;
   const int cell_shift = kRecordCountBits + key_task_bits;
   const uint64_t task_mask = (key_task_bits >= 64) ? ~0ull : ((1ull << key_task_bits) - 1ull);
   uint32_t* segs = reinterpret_cast<uint32_t*>(w.keys_alt);
-  k_det_scatter<<<L.num_sms * 8, 256, 0, L.s>>>(w.keys, w.sizes, w.rec_cap, cell_shift, task_mask, counters, cell_off,
+  k_det_scatter<<<L.num_sms * 8, 256, 0, L.s>>>(w.keys, w.sizes, w.rec_cap, cell_shift, task_mask, cell_off,
                                                 n_cells_all, stride, base, segs);
   // the slot array is free after the scatter: it lists the segments of more
   // than 8 records
   int64_t* lists = reinterpret_cast<int64_t*>(w.keys);
   k_det_fold<<<L.num_sms * 8, 256, 0, L.s>>>(segs, cell_off, n_cells_all, w.sizes, w.rec_cap, stride, base, w.tehit,
                                              w.acc, lists);
-  k_det_fold_mid<<<L.num_sms * 8, 256, 0, L.s>>>(segs, cell_off, n_cells_all, w.sizes, w.rec_cap, stride, base,
-                                                 w.tehit, w.acc, lists);
+  k_det_fold_mid<16><<<L.num_sms * 4, 256, 0, L.s>>>(segs, cell_off, n_cells_all, w.sizes, w.rec_cap, stride, base,
+                                                     w.tehit, w.acc, lists);
+  k_det_fold_mid<kThreadSortMax><<<L.num_sms * 2, 256, 0, L.s>>>(segs, cell_off, n_cells_all, w.sizes, w.rec_cap,
+                                                                stride, base, w.tehit, w.acc, lists);
   k_det_fold_big<<<L.num_sms * 4, 32 * kBigWarps, 0, L.s>>>(segs, cell_off, n_cells_all, w.sizes, w.rec_cap, stride,
                                                             base, w.tehit, w.acc, lists);
   return cudaGetLastError();
