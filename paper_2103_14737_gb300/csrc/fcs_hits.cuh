@@ -546,12 +546,8 @@ __global__ void __launch_bounds__(BLOCK, MODE == kModeAtomic ? 1280 / BLOCK : 0)
           T = make_tile_task(tb, w, t0 + tl, h0, kp.first_event_lo, kp.ev_lo, row_stride);
         }
         const uint32_t hit = (uint32_t)(i - T.rel);
-        // the atomic and gradient modes read the round keys from the parameters;
-        // the deterministic mode keeps the in-kernel key schedule, with which
-        // its register allocation (and time) is lower
-        uint4 x;
-        if constexpr (DET) x = philox4x32_10(make_uint4(hit, T.ctr_y, T.ctr_z, T.ctr_w), kp.k0, kp.k1);
-        else x = philox4x32_10_rk(make_uint4(hit, T.ctr_y, T.ctr_z, T.ctr_w), kp.rk);
+        // the round keys come from the kernel parameters
+        const uint4 x = philox4x32_10_rk(make_uint4(hit, T.ctr_y, T.ctr_z, T.ctr_w), kp.rk);
         const int bin = sample_bin(kp.p, T.entry, x.x);
         const FastHit f = fast_cell(tb, T, x, bin);
         const bool ok = valid && f.sure;

@@ -62,24 +62,30 @@ __global__ void __launch_bounds__(256) k_det_scatter(const uint64_t* __restrict_
                                                      int64_t n_cells_all, uint32_t acc_stride,
                                                      const int64_t* __restrict__ base, uint32_t* __restrict__ out) {
   if (sz->flags & FCS_FLAG_HIT_CAPACITY) return;
+  constexpr int R = 4;  // records per thread and trip: their counts-up are in flight together
   const int64_t n = min(sz->n_slots, cap);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
-    uint64_t k[4];
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += R * stride) {
+    uint64_t k[R];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) k[j] = (i0 + j * stride < n) ? slots[i0 + j * stride] : kEmpty;
+    for (int j = 0; j < R; ++j) k[j] = (i0 + j * stride < n) ? slots[i0 + j * stride] : kEmpty;
+    int32_t pos[R];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (k[j] == kEmpty) continue;
+    for (int j = 0; j < R; ++j) {
       const uint64_t c = k[j] >> cell_shift;
-      if (c >= (uint64_t)n_cells_all) continue;  // cannot happen for records of this range
-      const int64_t rel = (int64_t)((k[j] >> kRecordCountBits) & task_mask) - base[(uint32_t)c / acc_stride];
-      const int64_t pos = atomicAdd(cell_off + c, 1);
+      // (c is always in range for records of this range)
+      pos[j] = (k[j] != kEmpty && c < (uint64_t)n_cells_all) ? atomicAdd(cell_off + c, 1) : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      if (pos[j] < 0) continue;
+      const uint32_t c = (uint32_t)(k[j] >> cell_shift);
+      const int64_t rel = (int64_t)((k[j] >> kRecordCountBits) & task_mask) - base[c / acc_stride];
       if (rel < 0 || rel >= ((int64_t)1 << kRelTaskBits)) {
         atomicOr(&sz->flags, (uint32_t)FCS_FLAG_KEY_BITS);
         continue;
       }
-      if (pos >= 0 && pos < cap) out[pos] = ((uint32_t)rel << kRecordCountBits) | ((uint32_t)k[j] & kCountMask);
+      if (pos[j] < cap) out[pos[j]] = ((uint32_t)rel << kRecordCountBits) | ((uint32_t)k[j] & kCountMask);
     }
   }
 }
@@ -298,10 +304,12 @@ __global__ void __launch_bounds__(32 * kBigWarps) k_det_fold_big(uint32_t* __res
                                                                  double* __restrict__ acc,
                                                                  const int64_t* __restrict__ big) {
   __shared__ uint32_t s_rec[kBigWarps][kBigMax];
+  __shared__ float s_e[kBigWarps][kBigMax];  // the sorted records' hit energies
   if (sz->flags & (FCS_FLAG_HIT_CAPACITY | FCS_FLAG_KEY_BITS)) return;
   const int64_t n_big = sz->n_big;
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   uint32_t* s = s_rec[wi];
+  float* se = s_e[wi];
   for (int64_t q = (int64_t)blockIdx.x * kBigWarps + wi; q < n_big; q += (int64_t)gridDim.x * kBigWarps) {
     const int64_t c = big[q];
     int64_t a, b;
@@ -339,9 +347,12 @@ __global__ void __launch_bounds__(32 * kBigWarps) k_det_fold_big(uint32_t* __res
         __syncwarp();
       }
     }
+    // the hit energies, loaded by all lanes at once; then the first lane folds
+    for (int j = lane; j < n; j += 32) se[j] = ev_ehit[s[j] >> kRecordCountBits];
+    __syncwarp();
     if (lane == 0) {
       Fold f;
-      for (int64_t j = 0; j < n; ++j) f.add(s[j], ev_ehit);
+      for (int64_t j = 0; j < n; ++j) f.add(s[j], se[j]);
       acc[c] = f.result();
     }
     __syncwarp();
