@@ -63,10 +63,10 @@ OPS_PER_HIT = {
 }
 SMS, SM_MAX_MHZ = 152, 2070.0
 # DRAM bytes per hit of the hit kernel, from the committed ncu summary of its
-# 16-event capture (94.16 MB read + 4.23 MB written for 21,805,787 hits;
+# 16-event capture (94.18 MB read + 4.50 MB written for 21,805,787 hits;
 # traffic grows with the hits): valid for the kernel version captured there,
 # None after a kernel change.
-K_HITS_DRAM_BYTES_PER_HIT = 4.51
+K_HITS_DRAM_BYTES_PER_HIT = 4.53
 LANES_PER_SM_CLK = {"mulwide": 32, "int": 64, "fp32": 128, "mufu": 16, "lds": 32}
 
 
