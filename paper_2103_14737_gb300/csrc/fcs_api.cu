@@ -306,8 +306,10 @@ int ws_reserve_static(fcs_workspace* ws, const fcs_geo* geo, int64_t P, int32_t 
   FCS_TRY(grow(&ws->chunk_offsets, &ws->co_cap, chunks));
   // scan state for the largest array any scan of a call covers (zeroed; the
   // scans leave it zero)
+  // (the one-pass compaction takes a status word per chunk)
   FCS_TRY(grow(&ws->scan_state, &ws->ss_cap,
-               scan_state_words(std::max({Pc * NL, (int64_t)std::max(rows, 1) * stride, chunks})), true));
+               std::max(scan_state_words(std::max({Pc * NL, (int64_t)std::max(rows, 1) * stride, chunks})), chunks + 2),
+               true));
   if (mode == FCS_MODE_DETERMINISTIC)
     FCS_TRY(grow(&ws->cell_off, &ws->co_cells_cap, (int64_t)std::max(rows, 1) * (stride + 1)));
   return FCS_OK;
@@ -1635,7 +1637,7 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   const int64_t chunks = compact_chunks(geo->d.n_cells, n_events);
   w.chunk_counts = c.take<int64_t>(chunks);
   w.chunk_offsets = c.take<int64_t>(chunks);
-  w.ss_cap = scan_state_words(std::max({P * NL, (int64_t)n_events * geo->d.acc_stride, chunks}));
+  w.ss_cap = std::max(scan_state_words(std::max({P * NL, (int64_t)n_events * geo->d.acc_stride, chunks})), chunks + 2);
   w.scan_state = c.take<uint64_t>(w.ss_cap);
   w.recheck = c.take<uint2>(recheck_cap);
   w.recheck_cap = recheck_cap;

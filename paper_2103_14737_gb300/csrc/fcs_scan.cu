@@ -22,6 +22,7 @@
 #include <atomic>
 
 #include "fcs_internal.cuh"
+#include "fcs_lookback.cuh"
 
 namespace fcs {
 namespace {
@@ -34,20 +35,11 @@ constexpr int kHitScanItems = 32;
 // Dynamic shared memory of a scan with `items` elements per thread: its tile,
 // element j at j + j / items.
 constexpr size_t scan_smem_bytes(int items) { return (size_t)kScanThreads * (items + 1) * sizeof(int64_t); }
-constexpr uint64_t kFlagAgg = 1ull << 62;
-constexpr uint64_t kFlagPrefix = 2ull << 62;
-constexpr uint64_t kValueMask = (1ull << 62) - 1;
-constexpr uint32_t kSpinLimit = 1u << 20;  // status polls before a wait gives up (about 0.2 s on GB300)
 
 __device__ __forceinline__ int64_t load_n(const int64_t* n_dev, int64_t n_host) {
   return n_dev ? *n_dev : n_host;
 }
 
-__device__ __forceinline__ int64_t warp_sum(int64_t x) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
-}
 
 // Exclusive block scan of one int64 per thread; returns the block total in *total.
 __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* s_warp, int64_t* total) {
@@ -74,35 +66,6 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* s_warp, i
   *total = s_warp[(kScanThreads >> 5) - 1];
   __syncthreads();
   return warp_excl + x - v;
-}
-
-// Sum of the tiles before tile t, by warp 0: lane l reads the status of tile
-// j - l, 32 tiles per step from the nearest predecessor back, until a tile
-// with its inclusive prefix is found (position -1 counts as a prefix of 0).
-__device__ __forceinline__ int64_t look_back(const uint64_t* status, int64_t t, uint32_t* flags) {
-  const int lane = threadIdx.x & 31;
-  int64_t excl = 0;
-  for (int64_t j = t - 1;; j -= 32) {
-    const int64_t idx = j - lane;
-    uint64_t st = kFlagPrefix;
-    if (idx >= 0) {
-      const volatile uint64_t* p = status + idx;
-      uint32_t spins = 0;
-      st = *p;
-      while ((st >> 62) == 0 && ++spins < kSpinLimit) st = *p;
-      if ((st >> 62) == 0) {  // gave up: the result is invalid, the flag says so
-        atomicOr(flags, (uint32_t)FCS_FLAG_WAIT_TIMEOUT);
-        st = kFlagPrefix;
-      }
-    }
-    const unsigned pm = __ballot_sync(0xffffffffu, (st >> 62) == 2);
-    const int64_t v = (int64_t)(st & kValueMask);
-    if (pm) {
-      const int first = __ffs(pm) - 1;  // the nearest tile with a prefix
-      return excl + warp_sum(lane <= first ? v : 0);
-    }
-    excl += warp_sum(v);
-  }
 }
 
 // Out: the offsets' type (int64, or int32 for the deterministic mode's cell
