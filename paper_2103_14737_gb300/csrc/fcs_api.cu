@@ -173,9 +173,6 @@ struct fcs_workspace {
   double* acc = nullptr;  // FP64 accumulation rows
   int64_t acc_cap = 0, rows_cap = 0;
   int32_t acc_stride = 0;
-  int64_t* chunk_counts = nullptr;
-  int64_t* chunk_offsets = nullptr;
-  int64_t cc_cap = 0, co_cap = 0;
   uint64_t* scan_state = nullptr;  // zero between scans (see ScanTmp)
   int64_t ss_cap = 0;
   uint64_t* keys = nullptr;
@@ -224,8 +221,7 @@ struct fcs_workspace {
     if (s_in) cudaStreamDestroy(s_in);
     if (s_out) cudaStreamDestroy(s_out);
     if (scan_state2) cudaFree(scan_state2);
-    void* ps[] = {d_sizes, pcount, poff, pinfo, tasks, tehit, tn, th, pdefer, gmap, recheck, acc, chunk_counts, chunk_offsets,
-                  scan_state, keys, keys_alt, cell_off, stage, grad_acc, grad_touched};
+    void* ps[] = {d_sizes, pcount, poff, pinfo, tasks, tehit, tn, th, pdefer, gmap, recheck, acc, scan_state, keys, keys_alt, cell_off, stage, grad_acc, grad_touched};
     for (void* p : ps)
       if (p) cudaFree(p);
     if (h_sizes) cudaFreeHost(h_sizes);
@@ -302,11 +298,9 @@ int ws_reserve_static(fcs_workspace* ws, const fcs_geo* geo, int64_t P, int32_t 
     ws->acc_stride = stride;
   }
   const int64_t chunks = compact_chunks(geo->d.n_cells, std::max(rows, 1));
-  FCS_TRY(grow(&ws->chunk_counts, &ws->cc_cap, chunks));
-  FCS_TRY(grow(&ws->chunk_offsets, &ws->co_cap, chunks));
-  // scan state for the largest array any scan of a call covers (zeroed; the
-  // scans leave it zero)
-  // (the one-pass compaction takes a status word per chunk)
+  // scan state for the largest array any scan of a call covers, and a status
+  // word per compaction chunk (zeroed; the scans and the compaction leave it
+  // zero)
   FCS_TRY(grow(&ws->scan_state, &ws->ss_cap,
                std::max(scan_state_words(std::max({Pc * NL, (int64_t)std::max(rows, 1) * stride, chunks})), chunks + 2),
                true));
@@ -539,8 +533,8 @@ int enqueue_range_reduce(const CallArgs& a, WsDev w, int32_t ev_lo, int32_t rows
   const Launch L{s, ws->num_sms};
   if (a.cfg.mode == FCS_MODE_DETERMINISTIC)
     FCS_CUDA(launch_det_reduce(a.geo->d, w, rows, key_task_bits, ws->cell_off, a.parts.event_offsets, ev_lo, tmp, L));
-  FCS_CUDA(launch_compact(a.geo->d, w, rows, ev_lo, ws->chunk_counts, ws->chunk_offsets, tmp, a.cells_out,
-                          a.cell_ids, a.cell_E, a.event_offsets_out, a.capacity, max_ctas, L));
+  FCS_CUDA(launch_compact(a.geo->d, w, rows, ev_lo, tmp, a.cells_out, a.cell_ids, a.cell_E, a.event_offsets_out,
+                          a.capacity, max_ctas, L));
   return FCS_OK;
 }
 
@@ -756,8 +750,6 @@ int host_waves(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws, con
   put(&capacity, sizeof(capacity));
   put(&view, sizeof(view));
   put(&ws->acc_stride, sizeof(ws->acc_stride));
-  put(&ws->chunk_counts, sizeof(void*));
-  put(&ws->chunk_offsets, sizeof(void*));
   put(&ws->scan_state, sizeof(void*));
   put(&ws->ss_cap, sizeof(ws->ss_cap));
   put(&ws->scan_state2, sizeof(void*));
@@ -1635,16 +1627,13 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
   w.rows_cap = n_events;
   w.acc_stride = geo->d.acc_stride;
   const int64_t chunks = compact_chunks(geo->d.n_cells, n_events);
-  w.chunk_counts = c.take<int64_t>(chunks);
-  w.chunk_offsets = c.take<int64_t>(chunks);
   w.ss_cap = std::max(scan_state_words(std::max({P * NL, (int64_t)n_events * geo->d.acc_stride, chunks})), chunks + 2);
   w.scan_state = c.take<uint64_t>(w.ss_cap);
   w.recheck = c.take<uint2>(recheck_cap);
   w.recheck_cap = recheck_cap;
   const bool fits = w.d_sizes && w.pcount && w.poff && w.pinfo && w.tasks && w.tehit && w.tn && w.th && w.pdefer &&
                     w.acc &&
-                    w.chunk_counts &&
-                    w.chunk_offsets && w.scan_state && w.recheck && c.cap - c.off >= 4096;
+                    w.scan_state && w.recheck && c.cap - c.off >= 4096;
   if (fits) {
     // the rest of the array maps tiles to tasks: it bounds the hits per call
     w.gmap_cap = (int64_t)((c.cap - c.off) / sizeof(int32_t));
@@ -1661,8 +1650,6 @@ extern "C" int fcs_simulate_events_static(const fcs_geo* geo, const fcs_params* 
     w.th = nullptr;
     w.pdefer = nullptr;
     w.acc = nullptr;
-    w.chunk_counts = nullptr;
-    w.chunk_offsets = nullptr;
     w.scan_state = nullptr;
     w.recheck = nullptr;
     w.gmap = nullptr;

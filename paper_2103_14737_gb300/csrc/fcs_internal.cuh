@@ -331,12 +331,13 @@ cudaError_t launch_check_params(const float* frac, const float* mean_hit_E, cons
                                 int n_entries, uint32_t* bad, cudaStream_t s);
 
 // fcs_compact.cu
-// max_ctas > 0 caps the compaction's grid (its kernels loop over the chunks),
-// so that it leaves SMs to work running beside it on another stream.
-cudaError_t launch_compact(const GeoDev& g, WsDev w, int32_t rows, int32_t ev_lo, int64_t* chunk_counts,
-                           int64_t* chunk_offsets, ScanTmp tmp, float* cells_out, int32_t* cell_ids,
-                           float* cell_E, int64_t* event_offsets_out, int64_t capacity, int max_ctas,
-                           const Launch& L);
+// One pass over the rows with a decoupled look-back over the chunks (tmp:
+// zeroed scan state with a status word per chunk, left zeroed).  max_ctas > 0
+// caps the grid (its CTAs loop over the chunks), so that it leaves SMs to
+// work running beside it on another stream.
+cudaError_t launch_compact(const GeoDev& g, WsDev w, int32_t rows, int32_t ev_lo, ScanTmp tmp, float* cells_out,
+                           int32_t* cell_ids, float* cell_E, int64_t* event_offsets_out, int64_t capacity,
+                           int max_ctas, const Launch& L);
 
 // fcs_sort.cu
 int64_t compact_chunks(int32_t n_cells, int32_t rows);

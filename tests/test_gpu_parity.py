@@ -21,11 +21,7 @@ from parity import (ATOL, RTOL, check_cells_atomic, check_compacted, check_tasks
 
 # kernels of one event range in a replayed graph (begin and end of the call
 # add two more)
-KERNELS_PER_RANGE = 12
-# a range whose FP64 accumulation rows exceed 128 MiB (more than 89 events of
-# this geometry) compacts in one pass: one kernel in place of count, scan and
-# write
-KERNELS_PER_RANGE_ONE_PASS = KERNELS_PER_RANGE - 2
+KERNELS_PER_RANGE = 10
 
 
 @pytest.fixture(scope="module")
@@ -259,11 +255,11 @@ def test_async_graph_replay_matches(sim):
     assert rc == 0 and st.n_nonzero == ref["stats"]["n_nonzero"]
     diff = (outs["cells"] - ref["cells"]).abs()
     assert (diff <= RTOL * ref["cells"].abs() + ATOL).all()
-    # the launch sequence of one event range (12 kernels): range begin,
+    # the launch sequence of one event range (10 kernels): range begin,
     # particle counts, the task-offset scan, task records with their FP32
     # Poisson draws, the FP64 draws, the hit-offset scan with the tile map,
-    # hits, recheck, compaction (count, scan, write), range end; plus call
-    # begin and end
+    # hits, recheck, the one-pass compaction, range end; plus call begin and
+    # end
     assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + KERNELS_PER_RANGE
     sim.simulate(d, 21, sync=0, use_graph=1, outputs=outs, wave_events=2)
     torch.cuda.synchronize()
@@ -341,8 +337,7 @@ def test_host_entry_point_two_waves(sim):
 
 def test_host_entry_point_four_waves(sim):
     """A host-buffer call of 512 events or more runs as four waves (2/8 of the
-    events each, 128 events: their rows compact in one pass): one graph of
-    2 + 4 x KERNELS_PER_RANGE_ONE_PASS kernels,
+    events each): one graph of 2 + 4 x KERNELS_PER_RANGE kernels,
     whose ids and offsets equal the deterministic device call's and whose
     cells lie within the atomic tolerance, over repeated calls."""
     n_ev = 512
@@ -370,7 +365,7 @@ def test_host_entry_point_four_waves(sim):
         err = np.abs(E.numpy()[:nnz].astype(np.float64) - ref_E)
         assert (err <= RTOL * np.abs(ref_E) + ATOL).all()
         if call > 0:  # the first call may size the workspace synchronously
-            assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 4 * KERNELS_PER_RANGE_ONE_PASS
+            assert fcs.fcs_workspace_graph_kernels(sim.ws) == 2 + 4 * KERNELS_PER_RANGE
 
 
 @pytest.mark.parametrize("layout", ["two_events", "empty_first_wave"])
