@@ -221,7 +221,8 @@ struct fcs_workspace {
     if (s_in) cudaStreamDestroy(s_in);
     if (s_out) cudaStreamDestroy(s_out);
     if (scan_state2) cudaFree(scan_state2);
-    void* ps[] = {d_sizes, pcount, poff, pinfo, tasks, tehit, tn, th, pdefer, gmap, recheck, acc, scan_state, keys, keys_alt, cell_off, stage, grad_acc, grad_touched};
+    void* ps[] = {d_sizes, pcount, poff, pinfo, tasks, tehit, tn, th, pdefer, gmap,
+                  recheck, acc, scan_state, keys, keys_alt, cell_off, stage, grad_acc, grad_touched};
     for (void* p : ps)
       if (p) cudaFree(p);
     if (h_sizes) cudaFreeHost(h_sizes);

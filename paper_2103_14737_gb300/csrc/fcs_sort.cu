@@ -25,9 +25,9 @@
 //      in registers with a sorting network of 8, 16 or 32 records, each class
 //      in a kernel of its own - merges the records of a task (their counts
 //      add exactly) and folds; a warp per longer segment sorts it in shared
-//      memory (bitonic) before its first lane folds.  The float result goes to the (FP64) accumulation row,
-//      where the compaction of the atomic mode picks it up, rounds it back to
-//      the same float and re-zeroes it.
+//      memory (bitonic) before its first lane folds.  The float result goes
+//      to the (FP64) accumulation row, where the compaction of the atomic
+//      mode picks it up, rounds it back to the same float and re-zeroes it.
 // Only the order of places inside a segment depends on scheduling, and the
 // sort removes it, so the cells are bit-reproducible.
 #include "fcs_internal.cuh"
@@ -54,7 +54,7 @@ __global__ void k_det_bases(const int64_t* __restrict__ event_offsets, int32_t e
 
 // A range that outgrew the workspace (FCS_FLAG_HIT_CAPACITY) has slots the
 // hit kernel did not write: the scatter and the fold then do nothing (the
-// call reports the overflow; the compaction still re-zeroes the rows).
+// call reports the overflow; the counter scan has zeroed the rows).
 // A record whose task lies 2^27 or more past its event's first sets
 // FCS_FLAG_KEY_BITS and is dropped (the call then fails).
 __global__ void __launch_bounds__(256) k_det_scatter(const uint64_t* __restrict__ slots, Sizes* sz, int64_t cap,
