@@ -2,7 +2,8 @@
 bench times: one batched call of 128 threads x 8 hits per thread, replayed as
 a CUDA graph.
 
-* 64 pile-up events: every event, cell by cell.
+* 64 pile-up events: every event, cell by cell, in atomic mode and (bit-exact
+  against the canonical fold) in deterministic mode.
 * 1024 pile-up events (the bench step): sampled events cell by cell, and every
   event's energy total against the oracle's.
 
@@ -82,6 +83,38 @@ def test_pileup64_every_event(sim, ogeo, oprm):
     rows, _ = _oracle(ogeo, oprm, parts, events, set(events))
     for e in events:
         _check_event(ids, E, off, e, rows[e], sim.n_cells)
+
+
+def test_pileup64_deterministic_every_event(sim, ogeo, oprm):
+    """Deterministic mode on the 64-event batch, replayed as a graph: every
+    event's compacted cells bit-equal to the oracle's canonical fold (segments
+    of every size class, the per-event task bases, the one-pass compaction)."""
+    parts = synth.workload("pileup64", seed=SEED)
+    d = sim.to_device(parts)
+    first = sim.simulate(d, SEED, mode=fcs.MODE_DETERMINISTIC, **SHAPE)
+    nnz = first["stats"]["n_nonzero"]
+    outs = dict(cell_ids=torch.empty(nnz + 64, dtype=torch.int32, device="cuda"),
+                cell_E=torch.empty(nnz + 64, dtype=torch.float32, device="cuda"),
+                event_offsets=torch.empty(parts.n_events + 1, dtype=torch.int64, device="cuda"))
+    sim.simulate(d, SEED, mode=fcs.MODE_DETERMINISTIC, sync=0, use_graph=1, outputs=outs, **SHAPE)
+    torch.cuda.synchronize()
+    rc, st = fcs.fcs_workspace_status(sim.ws)
+    assert rc == fcs.FCS_OK and st.n_nonzero == nnz
+    ids = outs["cell_ids"][:nnz].cpu().numpy()
+    E = outs["cell_E"][:nnz].cpu().numpy()
+    off = outs["event_offsets"].cpu().numpy()
+
+    def one(e):
+        r = O.simulate(ogeo, oprm, parts.event(e), seed=SEED, first_event=e, tasks=False, cells64=False)
+        return e, r.cells_canon[0]
+
+    with ThreadPoolExecutor(THREADS) as ex:
+        ref = dict(ex.map(one, range(parts.n_events)))
+    for e in range(parts.n_events):
+        a, b = off[e], off[e + 1]
+        row = np.zeros(sim.n_cells, dtype=np.float32)
+        row[ids[a:b]] = E[a:b]
+        assert np.array_equal(row.view(np.uint32), ref[e].view(np.uint32)), f"event {e}: cells differ"
 
 
 def test_pileup1024_bench_step(sim, ogeo, oprm):
