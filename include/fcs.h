@@ -104,7 +104,8 @@ typedef struct fcs_particles {
 enum fcs_mode {
   FCS_MODE_ATOMIC = 0,       /* warp-aggregated atomics (Sec. 4: atomicAdd) of the float count x Ehit of
                                 each group of hits into FP64 cells, rounded once to float per cell */
-  FCS_MODE_DETERMINISTIC = 1 /* sort by (cell, task), fixed-order FP32 fold; bit-reproducible */
+  FCS_MODE_DETERMINISTIC = 1 /* records (cell, task, count) grouped by cell, sorted by task and folded
+                                in that order in FP32; bit-reproducible */
 };
 
 typedef struct fcs_config {
@@ -271,7 +272,10 @@ void fcs_workspace_free(fcs_workspace* ws);
  * dbg: optional validation dumps (NULL in production).
  * Errors: FCS_E_ARG for bad arguments, FCS_E_RANGE as above, when a
  * sync == 0 call needs more workspace than reserved or for 2^24 or more
- * events in one call, FCS_E_DEVICE_CHECK when
+ * events in one call, and in deterministic mode when an event range (a wave)
+ * has 2^31 or more hit slots, when its (cell, task) keys need more than 63
+ * bits, or when one event holds 2^27 tasks or more (use smaller waves),
+ * FCS_E_DEVICE_CHECK when
  * a particle fails its checks (its tasks are skipped), FCS_E_CUDA / OOM. */
 int fcs_simulate_events(const fcs_geo* geo, const fcs_params* prm, fcs_workspace* ws,
                         const fcs_particles* particles, int64_t n_particles, int32_t n_events,
