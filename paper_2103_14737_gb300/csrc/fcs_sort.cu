@@ -30,6 +30,9 @@
 //      mode picks it up, rounds it back to the same float and re-zeroes it.
 // Only the order of places inside a segment depends on scheduling, and the
 // sort removes it, so the cells are bit-reproducible.
+#include <algorithm>
+#include <atomic>
+
 #include "fcs_internal.cuh"
 
 namespace fcs {
@@ -359,6 +362,27 @@ __global__ void __launch_bounds__(32 * kBigWarps) k_det_fold_big(uint32_t* __res
   }
 }
 
+constexpr int kMaxDevices = 64;
+
+// Blocks of 256 threads of k_det_fold that one SM holds at once (per device,
+// looked up once): the kernel loops grid-stride, and a grid beyond one wave of
+// resident blocks would run its surplus as a second, mostly empty wave.
+int fold_resident_blocks() {
+  static std::atomic<int> occ_by_device[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = kMaxDevices - 1;
+  int occ = occ_by_device[dev].load(std::memory_order_relaxed);
+  if (!occ) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_det_fold, 256, 0) != cudaSuccess) {
+      (void)cudaGetLastError();
+      occ = 1;
+    }
+    occ = std::max(occ, 1);
+    occ_by_device[dev].store(occ, std::memory_order_relaxed);
+  }
+  return occ;
+}
+
 }  // namespace
 
 cudaError_t launch_det_reduce(const GeoDev& g, WsDev w, int32_t rows, int key_task_bits, int64_t* scratch,
@@ -379,8 +403,8 @@ cudaError_t launch_det_reduce(const GeoDev& g, WsDev w, int32_t rows, int key_ta
   // the slot array is free after the scatter: it lists the segments of more
   // than 8 records
   int64_t* lists = reinterpret_cast<int64_t*>(w.keys);
-  k_det_fold<<<L.num_sms * 8, 256, 0, L.s>>>(segs, cell_off, n_cells_all, w.sizes, w.rec_cap, stride, base, w.tehit,
-                                             w.acc, lists);
+  k_det_fold<<<L.num_sms * fold_resident_blocks(), 256, 0, L.s>>>(segs, cell_off, n_cells_all, w.sizes, w.rec_cap,
+                                                                  stride, base, w.tehit, w.acc, lists);
   k_det_fold_mid<16><<<L.num_sms * 4, 256, 0, L.s>>>(segs, cell_off, n_cells_all, w.sizes, w.rec_cap, stride, base,
                                                      w.tehit, w.acc, lists);
   k_det_fold_mid<kThreadSortMax><<<L.num_sms * 2, 256, 0, L.s>>>(segs, cell_off, n_cells_all, w.sizes, w.rec_cap,
